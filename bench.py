@@ -1,0 +1,336 @@
+"""Benchmark: batch-point x center distances per second, one mini-batch kernel
+k-means iteration per step, on the MNIST-shaped synthetic workload
+(n=70000, d=784, k=10, b=1024, tau=200, Gaussian kernel with the median
+heuristic, beta learning rate).
+
+A step is one full iteration of the method: sample the batch on the device,
+gather it, run the distance pass, assign by argmin, do the counting sort and
+window plan, move the rows, run the window Gram pass and the FP64 norm
+recurrence. The reported value is b*k / t_step, summed over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16|bf16x3]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+Under torchrun each rank runs an independent replica on its own GPU. The
+method has no exchange step between replicas, so there is no data-path
+collective and the scaling is weak.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2410_05902_gb300 import inputs  # noqa: E402
+
+WORKLOAD = inputs.WORKLOADS["image"]
+METRIC = "batch-point×center distances/s per iteration on 1 GB300 (BF16 vs FP32) at ≤1e-4 obj err"
+UNIT = "distances/s"
+PREP_ITERS = 20         # iterations that bring the windows to their steady-state size
+DTYPES = {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}
+
+
+def workload_desc(w) -> str:
+    return (f"MNIST-shaped synthetic mixture n={w.n} d={w.d} (~80% zeros, Beta(2,2) values, 10 latent "
+            f"classes), k={w.k}, b={w.b}, tau={w.tau}, Gaussian kernel kappa=2*sigma_median^2, beta rate")
+
+
+def load_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        d["source"] = "measured"
+        return d
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r.split(",") for r in out.strip().splitlines() if r.strip()]
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_workload(seed_offset: int = 0):
+    X, _ = WORKLOAD.make()
+    sigma = inputs.median_sigma(X, seed=1)
+    kappa = 2.0 * sigma * sigma
+    init = inputs.init_indices(WORKLOAD.n, WORKLOAD.k, seed=3 + seed_offset)
+    return X, kappa, init
+
+
+# ------------------------------------------------------------------ oracle leg
+def oracle_sample(X, kappa, init, budget_s: float = 20.0, prep: int = 4):
+    """FP64 oracle iterations of the same workload: `prep` untimed iterations
+    from the same start (the support grows towards its steady size), then
+    timed iterations until `budget_s` is spent. Returns (b*k/s median, cores, desc)."""
+    import oracle
+    w = WORKLOAD
+    ora = oracle.MiniBatchKernelKMeans(X, w.k, oracle.Kernel(oracle.GAUSSIAN, kappa), w.b, init, tau=w.tau)
+    batches = inputs.batch_stream(w.n, w.b, 200, seed=77)
+    for i in range(prep):
+        ora.step(batches[i])
+    times, S = [], []
+    t_start = time.perf_counter()
+    i = prep
+    while time.perf_counter() - t_start < budget_s and i < len(batches):
+        S.append(sum(len(ora.center(j).idx) for j in range(w.k)))
+        t0 = time.perf_counter()
+        ora.step(batches[i])
+        times.append(time.perf_counter() - t0)
+        i += 1
+    t = statistics.median(times)
+    desc = (f"FP64 oracle, full iterations {prep + 1}-{i} of the same workload from the same start "
+            f"(support S {min(S)}-{max(S)} rows), median over {len(times)} iterations")
+    return w.b * w.k / t, oracle.kernels.num_threads(), desc
+
+
+def run_reference(args):
+    """The oracle as the reference arm: rank 0 only, on the host cores."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    w = WORKLOAD
+    X, kappa, init = make_workload()
+    ora = oracle.MiniBatchKernelKMeans(X, w.k, oracle.Kernel(oracle.GAUSSIAN, kappa), w.b, init, tau=w.tau)
+    batches = inputs.batch_stream(w.n, w.b, 200, seed=77)
+    for i in range(4):
+        ora.step(batches[i])
+    S = sum(len(ora.center(j).idx) for j in range(w.k))
+    # one step = distances of m batch rows to all k centers at this support size;
+    # m is sized so the whole run stays within about two minutes
+    Xb = X[batches[4]].astype(np.float64)
+    t0 = time.perf_counter()
+    ora.distances(Xb[:8])
+    per_row = max((time.perf_counter() - t0) / 8, 1e-6)
+    m = int(max(1, min(w.b, 100.0 / max(args.steps + args.warmup, 1) / per_row)))
+    for s in range(args.warmup):
+        r0 = (s * m) % (w.b - m + 1)
+        ora.distances(Xb[r0:r0 + m])
+    times = []
+    for s in range(args.steps):
+        r0 = ((args.warmup + s) * m) % (w.b - m + 1)
+        t0 = time.perf_counter()
+        ora.distances(Xb[r0:r0 + m])
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = m * w.k * args.steps / total
+    cores = oracle.kernels.num_threads()
+    sample = (f"per step: FP64 oracle distances of {m} batch rows to all {w.k} centers at steady-state "
+              f"support S={S} rows (iteration 5 of the same workload)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": workload_desc(w)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ------------------------------------------------------------------- GPU leg
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2410_05902_gb300.kkm import KKM
+
+    world, rank, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    w = WORKLOAD
+    X, kappa, init = make_workload(seed_offset=rank)
+    Xd = torch.from_numpy(X).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    run = KKM(Xd, w.k, w.b, kernel="gaussian", param=kappa, tau=w.tau, precision=args.precision,
+              seed=1000 + rank, init_idx=init)
+    for _ in range(PREP_ITERS):
+        run.step()
+    for _ in range(args.warmup):
+        run.step()
+    run.sync()
+    run.stats(reset=True)
+    run.launches(reset=True)
+    run.timing(True)
+    run.timing_read(reset=True)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    clocks = Clocks(dev.index) if rank == 0 else None
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        run.step()
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop() if clocks else None
+    launches = run.launches(reset=True)
+    run.timing(False)
+    n_rec, k_ms = run.timing_read(reset=True)
+    steps_done, srows, tiles = run.stats(reset=True)
+    run.sync()
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * w.b * w.k * args.steps / (ms / 1e3)
+
+    # end to end through the public host-buffer call: index upload, step,
+    # assignment and objective download, synchronise, every step
+    e2e_steps = max(50, min(args.steps, 2000))
+    pinned_idx = torch.empty((e2e_steps, w.b), dtype=torch.int32, pin_memory=True)
+    pinned_idx.copy_(torch.from_numpy(inputs.batch_stream(w.n, w.b, e2e_steps, seed=500 + rank).astype(np.int32)))
+    idx_np = pinned_idx.numpy()
+    a_out = torch.empty(w.b, dtype=torch.int32, pin_memory=True).numpy()
+    o_out = torch.empty(1, dtype=torch.float64, pin_memory=True).numpy()
+    from paper_2410_05902_gb300 import kkm as kb
+    for s in range(3):
+        kb.kkm_step_host(run.ctx, idx_np[s], a_out, o_out)
+    barrier()
+    t0 = time.perf_counter()
+    for s in range(e2e_steps):
+        kb.kkm_step_host(run.ctx, idx_np[s], a_out, o_out)
+    t_e2e = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e_value = world * w.b * w.k * e2e_steps / t_e2e
+
+    if rank == 0:
+        peaks = load_peaks()
+        S = srows / max(steps_done, 1)
+        avg_ms = k_ms / max(n_rec, 1)
+        flops = 2.0 * w.b * S * w.d          # algorithmic Gram flops of one distance-pass launch
+        achieved = flops / (avg_ms / 1e3) / 1e12
+        if args.precision == "fp32":
+            sms = 152
+            peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "kernel": "k_dist_simt<FP32> (FP32 FFMA Gram + exp + weighted sums)",
+                    "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 x max SM clock (derived)"}
+        else:
+            peak = peaks["bf16_tflops"]
+            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "kernel": "distance pass (tcgen05 Gram + exp + weighted sums)",
+                    "peak_source": f"bf16_tflops burst, {peaks['source']}"}
+        roof["flops_per_launch"] = flops
+        roof["avg_launch_ms"] = avg_ms
+        roof["launches_timed"] = n_rec
+        Xs, kappa_s, init_s = X, kappa, init
+        cpu_v, cores, desc = oracle_sample(Xs.astype(np.float64), kappa_s, init_s, budget_s=args.oracle_budget)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision],
+            "data": "synthetic",
+            "config": {"workload": workload_desc(w), "precision": args.precision,
+                       "support_rows_S": S, "state_prep_iters": PREP_ITERS,
+                       "l2": "inputs larger than L2: X is 220 MB (L2 129 MB); the method's support "
+                             "state stays resident between iterations",
+                       "parallelism": f"replicas x{world} (independent runs, no collective)"},
+            "roofline": roof,
+            "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * w.b,
+                    "d2h_bytes_per_step": 4 * w.b + 8, "steps": e2e_steps,
+                    "call": "kkm_step_host (pinned host batch indices in, assignments and f_B out, synchronised)"},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    run.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "bf16", "bf16x3"], default="fp32")
+    ap.add_argument("--oracle-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,239 @@
+/*
+ * kkm.h -- C ABI of libkkm, truncated mini-batch kernel k-means on NVIDIA GB300
+ * (sm_103a). Jourdan & Schwartzman, "Mini-batch kernel k-means".
+ *
+ * One context holds one clustering run. The run covers the dataset X, the
+ * number of centers k, the kernel K and the batch size b of the problem
+ * statement (Sec. 1) and of the inputs of Algorithms 1/2, together with the
+ * truncation parameter tau of Sec. 4.1. Each center j is held implicitly, as
+ * Eq. (1) defines it: a weighted sum of feature vectors phi(y_s) over a sliding
+ * window of support rows, plus the FP64 norm ||C_j||^2.
+ *
+ * Conventions shared by every call:
+ *  - Pointers marked "device" must be CUDA device (or managed) memory that the
+ *    calling process can reach on the context's device. Pointers marked "host"
+ *    are ordinary CPU memory.
+ *  - Matrices are row-major. A "leading dimension" counts elements between the
+ *    starts of consecutive rows.
+ *  - Unless stated otherwise a call only enqueues work on the context's stream
+ *    and returns. Results are ready once that stream has been synchronised.
+ *  - The caller keeps ownership of every buffer it passes in. The library owns
+ *    only what it allocates inside a context, and kkm_destroy frees all of it.
+ *  - Every call returns a kkm_status, and no C++ exception crosses the ABI.
+ *    Arguments are validated on the host before any work is queued, and an
+ *    invalid call changes no state. Faults found on the device (an
+ *    out-of-range batch or assignment index) are recorded in a sticky device
+ *    status word. They are reported as KKM_EINVAL by the next call that
+ *    synchronises (kkm_sync, kkm_objective, kkm_get_state, kkm_step_host).
+ *    Once that happens the context is poisoned: every later call returns
+ *    KKM_ESTATE.
+ *  - kkm_last_error(ctx) gives a message for the last failure on that
+ *    context. kkm_last_error(NULL) gives the calling thread's last failure of
+ *    kkm_init.
+ *  - A context may be used by one host thread at a time.
+ */
+#ifndef KKM_H
+#define KKM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KKM_ABI_VERSION 1
+
+typedef enum kkm_status {
+  KKM_OK = 0,
+  KKM_EINVAL = 1,   /* invalid argument, or invalid index data found on the device */
+  KKM_ENOMEM = 2,   /* a device or pinned-host allocation failed */
+  KKM_ECUDA = 3,    /* a CUDA runtime or driver call failed */
+  KKM_ETIMEOUT = 4, /* a bounded device wait gave up */
+  KKM_ESTATE = 5,   /* the context is poisoned, or the call does not fit its state */
+  KKM_ENOTSUP = 6   /* the combination of options is not supported */
+} kkm_status;
+
+/* Kernel functions K(x, y). Sec. 6 prints the Gaussian kernel. Sec. 1 names
+ * the Laplacian kernel as normalised (gamma = 1) but prints no formula; the
+ * library reads it as exp(-||x - y||_2 / sigma). The linear and polynomial
+ * kernels are the textbook ones. */
+typedef enum kkm_kernel_kind {
+  KKM_GAUSSIAN = 0,  /* K = exp(-||x - y||^2 / param), param = kappa > 0      */
+  KKM_LAPLACIAN = 1, /* K = exp(-||x - y||_2 / param), param = sigma > 0      */
+  KKM_LINEAR = 2,    /* K = <x, y>                                            */
+  KKM_POLY = 3       /* K = (<x, y> + coef0)^degree, 1 <= degree <= 8         */
+} kkm_kernel_kind;
+
+typedef struct kkm_kernel {
+  int32_t kind;   /* kkm_kernel_kind */
+  double param;   /* kappa (Gaussian) or sigma (Laplacian) */
+  double coef0;   /* polynomial offset */
+  int32_t degree; /* polynomial degree */
+} kkm_kernel;
+
+/* Learning rates. KKM_LR_BETA is alpha_i^j = sqrt(b_i^j / b), the rate of
+ * Schwartzman (2023) that the truncation lemma's proof in Sec. 4.1 uses.
+ * KKM_LR_CONST is alpha = eta. Either way an empty cluster (b_i^j = 0) gets
+ * alpha = 0 and its center does not change. */
+typedef enum kkm_lr { KKM_LR_BETA = 0, KKM_LR_CONST = 1 } kkm_lr;
+
+/* Arithmetic of the batch-by-support Gram products x.y (Sec. 4.1, "Algorithm
+ * implementation and runtime"). Norms, kernel values and weighted sums are
+ * FP32 in every form. Center norms and weights are FP64 in every form.
+ *   FP32   : CUDA-core FP32 FMA products.
+ *   BF16   : tcgen05 tensor cores, BF16 operands, FP32 accumulation.
+ *   BF16X3 : tcgen05, split operands x = hi + lo (both BF16); the product is
+ *            hi.hi + hi.lo + lo.hi, accumulated in FP32. */
+typedef enum kkm_precision { KKM_PREC_FP32 = 0, KKM_PREC_BF16 = 1, KKM_PREC_BF16X3 = 2 } kkm_precision;
+
+typedef struct kkm_config {
+  int32_t tau;       /* truncation parameter tau of Sec. 4.1; <= 0 runs Algorithm 1 untruncated */
+  int32_t lr;        /* kkm_lr */
+  double eta;        /* rate for KKM_LR_CONST, in (0, 1] */
+  int32_t precision; /* kkm_precision */
+  int32_t max_iters; /* untruncated runs only: iterations the support store must hold (>= 1) */
+  uint64_t seed;     /* SplitMix64 seed of the built-in batch sampler */
+} kkm_config;
+
+typedef struct kkm_ctx kkm_ctx;
+
+/* ABI version of the loaded library (KKM_ABI_VERSION). */
+int32_t kkm_version(void);
+
+/* kkm_init -- creates a run (the inputs of Algorithms 1/2).
+ *   out        : host; receives the new context, or NULL on failure.
+ *   X          : device, n x d FP32 dataset, leading dimension ldx >= d.
+ *                Caller-owned. It must stay alive and unchanged until
+ *                kkm_destroy, because batches and support rows are read
+ *                from it.
+ *   n, d       : 1 <= n < 2^31, 1 <= d <= 4096.
+ *   k          : number of centers, 1 <= k <= min(n, 1024).
+ *   kernel     : host; copied.
+ *   b          : batch size, 1 <= b <= 8192.
+ *   cfg        : host; copied.
+ *   init_idx   : host, k data indices in [0, n): C_1^j = phi(x_{init_idx[j]}),
+ *                for example from kernel k-means++ (Secs. 1 and 5). NULL picks
+ *                k distinct indices with the library's own seeded sampler.
+ *   stream     : cudaStream_t on which every later call of this context
+ *                queues its work. NULL means the legacy default stream.
+ * Allocates all device state up front: the support store of k*(2*tau + 4*b + 8)
+ * rows (k*(1 + b*max_iters) when untruncated) and the step workspaces. No
+ * later call allocates. Sets ||C_1^j||^2 = K(x, x). */
+kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d, int64_t ldx, int32_t k,
+                    const kkm_kernel* kernel, int32_t b, const kkm_config* cfg,
+                    const int64_t* init_idx, void* stream);
+
+/* kkm_step -- one iteration i of Algorithm 2 (Algorithm 1 when untruncated),
+ * Appendix A. It samples or takes the batch B_i, computes the distances
+ * Delta(x, C_i^j) = K(x,x) - 2 sum_s w_s K(x, y_s) + ||C_i^j||^2 (Sec. 1 and
+ * Sec. 4), assigns each x to the argmin (ties go to the lowest j), forms
+ * b_i^j and alpha_i^j, and updates every window as Eq. (1) and the sliding
+ * window of Sec. 4.1 describe: decay the old weights by (1 - alpha), append
+ * B_i^j with weight alpha / b_i^j per row, drop the oldest blocks that fall
+ * out of Q_i^j, and drop C_1 once min Q_i^j > 1. It then carries ||C^j||^2 by
+ * the Sec. 4 recurrence, corrected for the dropped rows, in FP64.
+ *   batch_idx     : device, b int32 indices in [0, n), or NULL to draw them
+ *                   with SplitMix64: output (i-1)*b + s of the generator
+ *                   seeded with cfg->seed, mapped to [0, n) by floor(h*n/2^64).
+ *   forced_assign : device, b centers in [0, k) that replace the argmin in the
+ *                   update, or NULL. This is teacher forcing for tests; the
+ *                   distances are still computed.
+ *   assign_out    : device, b int32, or NULL. Receives argmin_j Delta(x, C_i^j).
+ *   dist_out      : device, b x k FP32 row-major, or NULL. Receives Delta(x, C_i^j).
+ *   batch_obj_out : device, one double, or NULL. Receives
+ *                   f_{B_i}(C_i) = (1/b) sum_x min_j Delta(x, C_i^j) (Sec. 3).
+ * An index out of range is found on the device, and it poisons the context. */
+kkm_status kkm_step(kkm_ctx* ctx, const int32_t* batch_idx, const int32_t* forced_assign,
+                    int32_t* assign_out, float* dist_out, double* batch_obj_out);
+
+/* kkm_step_host -- kkm_step with host buffers, for callers that keep the
+ * batch on the CPU. It copies the b indices in (batch_idx may be NULL for the
+ * built-in sampler), runs the step, copies the assignments and f_{B_i}(C_i)
+ * back (either output may be NULL), and synchronises the stream. Page-locked
+ * host buffers give the fastest copies. */
+kkm_status kkm_step_host(kkm_ctx* ctx, const int32_t* batch_idx, int32_t* assign_out,
+                         double* batch_obj_out);
+
+/* kkm_assign -- nearest centers of arbitrary query points (the assignment
+ * rule of Algorithms 1/2, applied to the current centers without updating
+ * them).
+ *   Q          : device, m x d FP32, leading dimension ldq >= d; m >= 0.
+ *   assign_out : device, m int32, or NULL.
+ *   mind_out   : device, m FP32 min_j Delta(q, C_j), or NULL.
+ *   dist_out   : device, m x k FP32, or NULL.
+ * Work goes in chunks of at most b rows through the same kernels as kkm_step. */
+kkm_status kkm_assign(kkm_ctx* ctx, const float* Q, int64_t m, int64_t ldq, int32_t* assign_out,
+                      float* mind_out, float* dist_out);
+
+/* kkm_objective -- f_A(C) = (1/|A|) sum_{a in A} min_j Delta(a, C_j) (Sec. 3)
+ * for A = the rows of Q (device, m x d, ldq), or for A = X when Q is NULL.
+ * The sum is taken in FP64. Synchronises the stream and writes the value to
+ * *out (host). */
+kkm_status kkm_objective(kkm_ctx* ctx, const float* Q, int64_t m, int64_t ldq, double* out);
+
+/* kkm_sync -- synchronises the context's stream and reports device-side faults. */
+kkm_status kkm_sync(kkm_ctx* ctx);
+
+/* Checkpoint / restore of the centers (Eq. (1) window layout). It is also
+ * how tests load a state computed elsewhere ("teacher forcing").
+ * kkm_get_state_sizes writes the total support rows S and the total block
+ * count; both are host outputs. kkm_get_state fills host arrays:
+ *   iteration         : the next iteration number i (1-based)
+ *   rows_per_center   : k int32, support rows of each center
+ *   row_idx, row_w    : S entries, center-major, window order. For each
+ *                       center this is C_1 first (when kept), then the blocks
+ *                       from oldest to newest, each in batch order. row_idx
+ *                       holds data indices, row_w the FP64 weights.
+ *   blocks_per_center : k int32
+ *   block_iter        : per block, the iteration that appended it (0 = C_1)
+ *   block_count       : per block, its rows
+ *   c1_kept           : k bytes, 1 while C_1 is part of the center
+ *   cnorm             : k doubles, ||C_j||^2
+ * Both calls synchronise. kkm_set_state takes the same arrays. It checks
+ * them against each other and the capacities (KKM_EINVAL on any mismatch),
+ * then gathers the support rows from X. */
+kkm_status kkm_get_state_sizes(kkm_ctx* ctx, int64_t* total_rows, int64_t* total_blocks);
+kkm_status kkm_get_state(kkm_ctx* ctx, int64_t* iteration, int32_t* rows_per_center,
+                         int64_t* row_idx, double* row_w, int32_t* blocks_per_center,
+                         int64_t* block_iter, int32_t* block_count, uint8_t* c1_kept,
+                         double* cnorm);
+kkm_status kkm_set_state(kkm_ctx* ctx, int64_t iteration, const int32_t* rows_per_center,
+                         const int64_t* row_idx, const double* row_w,
+                         const int32_t* blocks_per_center, const int64_t* block_iter,
+                         const int32_t* block_count, const uint8_t* c1_kept,
+                         const double* cnorm);
+
+/* kkm_stats -- counters accumulated on the device since kkm_init or the last
+ * reset (reset != 0 clears them after reading). Synchronises. Host outputs:
+ *   steps        : kkm_step calls
+ *   support_rows : sum over steps of S, the support rows the distance pass
+ *                  read (the algorithmic size of the b x S Gram product)
+ *   gram_tiles   : sum over steps of the support tiles the distance kernel ran
+ * Any output may be NULL. */
+kkm_status kkm_stats(kkm_ctx* ctx, int64_t* steps, int64_t* support_rows, int64_t* gram_tiles,
+                     int32_t reset);
+
+/* kkm_timing -- CUDA-event timing of the distance kernel (the b x S Gram
+ * product with its kernel and weighted-sum epilogue). While it is enabled,
+ * every kkm_step records a pair of events on the context's stream around
+ * that kernel's launch, for up to 4096 steps. kkm_timing_read synchronises
+ * and writes the launches recorded and their summed milliseconds (host).
+ * reset != 0 clears the record. */
+kkm_status kkm_timing_enable(kkm_ctx* ctx, int32_t enable);
+kkm_status kkm_timing_read(kkm_ctx* ctx, int64_t* launches, double* total_ms, int32_t reset);
+
+/* kkm_launches -- number of CUDA kernels this context has launched (counted on
+ * the host at each launch) since kkm_init or the last reset. Host output. */
+kkm_status kkm_launches(kkm_ctx* ctx, int64_t* launches, int32_t reset);
+
+/* Frees everything the context allocated. NULL is accepted. It synchronises first. */
+kkm_status kkm_destroy(kkm_ctx* ctx);
+
+/* Message of the last failure (see the conventions above). Never NULL. */
+const char* kkm_last_error(const kkm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KKM_H */

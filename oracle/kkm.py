@@ -157,9 +157,12 @@ class MiniBatchKernelKMeans:
 
     def center_norm(self, j: int, truncated: bool = True) -> float:
         """||C^j||^2 = sum_{s,t} w_s w_t K(y_s, y_t), computed directly."""
-        rep = self.center(j, truncated)
-        Y = self.X[rep.idx]
-        return float(rep.w @ kernel_matrix(Y, Y, self.kernel) @ rep.w)
+        key = ("norm", self.iteration, j, truncated)
+        if key not in self._rep_cache:
+            rep = self.center(j, truncated)
+            Y = self.X[rep.idx]
+            self._rep_cache[key] = float(rep.w @ kernel_matrix(Y, Y, self.kernel) @ rep.w)
+        return self._rep_cache[key]
 
     def center_norms(self, truncated: bool = True) -> np.ndarray:
         return np.array([self.center_norm(j, truncated) for j in range(self.k)])

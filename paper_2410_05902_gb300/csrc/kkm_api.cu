@@ -1,0 +1,643 @@
+// Host runtime and C ABI of libkkm (declared in include/kkm.h).
+//
+// One kkm_ctx owns one run: the device state sized at kkm_init (see
+// kkm_internal.cuh for the layout), the stream its work goes to, and a host
+// mirror of the iteration counter. kkm_step queues the whole iteration as a
+// fixed sequence of kernels on that stream. No step allocates, and nothing
+// crosses to the host unless the caller asks for a host result.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_set>
+#include <vector>
+
+#include "kkm_internal.cuh"
+#include "../../include/kkm.h"
+
+#define KKM_API extern "C" __attribute__((visibility("default")))
+
+using kkm::Dev;
+
+struct kkm_ctx {
+  Dev s{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int64_t iteration = 1;
+  int32_t max_iters = 0;
+  int32_t wmax = 0;          // most rows a window can hold
+  bool poisoned = false;
+  bool use_tc = false;
+  std::string err;
+  std::vector<void*> allocs;
+  int32_t* d_init_idx = nullptr;
+  int32_t* d_hbatch = nullptr;
+  int32_t* d_hassign = nullptr;
+  double* d_hobj = nullptr;
+  double* d_objpart = nullptr;
+  int32_t objpart_len = 0;
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;
+  int64_t ev_used = 0;
+  int64_t launches = 0;       // kernels launched (host count)
+};
+
+namespace {
+
+thread_local std::string g_init_error;
+
+kkm_status fail(kkm_ctx* c, kkm_status st, const std::string& msg) {
+  if (c) c->err = msg; else g_init_error = msg;
+  return st;
+}
+
+kkm_status cuda_fail(kkm_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, KKM_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+template <class T>
+cudaError_t dalloc(kkm_ctx* c, T** p, size_t count) {
+  void* q = nullptr;
+  const size_t bytes = count * sizeof(T) > 0 ? count * sizeof(T) : 16;
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) { *p = nullptr; return e; }
+  e = cudaMemset(q, 0, bytes);
+  c->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return e;
+}
+
+void free_all(kkm_ctx* c) {
+  for (void* p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  c->ev.clear();
+}
+
+kkm_status check_usable(kkm_ctx* c) {
+  if (!c) return fail(nullptr, KKM_EINVAL, "null context");
+  if (c->poisoned) return fail(c, KKM_ESTATE, "context poisoned by an earlier device-side fault");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, KKM_ECUDA, "cudaSetDevice failed");
+  return KKM_OK;
+}
+
+// Synchronises the stream and turns sticky device status bits into an error.
+kkm_status sync_and_check(kkm_ctx* c) {
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+  int32_t st = 0;
+  e = cudaMemcpy(&st, c->s.status, sizeof(st), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "status read");
+  if (st != 0) {
+    c->poisoned = true;
+    std::string m = "device status:";
+    if (st & kkm::ST_BAD_BATCH_INDEX) m += " batch/data index out of range;";
+    if (st & kkm::ST_BAD_ASSIGN) m += " forced assignment out of range;";
+    if (st & kkm::ST_CAPACITY) m += " capacity exceeded;";
+    if (st & kkm::ST_TIMEOUT) m += " bounded wait timed out;";
+    return fail(c, (st & kkm::ST_TIMEOUT) ? KKM_ETIMEOUT : KKM_EINVAL, m);
+  }
+  return KKM_OK;
+}
+
+#define KKM_CU(expr, where)                                  \
+  do {                                                       \
+    cudaError_t _e = (expr);                                 \
+    if (_e != cudaSuccess) return cuda_fail(c, _e, where);   \
+  } while (0)
+
+kkm_status launch_distance_pass(kkm_ctx* c, int rows) {
+  if (c->use_tc) KKM_CU(kkm::launch_dist_tc(c->s, rows, c->stream), "distance kernel (tcgen05)");
+  else KKM_CU(kkm::launch_dist_simt(c->s, rows, c->stream), "distance kernel");
+  return KKM_OK;
+}
+
+}  // namespace
+
+KKM_API int32_t kkm_version(void) { return KKM_ABI_VERSION; }
+
+KKM_API const char* kkm_last_error(const kkm_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_init_error.c_str();
+}
+
+KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d, int64_t ldx,
+                            int32_t k, const kkm_kernel* kernel, int32_t b, const kkm_config* cfg,
+                            const int64_t* init_idx, void* stream) {
+  if (!out) return fail(nullptr, KKM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!X || !kernel || !cfg) return fail(nullptr, KKM_EINVAL, "X, kernel and cfg are required");
+  if (n < 1 || n >= (int64_t(1) << 31)) return fail(nullptr, KKM_EINVAL, "n must be in [1, 2^31)");
+  if (d < 1 || d > 4096) return fail(nullptr, KKM_EINVAL, "d must be in [1, 4096]");
+  if (ldx < d) return fail(nullptr, KKM_EINVAL, "ldx must be >= d");
+  if (k < 1 || k > 1024 || k > n) return fail(nullptr, KKM_EINVAL, "k must be in [1, min(n, 1024)]");
+  if (b < 1 || b > 8192) return fail(nullptr, KKM_EINVAL, "b must be in [1, 8192]");
+  if (kernel->kind < KKM_GAUSSIAN || kernel->kind > KKM_POLY)
+    return fail(nullptr, KKM_EINVAL, "unknown kernel kind");
+  if ((kernel->kind == KKM_GAUSSIAN || kernel->kind == KKM_LAPLACIAN) &&
+      !(std::isfinite(kernel->param) && kernel->param > 0.0))
+    return fail(nullptr, KKM_EINVAL, "kernel param (kappa or sigma) must be finite and > 0");
+  if (kernel->kind == KKM_POLY &&
+      (kernel->degree < 1 || kernel->degree > 8 || !std::isfinite(kernel->coef0)))
+    return fail(nullptr, KKM_EINVAL, "polynomial degree must be in [1, 8] with a finite coef0");
+  if (cfg->lr != KKM_LR_BETA && cfg->lr != KKM_LR_CONST)
+    return fail(nullptr, KKM_EINVAL, "unknown learning rate");
+  if (cfg->lr == KKM_LR_CONST && !(cfg->eta > 0.0 && cfg->eta <= 1.0))
+    return fail(nullptr, KKM_EINVAL, "eta must be in (0, 1]");
+  if (cfg->precision < KKM_PREC_FP32 || cfg->precision > KKM_PREC_BF16X3)
+    return fail(nullptr, KKM_EINVAL, "unknown precision");
+  if (cfg->tau > 1000000) return fail(nullptr, KKM_EINVAL, "tau must be <= 1e6");
+  if (cfg->tau <= 0 && cfg->max_iters < 1)
+    return fail(nullptr, KKM_EINVAL, "an untruncated run needs max_iters >= 1");
+  if (init_idx)
+    for (int j = 0; j < k; ++j)
+      if (init_idx[j] < 0 || init_idx[j] >= n)
+        return fail(nullptr, KKM_EINVAL, "init_idx entry out of [0, n)");
+
+  const int64_t wmax = cfg->tau > 0 ? (int64_t)cfg->tau + b : 1 + (int64_t)cfg->max_iters * b;
+  const int64_t cap = cfg->tau > 0 ? kkm::round_up(2LL * cfg->tau + 4LL * b + 8, 8)
+                                   : kkm::round_up(wmax, 8);
+  const int64_t srows = (int64_t)k * cap + 256;
+  if (srows >= (int64_t(1) << 31)) return fail(nullptr, KKM_EINVAL, "support store too large (k*cap)");
+
+  kkm_ctx* c = new (std::nothrow) kkm_ctx();
+  if (!c) return fail(nullptr, KKM_ENOMEM, "host allocation failed");
+  auto bail = [&](kkm_status st) {
+    g_init_error = c->err;
+    free_all(c);
+    delete c;
+    return st;
+  };
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    c->err = "no CUDA device";
+    return bail(KKM_ECUDA);
+  }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->max_iters = cfg->max_iters;
+  c->wmax = (int32_t)wmax;
+
+  Dev& s = c->s;
+  s.n = n; s.d = d; s.k = k; s.b = b; s.ldx = ldx; s.X = X;
+  s.tau = cfg->tau > 0 ? cfg->tau : 0;
+  s.cap = (int32_t)cap;
+  s.nbcap = cfg->tau > 0 ? cfg->tau + 2 : cfg->max_iters + 2;
+  s.form = cfg->precision;
+  s.kind = kernel->kind; s.degree = kernel->degree; s.lr = cfg->lr;
+  s.param = kernel->param; s.coef0 = kernel->coef0; s.eta = cfg->eta;
+  s.negc = (kernel->kind == KKM_GAUSSIAN || kernel->kind == KKM_LAPLACIAN)
+               ? (float)(-1.4426950408889634 / kernel->param) : 0.0f;
+  s.num_sms = sms > 0 ? sms : 148;
+  s.seed = cfg->seed;
+  if (s.form == kkm::FORM_FP32) { s.dp = 0; s.ld = (int32_t)kkm::round_up(d, 16); }
+  else { s.dp = (int32_t)kkm::round_up(d, 64); s.ld = 2 * s.dp; }
+  s.bpad = (int32_t)kkm::round_up(b, 128);
+
+  // tensor-core distance pass for the BF16 forms when the device supports it
+  c->use_tc = false;
+  if (s.form != kkm::FORM_FP32) {
+    int maj = 0, min = 0;
+    cudaDeviceGetAttribute(&maj, cudaDevAttrComputeCapabilityMajor, c->device);
+    cudaDeviceGetAttribute(&min, cudaDevAttrComputeCapabilityMinor, c->device);
+    c->use_tc = (maj == 10 && min == 3) && kkm::tc_available();
+  }
+  s.tn = c->use_tc ? 128 : 64;
+  const int64_t T = 64;   // window-pass tile
+  s.max_tiles = (int32_t)((int64_t)k * ((wmax + s.tn - 1) / s.tn + 1));
+  const int64_t smax = (int64_t)k * wmax;
+  const int64_t p1 = ((smax + T - 1) / T + k) * ((wmax + b + T - 1) / T);
+  const int64_t p2 = ((b + T - 1) / T + k) * ((b + T - 1) / T + k);
+  if (p1 + p2 >= (int64_t(1) << 31)) {
+    c->err = "window pass would need too many tiles";
+    return bail(KKM_EINVAL);
+  }
+  s.max_pairs = (int32_t)(p1 + p2);
+
+  const int esz = s.form == kkm::FORM_FP32 ? 4 : 2;
+  cudaError_t e = cudaSuccess;
+#define ALLOC(ptr, count)                                        \
+  do {                                                           \
+    e = dalloc(c, &(ptr), (size_t)(count));                      \
+    if (e != cudaSuccess) {                                      \
+      c->err = std::string("device allocation: ") + cudaGetErrorString(e); \
+      return bail(KKM_ENOMEM);                                   \
+    }                                                            \
+  } while (0)
+  ALLOC(s.bidx, b);
+  if (esz == 4) ALLOC(s.xb32, (size_t)s.bpad * s.ld);
+  else ALLOC(s.xbh, (size_t)s.bpad * s.ld);
+  ALLOC(s.xbn, s.bpad);
+  ALLOC(s.xbi, s.bpad);
+  if (esz == 4) ALLOC(s.y32, (size_t)srows * s.ld);
+  else ALLOC(s.ybh, (size_t)srows * s.ld);
+  ALLOC(s.yn, srows);
+  ALLOC(s.yi, srows);
+  ALLOC(s.w64, srows);
+  ALLOC(s.w32, srows);
+  ALLOC(s.head, k); ALLOC(s.tail, k); ALLOC(s.c1, k); ALLOC(s.wsum, k); ALLOC(s.cnorm, k);
+  ALLOC(s.blk_iter, (size_t)k * s.nbcap); ALLOC(s.blk_cnt, (size_t)k * s.nbcap);
+  ALLOC(s.blk_first, k); ALLOC(s.blk_num, k);
+  ALLOC(s.assign, s.bpad); ALLOC(s.mind, s.bpad); ALLOC(s.inner_a, s.bpad);
+  ALLOC(s.counts, k); ALLOC(s.alpha, k); ALLOC(s.coff, k + 1); ALLOC(s.perm, s.bpad);
+  ALLOC(s.cmc, k); ALLOC(s.plan, k);
+  ALLOC(s.tiles, s.max_tiles); ALLOC(s.ntiles, 1); ALLOC(s.tile_first, k); ALLOC(s.tile_cnt, k);
+  ALLOC(s.part, (size_t)s.max_tiles * s.bpad);
+  ALLOC(s.wpairs, s.max_pairs); ALLOC(s.nwpairs, 1); ALLOC(s.wpair_first, k); ALLOC(s.wpair_cnt, k);
+  ALLOC(s.wpart, (size_t)s.max_pairs * 4);
+  ALLOC(s.iter, 1); ALLOC(s.status, 1); ALLOC(s.stats, 3); ALLOC(s.obj, 1); ALLOC(s.s_old, 1);
+  ALLOC(c->d_init_idx, k);
+  ALLOC(c->d_hbatch, b); ALLOC(c->d_hassign, b); ALLOC(c->d_hobj, 1);
+  c->objpart_len = 1024;
+  ALLOC(c->d_objpart, c->objpart_len);
+#undef ALLOC
+
+  // initial centers: caller's indices, or k distinct ones from SplitMix64
+  std::vector<int32_t> h_init(k);
+  if (init_idx) {
+    for (int j = 0; j < k; ++j) h_init[j] = (int32_t)init_idx[j];
+  } else {
+    std::unordered_set<int64_t> seen;
+    uint64_t ctr = 0;
+    for (int j = 0; j < k; ++j) {
+      int64_t i;
+      do { i = kkm::index_below(kkm::splitmix64(cfg->seed ^ 0x6a09e667f3bcc909ull, ctr++), n); }
+      while (seen.count(i));
+      seen.insert(i);
+      h_init[j] = (int32_t)i;
+    }
+  }
+  const int64_t one = 1;
+  e = cudaMemcpyAsync(c->d_init_idx, h_init.data(), k * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s.iter, &one, sizeof(one), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = kkm::launch_init_centers(s, c->d_init_idx, c->stream);
+  if (e == cudaSuccess && c->use_tc) e = kkm::tc_prepare(s);
+  if (e == cudaSuccess) e = kkm::launch_build_tiles(s, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    c->err = std::string("initialisation: ") + cudaGetErrorString(e);
+    return bail(KKM_ECUDA);
+  }
+  int32_t st = 0;
+  cudaMemcpy(&st, s.status, sizeof(st), cudaMemcpyDeviceToHost);
+  if (st != 0) {
+    c->err = "initialisation: invalid initial index";
+    return bail(KKM_EINVAL);
+  }
+  *out = c;
+  return KKM_OK;
+}
+
+KKM_API kkm_status kkm_step(kkm_ctx* c, const int32_t* batch_idx, const int32_t* forced_assign,
+                            int32_t* assign_out, float* dist_out, double* batch_obj_out) {
+  kkm_status st = check_usable(c);
+  if (st != KKM_OK) return st;
+  if (c->s.tau == 0 && c->iteration > c->max_iters)
+    return fail(c, KKM_ESTATE, "untruncated run: max_iters iterations already done");
+  const Dev& s = c->s;
+  const int32_t* idx = batch_idx;
+  if (!idx) {
+    KKM_CU(kkm::launch_sample(s, c->stream), "batch sampler");
+    idx = s.bidx;
+    ++c->launches;
+  }
+  KKM_CU(kkm::launch_gather_batch(s, idx, c->stream), "batch gather");
+  const bool rec = c->timing && c->ev_used < (int64_t)c->ev.size() / 2;
+  if (rec) KKM_CU(cudaEventRecord(c->ev[2 * c->ev_used], c->stream), "timing event");
+  st = launch_distance_pass(c, s.b);
+  if (st != KKM_OK) return st;
+  if (rec) {
+    KKM_CU(cudaEventRecord(c->ev[2 * c->ev_used + 1], c->stream), "timing event");
+    ++c->ev_used;
+  }
+  KKM_CU(kkm::launch_argmin(s, s.b, forced_assign, assign_out, nullptr, dist_out, true, c->stream),
+         "argmin");
+  KKM_CU(kkm::launch_sort_plan(s, c->stream), "sort/plan");
+  KKM_CU(kkm::launch_move(s, c->stream), "row moves");
+  KKM_CU(kkm::launch_wgram(s, c->stream), "window Gram");
+  KKM_CU(kkm::launch_finalize(s, batch_obj_out, c->stream), "finalize");
+  c->launches += 7;   // gather, distance, argmin, sort/plan, moves, window Gram, finalize
+  ++c->iteration;
+  return KKM_OK;
+}
+
+KKM_API kkm_status kkm_step_host(kkm_ctx* c, const int32_t* batch_idx, int32_t* assign_out,
+                                 double* batch_obj_out) {
+  kkm_status st = check_usable(c);
+  if (st != KKM_OK) return st;
+  const int b = c->s.b;
+  if (batch_idx)
+    KKM_CU(cudaMemcpyAsync(c->d_hbatch, batch_idx, b * sizeof(int32_t), cudaMemcpyHostToDevice,
+                           c->stream), "batch upload");
+  st = kkm_step(c, batch_idx ? c->d_hbatch : nullptr, nullptr, assign_out ? c->d_hassign : nullptr,
+                nullptr, batch_obj_out ? c->d_hobj : nullptr);
+  if (st != KKM_OK) return st;
+  if (assign_out)
+    KKM_CU(cudaMemcpyAsync(assign_out, c->d_hassign, b * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                           c->stream), "assignment download");
+  if (batch_obj_out)
+    KKM_CU(cudaMemcpyAsync(batch_obj_out, c->d_hobj, sizeof(double), cudaMemcpyDeviceToHost,
+                           c->stream), "objective download");
+  return sync_and_check(c);
+}
+
+// Runs the distance pass and argmin over query rows in chunks of b rows.
+static kkm_status assign_chunks(kkm_ctx* c, const float* Q, int64_t m, int64_t ldq, int32_t* assign_out,
+                                float* mind_out, float* dist_out, double* obj_sum) {
+  const Dev& s = c->s;
+  const bool is_x = (Q == s.X && ldq == s.ldx);
+  std::vector<double> partials;
+  int pending = 0;
+  double total = 0.0;
+  for (int64_t r0 = 0; r0 < m; r0 += s.b) {
+    const int rows = (int)std::min<int64_t>(s.b, m - r0);
+    KKM_CU(kkm::launch_gather_query(s, Q + r0 * ldq, ldq, rows, c->stream), "query gather");
+    c->launches += 3 + (obj_sum ? 1 : 0);   // gather, distance, argmin (+ sum)
+    if (is_x) {
+      // query rows that are data points keep their index, so a point meeting
+      // its own support copy gets ||x - y|| = 0 exactly
+      std::vector<int32_t> ids(rows);
+      for (int r = 0; r < rows; ++r) ids[r] = (int32_t)(r0 + r);
+      KKM_CU(cudaMemcpyAsync(s.xbi, ids.data(), rows * sizeof(int32_t), cudaMemcpyHostToDevice,
+                             c->stream), "query ids");
+      KKM_CU(cudaStreamSynchronize(c->stream), "query ids sync");
+    }
+    kkm_status st = launch_distance_pass(c, rows);
+    if (st != KKM_OK) return st;
+    KKM_CU(kkm::launch_argmin(s, rows, nullptr, assign_out ? assign_out + r0 : nullptr,
+                              obj_sum ? s.mind : (mind_out ? mind_out + r0 : nullptr),
+                              dist_out ? dist_out + r0 * s.k : nullptr, false, c->stream),
+           "query argmin");
+    if (obj_sum) {
+      if (mind_out)
+        KKM_CU(cudaMemcpyAsync(mind_out + r0, s.mind, rows * sizeof(float), cudaMemcpyDeviceToDevice,
+                               c->stream), "mind copy");
+      KKM_CU(kkm::launch_mind_sum(s, rows, c->d_objpart + pending, c->stream), "objective sum");
+      if (++pending == c->objpart_len || r0 + s.b >= m) {
+        partials.resize(pending);
+        KKM_CU(cudaMemcpyAsync(partials.data(), c->d_objpart, pending * sizeof(double),
+                               cudaMemcpyDeviceToHost, c->stream), "objective download");
+        KKM_CU(cudaStreamSynchronize(c->stream), "objective sync");
+        for (double v : partials) total += v;
+        pending = 0;
+      }
+    }
+  }
+  if (obj_sum) *obj_sum = total;
+  return KKM_OK;
+}
+
+KKM_API kkm_status kkm_assign(kkm_ctx* c, const float* Q, int64_t m, int64_t ldq, int32_t* assign_out,
+                              float* mind_out, float* dist_out) {
+  kkm_status st = check_usable(c);
+  if (st != KKM_OK) return st;
+  if (m < 0 || (m > 0 && (!Q || ldq < c->s.d))) return fail(c, KKM_EINVAL, "bad query matrix");
+  return assign_chunks(c, Q, m, ldq, assign_out, mind_out, dist_out, nullptr);
+}
+
+KKM_API kkm_status kkm_objective(kkm_ctx* c, const float* Q, int64_t m, int64_t ldq, double* out) {
+  kkm_status st = check_usable(c);
+  if (st != KKM_OK) return st;
+  if (!out) return fail(c, KKM_EINVAL, "out is NULL");
+  if (!Q) { Q = c->s.X; m = c->s.n; ldq = c->s.ldx; }
+  if (m < 1 || ldq < c->s.d) return fail(c, KKM_EINVAL, "bad query matrix");
+  double total = 0.0;
+  st = assign_chunks(c, Q, m, ldq, nullptr, nullptr, nullptr, &total);
+  if (st != KKM_OK) return st;
+  st = sync_and_check(c);
+  if (st != KKM_OK) return st;
+  *out = total / (double)m;
+  return KKM_OK;
+}
+
+KKM_API kkm_status kkm_sync(kkm_ctx* c) {
+  kkm_status st = check_usable(c);
+  if (st != KKM_OK) return st;
+  return sync_and_check(c);
+}
+
+KKM_API kkm_status kkm_get_state_sizes(kkm_ctx* c, int64_t* total_rows, int64_t* total_blocks) {
+  kkm_status st = check_usable(c);
+  if (st != KKM_OK) return st;
+  st = sync_and_check(c);
+  if (st != KKM_OK) return st;
+  const int k = c->s.k;
+  std::vector<int32_t> head(k), tail(k), c1(k), nb(k);
+  KKM_CU(cudaMemcpy(head.data(), c->s.head, k * 4, cudaMemcpyDeviceToHost), "state read");
+  KKM_CU(cudaMemcpy(tail.data(), c->s.tail, k * 4, cudaMemcpyDeviceToHost), "state read");
+  KKM_CU(cudaMemcpy(c1.data(), c->s.c1, k * 4, cudaMemcpyDeviceToHost), "state read");
+  KKM_CU(cudaMemcpy(nb.data(), c->s.blk_num, k * 4, cudaMemcpyDeviceToHost), "state read");
+  int64_t r = 0, bl = 0;
+  for (int j = 0; j < k; ++j) { r += tail[j] - head[j]; bl += nb[j] + (c1[j] ? 1 : 0); }
+  if (total_rows) *total_rows = r;
+  if (total_blocks) *total_blocks = bl;
+  return KKM_OK;
+}
+
+KKM_API kkm_status kkm_get_state(kkm_ctx* c, int64_t* iteration, int32_t* rows_per_center,
+                                 int64_t* row_idx, double* row_w, int32_t* blocks_per_center,
+                                 int64_t* block_iter, int32_t* block_count, uint8_t* c1_kept,
+                                 double* cnorm) {
+  kkm_status st = check_usable(c);
+  if (st != KKM_OK) return st;
+  st = sync_and_check(c);
+  if (st != KKM_OK) return st;
+  const Dev& s = c->s;
+  const int k = s.k;
+  std::vector<int32_t> head(k), tail(k), c1(k), bf(k), bn(k);
+  std::vector<int32_t> bi((size_t)k * s.nbcap), bc((size_t)k * s.nbcap);
+  std::vector<double> cn(k);
+  int64_t it = 0;
+  KKM_CU(cudaMemcpy(head.data(), s.head, k * 4, cudaMemcpyDeviceToHost), "state read");
+  KKM_CU(cudaMemcpy(tail.data(), s.tail, k * 4, cudaMemcpyDeviceToHost), "state read");
+  KKM_CU(cudaMemcpy(c1.data(), s.c1, k * 4, cudaMemcpyDeviceToHost), "state read");
+  KKM_CU(cudaMemcpy(bf.data(), s.blk_first, k * 4, cudaMemcpyDeviceToHost), "state read");
+  KKM_CU(cudaMemcpy(bn.data(), s.blk_num, k * 4, cudaMemcpyDeviceToHost), "state read");
+  KKM_CU(cudaMemcpy(bi.data(), s.blk_iter, bi.size() * 4, cudaMemcpyDeviceToHost), "state read");
+  KKM_CU(cudaMemcpy(bc.data(), s.blk_cnt, bc.size() * 4, cudaMemcpyDeviceToHost), "state read");
+  KKM_CU(cudaMemcpy(cn.data(), s.cnorm, k * 8, cudaMemcpyDeviceToHost), "state read");
+  KKM_CU(cudaMemcpy(&it, s.iter, 8, cudaMemcpyDeviceToHost), "state read");
+  if (iteration) *iteration = it;
+  int64_t ro = 0, bo = 0;
+  for (int j = 0; j < k; ++j) {
+    const int rows = tail[j] - head[j];
+    if (rows_per_center) rows_per_center[j] = rows;
+    if (rows > 0) {
+      std::vector<int32_t> yi(rows);
+      std::vector<double> w(rows);
+      const int64_t g = (int64_t)j * s.cap + head[j];
+      KKM_CU(cudaMemcpy(yi.data(), s.yi + g, rows * 4, cudaMemcpyDeviceToHost), "state read");
+      KKM_CU(cudaMemcpy(w.data(), s.w64 + g, rows * 8, cudaMemcpyDeviceToHost), "state read");
+      for (int r = 0; r < rows; ++r) {
+        if (row_idx) row_idx[ro + r] = yi[r];
+        if (row_w) row_w[ro + r] = w[r];
+      }
+    }
+    ro += rows;
+    const int nblk = bn[j] + (c1[j] ? 1 : 0);
+    if (blocks_per_center) blocks_per_center[j] = nblk;
+    int64_t q = bo;
+    if (c1[j]) {
+      if (block_iter) block_iter[q] = 0;
+      if (block_count) block_count[q] = 1;
+      ++q;
+    }
+    for (int t = 0; t < bn[j]; ++t, ++q) {
+      const int slot = (bf[j] + t) % s.nbcap;
+      if (block_iter) block_iter[q] = bi[(size_t)j * s.nbcap + slot];
+      if (block_count) block_count[q] = bc[(size_t)j * s.nbcap + slot];
+    }
+    bo += nblk;
+    if (c1_kept) c1_kept[j] = c1[j] ? 1 : 0;
+    if (cnorm) cnorm[j] = cn[j];
+  }
+  return KKM_OK;
+}
+
+KKM_API kkm_status kkm_set_state(kkm_ctx* c, int64_t iteration, const int32_t* rows_per_center,
+                                 const int64_t* row_idx, const double* row_w,
+                                 const int32_t* blocks_per_center, const int64_t* block_iter,
+                                 const int32_t* block_count, const uint8_t* c1_kept,
+                                 const double* cnorm) {
+  kkm_status st = check_usable(c);
+  if (st != KKM_OK) return st;
+  const Dev& s = c->s;
+  const int k = s.k;
+  if (!rows_per_center || !row_idx || !row_w || !blocks_per_center || !block_iter || !block_count ||
+      !c1_kept || !cnorm)
+    return fail(c, KKM_EINVAL, "all state arrays are required");
+  if (iteration < 1) return fail(c, KKM_EINVAL, "iteration must be >= 1");
+  if (s.tau == 0 && iteration - 1 > c->max_iters)
+    return fail(c, KKM_EINVAL, "iteration beyond max_iters of an untruncated run");
+  // validate everything before touching the device
+  int64_t ro = 0, bo = 0;
+  for (int j = 0; j < k; ++j) {
+    const int rows = rows_per_center[j], nblk = blocks_per_center[j];
+    if (rows < 0 || rows > c->wmax) return fail(c, KKM_EINVAL, "rows_per_center out of range");
+    if (nblk < 0) return fail(c, KKM_EINVAL, "blocks_per_center negative");
+    int64_t sum = 0, prev_it = 0;
+    int q0 = 0;
+    if (c1_kept[j]) {
+      if (nblk < 1 || block_iter[bo] != 0 || block_count[bo] != 1)
+        return fail(c, KKM_EINVAL, "a kept C_1 must be the first block (iteration 0, count 1)");
+      q0 = 1;
+      sum = 1;
+    }
+    if (nblk - q0 > s.nbcap - 1) return fail(c, KKM_EINVAL, "too many blocks for the window ring");
+    for (int q = q0; q < nblk; ++q) {
+      const int64_t bi = block_iter[bo + q];
+      if (bi <= prev_it || bi >= iteration) return fail(c, KKM_EINVAL, "block iterations must increase, below iteration");
+      if (block_count[bo + q] < 1) return fail(c, KKM_EINVAL, "block counts must be >= 1");
+      prev_it = bi;
+      sum += block_count[bo + q];
+    }
+    if (sum != rows) return fail(c, KKM_EINVAL, "block counts do not add up to rows_per_center");
+    if (!std::isfinite(cnorm[j])) return fail(c, KKM_EINVAL, "cnorm must be finite");
+    for (int r = 0; r < rows; ++r) {
+      if (row_idx[ro + r] < 0 || row_idx[ro + r] >= s.n) return fail(c, KKM_EINVAL, "row_idx out of range");
+      if (!std::isfinite(row_w[ro + r])) return fail(c, KKM_EINVAL, "row weights must be finite");
+    }
+    ro += rows;
+    bo += nblk;
+  }
+  KKM_CU(cudaStreamSynchronize(c->stream), "stream synchronize");
+  std::vector<int32_t> head(k, 0), tail(k), c1(k), wsum(k), bf(k, 0), bn(k);
+  std::vector<int32_t> bi((size_t)k * s.nbcap, 0), bc((size_t)k * s.nbcap, 0);
+  ro = 0; bo = 0;
+  for (int j = 0; j < k; ++j) {
+    const int rows = rows_per_center[j], nblk = blocks_per_center[j];
+    tail[j] = rows;
+    c1[j] = c1_kept[j] ? 1 : 0;
+    int q0 = c1[j];
+    bn[j] = nblk - q0;
+    int ws = 0;
+    for (int q = q0; q < nblk; ++q) {
+      bi[(size_t)j * s.nbcap + (q - q0)] = (int32_t)block_iter[bo + q];
+      bc[(size_t)j * s.nbcap + (q - q0)] = block_count[bo + q];
+      ws += block_count[bo + q];
+    }
+    wsum[j] = ws;
+    if (rows > 0) {
+      std::vector<int32_t> yi(rows);
+      std::vector<float> w32(rows);
+      for (int r = 0; r < rows; ++r) { yi[r] = (int32_t)row_idx[ro + r]; w32[r] = (float)row_w[ro + r]; }
+      const int64_t g = (int64_t)j * s.cap;
+      KKM_CU(cudaMemcpy(s.yi + g, yi.data(), rows * 4, cudaMemcpyHostToDevice), "state write");
+      KKM_CU(cudaMemcpy(s.w64 + g, row_w + ro, rows * 8, cudaMemcpyHostToDevice), "state write");
+      KKM_CU(cudaMemcpy(s.w32 + g, w32.data(), rows * 4, cudaMemcpyHostToDevice), "state write");
+    }
+    ro += rows;
+    bo += nblk;
+  }
+  KKM_CU(cudaMemcpy(s.head, head.data(), k * 4, cudaMemcpyHostToDevice), "state write");
+  KKM_CU(cudaMemcpy(s.tail, tail.data(), k * 4, cudaMemcpyHostToDevice), "state write");
+  KKM_CU(cudaMemcpy(s.c1, c1.data(), k * 4, cudaMemcpyHostToDevice), "state write");
+  KKM_CU(cudaMemcpy(s.wsum, wsum.data(), k * 4, cudaMemcpyHostToDevice), "state write");
+  KKM_CU(cudaMemcpy(s.blk_first, bf.data(), k * 4, cudaMemcpyHostToDevice), "state write");
+  KKM_CU(cudaMemcpy(s.blk_num, bn.data(), k * 4, cudaMemcpyHostToDevice), "state write");
+  KKM_CU(cudaMemcpy(s.blk_iter, bi.data(), bi.size() * 4, cudaMemcpyHostToDevice), "state write");
+  KKM_CU(cudaMemcpy(s.blk_cnt, bc.data(), bc.size() * 4, cudaMemcpyHostToDevice), "state write");
+  KKM_CU(cudaMemcpy(s.cnorm, cnorm, k * 8, cudaMemcpyHostToDevice), "state write");
+  KKM_CU(cudaMemcpy(s.iter, &iteration, 8, cudaMemcpyHostToDevice), "state write");
+  KKM_CU(kkm::launch_load_rows(s, 0, c->stream), "support row gather");
+  KKM_CU(kkm::launch_build_tiles(s, c->stream), "tile list");
+  c->iteration = iteration;
+  return sync_and_check(c);
+}
+
+KKM_API kkm_status kkm_stats(kkm_ctx* c, int64_t* steps, int64_t* support_rows, int64_t* gram_tiles,
+                             int32_t reset) {
+  kkm_status st = check_usable(c);
+  if (st != KKM_OK) return st;
+  st = sync_and_check(c);
+  if (st != KKM_OK) return st;
+  int64_t v[3] = {0, 0, 0};
+  KKM_CU(cudaMemcpy(v, c->s.stats, sizeof(v), cudaMemcpyDeviceToHost), "stats read");
+  if (steps) *steps = v[0];
+  if (support_rows) *support_rows = v[1];
+  if (gram_tiles) *gram_tiles = v[2];
+  if (reset) KKM_CU(cudaMemset(c->s.stats, 0, sizeof(v)), "stats reset");
+  return KKM_OK;
+}
+
+KKM_API kkm_status kkm_timing_enable(kkm_ctx* c, int32_t enable) {
+  kkm_status st = check_usable(c);
+  if (st != KKM_OK) return st;
+  if (enable && c->ev.empty()) {
+    c->ev.resize(2 * 4096);
+    for (auto& e : c->ev) KKM_CU(cudaEventCreate(&e), "event create");
+  }
+  c->timing = enable != 0;
+  return KKM_OK;
+}
+
+KKM_API kkm_status kkm_timing_read(kkm_ctx* c, int64_t* launches, double* total_ms, int32_t reset) {
+  kkm_status st = check_usable(c);
+  if (st != KKM_OK) return st;
+  KKM_CU(cudaStreamSynchronize(c->stream), "stream synchronize");
+  double tot = 0.0;
+  for (int64_t i = 0; i < c->ev_used; ++i) {
+    float ms = 0.0f;
+    KKM_CU(cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]), "event elapsed");
+    tot += ms;
+  }
+  if (launches) *launches = c->ev_used;
+  if (total_ms) *total_ms = tot;
+  if (reset) c->ev_used = 0;
+  return KKM_OK;
+}
+
+KKM_API kkm_status kkm_launches(kkm_ctx* c, int64_t* launches, int32_t reset) {
+  if (!c) return fail(nullptr, KKM_EINVAL, "null context");
+  if (launches) *launches = c->launches;
+  if (reset) c->launches = 0;
+  return KKM_OK;
+}
+
+KKM_API kkm_status kkm_destroy(kkm_ctx* c) {
+  if (!c) return KKM_OK;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+  return KKM_OK;
+}

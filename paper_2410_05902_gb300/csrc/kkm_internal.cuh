@@ -1,0 +1,204 @@
+// Internal declarations shared by the libkkm translation units.
+//
+// Device state of one run. Everything lives in HBM and is sized at kkm_init;
+// nothing is allocated per step.
+//
+//   support store  k regions of `cap` rows, one per center. Center j's
+//                  window (Eq. (1)) occupies rows [head_j, tail_j) of region j,
+//                  laid out as C_1 (while kept), then blocks oldest -> newest,
+//                  each block in batch order. Appends go at tail. Drops advance
+//                  head. When an append would pass the region's end, the
+//                  window is first copied down to row 0 ("compaction"). With
+//                  cap = 2*tau + 4*b + 8 the source and destination rows of
+//                  that copy never overlap, because a window holds at most
+//                  tau + b rows.
+//   row data       FP32 form: FP32 rows, ld = round_up(d, 16), zero padded.
+//                  BF16 forms: BF16 rows [hi(0..dp) | lo(0..dp)], dp =
+//                  round_up(d, 64), zero padded; ld = 2*dp.
+//   yn             FP32 ||y||^2 of the values the Gram product actually uses
+//   yi             int32 data index of the row (the key that forces K(x,x)=1
+//                  when a batch point meets its own support copy)
+//   w64 / w32      FP64 master weight and its FP32 copy for the distance kernel
+//
+// Per-center block ring: (iteration, count) of the window's blocks, oldest
+// first, at most tau + 2 entries. C_1 is not in the ring; c1[j] flags it.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace kkm {
+
+enum Form : int { FORM_FP32 = 0, FORM_BF16 = 1, FORM_BF16X3 = 2 };
+enum KernelKind : int { K_GAUSS = 0, K_LAPLACE = 1, K_LINEAR = 2, K_POLY = 3 };
+
+// device status bits (sticky until the context is destroyed)
+constexpr int ST_BAD_BATCH_INDEX = 1;
+constexpr int ST_BAD_ASSIGN = 2;
+constexpr int ST_CAPACITY = 4;
+constexpr int ST_TIMEOUT = 8;
+
+// Column tile of the distance pass: support rows [row0, row0 + ncols) of center j.
+struct Tile {
+  int32_t j;
+  int32_t row0;   // global support row
+  int32_t ncols;
+  int32_t pad;
+};
+
+// Tile pair of the window Gram pass (norm recurrence terms), see kkm_step.cu.
+struct WPair {
+  int32_t j;
+  int32_t kind;   // 0: dropped rows x (old window + new block); 1: new block x new block
+  int32_t rt;     // row tile index within the row range
+  int32_t ct;     // column tile index within the column range
+};
+
+// Per-center plan of one update, written by the sort/plan kernel.
+struct Plan {
+  int32_t head_c;    // window start after compaction
+  int32_t tail_c;    // window end after compaction (= start of the new block)
+  int32_t head_new;  // window start after the drops
+  int32_t tail_new;  // window end after the append
+  int32_t src_head;  // compaction source start (-1 when not compacting)
+  int32_t cnt;       // b_i^j
+  int32_t ndrop;     // rows dropped (C_1 included)
+  int32_t c1_new;    // C_1 kept after this update
+};
+
+struct Dev {
+  // problem
+  int64_t n;
+  int32_t d, k, b, tau, cap, nbcap;
+  int64_t ldx;
+  int32_t ld;        // row stride of batch and support rows, in elements
+  int32_t dp;        // BF16 forms: padded d (hi part length)
+  int32_t form, kind, degree, lr;
+  double param, coef0, eta;
+  float negc;        // -log2(e) / param (Gaussian, Laplacian)
+  int32_t num_sms;
+  uint64_t seed;
+  int32_t tn;        // support rows per distance tile
+  int32_t bpad;      // rows of the batch buffers (>= b, multiple of 128)
+  int32_t max_tiles, max_pairs;
+  const float* X;
+  // batch
+  int32_t* bidx;     // [b] indices of the batch being processed
+  float* xb32;       // [bpad * ld]   FP32 form
+  __nv_bfloat16* xbh;// [bpad * ld]   BF16 forms
+  float* xbn;        // [bpad]
+  int32_t* xbi;      // [bpad] data index, -1 for query rows
+  // support store
+  float* y32;
+  __nv_bfloat16* ybh;
+  float* yn;
+  int32_t* yi;
+  double* w64;
+  float* w32;
+  // per center
+  int32_t* head;
+  int32_t* tail;
+  int32_t* c1;
+  int32_t* wsum;     // sum of block counts in the window (C_1 excluded)
+  double* cnorm;
+  int32_t* blk_iter; // [k * nbcap]
+  int32_t* blk_cnt;  // [k * nbcap]
+  int32_t* blk_first;
+  int32_t* blk_num;
+  // step workspaces
+  int32_t* assign;   // [bpad] assignment used by the update
+  float* mind;       // [bpad]
+  float* inner_a;    // [bpad] <phi(x), C_a> at the used assignment a
+  int32_t* counts;   // [k]
+  double* alpha;     // [k]
+  int32_t* coff;     // [k + 1] exclusive offsets of the center-sorted batch
+  int32_t* perm;     // [b] batch rows sorted by center (stable)
+  double* cmc;       // [k] <C_j, cm(B_j)>
+  Plan* plan;        // [k]
+  Tile* tiles;       // [max_tiles]
+  int32_t* ntiles;   // [1]
+  int32_t* tile_first; // [k]
+  int32_t* tile_cnt;   // [k]
+  float* part;       // [max_tiles * bpad] per-tile weighted kernel sums
+  WPair* wpairs;     // [max_pairs]
+  int32_t* nwpairs;  // [1]
+  int32_t* wpair_first; // [k]
+  int32_t* wpair_cnt;   // [k]
+  double* wpart;     // [max_pairs * 4]
+  int64_t* iter;     // [1] next iteration number
+  int32_t* status;   // [1] sticky device status bits
+  int64_t* stats;    // [3] steps, support rows, tiles
+  double* obj;       // [1] last batch objective
+  int32_t* s_old;    // [1] support rows of the current step's distance pass
+};
+
+// ---------------------------------------------------------------- helpers
+__host__ __device__ inline int64_t round_up(int64_t a, int64_t m) { return (a + m - 1) / m * m; }
+
+// SplitMix64 (Steele, Lea, Flood 2014): output `counter` of the sequential
+// generator seeded with `seed`, i.e. the finaliser applied to
+// seed + (counter + 1) * golden gamma.
+__host__ __device__ inline uint64_t splitmix64(uint64_t seed, uint64_t counter) {
+  uint64_t z = seed + (counter + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Lemire's multiply-high reduction of a 64-bit value onto [0, n).
+__host__ __device__ inline int64_t index_below(uint64_t h, uint64_t n) {
+#ifdef __CUDA_ARCH__
+  return (int64_t)__umul64hi(h, n);
+#else
+  return (int64_t)(((unsigned __int128)h * n) >> 64);
+#endif
+}
+
+// Kernel value from the Gram entry g = <x,y> and the squared norms, in FP32.
+// `same` forces ||x - y|| = 0 when x and y are the same data point.
+__device__ __forceinline__ float kernel_from_gram(int kind, float g, float xn, float yn, bool same,
+                                                  float negc, float coef0, int degree) {
+  if (kind == K_GAUSS || kind == K_LAPLACE) {
+    float d2 = fmaxf(fmaf(-2.0f, g, xn + yn), 0.0f);
+    if (same) d2 = 0.0f;
+    float arg = (kind == K_GAUSS) ? d2 : sqrtf(d2);
+    return exp2f(arg * negc);       // negc = -log2(e) / param
+  }
+  if (kind == K_LINEAR) return g;
+  float base = g + coef0, r = 1.0f;
+  for (int p = 0; p < degree; ++p) r *= base;
+  return r;
+}
+
+// K(x, x) from ||x||^2 (FP64, for the distance formula).
+__host__ __device__ inline double kernel_self(int kind, double xn, double coef0, int degree) {
+  if (kind == K_GAUSS || kind == K_LAPLACE) return 1.0;
+  if (kind == K_LINEAR) return xn;
+  double base = xn + coef0, r = 1.0;
+  for (int p = 0; p < degree; ++p) r *= base;
+  return r;
+}
+
+// ------------------------------------------------------------ launchers
+// All return cudaGetLastError() of their launches.
+cudaError_t launch_sample(const Dev& s, cudaStream_t st);
+cudaError_t launch_gather_batch(const Dev& s, const int32_t* idx, cudaStream_t st);
+cudaError_t launch_gather_query(const Dev& s, const float* Q, int64_t ldq, int rows, cudaStream_t st);
+cudaError_t launch_dist_simt(const Dev& s, int rows, cudaStream_t st);
+cudaError_t launch_argmin(const Dev& s, int rows, const int32_t* forced, int32_t* assign_out,
+                          float* mind_out, float* dist_out, bool update, cudaStream_t st);
+cudaError_t launch_sort_plan(const Dev& s, cudaStream_t st);
+cudaError_t launch_move(const Dev& s, cudaStream_t st);
+cudaError_t launch_wgram(const Dev& s, cudaStream_t st);
+cudaError_t launch_finalize(const Dev& s, double* obj_out, cudaStream_t st);
+cudaError_t launch_build_tiles(const Dev& s, cudaStream_t st);
+cudaError_t launch_init_centers(const Dev& s, const int32_t* init_idx, cudaStream_t st);
+cudaError_t launch_load_rows(const Dev& s, int32_t rows_total, cudaStream_t st);
+cudaError_t launch_mind_sum(const Dev& s, int rows, double* out, cudaStream_t st);
+
+// tensor-core distance pass (BF16 forms); returns cudaErrorNotSupported when unavailable
+bool tc_available();
+cudaError_t tc_prepare(Dev& s);
+cudaError_t launch_dist_tc(const Dev& s, int rows, cudaStream_t st);
+
+}  // namespace kkm

@@ -96,12 +96,10 @@ def median_sigma(X, seed: int, sample: int = 2000) -> float:
     m = min(X.shape[0], sample)
     rows = rng.choice(X.shape[0], size=m, replace=False)
     S = X[rows].astype(np.float64)
+    sq = np.einsum("ij,ij->i", S, S)
+    G = sq[:, None] + sq[None, :] - 2.0 * (S @ S.T)
     iu = np.triu_indices(m, k=1)
-    diff_sq = np.zeros(len(iu[0]))
-    for t in range(S.shape[1]):
-        col = S[:, t]
-        diff_sq += (col[iu[0]] - col[iu[1]]) ** 2
-    return float(np.median(np.sqrt(diff_sq)))
+    return float(np.median(np.sqrt(np.maximum(G[iu], 0.0))))
 
 
 def init_indices(n: int, k: int, seed: int) -> np.ndarray:

@@ -1,0 +1,282 @@
+"""Thin Python binding of libkkm (include/kkm.h), argument marshalling only.
+
+The module-level functions carry the C names (``kkm_init``, ``kkm_step``, ...)
+and take raw integer pointers. ``KKM`` wraps one context for callers that
+hold PyTorch CUDA tensors: it passes ``data_ptr()`` values and the current
+CUDA stream, and every step of the method runs in the library's kernels.
+There is no CPU fallback. If libkkm.so has not been built, loading fails with
+an error.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int32, c_int64, c_uint8, c_uint64, c_void_p
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libkkm.so")
+
+KKM_OK, KKM_EINVAL, KKM_ENOMEM, KKM_ECUDA, KKM_ETIMEOUT, KKM_ESTATE, KKM_ENOTSUP = range(7)
+KKM_GAUSSIAN, KKM_LAPLACIAN, KKM_LINEAR, KKM_POLY = range(4)
+KKM_LR_BETA, KKM_LR_CONST = 0, 1
+KKM_PREC_FP32, KKM_PREC_BF16, KKM_PREC_BF16X3 = 0, 1, 2
+PRECISIONS = {"fp32": KKM_PREC_FP32, "bf16": KKM_PREC_BF16, "bf16x3": KKM_PREC_BF16X3}
+KERNELS = {"gaussian": KKM_GAUSSIAN, "laplacian": KKM_LAPLACIAN, "linear": KKM_LINEAR,
+           "poly": KKM_POLY}
+_STATUS = {0: "KKM_OK", 1: "KKM_EINVAL", 2: "KKM_ENOMEM", 3: "KKM_ECUDA", 4: "KKM_ETIMEOUT",
+           5: "KKM_ESTATE", 6: "KKM_ENOTSUP"}
+
+
+class kkm_kernel(ctypes.Structure):
+    _fields_ = [("kind", c_int32), ("param", c_double), ("coef0", c_double), ("degree", c_int32)]
+
+
+class kkm_config(ctypes.Structure):
+    _fields_ = [("tau", c_int32), ("lr", c_int32), ("eta", c_double), ("precision", c_int32),
+                ("max_iters", c_int32), ("seed", c_uint64)]
+
+
+class KKMError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+_P = c_void_p
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libkkm.so (built by paper_2410_05902_gb300.build) and declare its signatures."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libkkm.so is not built ({p}); run paper_2410_05902_gb300.build.build()")
+    lib = ctypes.CDLL(p)
+    sigs = {
+        "kkm_version": ([], c_int32),
+        "kkm_last_error": ([_P], ctypes.c_char_p),
+        "kkm_init": ([POINTER(_P), _P, c_int64, c_int32, c_int64, c_int32, POINTER(kkm_kernel),
+                      c_int32, POINTER(kkm_config), POINTER(c_int64), _P], c_int32),
+        "kkm_step": ([_P, _P, _P, _P, _P, _P], c_int32),
+        "kkm_step_host": ([_P, _P, _P, _P], c_int32),
+        "kkm_assign": ([_P, _P, c_int64, c_int64, _P, _P, _P], c_int32),
+        "kkm_objective": ([_P, _P, c_int64, c_int64, POINTER(c_double)], c_int32),
+        "kkm_sync": ([_P], c_int32),
+        "kkm_get_state_sizes": ([_P, POINTER(c_int64), POINTER(c_int64)], c_int32),
+        "kkm_get_state": ([_P, POINTER(c_int64), _P, _P, _P, _P, _P, _P, _P, _P], c_int32),
+        "kkm_set_state": ([_P, c_int64, _P, _P, _P, _P, _P, _P, _P, _P], c_int32),
+        "kkm_stats": ([_P, POINTER(c_int64), POINTER(c_int64), POINTER(c_int64), c_int32], c_int32),
+        "kkm_timing_enable": ([_P, c_int32], c_int32),
+        "kkm_timing_read": ([_P, POINTER(c_int64), POINTER(c_double), c_int32], c_int32),
+        "kkm_launches": ([_P, POINTER(c_int64), c_int32], c_int32),
+        "kkm_destroy": ([_P], c_int32),
+    }
+    for name, (args, res) in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(status: int, ctx) -> None:
+    if status != KKM_OK:
+        msg = load().kkm_last_error(ctx)
+        raise KKMError(status, msg.decode() if msg else "")
+
+
+def _np_ptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(c_void_p)
+
+
+# ------------------------------------------------------- C-named wrappers
+def kkm_version() -> int:
+    return load().kkm_version()
+
+
+def kkm_init(X_ptr: int, n: int, d: int, ldx: int, k: int, kernel: kkm_kernel, b: int,
+             cfg: kkm_config, init_idx: np.ndarray | None, stream: int):
+    ctx = c_void_p()
+    ii = None if init_idx is None else np.ascontiguousarray(init_idx, dtype=np.int64)
+    st = load().kkm_init(ctypes.byref(ctx), X_ptr, n, d, ldx, k, ctypes.byref(kernel), b,
+                         ctypes.byref(cfg), None if ii is None else ii.ctypes.data_as(POINTER(c_int64)),
+                         stream)
+    _check(st, None)
+    return ctx
+
+
+def kkm_step(ctx, batch_idx: int | None, forced_assign: int | None, assign_out: int | None,
+             dist_out: int | None, batch_obj_out: int | None) -> None:
+    _check(load().kkm_step(ctx, batch_idx, forced_assign, assign_out, dist_out, batch_obj_out), ctx)
+
+
+def kkm_step_host(ctx, batch_idx: np.ndarray | None, assign_out: np.ndarray | None,
+                  batch_obj_out: np.ndarray | None) -> None:
+    _check(load().kkm_step_host(ctx, _np_ptr(batch_idx), _np_ptr(assign_out), _np_ptr(batch_obj_out)), ctx)
+
+
+def kkm_assign(ctx, Q: int, m: int, ldq: int, assign_out: int | None, mind_out: int | None,
+               dist_out: int | None) -> None:
+    _check(load().kkm_assign(ctx, Q, m, ldq, assign_out, mind_out, dist_out), ctx)
+
+
+def kkm_objective(ctx, Q: int | None, m: int, ldq: int) -> float:
+    out = c_double()
+    _check(load().kkm_objective(ctx, Q, m, ldq, ctypes.byref(out)), ctx)
+    return out.value
+
+
+def kkm_sync(ctx) -> None:
+    _check(load().kkm_sync(ctx), ctx)
+
+
+def kkm_stats(ctx, reset: bool = False) -> tuple[int, int, int]:
+    a, b_, c = c_int64(), c_int64(), c_int64()
+    _check(load().kkm_stats(ctx, ctypes.byref(a), ctypes.byref(b_), ctypes.byref(c), int(reset)), ctx)
+    return a.value, b_.value, c.value
+
+
+def kkm_timing_enable(ctx, enable: bool) -> None:
+    _check(load().kkm_timing_enable(ctx, int(enable)), ctx)
+
+
+def kkm_timing_read(ctx, reset: bool = False) -> tuple[int, float]:
+    n, ms = c_int64(), c_double()
+    _check(load().kkm_timing_read(ctx, ctypes.byref(n), ctypes.byref(ms), int(reset)), ctx)
+    return n.value, ms.value
+
+
+def kkm_launches(ctx, reset: bool = False) -> int:
+    n = c_int64()
+    _check(load().kkm_launches(ctx, ctypes.byref(n), int(reset)), ctx)
+    return n.value
+
+
+def kkm_get_state(ctx, k: int) -> dict:
+    rows, blocks = c_int64(), c_int64()
+    _check(load().kkm_get_state_sizes(ctx, ctypes.byref(rows), ctypes.byref(blocks)), ctx)
+    it = c_int64()
+    out = {
+        "rows_per_center": np.zeros(k, np.int32), "row_idx": np.zeros(rows.value, np.int64),
+        "row_w": np.zeros(rows.value, np.float64), "blocks_per_center": np.zeros(k, np.int32),
+        "block_iter": np.zeros(blocks.value, np.int64), "block_count": np.zeros(blocks.value, np.int32),
+        "c1_kept": np.zeros(k, np.uint8), "cnorm": np.zeros(k, np.float64),
+    }
+    _check(load().kkm_get_state(ctx, ctypes.byref(it), *[_np_ptr(out[key]) for key in (
+        "rows_per_center", "row_idx", "row_w", "blocks_per_center", "block_iter", "block_count",
+        "c1_kept", "cnorm")]), ctx)
+    out["iteration"] = it.value
+    return out
+
+
+def kkm_set_state(ctx, state: dict) -> None:
+    arrs = [np.ascontiguousarray(state[key], dtype=dt) for key, dt in (
+        ("rows_per_center", np.int32), ("row_idx", np.int64), ("row_w", np.float64),
+        ("blocks_per_center", np.int32), ("block_iter", np.int64), ("block_count", np.int32),
+        ("c1_kept", np.uint8), ("cnorm", np.float64))]
+    _check(load().kkm_set_state(ctx, int(state["iteration"]), *[_np_ptr(a) for a in arrs]), ctx)
+
+
+def kkm_destroy(ctx) -> None:
+    _check(load().kkm_destroy(ctx), None)
+
+
+# ------------------------------------------------------------ torch wrapper
+class KKM:
+    """One clustering run on the current CUDA device (tensors in, tensors out).
+
+    X is a CUDA float32 tensor (n x d, row stride >= d). It is kept alive
+    here because the library reads batches and support rows from it. kernel is
+    one of "gaussian", "laplacian", "linear" or "poly". param is kappa for the
+    Gaussian kernel and sigma for the Laplacian kernel.
+    """
+
+    def __init__(self, X, k: int, b: int, kernel: str = "gaussian", param: float = 1.0,
+                 coef0: float = 0.0, degree: int = 2, tau: int = 200, lr: str = "beta",
+                 eta: float = 0.0, precision: str = "fp32", seed: int = 0, init_idx=None,
+                 max_iters: int = 0, stream=None):
+        import torch
+        if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float32 and X.dim() == 2):
+            raise TypeError("X must be a 2-D float32 CUDA tensor")
+        if X.stride(1) != 1:
+            raise ValueError("X rows must be contiguous")
+        self._torch = torch
+        self.X = X
+        self.n, self.d = X.shape
+        self.k, self.b = int(k), int(b)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(X.device)
+        kern = kkm_kernel(KERNELS[kernel], float(param), float(coef0), int(degree))
+        cfg = kkm_config(int(tau), KKM_LR_BETA if lr == "beta" else KKM_LR_CONST, float(eta),
+                         PRECISIONS[precision], int(max_iters), int(seed) & ((1 << 64) - 1))
+        with torch.cuda.device(X.device):
+            self.ctx = kkm_init(X.data_ptr(), self.n, self.d, X.stride(0), self.k, kern, self.b, cfg,
+                                None if init_idx is None else np.asarray(init_idx), self.stream.cuda_stream)
+
+    @staticmethod
+    def _ptr(t):
+        return None if t is None else t.data_ptr()
+
+    def step(self, batch_idx=None, forced_assign=None, assign_out=None, dist_out=None, obj_out=None):
+        """One iteration. Optional outputs are CUDA tensors the caller allocated."""
+        kkm_step(self.ctx, self._ptr(batch_idx), self._ptr(forced_assign), self._ptr(assign_out),
+                 self._ptr(dist_out), self._ptr(obj_out))
+
+    def step_host(self, batch_idx: np.ndarray | None = None):
+        """One iteration with host buffers; returns (assignments, f_B) as numpy / float."""
+        bi = None if batch_idx is None else np.ascontiguousarray(batch_idx, dtype=np.int32)
+        a = np.zeros(self.b, np.int32)
+        o = np.zeros(1, np.float64)
+        kkm_step_host(self.ctx, bi, a, o)
+        return a, float(o[0])
+
+    def assign(self, Q, want_dist: bool = False):
+        torch = self._torch
+        m = Q.shape[0]
+        a = torch.empty(m, dtype=torch.int32, device=Q.device)
+        md = torch.empty(m, dtype=torch.float32, device=Q.device)
+        dist = torch.empty((m, self.k), dtype=torch.float32, device=Q.device) if want_dist else None
+        kkm_assign(self.ctx, Q.data_ptr(), m, Q.stride(0), a.data_ptr(), md.data_ptr(), self._ptr(dist))
+        return a, md, dist
+
+    def objective(self, Q=None) -> float:
+        if Q is None:
+            return kkm_objective(self.ctx, None, 0, 0)
+        return kkm_objective(self.ctx, Q.data_ptr(), Q.shape[0], Q.stride(0))
+
+    def sync(self):
+        kkm_sync(self.ctx)
+
+    def get_state(self) -> dict:
+        return kkm_get_state(self.ctx, self.k)
+
+    def set_state(self, state: dict):
+        kkm_set_state(self.ctx, state)
+
+    def stats(self, reset: bool = False):
+        return kkm_stats(self.ctx, reset)
+
+    def timing(self, enable: bool):
+        kkm_timing_enable(self.ctx, enable)
+
+    def timing_read(self, reset: bool = False):
+        return kkm_timing_read(self.ctx, reset)
+
+    def launches(self, reset: bool = False) -> int:
+        return kkm_launches(self.ctx, reset)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            kkm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

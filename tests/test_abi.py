@@ -1,0 +1,96 @@
+"""C-ABI checks that need no GPU.
+
+libkkm.so builds with nvcc (it cross-compiles without a GPU) and loads. It
+exports every function include/kkm.h declares, and it rejects invalid
+arguments on the host before any CUDA call. No compute call is made here.
+"""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+from paper_2410_05902_gb300 import build as kbuild
+from paper_2410_05902_gb300 import kkm
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "kkm.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    path = kbuild.build()
+    return kkm.load(path)
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:kkm_status|int32_t|const char\*)\s+(kkm_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("kkm_init", "kkm_step", "kkm_assign", "kkm_objective", "kkm_destroy"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared in kkm.h but not exported"
+
+
+def test_version(lib):
+    assert lib.kkm_version() == 1
+
+
+def _init(lib, **over):
+    args = dict(X=ctypes.c_void_p(0x1000), n=100, d=8, ldx=8, k=4, b=32)
+    args.update(over)
+    kern = over.pop("kernel", kkm.kkm_kernel(kkm.KKM_GAUSSIAN, 2.0, 0.0, 2))
+    cfg = over.pop("cfg", kkm.kkm_config(50, kkm.KKM_LR_BETA, 0.0, kkm.KKM_PREC_FP32, 0, 7))
+    ctx = ctypes.c_void_p()
+    st = lib.kkm_init(ctypes.byref(ctx), args["X"], args["n"], args["d"], args["ldx"], args["k"],
+                      ctypes.byref(args.get("kernel", kern)), args["b"],
+                      ctypes.byref(args.get("cfg", cfg)), None, None)
+    return st, ctx
+
+
+@pytest.mark.parametrize("over,needle", [
+    (dict(n=0), "n must be"),
+    (dict(d=0), "d must be"),
+    (dict(ldx=4), "ldx"),
+    (dict(k=0), "k must be"),
+    (dict(k=200), "k must be"),
+    (dict(b=0), "b must be"),
+    (dict(X=None), "required"),
+    (dict(kernel=kkm.kkm_kernel(kkm.KKM_GAUSSIAN, -1.0, 0.0, 2)), "kernel param"),
+    (dict(kernel=kkm.kkm_kernel(9, 1.0, 0.0, 2)), "unknown kernel"),
+    (dict(kernel=kkm.kkm_kernel(kkm.KKM_POLY, 1.0, 0.0, 0)), "degree"),
+    (dict(cfg=kkm.kkm_config(50, 7, 0.0, 0, 0, 0)), "learning rate"),
+    (dict(cfg=kkm.kkm_config(50, kkm.KKM_LR_CONST, 1.5, 0, 0, 0)), "eta"),
+    (dict(cfg=kkm.kkm_config(50, 0, 0.0, 9, 0, 0)), "precision"),
+    (dict(cfg=kkm.kkm_config(0, 0, 0.0, 0, 0, 0)), "max_iters"),
+])
+def test_init_rejects_invalid_arguments_on_host(lib, over, needle):
+    st, ctx = _init(lib, **over)
+    assert st == kkm.KKM_EINVAL
+    assert not ctx.value
+    assert needle in lib.kkm_last_error(None).decode()
+
+
+def test_null_context_calls(lib):
+    assert lib.kkm_destroy(None) == kkm.KKM_OK
+    assert lib.kkm_step(None, None, None, None, None, None) == kkm.KKM_EINVAL
+    assert lib.kkm_sync(None) == kkm.KKM_EINVAL
+    out = ctypes.c_double()
+    assert lib.kkm_objective(None, None, 0, 0, ctypes.byref(out)) == kkm.KKM_EINVAL
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    with pytest.raises(RuntimeError, match="not built"):
+        kkm.load(str(tmp_path / "missing.so"))

@@ -1,0 +1,202 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle.
+
+Protocols:
+  teacher-forced   the oracle's state is loaded into the GPU (kkm_set_state),
+                   both take one step on the same batch with the GPU forced to
+                   the oracle's assignment, and every output is compared:
+                   distances, argmin, f_B, counts, and the new windows,
+                   weights and center norms.
+  free-running     both run from the same initial centers on the same batch
+                   stream. f_B and the assignments are compared every
+                   iteration until a certified near-tie legitimately flips an
+                   assignment.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_05902_gb300 import inputs
+from gpu_helpers import DIST_TOL, OBJ_TOL, Pair, compare_states, dist_rel_err, near_tie_ok, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def small_data(n=2000, d=16, c=10, seed=12345):
+    X, _ = inputs.isotropic_mixture(n, d, c, seed=seed)
+    return X
+
+
+def teacher_forced(pair, batches, w_rtol=1e-12, cn_rtol=1e-6, check_assign=True):
+    tol = DIST_TOL[pair.precision]
+    worst = 0.0
+    for B in batches:
+        ora_state = pair.ora.state()
+        pair.gpu.set_state(ora_state)
+        rec = pair.ora.step(B)
+        d, a, f = pair.gpu_step(B, forced=rec.assign)
+        err = dist_rel_err(d, rec.dist)
+        worst = max(worst, err)
+        assert err <= tol, f"iteration {rec.iteration}: distance rel err {err:.3e} > {tol}"
+        if check_assign:
+            ok, nbad = near_tie_ok(a, rec, pair.abs_tol(rec))
+            assert ok, f"iteration {rec.iteration}: {nbad} assignments differ outside near-ties"
+        assert abs(f - rec.batch_objective) <= OBJ_TOL * abs(rec.batch_objective) + 1e-12
+        compare_states(pair.gpu.get_state(), pair.ora.state(), w_rtol=w_rtol, cn_rtol=cn_rtol)
+    return worst
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3", "bf16"])
+def test_teacher_forced_small(precision):
+    X = small_data()
+    p = Pair(X, k=10, b=256, tau=200, precision=precision)
+    batches = inputs.batch_stream(len(X), 256, 12, seed=21)
+    cn_rtol = 1e-6 if precision != "bf16" else 5e-3
+    teacher_forced(p, batches, cn_rtol=cn_rtol)
+    p.close()
+
+
+def test_free_running_small_fp32():
+    """50 iterations of the small mixture (n=2000, d=16, k=10, b=256, tau=200)."""
+    X = small_data()
+    p = Pair(X, k=10, b=256, tau=200, precision="fp32")
+    batches = inputs.batch_stream(len(X), 256, 50, seed=22)
+    for B in batches:
+        rec = p.ora.step(B)
+        d, a, f = p.gpu_step(B)
+        assert dist_rel_err(d, rec.dist) <= DIST_TOL["fp32"]
+        assert abs(f - rec.batch_objective) <= OBJ_TOL * rec.batch_objective
+        if not np.array_equal(a, rec.assign):
+            ok, _ = near_tie_ok(a, rec, p.abs_tol(rec))
+            assert ok
+            break                       # a certified tie flipped: trajectories may diverge now
+    compare_states(p.gpu.get_state(), p.ora.state())
+    p.close()
+
+
+def test_builtin_sampler_is_splitmix64():
+    X = small_data(n=3000, d=8, c=4)
+    p = Pair(X, k=4, b=300, tau=0, max_iters=3, seed=987654321)
+    for it in (1, 2):
+        B = oracle.batch_indices(987654321, it, 300, len(X))
+        rec = p.ora.step(B)
+        p.gpu.step(None, None, p.assign, p.dist, p.obj)
+        p.torch.cuda.synchronize()
+        np.testing.assert_array_equal(p.assign.cpu().numpy(), rec.assign)
+    compare_states(p.gpu.get_state(), p.ora.state())   # row_idx carries the sampled indices
+    p.close()
+
+
+@pytest.mark.parametrize("kernel,extra", [
+    ("laplacian", {}),
+    ("linear", {}),
+    ("poly", {"coef0": 1.0, "degree": 2}),
+])
+def test_other_kernels_teacher_forced(kernel, extra):
+    rng = np.random.default_rng(4)
+    X = small_data(n=600, d=12, c=5)
+    if kernel in ("linear", "poly"):
+        X = (X / 4.0).astype(np.float32)          # keep polynomial values moderate
+    param = 1.0 if kernel in ("linear", "poly") else None
+    p = Pair(X, k=5, b=96, kernel=kernel, param=param, tau=60, **extra)
+    batches = inputs.batch_stream(len(X), 96, 8, seed=int(rng.integers(1 << 30)))
+    teacher_forced(p, batches, cn_rtol=1e-5)
+    p.close()
+
+
+@pytest.mark.parametrize("n,d,k,b,tau", [
+    (500, 13, 3, 77, 50),     # ragged d (not a multiple of 16/64) and b (not a multiple of 64/128)
+    (400, 70, 1, 64, 30),     # a single center
+    (300, 5, 7, 33, 1),       # tau = 1: only the newest block survives
+    (300, 9, 4, 200, 500),    # tau larger than anything reached: no truncation
+    (2500, 3, 12, 1000, 64),  # many centers, large batch, tiny d
+])
+def test_edge_shapes_teacher_forced(n, d, k, b, tau):
+    X = small_data(n=n, d=d, c=max(k, 2))
+    p = Pair(X, k=k, b=b, tau=tau)
+    batches = inputs.batch_stream(n, b, 6, seed=n + d)
+    teacher_forced(p, batches)
+    p.close()
+
+
+def test_untruncated_algorithm1():
+    X = small_data(n=800, d=10, c=4)
+    p = Pair(X, k=4, b=64, tau=0, max_iters=10)
+    teacher_forced(p, inputs.batch_stream(len(X), 64, 10, seed=5))
+    for j in range(4):                    # Algorithm 1 keeps C_1 and every block
+        assert p.ora.center(j).c1_kept
+    p.close()
+
+
+def test_full_rate_and_empty_clusters():
+    """Every point forced into center 0: alpha_0 = 1 erases the old center and the
+    other centers, being empty, must not change (alpha = 0)."""
+    X = small_data(n=500, d=6, c=3)
+    p = Pair(X, k=3, b=50, tau=20)
+    B = inputs.batch_stream(len(X), 50, 1, seed=9)[0]
+    p.gpu.set_state(p.ora.state())
+    forced = np.zeros(50, dtype=np.int64)
+    rec = p.ora.step(B, forced_assign=forced)
+    p.gpu_step(B, forced=forced)
+    compare_states(p.gpu.get_state(), p.ora.state())
+    assert rec.alpha[0] == 1.0 and np.all(rec.alpha[1:] == 0.0)
+    p.close()
+
+
+def test_duplicate_batch_rows_and_const_rate():
+    X = small_data(n=50, d=4, c=2)
+    p = Pair(X, k=2, b=40, tau=25, lr="const", eta=0.5)
+    batches = inputs.batch_stream(len(X), 40, 6, seed=2)   # 40 draws from 50 points repeat
+    teacher_forced(p, batches)
+    p.close()
+
+
+def test_assign_and_objective_queries():
+    X = small_data(n=1500, d=16, c=6)
+    p = Pair(X, k=6, b=128, tau=100)
+    for B in inputs.batch_stream(len(X), 128, 5, seed=31):
+        p.ora.step(B)
+        p.gpu_step(B)
+    p.gpu.set_state(p.ora.state())
+    torch = p.torch
+    Q = torch.from_numpy(X[:700]).cuda()
+    a, md, dist = p.gpu.assign(Q, want_dist=True)
+    ref = p.ora.distances(X[:700].astype(np.float64))
+    assert dist_rel_err(dist.cpu().numpy(), ref) <= DIST_TOL["fp32"]
+    order = np.sort(ref, 1)
+    bad = np.nonzero(a.cpu().numpy() != ref.argmin(1))[0]
+    assert np.all(order[bad, 1] - order[bad, 0] <= 1e-5 * 4)
+    np.testing.assert_allclose(md.cpu().numpy(), ref.min(1), rtol=1e-5, atol=1e-6)
+    f_gpu = p.gpu.objective()
+    f_ref = p.ora.objective()
+    assert abs(f_gpu - f_ref) <= OBJ_TOL * f_ref
+    p.close()
+
+
+def test_image_like_full_size_first_iterations():
+    """The MNIST-shaped workload at full size (70000 x 784, k=10, b=1024, tau=200):
+    the first three iterations from the same start, on both sides."""
+    X, _ = inputs.image_like(70000, seed=12345)
+    p = Pair(X, k=10, b=1024, tau=200, precision="fp32")
+    for B in inputs.batch_stream(len(X), 1024, 3, seed=41):
+        rec = p.ora.step(B)
+        d, a, f = p.gpu_step(B)
+        assert dist_rel_err(d, rec.dist) <= DIST_TOL["fp32"]
+        ok, _ = near_tie_ok(a, rec, p.abs_tol(rec))
+        assert ok and np.array_equal(a, rec.assign)
+        assert abs(f - rec.batch_objective) <= OBJ_TOL * rec.batch_objective
+    compare_states(p.gpu.get_state(), p.ora.state())
+    p.close()
+
+
+def test_invalid_batch_index_poisons_context():
+    torch = torch_cuda()
+    from paper_2410_05902_gb300.kkm import KKMError
+    X = small_data(n=200, d=4, c=2)
+    p = Pair(X, k=2, b=16, tau=10)
+    bad = torch.full((16,), 10_000, dtype=torch.int32, device="cuda")   # rejected, never read
+    p.gpu.step(bad)
+    with pytest.raises(KKMError, match="KKM_EINVAL"):
+        p.gpu.sync()
+    with pytest.raises(KKMError, match="KKM_ESTATE"):
+        p.gpu.step(None)
+    p.close()
