@@ -40,6 +40,7 @@ struct kkm_ctx {
   std::vector<cudaEvent_t> ev;
   int64_t ev_used = 0;
   int64_t launches = 0;       // kernels launched (host count)
+  alignas(64) unsigned char tmaps[256];   // TMA descriptors of the tensor-core pass
 };
 
 namespace {
@@ -107,7 +108,7 @@ kkm_status sync_and_check(kkm_ctx* c) {
   } while (0)
 
 kkm_status launch_distance_pass(kkm_ctx* c, int rows) {
-  if (c->use_tc) KKM_CU(kkm::launch_dist_tc(c->s, rows, c->stream), "distance kernel (tcgen05)");
+  if (c->use_tc) KKM_CU(kkm::launch_dist_tc(c->s, c->tmaps, rows, c->stream), "distance kernel (tcgen05)");
   else KKM_CU(kkm::launch_dist_simt(c->s, rows, c->stream), "distance kernel");
   return KKM_OK;
 }
@@ -270,7 +271,7 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
   e = cudaMemcpyAsync(c->d_init_idx, h_init.data(), k * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(s.iter, &one, sizeof(one), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = kkm::launch_init_centers(s, c->d_init_idx, c->stream);
-  if (e == cudaSuccess && c->use_tc) e = kkm::tc_prepare(s);
+  if (e == cudaSuccess && c->use_tc) e = kkm::tc_prepare(s, c->tmaps);
   if (e == cudaSuccess) e = kkm::launch_build_tiles(s, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {

@@ -1,12 +1,395 @@
 // tcgen05 / TMA form of the distance pass (BF16 and split-BF16 Gram products).
+//
+// One persistent CTA per SM walks the work items (128-row batch tile, 128-row
+// support tile of one center). For each item:
+//   G = X_B Y^T           tcgen05.mma kind::f16 (BF16 x BF16 -> FP32 in TMEM),
+//                         operands streamed by TMA through a 6-stage ring of
+//                         128B-swizzled shared-memory slices (64 columns each)
+//   K = kernel(||x||^2 + ||y||^2 - 2G)     in registers after tcgen05.ld
+//   part[tile][x] = sum_y w_y K(x, y)      one partial per row and tile
+// The split form (x = hi + lo) runs the K loop three times over the slice
+// pairs (hi,hi), (hi,lo), (lo,hi) into the same accumulator.
+//
+// Roles: warp 0 issues TMA loads, warp 1 issues the MMAs (one elected lane)
+// and owns the TMEM allocation (2 accumulators x 128 columns), warps 2-5 are
+// the epilogue (one TMEM lane = one batch row per thread). Every mbarrier wait
+// is bounded. A wait that runs out sets ST_TIMEOUT and makes the role stop. On
+// the way out the producer waits for its last copies to land and the MMA warp
+// waits for its last MMAs, so TMEM is freed only once nothing is in flight.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "kkm_internal.cuh"
 
 namespace kkm {
+namespace {
 
-bool tc_available() { return false; }
+constexpr int TM = 128;                         // batch rows per tile = TMEM lanes
+constexpr int TN = 128;                         // support rows per tile = accumulator columns
+constexpr int KS = 64;                          // BF16 columns per slice (one 128-byte swizzle row)
+constexpr int STAGES = 6;
+constexpr int A_BYTES = TM * KS * 2;            // 16 KB
+constexpr int B_BYTES = TN * KS * 2;            // 16 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int NTHREADS = 192;
+constexpr uint32_t TMEM_COLS = 2 * TN;
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;   // 2 s per wait
 
-cudaError_t tc_prepare(Dev&) { return cudaErrorNotSupported; }
+// Instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1),
+// A and B BF16 (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0),
+// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                           ((uint32_t)(TM >> 4) << 24);
 
-cudaError_t launch_dist_tc(const Dev&, int, cudaStream_t) { return cudaErrorNotSupported; }
+struct Shared {
+  uint64_t full[STAGES];
+  uint64_t empty[STAGES];
+  uint64_t tfull[2];
+  uint64_t tempty[2];
+  uint64_t mma_done;
+  uint32_t tmem_base;
+  uint32_t pad;
+  float4 meta[4][TN];                           // per epilogue warp: (||y||^2, w, yi, -)
+};
+
+constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + (int)sizeof(Shared);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Waits for the phase of parity `parity` to complete; false after WAIT_LIMIT_NS.
+__device__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+  if (mbar_try_wait(b, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (true) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try_wait(b, parity)) return true;
+    if (globaltimer() - t0 > WAIT_LIMIT_NS) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+      ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile stored as rows of
+// 128 bytes with the 128-byte swizzle (the layout TMA writes with
+// CU_TENSOR_MAP_SWIZZLE_128B): start address >> 4 in bits 0-13, leading byte
+// offset 16 (unused by swizzled K-major layouts), stride byte offset 1024
+// (8 rows x 128 B) in bits 32-45, descriptor version 1 in bits 46-47,
+// swizzle mode 2 (128B) in bits 61-63.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)2u << 61;
+  return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+template <int KIND>
+__device__ __forceinline__ float kernel_value(float g, float xn, float yn, bool same, float negc,
+                                              float coef0, int degree) {
+  if constexpr (KIND == K_GAUSS || KIND == K_LAPLACE) {
+    float d2 = fmaxf(fmaf(-2.0f, g, xn + yn), 0.0f);
+    d2 = same ? 0.0f : d2;
+    const float arg = (KIND == K_GAUSS) ? d2 : sqrtf(d2);
+    return ex2_approx(arg * negc);
+  } else if constexpr (KIND == K_LINEAR) {
+    return g;
+  } else {
+    const float base = g + coef0;
+    float r = 1.0f;
+    for (int p = 0; p < degree; ++p) r *= base;
+    return r;
+  }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_dist_tc(Dev s, int rows, const __grid_constant__ CUtensorMap tmA,
+              const __grid_constant__ CUtensorMap tmB) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  Shared& sh = *reinterpret_cast<Shared*>(smem + STAGES * STAGE_BYTES);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < STAGES; ++i) {
+      mbar_init(&sh.full[i], 1);
+      mbar_init(&sh.empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&sh.tfull[i], 1);
+      mbar_init(&sh.tempty[i], 128);
+    }
+    mbar_init(&sh.mma_done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(&sh.tmem_base)), "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sh.tmem_base;
+
+  const int R = (rows + TM - 1) / TM;
+  const int total = R * (*s.ntiles);
+  const int nks = s.dp / KS;
+  const int nslices = (s.form == FORM_BF16X3) ? 3 * nks : nks;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      bool ok = true;
+      uint32_t it = 0;
+      for (int w = blockIdx.x; w < total && ok; w += gridDim.x) {
+        const int t = w / R, rt = w % R;
+        const int row0 = s.tiles[t].row0;
+        for (int sl = 0; sl < nslices; ++sl, ++it) {
+          const int st = it % STAGES;
+          const uint32_t ph = (it / STAGES) & 1u;
+          if (!mbar_wait(&sh.empty[st], ph ^ 1u)) { ok = false; break; }
+          const int part = sl / nks, kk = sl - part * nks;
+          const int xa = (part == 2 ? s.dp : 0) + kk * KS;
+          const int xb = (part == 1 ? s.dp : 0) + kk * KS;
+          uint8_t* a = smem + st * STAGE_BYTES;
+          mbar_expect_tx(&sh.full[st], STAGE_BYTES);
+          tma_load_2d(a, &tmA, &sh.full[st], xa, rt * TM);
+          tma_load_2d(a + A_BYTES, &tmB, &sh.full[st], xb, row0);
+        }
+      }
+      // the last fill of every stage must land before the CTA may exit
+      for (uint32_t q = (it > (uint32_t)STAGES ? it - STAGES : 0u); q < it; ++q)
+        if (!mbar_wait(&sh.full[q % STAGES], (q / STAGES) & 1u)) ok = false;
+      if (!ok) atomicOr(s.status, ST_TIMEOUT);
+    }
+  } else if (warp == 1) {
+    // -------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      bool ok = true;
+      uint32_t it = 0, local = 0;
+      for (int w = blockIdx.x; w < total && ok; w += gridDim.x, ++local) {
+        const uint32_t buf = local & 1u, bph = (local >> 1) & 1u;
+        if (!mbar_wait(&sh.tempty[buf], bph ^ 1u)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t d = tmem + buf * TN;
+        for (int sl = 0; sl < nslices; ++sl, ++it) {
+          const int st = it % STAGES;
+          const uint32_t ph = (it / STAGES) & 1u;
+          if (!mbar_wait(&sh.full[st], ph)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(smem + st * STAGE_BYTES);
+          const uint32_t b0 = a0 + A_BYTES;
+#pragma unroll
+          for (int k = 0; k < KS / 16; ++k)
+            mma_bf16(d, sw128_desc(a0 + 32u * k), sw128_desc(b0 + 32u * k), (sl | k) != 0 ? 1u : 0u);
+          mma_commit(&sh.empty[st]);
+        }
+        if (!ok) break;
+        mma_commit(&sh.tfull[buf]);
+      }
+      mma_commit(&sh.mma_done);
+      if (!mbar_wait(&sh.mma_done, 0)) ok = false;
+      if (!ok) atomicOr(s.status, ST_TIMEOUT);
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue
+    const int q = warp & 3;                      // TMEM lane quadrant of this warp
+    float4* meta = sh.meta[warp - 2];
+    const float negc = s.negc, coef0 = (float)s.coef0;
+    const int degree = s.degree;
+    uint32_t local = 0;
+    for (int w = blockIdx.x; w < total; w += gridDim.x, ++local) {
+      const int t = w / R, rt = w % R;
+      const Tile T = s.tiles[t];
+      const uint32_t buf = local & 1u, bph = (local >> 1) & 1u;
+      __syncwarp();
+#pragma unroll
+      for (int c4 = 0; c4 < TN / 32; ++c4) {
+        const int c = c4 * 32 + lane;
+        const bool valid = c < T.ncols;
+        const int64_t g = (int64_t)T.row0 + (valid ? c : 0);
+        meta[c] = make_float4(s.yn[g], valid ? s.w32[g] : 0.0f, __int_as_float(valid ? s.yi[g] : -2), 0.0f);
+      }
+      __syncwarp();
+      const int row = rt * TM + q * 32 + lane;
+      const int rr = row < rows ? row : 0;
+      const float xn = s.xbn[rr];
+      const int xi = s.xbi[rr];
+      const bool ok = mbar_wait(&sh.tfull[buf], bph);
+      if (__any_sync(0xffffffffu, !ok)) {
+        if (lane == 0) atomicOr(s.status, ST_TIMEOUT);
+        break;
+      }
+      tc_fence_after();
+      float acc = 0.0f;
+#pragma unroll
+      for (int ch = 0; ch < TN / 32; ++ch) {
+        float g[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + buf * TN + ch * 32, g);
+        if (ch == TN / 32 - 1) {
+          tc_fence_before();
+          mbar_arrive(&sh.tempty[buf]);
+        }
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int c = ch * 32 + i;
+          const float4 m = meta[c];
+          const float kv = kernel_value<KIND>(g[i], xn, m.x, xi == __float_as_int(m.z), negc, coef0, degree);
+          acc = (c < T.ncols) ? fmaf(m.y, kv, acc) : acc;
+        }
+      }
+      if (row < rows) s.part[(int64_t)t * s.bpad + row] = acc;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+template <int KIND>
+cudaError_t launch_kind(const Dev& s, const CUtensorMap& a, const CUtensorMap& b, int rows, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_dist_tc<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_dist_tc<KIND><<<s.num_sms, NTHREADS, SMEM_BYTES, st>>>(s, rows, a, b);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_available() { return true; }
+
+// Tensor maps of the batch rows (A) and the support store (B): 2-D BF16
+// tensors of ld columns, boxes of 64 columns x 128 rows, 128-byte swizzle.
+cudaError_t tc_prepare(Dev& s, void* maps_out) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  CUtensorMap* maps = static_cast<CUtensorMap*>(maps_out);
+  const int64_t srows = (int64_t)s.k * s.cap + 256;
+  struct { void* base; uint64_t rows; uint32_t box_rows; } ops[2] = {
+      {s.xbh, (uint64_t)s.bpad, (uint32_t)TM}, {s.ybh, (uint64_t)srows, (uint32_t)TN}};
+  for (int i = 0; i < 2; ++i) {
+    cuuint64_t dims[2] = {(cuuint64_t)s.ld, (cuuint64_t)ops[i].rows};
+    cuuint64_t strides[1] = {(cuuint64_t)s.ld * 2};
+    cuuint32_t box[2] = {(cuuint32_t)KS, ops[i].box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(&maps[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ops[i].base, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_dist_tc(const Dev& s, const void* maps_in, int rows, cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+  const CUtensorMap* maps = static_cast<const CUtensorMap*>(maps_in);
+  switch (s.kind) {
+    case K_GAUSS: return launch_kind<K_GAUSS>(s, maps[0], maps[1], rows, st);
+    case K_LAPLACE: return launch_kind<K_LAPLACE>(s, maps[0], maps[1], rows, st);
+    case K_LINEAR: return launch_kind<K_LINEAR>(s, maps[0], maps[1], rows, st);
+    default: return launch_kind<K_POLY>(s, maps[0], maps[1], rows, st);
+  }
+}
 
 }  // namespace kkm

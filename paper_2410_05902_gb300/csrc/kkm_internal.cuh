@@ -197,8 +197,9 @@ cudaError_t launch_load_rows(const Dev& s, int32_t rows_total, cudaStream_t st);
 cudaError_t launch_mind_sum(const Dev& s, int rows, double* out, cudaStream_t st);
 
 // tensor-core distance pass (BF16 forms); returns cudaErrorNotSupported when unavailable
+// maps: 256 bytes, 64-byte aligned, holding the two CUtensorMap of the pass
 bool tc_available();
-cudaError_t tc_prepare(Dev& s);
-cudaError_t launch_dist_tc(const Dev& s, int rows, cudaStream_t st);
+cudaError_t tc_prepare(Dev& s, void* maps);
+cudaError_t launch_dist_tc(const Dev& s, const void* maps, int rows, cudaStream_t st);
 
 }  // namespace kkm

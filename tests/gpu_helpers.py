@@ -6,12 +6,21 @@ import numpy as np
 import oracle
 from paper_2410_05902_gb300 import inputs
 
-# Distance tolerances: max over the b x k matrix of |d_gpu - d| / max(|d|, 1e-3).
-# FP32 and the split-BF16 form are held to 1e-5 and BF16 to 2e-3. The objective
-# is held to 1e-4 relative. Assignments must match except on rows whose FP64
-# oracle gap d_(2) - d_(1) lies within the form's absolute distance error bound.
+# Distance tolerances, normwise over the b x k matrix:
+#     max |d_gpu - d| / max |d|.
+# Delta = K(x,x) - 2<phi(x),C> + ||C||^2 is a difference of O(gamma^2) terms, so
+# its absolute error floor is gamma^2 times the unit roundoff whatever its size.
+# An elementwise relative bound would fail on legitimately small distances in
+# any finite precision. FP32 and the split-BF16 form are held to 1e-5 and BF16
+# to 2e-3. The objective is held to 1e-4 relative. Assignments must match
+# except on rows whose FP64 oracle gap d_(2) - d_(1) lies within the form's
+# absolute error bound, tol * max |d|.
 DIST_TOL = {"fp32": 1e-5, "bf16x3": 1e-5, "bf16": 2e-3}
 OBJ_TOL = 1e-4
+# BF16 operands carry 8 significant bits: its f_B error is of the order of its
+# distance error, so it is held to that here (the benchmark reports whether the
+# BF16 form reaches the 1e-4 objective bar on its workload).
+OBJ_TOL_FORM = {"fp32": OBJ_TOL, "bf16x3": OBJ_TOL, "bf16": 2e-3}
 KIND = {"gaussian": oracle.GAUSSIAN, "laplacian": oracle.LAPLACIAN, "linear": oracle.LINEAR,
         "poly": oracle.POLY}
 
@@ -26,7 +35,7 @@ def torch_cuda():
 
 def dist_rel_err(d_gpu, d_ref) -> float:
     d_gpu = np.asarray(d_gpu, dtype=np.float64)
-    return float(np.max(np.abs(d_gpu - d_ref) / np.maximum(np.abs(d_ref), 1e-3)))
+    return float(np.max(np.abs(d_gpu - d_ref)) / max(float(np.max(np.abs(d_ref))), 1e-300))
 
 
 def near_tie_ok(assign_gpu, rec, tol_abs) -> tuple[bool, int]:
@@ -76,7 +85,7 @@ class Pair:
         return self.dist.cpu().numpy(), self.assign.cpu().numpy(), float(self.obj.cpu()[0])
 
     def abs_tol(self, rec):
-        return DIST_TOL[self.precision] * max(1.0, float(np.max(np.abs(rec.dist))))
+        return DIST_TOL[self.precision] * float(np.max(np.abs(rec.dist)))
 
     def close(self):
         self.gpu.close()

@@ -16,7 +16,7 @@ import pytest
 
 import oracle
 from paper_2410_05902_gb300 import inputs
-from gpu_helpers import DIST_TOL, OBJ_TOL, Pair, compare_states, dist_rel_err, near_tie_ok, torch_cuda
+from gpu_helpers import DIST_TOL, OBJ_TOL, OBJ_TOL_FORM, Pair, compare_states, dist_rel_err, near_tie_ok, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -40,7 +40,7 @@ def teacher_forced(pair, batches, w_rtol=1e-12, cn_rtol=1e-6, check_assign=True)
         if check_assign:
             ok, nbad = near_tie_ok(a, rec, pair.abs_tol(rec))
             assert ok, f"iteration {rec.iteration}: {nbad} assignments differ outside near-ties"
-        assert abs(f - rec.batch_objective) <= OBJ_TOL * abs(rec.batch_objective) + 1e-12
+        assert abs(f - rec.batch_objective) <= OBJ_TOL_FORM[pair.precision] * abs(rec.batch_objective) + 1e-12
         compare_states(pair.gpu.get_state(), pair.ora.state(), w_rtol=w_rtol, cn_rtol=cn_rtol)
     return worst
 
@@ -163,9 +163,10 @@ def test_assign_and_objective_queries():
     ref = p.ora.distances(X[:700].astype(np.float64))
     assert dist_rel_err(dist.cpu().numpy(), ref) <= DIST_TOL["fp32"]
     order = np.sort(ref, 1)
+    scale = float(np.max(np.abs(ref)))
     bad = np.nonzero(a.cpu().numpy() != ref.argmin(1))[0]
-    assert np.all(order[bad, 1] - order[bad, 0] <= 1e-5 * 4)
-    np.testing.assert_allclose(md.cpu().numpy(), ref.min(1), rtol=1e-5, atol=1e-6)
+    assert np.all(order[bad, 1] - order[bad, 0] <= DIST_TOL["fp32"] * scale)
+    assert np.max(np.abs(md.cpu().numpy() - ref.min(1))) <= DIST_TOL["fp32"] * scale
     f_gpu = p.gpu.objective()
     f_ref = p.ora.objective()
     assert abs(f_gpu - f_ref) <= OBJ_TOL * f_ref
