@@ -227,6 +227,56 @@ kkm_status kkm_timing_read(kkm_ctx* ctx, int64_t* launches, double* total_ms, in
  * the host at each launch) since kkm_init or the last reset. Host output. */
 kkm_status kkm_launches(kkm_ctx* ctx, int64_t* launches, int32_t reset);
 
+/* kkm_distances_noalloc -- distances and nearest centers with no allocation.
+ *
+ * The paper has no counterpart to this call. It exists for callers that
+ * cannot call cudaMalloc. One kind is a process whose device memory a
+ * framework's caching allocator or a pre-sized arena owns completely (a
+ * serving process that reserved the free memory at start-up). There, a stray
+ * cudaMalloc fails or fragments the reservation. The other kind is a loop on a
+ * latency-critical path, where cudaMalloc and cudaFree can synchronise the
+ * device. Such a caller keeps its centers itself, as weighted support rows in
+ * the window layout that kkm_get_state exports. The call needs no context.
+ *
+ * It computes Delta(q, C_j) = K(q,q) - 2 sum_s w_s K(q, y_s) + ||C_j||^2 for
+ * every query row q and center j, in FP32 arithmetic with FP64 combination,
+ * and the argmin over j (ties go to the lowest j).
+ *   Q        : device, m x d FP32, leading dimension ldq >= d; m >= 0
+ *   Y        : device, S x d FP32 support rows, leading dimension ldy >= d
+ *   w        : device, S FP32 weights
+ *   seg_off  : device, k + 1 int32 offsets. Center j owns the rows
+ *              [seg_off[j], seg_off[j+1]) of Y. The offsets must be
+ *              non-decreasing from 0 to S; values outside [0, S] are clamped.
+ *   cnorm    : device, k doubles, ||C_j||^2
+ *   kernel   : host, as in kkm_init
+ *   dist_out : device, m x k FP32 row-major, or NULL
+ *   assign_out: device, m int32, or NULL
+ *   stream   : cudaStream_t, NULL for the legacy default stream
+ * Limits: k <= 1024, d <= 4096, S <= KKM_NOALLOC_MAX_SUPPORT and
+ * ceil(S / 64) + k <= KKM_NOALLOC_MAX_TILES. Larger sizes are rejected with
+ * KKM_EINVAL before any work is queued. Query rows go through in passes of
+ * KKM_NOALLOC_MAX_ROWS_PER_PASS.
+ *
+ * Memory: the only scratch is one fixed array of KKM_NOALLOC_SCRATCH_BYTES
+ * inside the library. It is device memory that every GPU loading the library
+ * holds until the process exits. The call never allocates or frees, neither
+ * directly nor through a library. The first call on each device, with that
+ * device current, looks up the array's address (cudaGetSymbolAddress). Make
+ * that first call before any stream capture. Every call shares the array:
+ * calls whose work overlaps on the GPU (two streams with no ordering between
+ * them) race on it, while calls queued one after another on one stream are
+ * safe. The call only queues work on `stream`. Errors are reported through
+ * kkm_noalloc_last_error(), a per-thread message. */
+#define KKM_NOALLOC_MAX_ROWS_PER_PASS 1024
+#define KKM_NOALLOC_MAX_TILES 1024
+#define KKM_NOALLOC_MAX_SUPPORT 65536
+#define KKM_NOALLOC_SCRATCH_BYTES (4718592) /* 4.5 MiB */
+kkm_status kkm_distances_noalloc(const float* Q, int64_t m, int64_t ldq, int32_t d, const float* Y,
+                                 int64_t S, int64_t ldy, const float* w, const int32_t* seg_off,
+                                 const double* cnorm, int32_t k, const kkm_kernel* kernel,
+                                 float* dist_out, int32_t* assign_out, void* stream);
+const char* kkm_noalloc_last_error(void);
+
 /* Frees everything the context allocated. NULL is accepted. It synchronises first. */
 kkm_status kkm_destroy(kkm_ctx* ctx);
 

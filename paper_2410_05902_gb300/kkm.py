@@ -74,6 +74,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "kkm_timing_enable": ([_P, c_int32], c_int32),
         "kkm_timing_read": ([_P, POINTER(c_int64), POINTER(c_double), c_int32], c_int32),
         "kkm_launches": ([_P, POINTER(c_int64), c_int32], c_int32),
+        "kkm_distances_noalloc": ([_P, c_int64, c_int64, c_int32, _P, c_int64, c_int64, _P, _P, _P,
+                                   c_int32, POINTER(kkm_kernel), _P, _P, _P], c_int32),
+        "kkm_noalloc_last_error": ([], ctypes.c_char_p),
         "kkm_destroy": ([_P], c_int32),
     }
     for name, (args, res) in sigs.items():
@@ -156,6 +159,17 @@ def kkm_launches(ctx, reset: bool = False) -> int:
     n = c_int64()
     _check(load().kkm_launches(ctx, ctypes.byref(n), int(reset)), ctx)
     return n.value
+
+
+def kkm_distances_noalloc(Q: int, m: int, ldq: int, d: int, Y: int, S: int, ldy: int, w: int,
+                          seg_off: int, cnorm: int, k: int, kernel: kkm_kernel, dist_out: int | None,
+                          assign_out: int | None, stream: int | None) -> None:
+    """Distances and argmin against caller-held centers, with no allocation (see kkm.h)."""
+    lib = load()
+    st = lib.kkm_distances_noalloc(Q, m, ldq, d, Y, S, ldy, w, seg_off, cnorm, k, ctypes.byref(kernel),
+                                   dist_out, assign_out, stream)
+    if st != KKM_OK:
+        raise KKMError(st, lib.kkm_noalloc_last_error().decode())
 
 
 def kkm_get_state(ctx, k: int) -> dict:
