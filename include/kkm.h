@@ -147,6 +147,14 @@ kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d, int64_t
 kkm_status kkm_step(kkm_ctx* ctx, const int32_t* batch_idx, const int32_t* forced_assign,
                     int32_t* assign_out, float* dist_out, double* batch_obj_out);
 
+/* kkm_graph_enable -- with enable != 0, kkm_step captures its kernel sequence
+ * in a CUDA graph and replays that graph. The graph is built once for each
+ * combination of kkm_step pointer arguments (rebuilt when they change) and
+ * launched on the context's stream. Replays give results identical to eager
+ * steps. Capture starts only after one eager step, and never while event
+ * timing is enabled. Reuse the same buffers to keep replaying one graph. */
+kkm_status kkm_graph_enable(kkm_ctx* ctx, int32_t enable);
+
 /* kkm_step_host -- kkm_step with host buffers, for callers that keep the
  * batch on the CPU. It copies the b indices in (batch_idx may be NULL for the
  * built-in sampler), runs the step, copies the assignments and f_{B_i}(C_i)

@@ -41,6 +41,13 @@ struct kkm_ctx {
   int64_t ev_used = 0;
   int64_t launches = 0;       // kernels launched (host count)
   alignas(64) unsigned char tmaps[256];   // TMA descriptors of the tensor-core pass
+  // CUDA graph of one step (kkm_graph_enable): captured on a private stream
+  // per set of kkm_step pointer arguments and launched on `stream`
+  bool graph_on = false;
+  int64_t eager_steps = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const void* gkey[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -69,6 +76,10 @@ cudaError_t dalloc(kkm_ctx* c, T** p, size_t count) {
 }
 
 void free_all(kkm_ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  c->cap_stream = nullptr;
   for (void* p : c->allocs) cudaFree(p);
   c->allocs.clear();
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -186,6 +197,7 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
   s.form = cfg->precision;
   s.kind = kernel->kind; s.degree = kernel->degree; s.lr = cfg->lr;
   s.param = kernel->param; s.coef0 = kernel->coef0; s.eta = cfg->eta;
+  s.inv_b = 1.0 / (double)b;
   s.negc = (kernel->kind == KKM_GAUSSIAN || kernel->kind == KKM_LAPLACIAN)
                ? (float)(-1.4426950408889634 / kernel->param) : 0.0f;
   s.num_sms = sms > 0 ? sms : 148;
@@ -203,7 +215,8 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
     c->use_tc = (maj == 10 && min == 3) && kkm::tc_available();
   }
   s.tn = c->use_tc ? 128 : 64;
-  const int64_t T = 64;   // window-pass tile
+  s.pair_tile = c->use_tc ? 128 : 64;
+  const int64_t T = s.pair_tile;   // window-pass tile
   s.max_tiles = (int32_t)((int64_t)k * ((wmax + s.tn - 1) / s.tn + 1));
   const int64_t smax = (int64_t)k * wmax;
   const int64_t p1 = ((smax + T - 1) / T + k) * ((wmax + b + T - 1) / T);
@@ -236,15 +249,16 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
   ALLOC(s.w64, srows);
   ALLOC(s.w32, srows);
   ALLOC(s.head, k); ALLOC(s.tail, k); ALLOC(s.c1, k); ALLOC(s.wsum, k); ALLOC(s.cnorm, k);
+  ALLOC(s.cnorm32, k); ALLOC(s.done_ctr, 1); ALLOC(s.objpart, k);
   ALLOC(s.blk_iter, (size_t)k * s.nbcap); ALLOC(s.blk_cnt, (size_t)k * s.nbcap);
   ALLOC(s.blk_first, k); ALLOC(s.blk_num, k);
   ALLOC(s.assign, s.bpad); ALLOC(s.mind, s.bpad); ALLOC(s.inner_a, s.bpad);
   ALLOC(s.counts, k); ALLOC(s.alpha, k); ALLOC(s.coff, k + 1); ALLOC(s.perm, s.bpad);
-  ALLOC(s.cmc, k); ALLOC(s.plan, k);
+  ALLOC(s.cmc, k); ALLOC(s.plan, k); ALLOC(s.comp_off, k); ALLOC(s.comp_total, 1);
   ALLOC(s.tiles, s.max_tiles); ALLOC(s.ntiles, 1); ALLOC(s.tile_first, k); ALLOC(s.tile_cnt, k);
   ALLOC(s.part, (size_t)s.max_tiles * s.bpad);
   ALLOC(s.wpairs, s.max_pairs); ALLOC(s.nwpairs, 1); ALLOC(s.wpair_first, k); ALLOC(s.wpair_cnt, k);
-  ALLOC(s.wpart, (size_t)s.max_pairs * 4);
+  ALLOC(s.wpart, (size_t)s.max_pairs * 16);
   ALLOC(s.iter, 1); ALLOC(s.status, 1); ALLOC(s.stats, 3); ALLOC(s.obj, 1); ALLOC(s.s_old, 1);
   ALLOC(c->d_init_idx, k);
   ALLOC(c->d_hbatch, b); ALLOC(c->d_hassign, b); ALLOC(c->d_hobj, 1);
@@ -288,36 +302,73 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
   return KKM_OK;
 }
 
+// The kernel sequence of one step, queued on `st`.
+static kkm_status enqueue_step(kkm_ctx* c, cudaStream_t st, const int32_t* batch_idx,
+                               const int32_t* forced_assign, int32_t* assign_out, float* dist_out,
+                               double* batch_obj_out, bool timed) {
+  const Dev& s = c->s;
+  // with batch_idx NULL the gather draws the indices itself (SplitMix64)
+  KKM_CU(kkm::launch_gather_batch(s, batch_idx, st), "batch gather");
+  if (timed) KKM_CU(cudaEventRecord(c->ev[2 * c->ev_used], st), "timing event");
+  if (c->use_tc) KKM_CU(kkm::launch_dist_tc(s, c->tmaps, s.b, st), "distance kernel (tcgen05)");
+  else KKM_CU(kkm::launch_dist_simt(s, s.b, st), "distance kernel");
+  if (timed) {
+    KKM_CU(cudaEventRecord(c->ev[2 * c->ev_used + 1], st), "timing event");
+    ++c->ev_used;
+  }
+  KKM_CU(kkm::launch_argmin(s, s.b, forced_assign, assign_out, nullptr, dist_out, true, st), "argmin");
+  KKM_CU(kkm::launch_sort_plan(s, st), "sort/plan");
+  KKM_CU(kkm::launch_move(s, st), "row moves");
+  if (c->use_tc) KKM_CU(kkm::launch_wgram_tc(s, c->tmaps, st), "window Gram (tcgen05)");
+  else KKM_CU(kkm::launch_wgram(s, st), "window Gram");
+  KKM_CU(kkm::launch_finalize(s, batch_obj_out, st), "finalize");
+  return KKM_OK;
+}
+
 KKM_API kkm_status kkm_step(kkm_ctx* c, const int32_t* batch_idx, const int32_t* forced_assign,
                             int32_t* assign_out, float* dist_out, double* batch_obj_out) {
   kkm_status st = check_usable(c);
   if (st != KKM_OK) return st;
   if (c->s.tau == 0 && c->iteration > c->max_iters)
     return fail(c, KKM_ESTATE, "untruncated run: max_iters iterations already done");
-  const Dev& s = c->s;
-  const int32_t* idx = batch_idx;
-  if (!idx) {
-    KKM_CU(kkm::launch_sample(s, c->stream), "batch sampler");
-    idx = s.bidx;
-    ++c->launches;
+  const bool timed = c->timing && c->ev_used < (int64_t)c->ev.size() / 2;
+  if (c->graph_on && !timed && c->eager_steps > 0) {
+    const void* key[5] = {batch_idx, forced_assign, assign_out, dist_out, batch_obj_out};
+    if (!c->gexec || std::memcmp(key, c->gkey, sizeof(key)) != 0) {
+      if (!c->cap_stream)
+        KKM_CU(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "capture stream");
+      KKM_CU(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+      st = enqueue_step(c, c->cap_stream, batch_idx, forced_assign, assign_out, dist_out, batch_obj_out, false);
+      cudaGraph_t g = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+      if (st != KKM_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+      }
+      if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+      cudaGraphExec_t ex = nullptr;
+      const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+      cudaGraphDestroy(g);
+      if (ei != cudaSuccess) return cuda_fail(c, ei, "graph instantiate");
+      if (c->gexec) cudaGraphExecDestroy(c->gexec);
+      c->gexec = ex;
+      std::memcpy(c->gkey, key, sizeof(key));
+    }
+    KKM_CU(cudaGraphLaunch(c->gexec, c->stream), "graph launch");
+  } else {
+    st = enqueue_step(c, c->stream, batch_idx, forced_assign, assign_out, dist_out, batch_obj_out, timed);
+    if (st != KKM_OK) return st;
+    ++c->eager_steps;
   }
-  KKM_CU(kkm::launch_gather_batch(s, idx, c->stream), "batch gather");
-  const bool rec = c->timing && c->ev_used < (int64_t)c->ev.size() / 2;
-  if (rec) KKM_CU(cudaEventRecord(c->ev[2 * c->ev_used], c->stream), "timing event");
-  st = launch_distance_pass(c, s.b);
-  if (st != KKM_OK) return st;
-  if (rec) {
-    KKM_CU(cudaEventRecord(c->ev[2 * c->ev_used + 1], c->stream), "timing event");
-    ++c->ev_used;
-  }
-  KKM_CU(kkm::launch_argmin(s, s.b, forced_assign, assign_out, nullptr, dist_out, true, c->stream),
-         "argmin");
-  KKM_CU(kkm::launch_sort_plan(s, c->stream), "sort/plan");
-  KKM_CU(kkm::launch_move(s, c->stream), "row moves");
-  KKM_CU(kkm::launch_wgram(s, c->stream), "window Gram");
-  KKM_CU(kkm::launch_finalize(s, batch_obj_out, c->stream), "finalize");
   c->launches += 7;   // gather, distance, argmin, sort/plan, moves, window Gram, finalize
   ++c->iteration;
+  return KKM_OK;
+}
+
+KKM_API kkm_status kkm_graph_enable(kkm_ctx* c, int32_t enable) {
+  kkm_status st = check_usable(c);
+  if (st != KKM_OK) return st;
+  c->graph_on = enable != 0;
   return KKM_OK;
 }
 

@@ -97,6 +97,7 @@ __device__ __forceinline__ float sum16(float v) {
 
 template <int F>
 __global__ void __launch_bounds__(NT) k_dist_simt(Dev s, int rows) {
+  KKM_GRID_DEP_WAIT();
   __shared__ __align__(16) float As[BK][BM + 4];
   __shared__ __align__(16) float Bs[BK][BN + 4];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -140,6 +141,7 @@ __global__ void __launch_bounds__(NT) k_dist_simt(Dev s, int rows) {
 
 template <int F>
 __global__ void __launch_bounds__(NT) k_wgram_simt(Dev s) {
+  KKM_GRID_DEP_WAIT();
   __shared__ __align__(16) float As[BK][BM + 4];
   __shared__ __align__(16) float Bs[BK][BN + 4];
   __shared__ double red[4][NT / 32];
@@ -197,10 +199,11 @@ __global__ void __launch_bounds__(NT) k_wgram_simt(Dev s) {
     }
     if (lane == 0) { red[0][warp] = sA; red[1][warp] = sB; red[2][warp] = sE; red[3][warp] = sM; }
     __syncthreads();
-    if (tid < 4) {
+    if (tid < 16) {   // slot 0 holds the tile's sums, slots 1-3 are zero
       double v = 0.0;
-      for (int q = 0; q < NT / 32; ++q) v += red[tid][q];
-      s.wpart[(int64_t)w * 4 + tid] = v;
+      if (tid < 4)
+        for (int q = 0; q < NT / 32; ++q) v += red[tid][q];
+      s.wpart[(int64_t)w * 16 + tid] = v;
     }
     __syncthreads();
   }
@@ -212,9 +215,9 @@ cudaError_t launch_dist_simt(const Dev& s, int rows, cudaStream_t st) {
   if (rows <= 0) return cudaSuccess;
   const int blocks = s.num_sms * 4;
   switch (s.form) {
-    case FORM_FP32: k_dist_simt<FORM_FP32><<<blocks, NT, 0, st>>>(s, rows); break;
-    case FORM_BF16: k_dist_simt<FORM_BF16><<<blocks, NT, 0, st>>>(s, rows); break;
-    default: k_dist_simt<FORM_BF16X3><<<blocks, NT, 0, st>>>(s, rows); break;
+    case FORM_FP32: return launch_pdl(k_dist_simt<FORM_FP32>, dim3(blocks), dim3(NT), 0, st, s, rows);
+    case FORM_BF16: return launch_pdl(k_dist_simt<FORM_BF16>, dim3(blocks), dim3(NT), 0, st, s, rows);
+    default: return launch_pdl(k_dist_simt<FORM_BF16X3>, dim3(blocks), dim3(NT), 0, st, s, rows);
   }
   return cudaGetLastError();
 }
@@ -222,9 +225,9 @@ cudaError_t launch_dist_simt(const Dev& s, int rows, cudaStream_t st) {
 cudaError_t launch_wgram(const Dev& s, cudaStream_t st) {
   const int blocks = s.num_sms * 4;
   switch (s.form) {
-    case FORM_FP32: k_wgram_simt<FORM_FP32><<<blocks, NT, 0, st>>>(s); break;
-    case FORM_BF16: k_wgram_simt<FORM_BF16><<<blocks, NT, 0, st>>>(s); break;
-    default: k_wgram_simt<FORM_BF16X3><<<blocks, NT, 0, st>>>(s); break;
+    case FORM_FP32: return launch_pdl(k_wgram_simt<FORM_FP32>, dim3(blocks), dim3(NT), 0, st, s);
+    case FORM_BF16: return launch_pdl(k_wgram_simt<FORM_BF16>, dim3(blocks), dim3(NT), 0, st, s);
+    default: return launch_pdl(k_wgram_simt<FORM_BF16X3>, dim3(blocks), dim3(NT), 0, st, s);
   }
   return cudaGetLastError();
 }

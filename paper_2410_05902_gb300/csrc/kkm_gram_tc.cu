@@ -27,10 +27,18 @@ namespace {
 constexpr int TM = 128;                         // batch rows per tile = TMEM lanes
 constexpr int TN = 128;                         // support rows per tile = accumulator columns
 constexpr int KS = 64;                          // BF16 columns per slice (one 128-byte swizzle row)
-constexpr int STAGES = 6;
-constexpr int A_BYTES = TM * KS * 2;            // 16 KB
+constexpr int A_BYTES = TM * KS * 2;            // 16 KB: one operand tile of one slice
 constexpr int B_BYTES = TN * KS * 2;            // 16 KB
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int RING_BYTES = 6 * (A_BYTES + B_BYTES);   // 192 KB of shared memory for the operand ring
+constexpr int STAGES = 6;                       // most stages any form uses
+// BF16:   a stage is one 64-column slice (A, B): 32 KB, 6 stages, 4 MMAs.
+// BF16X3: a stage is one 64-column slice of all four operand tiles
+//         (A_hi, A_lo, B_hi, B_lo): 64 KB, 3 stages, 12 MMAs (hi.hi, hi.lo, lo.hi),
+//         so hi tiles are fetched once per slice instead of twice.
+template <bool X3> struct Ring {
+  static constexpr int stages = X3 ? 3 : 6;
+  static constexpr int bytes = X3 ? 4 * A_BYTES : A_BYTES + B_BYTES;
+};
 constexpr int NTHREADS = 192;
 constexpr uint32_t TMEM_COLS = 2 * TN;
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;   // 2 s per wait
@@ -52,7 +60,7 @@ struct Shared {
   float4 meta[4][TN];                           // per epilogue warp: (||y||^2, w, yi, -)
 };
 
-constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + (int)sizeof(Shared);
+constexpr int SMEM_BYTES = 1024 + RING_BYTES + (int)sizeof(Shared);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -185,13 +193,45 @@ __device__ __forceinline__ float kernel_value(float g, float xn, float yn, bool 
   }
 }
 
-template <int KIND>
+// A window-pass tile (mode 1): rows of the support store of center j, as
+// positions inside its region. Kind 0 pairs the dropped prefix D with the old
+// window plus the new block; kind 1 pairs the new block with itself.
+struct PairTile {
+  int64_t base;      // first row of the center's region
+  int rs, rrem;      // first row position, rows left in the row range from rs
+  int cs, crem;      // first column position, rows left in the column range from cs
+  int kind, head_new, tail_c;
+};
+
+__device__ __forceinline__ PairTile pair_tile(const Dev& s, int w) {
+  const WPair pr = s.wpairs[w];
+  const Plan P = s.plan[pr.j];
+  PairTile t;
+  t.base = (int64_t)pr.j * s.cap;
+  int r0, rn, c0, cn;
+  if (pr.kind == 0) { r0 = P.head_c; rn = P.ndrop; c0 = P.head_c; cn = P.tail_new - P.head_c; }
+  else { r0 = P.tail_c; rn = P.cnt; c0 = P.tail_c; cn = P.cnt; }
+  t.rs = r0 + pr.rt * TM;
+  t.rrem = rn - pr.rt * TM;
+  t.cs = c0 + pr.ct * TN;
+  t.crem = cn - pr.ct * TN;
+  t.kind = pr.kind;
+  t.head_new = P.head_new;
+  t.tail_c = P.tail_c;
+  return t;
+}
+
+// MODE 0: distance pass (A = batch tile, B = support tile, one FP32 partial per row).
+// MODE 1: window pass (A and B = support rows of one center, four FP64 sums per warp).
+template <int KIND, int MODE, bool X3>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_dist_tc(Dev s, int rows, const __grid_constant__ CUtensorMap tmA,
               const __grid_constant__ CUtensorMap tmB) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  Shared& sh = *reinterpret_cast<Shared*>(smem + STAGES * STAGE_BYTES);
+  Shared& sh = *reinterpret_cast<Shared*>(smem + RING_BYTES);
+  constexpr int NST = Ring<X3>::stages;
+  constexpr int SB = Ring<X3>::bytes;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
@@ -216,11 +256,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = sh.tmem_base;
+  KKM_GRID_DEP_WAIT();   // everything above touches only this CTA's shared memory and TMEM
 
   const int R = (rows + TM - 1) / TM;
-  const int total = R * (*s.ntiles);
+  const int total = (MODE == 0) ? R * (*s.ntiles) : *s.nwpairs;
   const int nks = s.dp / KS;
-  const int nslices = (s.form == FORM_BF16X3) ? 3 * nks : nks;
+  const int nslices = nks;
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
@@ -228,24 +269,40 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       bool ok = true;
       uint32_t it = 0;
       for (int w = blockIdx.x; w < total && ok; w += gridDim.x) {
-        const int t = w / R, rt = w % R;
-        const int row0 = s.tiles[t].row0;
+        int ya, yb;
+        const CUtensorMap* am;
+        if constexpr (MODE == 0) {
+          const int t = w / R, rt = w % R;
+          ya = rt * TM;
+          yb = s.tiles[t].row0;
+          am = &tmA;
+        } else {
+          const PairTile pt = pair_tile(s, w);
+          ya = (int)(pt.base + pt.rs);
+          yb = (int)(pt.base + pt.cs);
+          am = &tmB;
+        }
         for (int sl = 0; sl < nslices; ++sl, ++it) {
-          const int st = it % STAGES;
-          const uint32_t ph = (it / STAGES) & 1u;
+          const int st = it % NST;
+          const uint32_t ph = (it / NST) & 1u;
           if (!mbar_wait(&sh.empty[st], ph ^ 1u)) { ok = false; break; }
-          const int part = sl / nks, kk = sl - part * nks;
-          const int xa = (part == 2 ? s.dp : 0) + kk * KS;
-          const int xb = (part == 1 ? s.dp : 0) + kk * KS;
-          uint8_t* a = smem + st * STAGE_BYTES;
-          mbar_expect_tx(&sh.full[st], STAGE_BYTES);
-          tma_load_2d(a, &tmA, &sh.full[st], xa, rt * TM);
-          tma_load_2d(a + A_BYTES, &tmB, &sh.full[st], xb, row0);
+          const int x = sl * KS;
+          uint8_t* a = smem + st * SB;
+          mbar_expect_tx(&sh.full[st], SB);
+          if constexpr (X3) {   // stage layout: A_hi | A_lo | B_hi | B_lo
+            tma_load_2d(a, am, &sh.full[st], x, ya);
+            tma_load_2d(a + A_BYTES, am, &sh.full[st], s.dp + x, ya);
+            tma_load_2d(a + 2 * A_BYTES, &tmB, &sh.full[st], x, yb);
+            tma_load_2d(a + 3 * A_BYTES, &tmB, &sh.full[st], s.dp + x, yb);
+          } else {              // stage layout: A | B
+            tma_load_2d(a, am, &sh.full[st], x, ya);
+            tma_load_2d(a + A_BYTES, &tmB, &sh.full[st], x, yb);
+          }
         }
       }
       // the last fill of every stage must land before the CTA may exit
-      for (uint32_t q = (it > (uint32_t)STAGES ? it - STAGES : 0u); q < it; ++q)
-        if (!mbar_wait(&sh.full[q % STAGES], (q / STAGES) & 1u)) ok = false;
+      for (uint32_t q = (it > (uint32_t)NST ? it - NST : 0u); q < it; ++q)
+        if (!mbar_wait(&sh.full[q % NST], (q / NST) & 1u)) ok = false;
       if (!ok) atomicOr(s.status, ST_TIMEOUT);
     }
   } else if (warp == 1) {
@@ -259,15 +316,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         tc_fence_after();
         const uint32_t d = tmem + buf * TN;
         for (int sl = 0; sl < nslices; ++sl, ++it) {
-          const int st = it % STAGES;
-          const uint32_t ph = (it / STAGES) & 1u;
+          const int st = it % NST;
+          const uint32_t ph = (it / NST) & 1u;
           if (!mbar_wait(&sh.full[st], ph)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t a0 = smem_u32(smem + st * STAGE_BYTES);
-          const uint32_t b0 = a0 + A_BYTES;
+          const uint32_t a0 = smem_u32(smem + st * SB);
+          if constexpr (X3) {
+            const uint32_t alo = a0 + A_BYTES, bhi = a0 + 2 * A_BYTES, blo = a0 + 3 * A_BYTES;
 #pragma unroll
-          for (int k = 0; k < KS / 16; ++k)
-            mma_bf16(d, sw128_desc(a0 + 32u * k), sw128_desc(b0 + 32u * k), (sl | k) != 0 ? 1u : 0u);
+            for (int k = 0; k < KS / 16; ++k) {
+              mma_bf16(d, sw128_desc(a0 + 32u * k), sw128_desc(bhi + 32u * k), (sl | k) != 0 ? 1u : 0u);
+              mma_bf16(d, sw128_desc(a0 + 32u * k), sw128_desc(blo + 32u * k), 1u);
+              mma_bf16(d, sw128_desc(alo + 32u * k), sw128_desc(bhi + 32u * k), 1u);
+            }
+          } else {
+            const uint32_t b0 = a0 + A_BYTES;
+#pragma unroll
+            for (int k = 0; k < KS / 16; ++k)
+              mma_bf16(d, sw128_desc(a0 + 32u * k), sw128_desc(b0 + 32u * k), (sl | k) != 0 ? 1u : 0u);
+          }
           mma_commit(&sh.empty[st]);
         }
         if (!ok) break;
@@ -284,47 +351,115 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const float negc = s.negc, coef0 = (float)s.coef0;
     const int degree = s.degree;
     uint32_t local = 0;
+    if constexpr (MODE == 0) {
     for (int w = blockIdx.x; w < total; w += gridDim.x, ++local) {
-      const int t = w / R, rt = w % R;
-      const Tile T = s.tiles[t];
-      const uint32_t buf = local & 1u, bph = (local >> 1) & 1u;
-      __syncwarp();
-#pragma unroll
-      for (int c4 = 0; c4 < TN / 32; ++c4) {
-        const int c = c4 * 32 + lane;
-        const bool valid = c < T.ncols;
-        const int64_t g = (int64_t)T.row0 + (valid ? c : 0);
-        meta[c] = make_float4(s.yn[g], valid ? s.w32[g] : 0.0f, __int_as_float(valid ? s.yi[g] : -2), 0.0f);
+        const int t = w / R, rt = w % R;
+        const Tile T = s.tiles[t];
+        const uint32_t buf = local & 1u, bph = (local >> 1) & 1u;
+        __syncwarp();
+  #pragma unroll
+        for (int c4 = 0; c4 < TN / 32; ++c4) {
+          const int c = c4 * 32 + lane;
+          const bool valid = c < T.ncols;
+          const int64_t g = (int64_t)T.row0 + (valid ? c : 0);
+          meta[c] = make_float4(s.yn[g], valid ? s.w32[g] : 0.0f, __int_as_float(valid ? s.yi[g] : -2), 0.0f);
+        }
+        __syncwarp();
+        const int row = rt * TM + q * 32 + lane;
+        const int rr = row < rows ? row : 0;
+        const float xn = s.xbn[rr];
+        const int xi = s.xbi[rr];
+        const bool ok = mbar_wait(&sh.tfull[buf], bph);
+        if (__any_sync(0xffffffffu, !ok)) {
+          if (lane == 0) atomicOr(s.status, ST_TIMEOUT);
+          break;
+        }
+        tc_fence_after();
+        float acc = 0.0f;
+  #pragma unroll
+        for (int ch = 0; ch < TN / 32; ++ch) {
+          float g[32];
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + buf * TN + ch * 32, g);
+          if (ch == TN / 32 - 1) {
+            tc_fence_before();
+            mbar_arrive(&sh.tempty[buf]);
+          }
+  #pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int c = ch * 32 + i;
+            const float4 m = meta[c];
+            const float kv = kernel_value<KIND>(g[i], xn, m.x, xi == __float_as_int(m.z), negc, coef0, degree);
+            acc = (c < T.ncols) ? fmaf(m.y, kv, acc) : acc;
+          }
+        }
+        if (row < rows) s.part[(int64_t)t * s.bpad + row] = acc;
       }
-      __syncwarp();
-      const int row = rt * TM + q * 32 + lane;
-      const int rr = row < rows ? row : 0;
-      const float xn = s.xbn[rr];
-      const int xi = s.xbi[rr];
-      const bool ok = mbar_wait(&sh.tfull[buf], bph);
-      if (__any_sync(0xffffffffu, !ok)) {
-        if (lane == 0) atomicOr(s.status, ST_TIMEOUT);
-        break;
-      }
-      tc_fence_after();
-      float acc = 0.0f;
+    } else {
+      for (int w = blockIdx.x; w < total; w += gridDim.x, ++local) {
+        const PairTile pt = pair_tile(s, w);
+        const uint32_t buf = local & 1u, bph = (local >> 1) & 1u;
+        __syncwarp();
 #pragma unroll
-      for (int ch = 0; ch < TN / 32; ++ch) {
-        float g[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + buf * TN + ch * 32, g);
-        if (ch == TN / 32 - 1) {
-          tc_fence_before();
-          mbar_arrive(&sh.tempty[buf]);
+        for (int c4 = 0; c4 < TN / 32; ++c4) {
+          const int c = c4 * 32 + lane;
+          const int qpos = pt.cs + c;
+          const bool valid = c < pt.crem;
+          const int64_t g = pt.base + (valid ? qpos : pt.cs);
+          // column class: 0 dropped (in D and the old window), 1 old window, 2 new block, 3 none
+          const float cls = !valid ? 3.0f : (qpos < pt.head_new ? 0.0f : (qpos < pt.tail_c ? 1.0f : 2.0f));
+          meta[c] = make_float4(s.yn[g], valid ? s.w32[g] : 0.0f, __int_as_float(valid ? s.yi[g] : -2), cls);
+        }
+        __syncwarp();
+        const int rloc = q * 32 + lane;
+        const bool rvalid = rloc < pt.rrem;
+        const int64_t p = pt.base + pt.rs + (rvalid ? rloc : 0);
+        const float xn = s.yn[p];
+        const int xi = s.yi[p];
+        const double wp = rvalid ? s.w64[p] : 0.0;
+        const bool ok = mbar_wait(&sh.tfull[buf], bph);
+        if (__any_sync(0xffffffffu, !ok)) {
+          if (lane == 0) atomicOr(s.status, ST_TIMEOUT);
+          break;
+        }
+        tc_fence_after();
+        float fA = 0.0f, fB = 0.0f, fE = 0.0f;
+#pragma unroll
+        for (int ch = 0; ch < TN / 32; ++ch) {
+          float g[32];
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + buf * TN + ch * 32, g);
+          if (ch == TN / 32 - 1) {
+            tc_fence_before();
+            mbar_arrive(&sh.tempty[buf]);
+          }
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const float4 m = meta[ch * 32 + i];
+            const float kv = kernel_value<KIND>(g[i], xn, m.x, xi == __float_as_int(m.z), negc, coef0, degree);
+            const float wk = m.y * kv;
+            fA += (m.w < 1.5f) ? wk : 0.0f;
+            fB += (m.w < 0.5f) ? wk : 0.0f;
+            fE += (m.w > 1.5f && m.w < 2.5f) ? kv : 0.0f;
+          }
+        }
+        // kind 0: A = w_p sum_{q in W} w_q K, Bdd = w_p sum_{q in D} w_q K, E = w_p sum_{q in B} K
+        // kind 1: M = sum_{q in B} K (every valid column of a kind-1 tile is in B)
+        double sA = 0.0, sB = 0.0, sE = 0.0, sM = 0.0;
+        if (rvalid) {
+          if (pt.kind == 0) { sA = wp * (double)fA; sB = wp * (double)fB; sE = wp * (double)fE; }
+          else sM = (double)fE;
         }
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int c = ch * 32 + i;
-          const float4 m = meta[c];
-          const float kv = kernel_value<KIND>(g[i], xn, m.x, xi == __float_as_int(m.z), negc, coef0, degree);
-          acc = (c < T.ncols) ? fmaf(m.y, kv, acc) : acc;
+        for (int o = 16; o > 0; o >>= 1) {
+          sA += __shfl_xor_sync(0xffffffffu, sA, o);
+          sB += __shfl_xor_sync(0xffffffffu, sB, o);
+          sE += __shfl_xor_sync(0xffffffffu, sE, o);
+          sM += __shfl_xor_sync(0xffffffffu, sM, o);
+        }
+        if (lane == 0) {
+          double* out = s.wpart + ((int64_t)w * 4 + (warp - 2)) * 4;
+          out[0] = sA; out[1] = sB; out[2] = sE; out[3] = sM;
         }
       }
-      if (row < rows) s.part[(int64_t)t * s.bpad + row] = acc;
     }
   }
   tc_fence_before();
@@ -336,16 +471,33 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 }
 
-template <int KIND>
-cudaError_t launch_kind(const Dev& s, const CUtensorMap& a, const CUtensorMap& b, int rows, cudaStream_t st) {
+template <int KIND, int MODE, bool X3>
+cudaError_t launch_form(const Dev& s, const CUtensorMap& a, const CUtensorMap& b, int rows, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_dist_tc<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(k_dist_tc<KIND, MODE, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SMEM_BYTES);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_dist_tc<KIND><<<s.num_sms, NTHREADS, SMEM_BYTES, st>>>(s, rows, a, b);
-  return cudaGetLastError();
+  return launch_pdl(k_dist_tc<KIND, MODE, X3>, dim3(s.num_sms), dim3(NTHREADS), SMEM_BYTES, st, s, rows, a, b);
+}
+
+template <int KIND, int MODE>
+cudaError_t launch_kind(const Dev& s, const CUtensorMap& a, const CUtensorMap& b, int rows, cudaStream_t st) {
+  return s.form == FORM_BF16X3 ? launch_form<KIND, MODE, true>(s, a, b, rows, st)
+                               : launch_form<KIND, MODE, false>(s, a, b, rows, st);
+}
+
+template <int MODE>
+cudaError_t launch_mode(const Dev& s, const void* maps_in, int rows, cudaStream_t st) {
+  const CUtensorMap* maps = static_cast<const CUtensorMap*>(maps_in);
+  switch (s.kind) {
+    case K_GAUSS: return launch_kind<K_GAUSS, MODE>(s, maps[0], maps[1], rows, st);
+    case K_LAPLACE: return launch_kind<K_LAPLACE, MODE>(s, maps[0], maps[1], rows, st);
+    case K_LINEAR: return launch_kind<K_LINEAR, MODE>(s, maps[0], maps[1], rows, st);
+    default: return launch_kind<K_POLY, MODE>(s, maps[0], maps[1], rows, st);
+  }
 }
 
 }  // namespace
@@ -381,15 +533,13 @@ cudaError_t tc_prepare(Dev& s, void* maps_out) {
   return cudaSuccess;
 }
 
-cudaError_t launch_dist_tc(const Dev& s, const void* maps_in, int rows, cudaStream_t st) {
+cudaError_t launch_dist_tc(const Dev& s, const void* maps, int rows, cudaStream_t st) {
   if (rows <= 0) return cudaSuccess;
-  const CUtensorMap* maps = static_cast<const CUtensorMap*>(maps_in);
-  switch (s.kind) {
-    case K_GAUSS: return launch_kind<K_GAUSS>(s, maps[0], maps[1], rows, st);
-    case K_LAPLACE: return launch_kind<K_LAPLACE>(s, maps[0], maps[1], rows, st);
-    case K_LINEAR: return launch_kind<K_LINEAR>(s, maps[0], maps[1], rows, st);
-    default: return launch_kind<K_POLY>(s, maps[0], maps[1], rows, st);
-  }
+  return launch_mode<0>(s, maps, rows, st);
+}
+
+cudaError_t launch_wgram_tc(const Dev& s, const void* maps, cudaStream_t st) {
+  return launch_mode<1>(s, maps, 0, st);
 }
 
 }  // namespace kkm

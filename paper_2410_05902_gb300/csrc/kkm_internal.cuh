@@ -75,10 +75,12 @@ struct Dev {
   int32_t dp;        // BF16 forms: padded d (hi part length)
   int32_t form, kind, degree, lr;
   double param, coef0, eta;
+  double inv_b;      // 1 / b
   float negc;        // -log2(e) / param (Gaussian, Laplacian)
   int32_t num_sms;
   uint64_t seed;
   int32_t tn;        // support rows per distance tile
+  int32_t pair_tile; // rows per side of a window-pass tile (64 SIMT, 128 tcgen05)
   int32_t bpad;      // rows of the batch buffers (>= b, multiple of 128)
   int32_t max_tiles, max_pairs;
   const float* X;
@@ -101,6 +103,7 @@ struct Dev {
   int32_t* c1;
   int32_t* wsum;     // sum of block counts in the window (C_1 excluded)
   double* cnorm;
+  float* cnorm32;    // FP32 copy of cnorm for the argmin
   int32_t* blk_iter; // [k * nbcap]
   int32_t* blk_cnt;  // [k * nbcap]
   int32_t* blk_first;
@@ -115,6 +118,8 @@ struct Dev {
   int32_t* perm;     // [b] batch rows sorted by center (stable)
   double* cmc;       // [k] <C_j, cm(B_j)>
   Plan* plan;        // [k]
+  int32_t* comp_off; // [k] first flat row of each center's compaction copy
+  int32_t* comp_total; // [1] rows copied by this step's compactions
   Tile* tiles;       // [max_tiles]
   int32_t* ntiles;   // [1]
   int32_t* tile_first; // [k]
@@ -124,13 +129,37 @@ struct Dev {
   int32_t* nwpairs;  // [1]
   int32_t* wpair_first; // [k]
   int32_t* wpair_cnt;   // [k]
-  double* wpart;     // [max_pairs * 4]
+  double* wpart;     // [max_pairs][4 slots][4 sums]: A, Bdd, E, M partials per tile
   int64_t* iter;     // [1] next iteration number
   int32_t* status;   // [1] sticky device status bits
   int64_t* stats;    // [3] steps, support rows, tiles
   double* obj;       // [1] last batch objective
+  double* objpart;   // [k] f_B partial sums, one slice of the batch per finalize warp
   int32_t* s_old;    // [1] support rows of the current step's distance pass
+  int32_t* done_ctr; // [1] blocks of k_finalize that have finished (reset by the last)
 };
+
+// Programmatic dependent launch: every step kernel is launched so that it may
+// be scheduled while its predecessor drains. It must wait here before it reads
+// anything the predecessor writes (a no-op when launched without the attribute).
+#define KKM_GRID_DEP_WAIT() asm volatile("griddepcontrol.wait;" ::: "memory")
+
+// Launches `kern` with the programmatic-stream-serialization attribute.
+template <typename... Params, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<Params>(args)...);
+}
 
 // ---------------------------------------------------------------- helpers
 __host__ __device__ inline int64_t round_up(int64_t a, int64_t m) { return (a + m - 1) / m * m; }
@@ -201,5 +230,6 @@ cudaError_t launch_mind_sum(const Dev& s, int rows, double* out, cudaStream_t st
 bool tc_available();
 cudaError_t tc_prepare(Dev& s, void* maps);
 cudaError_t launch_dist_tc(const Dev& s, const void* maps, int rows, cudaStream_t st);
+cudaError_t launch_wgram_tc(const Dev& s, const void* maps, cudaStream_t st);
 
 }  // namespace kkm

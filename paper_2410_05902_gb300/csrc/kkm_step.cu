@@ -3,6 +3,8 @@
 // window plan, row moves, and the finalise step that carries ||C||^2 by the
 // Sec. 4 recurrence (FP64) corrected for the rows Eq. (1) drops.
 // The distance kernels themselves are in kkm_gram_simt.cu and kkm_gram_tc.cu.
+#include <algorithm>
+
 #include "kkm_internal.cuh"
 
 namespace kkm {
@@ -46,36 +48,71 @@ __device__ int block_exclusive_scan_1024(int v, int* total) {
   return excl;
 }
 
-// Writes one FP32 source row into a batch/support row of the run's form and
-// returns ||row||^2 of the values the Gram product will use (FP64 sum).
-// Called by a whole warp; columns are strided over lanes.
-__device__ double warp_store_row(const Dev& s, const float* src, int64_t dst_row, bool to_support) {
-  const int lane = threadIdx.x & 31;
-  double acc = 0.0;
+// Stores four consecutive source values at column c of a batch/support row in
+// the run's form and returns their contribution to ||row||^2 (the values the
+// Gram product will use: FP32, BF16 hi, or BF16 hi + lo). Per-element work
+// stays in FP32: FP64 throughput on GB300 is a small fraction of FP32's.
+__device__ __forceinline__ float store4(const Dev& s, int64_t dst_row, bool to_support, int c, float4 v) {
   if (s.form == FORM_FP32) {
-    float* dst = (to_support ? s.y32 : s.xb32) + dst_row * s.ld;
-    for (int c = lane; c < s.d; c += kWarp) {
-      float v = src[c];
-      dst[c] = v;
-      acc += (double)v * (double)v;
-    }
-  } else {
-    __nv_bfloat16* dst = (to_support ? s.ybh : s.xbh) + dst_row * s.ld;
-    for (int c = lane; c < s.d; c += kWarp) {
-      float v = src[c];
-      __nv_bfloat16 hi = __float2bfloat16_rn(v);
-      float hf = __bfloat162float(hi);
-      __nv_bfloat16 lo = __float2bfloat16_rn(v - hf);
-      dst[c] = hi;
-      dst[s.dp + c] = lo;
-      double used = (s.form == FORM_BF16) ? (double)hf : (double)hf + (double)__bfloat162float(lo);
-      acc += used * used;
-    }
+    float* dst = (to_support ? s.y32 : s.xb32) + dst_row * s.ld + c;
+    *reinterpret_cast<float4*>(dst) = v;
+    return fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, v.w * v.w)));
   }
-  return warp_sum(acc);
+  __nv_bfloat16* dst = (to_support ? s.ybh : s.xbh) + dst_row * s.ld + c;
+  const float f[4] = {v.x, v.y, v.z, v.w};
+  __align__(8) __nv_bfloat16 hi[4], lo[4];
+  float acc = 0.0f;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    hi[e] = __float2bfloat16_rn(f[e]);
+    const float hf = __bfloat162float(hi[e]);
+    lo[e] = __float2bfloat16_rn(f[e] - hf);
+    const float used = (s.form == FORM_BF16) ? hf : hf + __bfloat162float(lo[e]);
+    acc = fmaf(used, used, acc);
+  }
+  *reinterpret_cast<uint2*>(dst) = *reinterpret_cast<const uint2*>(hi);
+  *reinterpret_cast<uint2*>(dst + s.dp) = *reinterpret_cast<const uint2*>(lo);
+  return acc;
 }
 
-// Copies a whole row (ld elements) between two rows of the run's row buffers.
+// Writes one FP32 source row (d values) into a batch/support row of the run's
+// form and returns ||row||^2 of the values the Gram product will use. Each
+// lane sums its columns in FP32 (at most d/32 terms) and the 32 lane sums are
+// combined in FP64. Called by a whole warp. Each lane issues up to eight loads
+// before it stores, so a row costs about one memory latency.
+__device__ double warp_store_row(const Dev& s, const float* src, int64_t dst_row, bool to_support) {
+  const int lane = threadIdx.x & 31;
+  float acc = 0.0f;
+  const int n4 = (s.d + 3) >> 2;
+  const bool vec = ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) && ((s.d & 3) == 0);
+  for (int c0 = 0; c0 < n4; c0 += 32 * 8) {
+    float4 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int c = c0 + u * 32 + lane;
+      if (c < n4) {
+        if (vec) {
+          v[u] = __ldg(reinterpret_cast<const float4*>(src) + c);
+        } else {
+          const int b = 4 * c;
+          v[u].x = __ldg(src + b);
+          v[u].y = b + 1 < s.d ? __ldg(src + b + 1) : 0.0f;
+          v[u].z = b + 2 < s.d ? __ldg(src + b + 2) : 0.0f;
+          v[u].w = b + 3 < s.d ? __ldg(src + b + 3) : 0.0f;
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int c = c0 + u * 32 + lane;
+      if (c < n4) acc += store4(s, dst_row, to_support, 4 * c, v[u]);
+    }
+  }
+  return warp_sum((double)acc);
+}
+
+// Copies a whole row (ld elements) between two rows of the run's row buffers,
+// loads first (up to eight 16-byte loads per lane in flight), then stores.
 __device__ void warp_copy_row(const Dev& s, bool src_support, int64_t src_row, int64_t dst_row) {
   const int lane = threadIdx.x & 31;
   const int elem = (s.form == FORM_FP32) ? 4 : 2;
@@ -85,7 +122,19 @@ __device__ void warp_copy_row(const Dev& s, bool src_support, int64_t src_row, i
   char* dst = (char*)(s.form == FORM_FP32 ? (void*)s.y32 : (void*)s.ybh);
   const int4* sp = (const int4*)(src + src_row * (int64_t)s.ld * elem);
   int4* dp = (int4*)(dst + dst_row * (int64_t)s.ld * elem);
-  for (int c = lane; c < n16; c += kWarp) dp[c] = sp[c];
+  for (int c0 = 0; c0 < n16; c0 += 32 * 8) {
+    int4 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int c = c0 + u * 32 + lane;
+      if (c < n16) v[u] = sp[c];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int c = c0 + u * 32 + lane;
+      if (c < n16) dp[c] = v[u];
+    }
+  }
 }
 
 // ------------------------------------------------------------------ kernels
@@ -97,11 +146,20 @@ __global__ void k_sample(Dev s) {
   s.bidx[t] = (int32_t)index_below(splitmix64(s.seed, c), (uint64_t)s.n);
 }
 
-// One warp per batch slot: X[idx] -> batch row, norm, data index.
+// One warp per batch slot: X[idx] -> batch row, norm, data index. With idx
+// NULL the slot's index is drawn here: SplitMix64 output (i-1)*b + slot.
 __global__ void k_gather_batch(Dev s, const int32_t* __restrict__ idx) {
+  KKM_GRID_DEP_WAIT();
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (warp >= s.b) return;
-  int64_t i = idx[warp];
+  int64_t i;
+  if (idx) {
+    i = idx[warp];
+  } else {
+    const uint64_t c = (uint64_t)(*s.iter - 1) * (uint64_t)s.b + (uint64_t)warp;
+    i = index_below(splitmix64(s.seed, c), (uint64_t)s.n);
+    if ((threadIdx.x & 31) == 0) s.bidx[warp] = (int32_t)i;
+  }
   if (i < 0 || i >= s.n) {
     if ((threadIdx.x & 31) == 0) atomicOr(s.status, ST_BAD_BATCH_INDEX);
     i = 0;
@@ -115,6 +173,7 @@ __global__ void k_gather_batch(Dev s, const int32_t* __restrict__ idx) {
 
 // One warp per query row: Q[r] -> batch row (no data index: K(x,x) is never forced).
 __global__ void k_gather_query(Dev s, const float* __restrict__ Q, int64_t ldq, int rows) {
+  KKM_GRID_DEP_WAIT();
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (warp >= rows) return;
   double nrm = warp_store_row(s, Q + (int64_t)warp * ldq, warp, false);
@@ -124,44 +183,57 @@ __global__ void k_gather_query(Dev s, const float* __restrict__ Q, int64_t ldq, 
   }
 }
 
-// One thread per batch row: sum the per-tile weighted kernel sums of each
-// center, form Delta(x, C_j) = K(x,x) - 2 <phi(x), C_j> + ||C_j||^2 (FP64
-// combine), and take the argmin (strict <, so ties go to the lowest j).
+// One warp per batch row, one lane per center (lane j handles centers j,
+// j+32, ...): <phi(x), C_j> is the sum of center j's per-tile partials (its
+// tiles are the consecutive list entries tile_first[j] ..), then
+// Delta(x, C_j) = K(x,x) - 2 <phi(x), C_j> + ||C_j||^2 in FP64, and a warp
+// argmin with ties to the lowest j. Every lane's loads are independent, so a
+// row costs a few memory latencies whatever k is.
 __global__ void k_argmin(Dev s, int rows, const int32_t* __restrict__ forced,
                          int32_t* __restrict__ assign_out, float* __restrict__ mind_out,
                          float* __restrict__ dist_out, int update) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  KKM_GRID_DEP_WAIT();
+  const int x = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (x >= rows) return;
-  const double kxx = kernel_self(s.kind, (double)s.xbn[x], s.coef0, s.degree);
-  double best = 1e300, best_inner = 0.0;
-  int bj = 0;
-  for (int j = 0; j < s.k; ++j) {
+  const float kxx = (float)kernel_self(s.kind, (double)s.xbn[x], s.coef0, s.degree);
+  const int fa = forced ? forced[x] : -1;
+  float best = 3.0e38f, best_inner = 0.0f, f_inner = 0.0f;
+  int bj = 0x7fffffff;
+  for (int j = lane; j < s.k; j += 32) {
     const int t0 = s.tile_first[j], nt = s.tile_cnt[j];
-    double inner = 0.0;
-    for (int t = 0; t < nt; ++t) inner += (double)s.part[(int64_t)(t0 + t) * s.bpad + x];
-    const double dist = kxx - 2.0 * inner + s.cnorm[j];
+    float inner = 0.0f;
+    for (int t = 0; t < nt; ++t) inner += s.part[(int64_t)(t0 + t) * s.bpad + x];
+    const float dist = fmaf(-2.0f, inner, kxx + s.cnorm32[j]);
     if (dist_out) dist_out[(int64_t)x * s.k + j] = (float)dist;
-    if (dist < best) { best = dist; bj = j; best_inner = inner; }
+    if (dist < best) { best = dist; bj = j; best_inner = inner; }   // j increases: ties keep the lowest
+    if (j == fa) f_inner = inner;
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+    const float oi = __shfl_xor_sync(0xffffffffu, best_inner, o);
+    if (ob < best || (ob == best && oj < bj)) { best = ob; bj = oj; best_inner = oi; }
+    f_inner += __shfl_xor_sync(0xffffffffu, f_inner, o);   // only the lane owning fa is non-zero
+  }
+  if (lane != 0) return;
   int a = bj;
-  double a_inner = best_inner;
+  float a_inner = best_inner;
   if (forced) {
-    a = forced[x];
-    if (a < 0 || a >= s.k) {
+    if (fa < 0 || fa >= s.k) {
       atomicOr(s.status, ST_BAD_ASSIGN);
-      a = bj;
-    } else if (a != bj) {
-      const int t0 = s.tile_first[a], nt = s.tile_cnt[a];
-      a_inner = 0.0;
-      for (int t = 0; t < nt; ++t) a_inner += (double)s.part[(int64_t)(t0 + t) * s.bpad + x];
+    } else {
+      a = fa;
+      a_inner = f_inner;
     }
   }
   if (assign_out) assign_out[x] = bj;
-  if (mind_out) mind_out[x] = (float)best;
+  if (mind_out) mind_out[x] = best;
   if (update) {
     s.assign[x] = a;
-    s.mind[x] = (float)best;
-    s.inner_a[x] = (float)a_inner;
+    s.mind[x] = best;
+    s.inner_a[x] = a_inner;
   }
 }
 
@@ -170,21 +242,37 @@ __global__ void k_argmin(Dev s, int rows, const int32_t* __restrict__ forced,
 // block push, the drops of Eq. (1), C_1 retirement, and the tile pairs of the
 // norm-recurrence Gram pass.
 __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, int pair_tile) {
-  extern __shared__ unsigned char smem[];
+  KKM_GRID_DEP_WAIT();
+  extern __shared__ __align__(16) unsigned char smem[];
   const int k = s.k, b = s.b, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  int32_t* cnt = (int32_t*)smem;      // [k]
-  int32_t* base = cnt + k;            // [k]
-  int32_t* tot = base + k;            // [k]
-  uint16_t* wtab = (uint16_t*)(tot + k);   // [32][k]
+  int32_t* cnt = (int32_t*)smem;            // [k]
+  int32_t* base = cnt + k;                  // [k]
+  int32_t* tot = base + k;                  // [k]
+  int32_t* coff = tot + k;                  // [k]
+  int16_t* sassign = (int16_t*)(coff + k);  // [b]   assignments (k <= 1024)
+  int16_t* sperm = sassign + b;             // [b]   batch rows sorted by center (b <= 8192)
+  uint16_t* wtab = (uint16_t*)(sperm + b);  // [32][k] per-warp counts / offsets of a chunk
+  // per-center window state, loaded up front together with the assignments
+  int c_head = 0, c_tail = 0, c_c1 = 0, c_wsum = 0, c_first = 0, c_nb = 0, c_oldest = 0;
+  if (tid < k) {
+    c_head = s.head[tid];
+    c_tail = s.tail[tid];
+    c_c1 = s.c1[tid];
+    c_wsum = s.wsum[tid];
+    c_first = s.blk_first[tid];
+    c_nb = s.blk_num[tid];
+    c_oldest = s.blk_cnt[(int64_t)tid * s.nbcap + c_first];
+  }
+  for (int x = tid; x < b; x += 1024) sassign[x] = (int16_t)s.assign[x];
   for (int j = tid; j < k; j += 1024) { cnt[j] = 0; base[j] = 0; }
   __syncthreads();
-  for (int x = tid; x < b; x += 1024) atomicAdd(&cnt[s.assign[x]], 1);
+  for (int x = tid; x < b; x += 1024) atomicAdd(&cnt[sassign[x]], 1);
   __syncthreads();
   // exclusive offsets over centers (k <= 1024: one center per thread)
   const int my = tid < k ? cnt[tid] : 0;
   int total_rows = 0;
   const int off = block_exclusive_scan_1024(my, &total_rows);
-  if (tid < k) { s.coff[tid] = off; s.counts[tid] = my; }
+  if (tid < k) { coff[tid] = off; s.coff[tid] = off; s.counts[tid] = my; }
   if (tid == 0) s.coff[k] = total_rows;
   __syncthreads();
   // stable ranks in chunks of 1024 rows
@@ -192,7 +280,7 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, int pair_tile) {
     for (int e = tid; e < 32 * k; e += 1024) wtab[e] = 0;
     __syncthreads();
     const int x = c0 + tid;
-    const int j = x < b ? s.assign[x] : -1;
+    const int j = x < b ? (int)sassign[x] : -1;
     const unsigned peers = __match_any_sync(0xffffffffu, j);
     const int rank = __popc(peers & ((1u << lane) - 1u));
     if (j >= 0 && rank == 0) wtab[warp * k + j] = (uint16_t)__popc(peers);
@@ -207,52 +295,41 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, int pair_tile) {
       tot[jj] = run;
     }
     __syncthreads();
-    if (j >= 0) s.perm[s.coff[j] + base[j] + wtab[warp * k + j] + rank] = x;
+    if (j >= 0) sperm[coff[j] + base[j] + wtab[warp * k + j] + rank] = (int16_t)x;
     __syncthreads();
     for (int jj = tid; jj < k; jj += 1024) base[jj] += tot[jj];
     __syncthreads();
   }
-  // learning rate and <C_j, cm(B_j)> = (1/b_j) sum_{x in B_j} <phi(x), C_j>
-  for (int j = warp; j < k; j += 32) {
-    const int n = cnt[j], o = s.coff[j];
-    double acc = 0.0;
-    for (int r = lane; r < n; r += 32) acc += (double)s.inner_a[s.perm[o + r]];
-    acc = warp_sum(acc);
-    if (lane == 0) {
-      double a = 0.0;
-      if (n > 0) a = (s.lr == 0) ? sqrt((double)n / (double)b) : s.eta;
-      s.alpha[j] = a;
-      s.cmc[j] = n > 0 ? acc / (double)n : 0.0;
-    }
-  }
+  for (int r = tid; r < b; r += 1024) s.perm[r] = sperm[r];
   // support rows read by this step's distance pass
-  int sz = tid < k ? s.tail[tid] - s.head[tid] : 0;
+  const int sz = tid < k ? c_tail - c_head : 0;
   int s_total = 0;
   block_exclusive_scan_1024(sz, &s_total);
   if (tid == 0) *s.s_old = s_total;
   // window plan, one thread per center
-  int npairs = 0;
+  int npairs = 0, ncomp = 0;
   if (tid < k) {
     const int j = tid;
     const int n = cnt[j];
     Plan P;
-    P.head_c = s.head[j];
-    P.tail_c = s.tail[j];
+    P.head_c = c_head;
+    P.tail_c = c_tail;
     P.head_new = P.head_c;
     P.tail_new = P.tail_c;
     P.src_head = -1;
     P.cnt = n;
     P.ndrop = 0;
-    P.c1_new = s.c1[j];
+    P.c1_new = c_c1;
     if (n > 0) {
       if (P.tail_c + n > s.cap) {       // compaction: move the window down to row 0
         P.src_head = P.head_c;
         P.tail_c = P.tail_c - P.head_c;
         P.head_c = 0;
+        ncomp = P.tail_c;
       }
       P.tail_new = P.tail_c + n;
       if (P.tail_new > s.cap) atomicOr(s.status, ST_CAPACITY);
-      int first = s.blk_first[j], nb = s.blk_num[j];
+      int first = c_first, nb = c_nb;
       int32_t* bi = s.blk_iter + (int64_t)j * s.nbcap;
       int32_t* bc = s.blk_cnt + (int64_t)j * s.nbcap;
       if (nb >= s.nbcap) {
@@ -263,16 +340,18 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, int pair_tile) {
         bc[slot] = n;
         ++nb;
       }
-      int total = s.wsum[j] + n;
+      int total = c_wsum + n;
       int drop_rows = 0;
       if (s.tau > 0) {
         // Q_i^j keeps the newest blocks whose counts reach tau: drop the
         // oldest block while the rest still sums to >= tau.
-        while (nb > 1 && total - bc[first] >= s.tau) {
-          drop_rows += bc[first];
-          total -= bc[first];
+        int oldest = (c_nb > 0) ? c_oldest : n;    // count of the oldest block in the ring
+        while (nb > 1 && total - oldest >= s.tau) {
+          drop_rows += oldest;
+          total -= oldest;
           first = (first + 1) % s.nbcap;
           --nb;
+          oldest = bc[first];
         }
         // C_1 stays only while min Q_i^j = 1 (Eq. (1), Sec. 4.1).
         if (P.c1_new && total >= s.tau && bi[first] != 1) {
@@ -292,6 +371,10 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, int pair_tile) {
     s.plan[j] = P;
   }
   __syncthreads();
+  int ctotal = 0;
+  const int cfirst = block_exclusive_scan_1024(ncomp, &ctotal);
+  if (tid < k) s.comp_off[tid] = cfirst;
+  if (tid == 0) *s.comp_total = ctotal;
   int ptotal = 0;
   const int pfirst = block_exclusive_scan_1024(npairs, &ptotal);
   if (tid == 0) {
@@ -315,18 +398,40 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, int pair_tile) {
   }
 }
 
-// Compaction of the windows that need it (blocks 0..k-1) and the append of the
-// new blocks (remaining blocks, one warp per batch row). Sources and
-// destinations never overlap (see the capacity argument in kkm_internal.cuh).
+// The append of the new blocks and the compaction of the windows that need
+// it, one warp per row: work items 0..b-1 append batch row perm[w] at the end
+// of its center's window; items b.. copy the compacting windows' rows down to
+// row 0, all compactions laid end to end (comp_off). Sources and destinations
+// never overlap (see the capacity argument in kkm_internal.cuh).
 __global__ void k_move(Dev s) {
-  const int warps = blockDim.x >> 5, wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if ((int)blockIdx.x < s.k) {
-    const int j = blockIdx.x;
-    const Plan P = s.plan[j];
-    if (P.src_head < 0) return;
-    const int64_t base = (int64_t)j * s.cap;
-    const int size = P.tail_c - P.head_c;
-    for (int r = wib; r < size; r += warps) {
+  KKM_GRID_DEP_WAIT();
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  const int nwarps = gridDim.x * wpb;
+  const int items = s.b + *s.comp_total;
+  for (int w = blockIdx.x * wpb + (threadIdx.x >> 5); w < items; w += nwarps) {
+    if (w < s.b) {
+      const int x = s.perm[w];
+      const int j = s.assign[x];
+      const Plan P = s.plan[j];
+      const int pos = P.tail_c + (w - s.coff[j]);
+      if (pos >= s.cap) continue;                   // flagged ST_CAPACITY in the plan
+      const int64_t dst = (int64_t)j * s.cap + pos;
+      warp_copy_row(s, false, x, dst);
+      if (lane == 0) {
+        s.yn[dst] = s.xbn[x];
+        s.yi[dst] = s.xbi[x];
+      }
+    } else {
+      const int f = w - s.b;
+      int lo = 0, hi = s.k;                         // last center with comp_off <= f
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s.comp_off[mid] <= f) lo = mid; else hi = mid;
+      }
+      const Plan P = s.plan[lo];
+      const int r = f - s.comp_off[lo];
+      const int64_t base = (int64_t)lo * s.cap;
       const int64_t src = base + P.src_head + r, dst = base + r;
       warp_copy_row(s, true, src, dst);
       if (lane == 0) {
@@ -336,32 +441,14 @@ __global__ void k_move(Dev s) {
         s.w32[dst] = s.w32[src];
       }
     }
-    return;
-  }
-  const int r = (blockIdx.x - s.k) * warps + wib;
-  if (r >= s.b) return;
-  const int x = s.perm[r];
-  const int j = s.assign[x];
-  const Plan P = s.plan[j];
-  const int pos = P.tail_c + (r - s.coff[j]);
-  if (pos >= s.cap) return;                       // flagged ST_CAPACITY in the plan
-  const int64_t dst = (int64_t)j * s.cap + pos;
-  warp_copy_row(s, false, x, dst);
-  if (lane == 0) {
-    s.yn[dst] = s.xbn[x];
-    s.yi[dst] = s.xbi[x];
   }
 }
 
-// Tile list of the distance pass from the current windows (block of 1024, k <= 1024).
-__device__ void build_tiles_block(const Dev& s) {
+// Tile list of the distance pass (block of 1024, k <= 1024). Thread j < k
+// passes the window [head, head + size) of center j.
+__device__ void build_tiles_block(const Dev& s, int head, int size) {
   const int tid = threadIdx.x;
-  int nt = 0, size = 0, head = 0;
-  if (tid < s.k) {
-    head = s.head[tid];
-    size = s.tail[tid] - head;
-    nt = (size + s.tn - 1) / s.tn;
-  }
+  const int nt = tid < s.k ? (size + s.tn - 1) / s.tn : 0;
   int total = 0;
   const int first = block_exclusive_scan_1024(nt, &total);
   if (tid == 0) {
@@ -381,71 +468,152 @@ __device__ void build_tiles_block(const Dev& s) {
   }
 }
 
-__global__ void __launch_bounds__(1024) k_build_tiles(Dev s) { build_tiles_block(s); }
+__device__ void build_tiles_block(const Dev& s) {
+  int head = 0, size = 0;
+  if ((int)threadIdx.x < s.k) {
+    head = s.head[threadIdx.x];
+    size = s.tail[threadIdx.x] - head;
+  }
+  build_tiles_block(s, head, size);
+}
 
-// Single CTA of 1024 threads: the FP64 norm recurrence, weight decay/append,
-// window bookkeeping, the next tile list, f_B and the iteration counter.
-__global__ void __launch_bounds__(1024) k_finalize(Dev s, double* obj_out) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int tiles_used = *s.ntiles;   // tiles of this step's distance pass
-  for (int j = warp; j < s.k; j += 32) {
-    const Plan P = s.plan[j];
-    if (P.cnt == 0) continue;
-    // window Gram sums of this center, in pair order
-    double A = 0.0, Bdd = 0.0, E = 0.0, M = 0.0;
+__global__ void __launch_bounds__(1024) k_build_tiles(Dev s) {
+  for (int j = threadIdx.x; j < s.k; j += 1024) s.cnorm32[j] = (float)s.cnorm[j];
+  build_tiles_block(s);
+}
+
+// Exclusive scan of one int per lane over a warp; *total receives the sum.
+__device__ __forceinline__ int warp_exclusive_scan(int v, int* total) {
+  const int lane = threadIdx.x & 31;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  *total = __shfl_sync(0xffffffffu, x, 31);
+  return x - v;
+}
+
+// Tile list of the distance pass built by one warp (centers in chunks of 32).
+__device__ void build_tiles_warp(const Dev& s) {
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  for (int j0 = 0; j0 < s.k; j0 += 32) {
+    const int j = j0 + lane;
+    int head = 0, size = 0, nt = 0;
+    if (j < s.k) {
+      head = s.head[j];
+      size = s.tail[j] - head;
+      nt = (size + s.tn - 1) / s.tn;
+    }
+    int chunk = 0;
+    const int first = base + warp_exclusive_scan(nt, &chunk);
+    if (j < s.k) {
+      const bool fits = first + nt <= s.max_tiles;   // never false by the capacity bound
+      s.tile_first[j] = fits ? first : 0;
+      s.tile_cnt[j] = fits ? nt : 0;
+      if (fits)
+        for (int t = 0; t < nt; ++t) {
+          const int c = t * s.tn;
+          s.tiles[first + t] = Tile{j, (int32_t)((int64_t)j * s.cap + head + c), min(s.tn, size - c), 0};
+        }
+    }
+    base += chunk;
+  }
+  if (lane == 0) {
+    *s.ntiles = base <= s.max_tiles ? base : s.max_tiles;
+    if (base > s.max_tiles) atomicOr(s.status, ST_CAPACITY);
+  }
+}
+
+// One warp per center j (block j). For a center that received points, with
+// FP64 where the values accumulate over iterations:
+//   alpha_j = sqrt(b_j / b) (or eta), <C_j, cm(B_j)> = (1/b_j) sum_x <phi(x), C_j>,
+//   the window-pass sums, the Sec. 4 recurrence for ||C_j||^2 corrected for
+//   the rows Eq. (1) drops, and the weights: rows [head_new, tail_c) decay by
+//   (1 - alpha), rows [tail_c, tail_new) get alpha / b_j.
+// The last warp to finish (atomic ticket, no waiting) builds the next tile
+// list, f_B and the iteration counter. GB300 issues FP64 slowly and charges
+// each FP64 warp instruction in full, so the FP64 work is kept to one warp
+// per center, on sums already reduced in FP32 where the terms are FP32.
+__global__ void __launch_bounds__(32) k_finalize(Dev s, double* obj_out) {
+  KKM_GRID_DEP_WAIT();
+  const int lane = threadIdx.x, j = blockIdx.x;
+  const Plan P = s.plan[j];
+  if (P.cnt > 0) {
+    const int n = P.cnt, o = s.coff[j];
+    float part = 0.0f;
+    for (int r = lane; r < n; r += 32) part += s.inner_a[s.perm[o + r]];
+    const double cm_sum = warp_sum((double)part);
     const int p0 = s.wpair_first[j];
     const int np = (p0 + s.wpair_cnt[j] <= s.max_pairs) ? s.wpair_cnt[j] : 0;
-    for (int p = lane; p < np; p += 32) {
-      const double* q = s.wpart + (int64_t)(p0 + p) * 4;
-      A += q[0]; Bdd += q[1]; E += q[2]; M += q[3];
-    }
-    A = warp_sum(A); Bdd = warp_sum(Bdd); E = warp_sum(E); M = warp_sum(M);
-    const double a = s.alpha[j];
-    const double n = (double)P.cnt;
+    double q[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int e = lane; e < np * 16; e += 32) q[e & 3] += s.wpart[(int64_t)p0 * 16 + e];
+    const double A = warp_sum(q[0]), Bdd = warp_sum(q[1]), E = warp_sum(q[2]), M = warp_sum(q[3]);
+    const double dn = (double)n;
+    const double a = (s.lr == 0) ? sqrt(dn * s.inv_b) : s.eta;
+    const double keep = 1.0 - a, wnew = a / dn;
     if (lane == 0) {
-      // Sec. 4: ||C'||^2 = (1-a)^2 ||R||^2 + 2a(1-a) <R, m> + a^2 ||m||^2, with
-      // m = cm(B_j) and R = C - D the part of the old center that Eq. (1) keeps
-      // (D = the dropped rows with their old weights).
-      const double m2 = M / (n * n);
+      s.alpha[j] = a;
+      const double cmc = cm_sum / dn;
+      s.cmc[j] = cmc;
+      // Sec. 4: ||C'||^2 = (1-a)^2 ||R||^2 + 2a(1-a) <R, m> + a^2 ||m||^2 with
+      // m = cm(B_j) and R = C - D, the part of the old center Eq. (1) keeps
+      const double m2 = M / (dn * dn);
       const double R2 = s.cnorm[j] - 2.0 * A + Bdd;
-      const double Rm = s.cmc[j] - E / n;
-      s.cnorm[j] = (1.0 - a) * (1.0 - a) * R2 + 2.0 * a * (1.0 - a) * Rm + a * a * m2;
-    }
-    const int64_t base = (int64_t)j * s.cap;
-    const double keep = 1.0 - a, wnew = a / n;
-    const int tail_new = min(P.tail_new, s.cap);
-    for (int r = P.head_new + lane; r < tail_new; r += 32) {
-      const int64_t row = base + r;
-      const double w = (r < P.tail_c) ? s.w64[row] * keep : wnew;
-      s.w64[row] = w;
-      s.w32[row] = (float)w;
-    }
-    if (lane == 0) {
+      const double Rm = cmc - E / dn;
+      const double cn = keep * keep * R2 + 2.0 * a * keep * Rm + a * a * m2;
+      s.cnorm[j] = cn;
+      s.cnorm32[j] = (float)cn;
       s.head[j] = P.head_new;
       s.tail[j] = P.tail_new;
       s.c1[j] = P.c1_new;
     }
+    const float wnew32 = (float)wnew;
+    const int64_t base = (int64_t)j * s.cap;
+    for (int r = P.head_new + lane; r < min(P.tail_c, s.cap); r += 32) {
+      const double w = s.w64[base + r] * keep;
+      s.w64[base + r] = w;
+      s.w32[base + r] = (float)w;
+    }
+    for (int r = P.tail_c + lane; r < min(P.tail_new, s.cap); r += 32) {
+      s.w64[base + r] = wnew;
+      s.w32[base + r] = wnew32;
+    }
   }
-  __syncthreads();
-  build_tiles_block(s);
-  // f_B(C_i): mean of the minimum distances, FP64, fixed summation order
-  __shared__ double red[1024];
-  double acc = 0.0;
-  for (int x = tid; x < s.b; x += 1024) acc += (double)s.mind[x];
-  red[tid] = acc;
-  __syncthreads();
-  for (int w = 512; w > 0; w >>= 1) {
-    if (tid < w) red[tid] += red[tid + w];
-    __syncthreads();
+  // this warp's slice of sum_x min_j Delta(x, C_j) (FP32 lane partials, FP64 combine)
+  {
+    const int chunk = (s.b + gridDim.x - 1) / gridDim.x;
+    const int x0 = j * chunk, x1 = min(s.b, x0 + chunk);
+    float macc = 0.0f;
+    for (int x = x0 + lane; x < x1; x += 32) macc += s.mind[x];
+    const double t = warp_sum((double)macc);
+    if (lane == 0) s.objpart[j] = t;
   }
-  if (tid == 0) {
-    const double f = red[0] / (double)s.b;
+  // the last warp to arrive finishes the step
+  __threadfence();
+  __syncwarp();
+  int last = 0;
+  if (lane == 0) last = (atomicAdd(s.done_ctr, 1) == (int)gridDim.x - 1);
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (!last) return;
+  __threadfence();
+  const int tiles_used = *s.ntiles;            // tiles of this step's distance pass
+  build_tiles_warp(s);
+  // f_B(C_i): mean of the minimum distances, from the warps' partials in center order
+  double tpart = 0.0;
+  for (int q = lane; q < (int)gridDim.x; q += 32) tpart += s.objpart[q];
+  const double total = warp_sum(tpart);
+  if (lane == 0) {
+    const double f = total / (double)s.b;
     *s.obj = f;
     if (obj_out) *obj_out = f;
     s.stats[0] += 1;
     s.stats[1] += *s.s_old;
     s.stats[2] += tiles_used;
     *s.iter += 1;
+    *s.done_ctr = 0;
   }
 }
 
@@ -477,6 +645,7 @@ __global__ void k_init_centers(Dev s, const int32_t* __restrict__ init_idx) {
     s.blk_first[j] = 0;
     s.blk_num[j] = 0;
     s.cnorm[j] = kernel_self(s.kind, exact, s.coef0, s.degree);
+    s.cnorm32[j] = (float)s.cnorm[j];
   }
 }
 
@@ -499,6 +668,7 @@ __global__ void k_load_rows(Dev s) {
 
 // FP64 sum of mind[0..rows) into *out (single CTA, fixed order).
 __global__ void __launch_bounds__(1024) k_mind_sum(Dev s, int rows, double* out) {
+  KKM_GRID_DEP_WAIT();
   __shared__ double red[1024];
   double acc = 0.0;
   for (int x = threadIdx.x; x < rows; x += 1024) acc += (double)s.mind[x];
@@ -520,46 +690,52 @@ cudaError_t launch_sample(const Dev& s, cudaStream_t st) {
 }
 
 cudaError_t launch_gather_batch(const Dev& s, const int32_t* idx, cudaStream_t st) {
-  k_gather_batch<<<(s.b * 32 + 255) / 256, 256, 0, st>>>(s, idx);
+  cudaError_t e = launch_pdl(k_gather_batch, dim3((s.b * 32 + 255) / 256), dim3(256), 0, st, s, idx);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 cudaError_t launch_gather_query(const Dev& s, const float* Q, int64_t ldq, int rows, cudaStream_t st) {
   if (rows <= 0) return cudaSuccess;
-  k_gather_query<<<(rows * 32 + 255) / 256, 256, 0, st>>>(s, Q, ldq, rows);
+  cudaError_t e = launch_pdl(k_gather_query, dim3((rows * 32 + 255) / 256), dim3(256), 0, st, s, Q, ldq, rows);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 cudaError_t launch_argmin(const Dev& s, int rows, const int32_t* forced, int32_t* assign_out,
                           float* mind_out, float* dist_out, bool update, cudaStream_t st) {
   if (rows <= 0) return cudaSuccess;
-  k_argmin<<<(rows + 127) / 128, 128, 0, st>>>(s, rows, forced, assign_out, mind_out, dist_out,
-                                                update ? 1 : 0);
+  cudaError_t e = launch_pdl(k_argmin, dim3((rows * 32 + 127) / 128), dim3(128), 0, st, s, rows, forced,
+                             assign_out, mind_out, dist_out, update ? 1 : 0);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
-int sort_plan_smem(int k) { return 3 * k * 4 + 32 * k * 2; }
+int sort_plan_smem(int k, int b) { return 4 * k * 4 + b * (2 + 2) + 32 * k * 2; }
 
 cudaError_t launch_sort_plan(const Dev& s, cudaStream_t st) {
-  const int smem = sort_plan_smem(s.k);
+  const int smem = sort_plan_smem(s.k, s.b);
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_sort_plan, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
-  k_sort_plan<<<1, 1024, smem, st>>>(s, 64);   // window-pass tile (k_wgram_simt)
+  cudaError_t e = launch_pdl(k_sort_plan, dim3(1), dim3(1024), smem, st, s, s.pair_tile);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 cudaError_t launch_move(const Dev& s, cudaStream_t st) {
   const int warps = 8;
-  const int blocks = s.k + (s.b + warps - 1) / warps;
-  k_move<<<blocks, warps * 32, 0, st>>>(s);
+  const int blocks = std::max((s.b + warps - 1) / warps, s.num_sms * 2);
+  cudaError_t e = launch_pdl(k_move, dim3(blocks), dim3(warps * 32), 0, st, s);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(const Dev& s, double* obj_out, cudaStream_t st) {
-  k_finalize<<<1, 1024, 0, st>>>(s, obj_out);
+  cudaError_t e = launch_pdl(k_finalize, dim3(s.k), dim3(32), 0, st, s, obj_out);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -579,7 +755,8 @@ cudaError_t launch_load_rows(const Dev& s, int32_t, cudaStream_t st) {
 }
 
 cudaError_t launch_mind_sum(const Dev& s, int rows, double* out, cudaStream_t st) {
-  k_mind_sum<<<1, 1024, 0, st>>>(s, rows, out);
+  cudaError_t e = launch_pdl(k_mind_sum, dim3(1), dim3(1024), 0, st, s, rows, out);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -72,6 +72,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "kkm_set_state": ([_P, c_int64, _P, _P, _P, _P, _P, _P, _P, _P], c_int32),
         "kkm_stats": ([_P, POINTER(c_int64), POINTER(c_int64), POINTER(c_int64), c_int32], c_int32),
         "kkm_timing_enable": ([_P, c_int32], c_int32),
+        "kkm_graph_enable": ([_P, c_int32], c_int32),
         "kkm_timing_read": ([_P, POINTER(c_int64), POINTER(c_double), c_int32], c_int32),
         "kkm_launches": ([_P, POINTER(c_int64), c_int32], c_int32),
         "kkm_distances_noalloc": ([_P, c_int64, c_int64, c_int32, _P, c_int64, c_int64, _P, _P, _P,
@@ -147,6 +148,10 @@ def kkm_stats(ctx, reset: bool = False) -> tuple[int, int, int]:
 
 def kkm_timing_enable(ctx, enable: bool) -> None:
     _check(load().kkm_timing_enable(ctx, int(enable)), ctx)
+
+
+def kkm_graph_enable(ctx, enable: bool) -> None:
+    _check(load().kkm_graph_enable(ctx, int(enable)), ctx)
 
 
 def kkm_timing_read(ctx, reset: bool = False) -> tuple[int, float]:
@@ -277,6 +282,9 @@ class KKM:
 
     def timing(self, enable: bool):
         kkm_timing_enable(self.ctx, enable)
+
+    def graph(self, enable: bool):
+        kkm_graph_enable(self.ctx, enable)
 
     def timing_read(self, reset: bool = False):
         return kkm_timing_read(self.ctx, reset)
