@@ -5,6 +5,7 @@
 // mirror of the iteration counter. kkm_step queues the whole iteration as a
 // fixed sequence of kernels on that stream. No step allocates, and nothing
 // crosses to the host unless the caller asks for a host result.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -259,6 +260,11 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
   ALLOC(s.part, (size_t)s.max_tiles * s.bpad);
   ALLOC(s.wpairs, s.max_pairs); ALLOC(s.nwpairs, 1); ALLOC(s.wpair_first, k); ALLOC(s.wpair_cnt, k);
   ALLOC(s.wpart, (size_t)s.max_pairs * 16);
+  if (c->use_tc) {
+    const int64_t max_items = std::max<int64_t>((int64_t)(s.bpad / 128) * s.max_tiles, s.max_pairs);
+    ALLOC(s.skpart, (size_t)s.num_sms * 2 * 128 * 128);
+    ALLOC(s.skcnt, (size_t)max_items * 4);
+  }
   ALLOC(s.iter, 1); ALLOC(s.status, 1); ALLOC(s.stats, 3); ALLOC(s.obj, 1); ALLOC(s.s_old, 1);
   ALLOC(c->d_init_idx, k);
   ALLOC(c->d_hbatch, b); ALLOC(c->d_hassign, b); ALLOC(c->d_hobj, 1);

@@ -223,6 +223,77 @@ __device__ __forceinline__ PairTile pair_tile(const Dev& s, int w) {
 
 // MODE 0: distance pass (A = batch tile, B = support tile, one FP32 partial per row).
 // MODE 1: window pass (A and B = support rows of one center, four FP64 sums per warp).
+// Schedule: data-parallel waves plus stream-K for the tail (Osama et al.,
+// "Stream-K: Work-centric parallel decomposition for dense matrix
+// multiplication", PPoPP 2023). With T items and G CTAs, every CTA first
+// takes floor(T/G) whole items round-robin. The remaining T mod G items are
+// cut into their U = (T mod G) * nks slice units, and the units are split into
+// G contiguous ranges of near-equal length, one per CTA. So every SM gets the
+// same amount of MMA work. An item whose slices span several CTAs ("split") is
+// finished by whichever CTA is the last to deliver its part: every part
+// spills its partial accumulator to global scratch and adds its slice count to
+// the item's arrival counter (one counter per 32-row quadrant, so the four
+// epilogue warps never wait for one another). The warp that completes the
+// count sums all parts and runs the epilogue. Nobody waits on another CTA.
+__device__ __forceinline__ int64_t unit_start(int64_t U, int c, int G) { return U * c / G; }
+
+// The CTA whose stream-K range holds unit u (every such range is non-empty).
+__device__ int unit_owner(int64_t U, int64_t u, int G) {
+  int c = (int)((u * G) / U);
+  while (c + 1 < G && unit_start(U, c + 1, G) <= u) ++c;
+  while (c > 0 && unit_start(U, c, G) > u) --c;
+  return c;
+}
+
+// Partial accumulator slot of CTA c for tail item r (counted from the first
+// tail item): 0 for the first item of the CTA's range, 1 for its last.
+__device__ __forceinline__ int64_t part_slot(int64_t U, int nks, int G, int c, int r) {
+  const int first_r = (int)(unit_start(U, c, G) / nks);
+  return (int64_t)c * 2 + (r == first_r ? 0 : 1);
+}
+
+// The work of one CTA: whole items first, then its stream-K range of tail
+// units. The tail goes to Gs = min(G, tail items * pmax) CTAs, so a tail item
+// is split into at most about pmax parts (pmax = 1: whole items only), which
+// bounds the partial accumulators a merge has to read.
+struct Work {
+  int nks, G, c, full, base, Gs;   // base = first tail item = full * G
+  int64_t U, ub, ue, u;
+  int i;
+  __device__ Work(int total, int nks_, int G_, int c_, int pmax) : nks(nks_), G(G_), c(c_) {
+    full = total / G;
+    base = full * G;
+    const int tail = total - base;
+    Gs = tail * pmax < G ? tail * pmax : G;
+    if (Gs < 1) Gs = 1;
+    U = (int64_t)tail * nks;
+    ub = c < Gs ? unit_start(U, c, Gs) : U;
+    ue = c < Gs ? unit_start(U, c + 1, Gs) : U;
+    u = ub;
+    i = 0;
+  }
+  // next part: item, slice range [s0, s1), and whether it is the range's first tail item
+  __device__ bool next(int& item, int& s0, int& s1, bool& first_tail) {
+    if (i < full) {
+      item = c + i * G;
+      s0 = 0;
+      s1 = nks;
+      first_tail = false;
+      ++i;
+      return true;
+    }
+    if (u >= ue) return false;
+    const int r = (int)(u / nks);
+    item = base + r;
+    s0 = (int)(u - (int64_t)r * nks);
+    const int64_t left = ue - u;
+    s1 = (int64_t)nks < s0 + left ? nks : (int)(s0 + left);
+    first_tail = (u == ub);
+    u += s1 - s0;
+    return true;
+  }
+};
+
 template <int KIND, int MODE, bool X3>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_dist_tc(Dev s, int rows, const __grid_constant__ CUtensorMap tmA,
@@ -261,28 +332,34 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int R = (rows + TM - 1) / TM;
   const int total = (MODE == 0) ? R * (*s.ntiles) : *s.nwpairs;
   const int nks = s.dp / KS;
-  const int nslices = nks;
+  const int G = gridDim.x;
+  // most parts a tail item is split into: the distance pass has enough items
+  // to keep whole ones, the window pass (few items) splits them in two
+  constexpr int PMAX = (MODE == 0) ? 1 : 2;
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
       bool ok = true;
       uint32_t it = 0;
-      for (int w = blockIdx.x; w < total && ok; w += gridDim.x) {
+      Work wk(total, nks, G, blockIdx.x, PMAX);
+      int item, s0, s1;
+      bool ft;
+      while (ok && wk.next(item, s0, s1, ft)) {
         int ya, yb;
         const CUtensorMap* am;
         if constexpr (MODE == 0) {
-          const int t = w / R, rt = w % R;
+          const int t = item / R, rt = item % R;
           ya = rt * TM;
           yb = s.tiles[t].row0;
           am = &tmA;
         } else {
-          const PairTile pt = pair_tile(s, w);
+          const PairTile pt = pair_tile(s, item);
           ya = (int)(pt.base + pt.rs);
           yb = (int)(pt.base + pt.cs);
           am = &tmB;
         }
-        for (int sl = 0; sl < nslices; ++sl, ++it) {
+        for (int sl = s0; sl < s1; ++sl, ++it) {
           const int st = it % NST;
           const uint32_t ph = (it / NST) & 1u;
           if (!mbar_wait(&sh.empty[st], ph ^ 1u)) { ok = false; break; }
@@ -310,22 +387,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (lane == 0) {
       bool ok = true;
       uint32_t it = 0, local = 0;
-      for (int w = blockIdx.x; w < total && ok; w += gridDim.x, ++local) {
+      Work wk(total, nks, G, blockIdx.x, PMAX);
+      int item, s0, s1;
+      bool ft;
+      for (; ok && wk.next(item, s0, s1, ft); ++local) {
         const uint32_t buf = local & 1u, bph = (local >> 1) & 1u;
         if (!mbar_wait(&sh.tempty[buf], bph ^ 1u)) { ok = false; break; }
         tc_fence_after();
         const uint32_t d = tmem + buf * TN;
-        for (int sl = 0; sl < nslices; ++sl, ++it) {
+        for (int sl = s0; sl < s1; ++sl, ++it) {
           const int st = it % NST;
           const uint32_t ph = (it / NST) & 1u;
           if (!mbar_wait(&sh.full[st], ph)) { ok = false; break; }
           tc_fence_after();
           const uint32_t a0 = smem_u32(smem + st * SB);
+          const uint32_t first = (sl == s0) ? 0u : 1u;
           if constexpr (X3) {
             const uint32_t alo = a0 + A_BYTES, bhi = a0 + 2 * A_BYTES, blo = a0 + 3 * A_BYTES;
 #pragma unroll
             for (int k = 0; k < KS / 16; ++k) {
-              mma_bf16(d, sw128_desc(a0 + 32u * k), sw128_desc(bhi + 32u * k), (sl | k) != 0 ? 1u : 0u);
+              mma_bf16(d, sw128_desc(a0 + 32u * k), sw128_desc(bhi + 32u * k), (first | k) != 0 ? 1u : 0u);
               mma_bf16(d, sw128_desc(a0 + 32u * k), sw128_desc(blo + 32u * k), 1u);
               mma_bf16(d, sw128_desc(alo + 32u * k), sw128_desc(bhi + 32u * k), 1u);
             }
@@ -333,7 +414,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const uint32_t b0 = a0 + A_BYTES;
 #pragma unroll
             for (int k = 0; k < KS / 16; ++k)
-              mma_bf16(d, sw128_desc(a0 + 32u * k), sw128_desc(b0 + 32u * k), (sl | k) != 0 ? 1u : 0u);
+              mma_bf16(d, sw128_desc(a0 + 32u * k), sw128_desc(b0 + 32u * k), (first | k) != 0 ? 1u : 0u);
           }
           mma_commit(&sh.empty[st]);
         }
@@ -347,58 +428,43 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else {
     // ---------------------------------------------------------------- epilogue
     const int q = warp & 3;                      // TMEM lane quadrant of this warp
+    const int rloc = q * 32 + lane;              // this thread's row inside the tile
     float4* meta = sh.meta[warp - 2];
     const float negc = s.negc, coef0 = (float)s.coef0;
     const int degree = s.degree;
     uint32_t local = 0;
-    if constexpr (MODE == 0) {
-    for (int w = blockIdx.x; w < total; w += gridDim.x, ++local) {
-        const int t = w / R, rt = w % R;
+    Work wk(total, nks, G, blockIdx.x, PMAX);
+    int item, s0, s1;
+    bool is_first;
+    for (; wk.next(item, s0, s1, is_first); ++local) {
+      const bool whole = (s0 == 0 && s1 == nks);
+      const uint32_t buf = local & 1u, bph = (local >> 1) & 1u;
+      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + buf * TN;
+      // column metadata and row data first: their global loads overlap the MMAs
+      int t = 0, row = 0, ncols = 0;
+      float xn;
+      int xi;
+      PairTile pt;
+      double wp = 0.0;
+      bool rvalid = true;
+      __syncwarp();
+      if constexpr (MODE == 0) {
+        t = item / R;
         const Tile T = s.tiles[t];
-        const uint32_t buf = local & 1u, bph = (local >> 1) & 1u;
-        __syncwarp();
-  #pragma unroll
+        ncols = T.ncols;
+#pragma unroll
         for (int c4 = 0; c4 < TN / 32; ++c4) {
           const int c = c4 * 32 + lane;
           const bool valid = c < T.ncols;
           const int64_t g = (int64_t)T.row0 + (valid ? c : 0);
           meta[c] = make_float4(s.yn[g], valid ? s.w32[g] : 0.0f, __int_as_float(valid ? s.yi[g] : -2), 0.0f);
         }
-        __syncwarp();
-        const int row = rt * TM + q * 32 + lane;
+        row = (item % R) * TM + rloc;
         const int rr = row < rows ? row : 0;
-        const float xn = s.xbn[rr];
-        const int xi = s.xbi[rr];
-        const bool ok = mbar_wait(&sh.tfull[buf], bph);
-        if (__any_sync(0xffffffffu, !ok)) {
-          if (lane == 0) atomicOr(s.status, ST_TIMEOUT);
-          break;
-        }
-        tc_fence_after();
-        float acc = 0.0f;
-  #pragma unroll
-        for (int ch = 0; ch < TN / 32; ++ch) {
-          float g[32];
-          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + buf * TN + ch * 32, g);
-          if (ch == TN / 32 - 1) {
-            tc_fence_before();
-            mbar_arrive(&sh.tempty[buf]);
-          }
-  #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const int c = ch * 32 + i;
-            const float4 m = meta[c];
-            const float kv = kernel_value<KIND>(g[i], xn, m.x, xi == __float_as_int(m.z), negc, coef0, degree);
-            acc = (c < T.ncols) ? fmaf(m.y, kv, acc) : acc;
-          }
-        }
-        if (row < rows) s.part[(int64_t)t * s.bpad + row] = acc;
-      }
-    } else {
-      for (int w = blockIdx.x; w < total; w += gridDim.x, ++local) {
-        const PairTile pt = pair_tile(s, w);
-        const uint32_t buf = local & 1u, bph = (local >> 1) & 1u;
-        __syncwarp();
+        xn = s.xbn[rr];
+        xi = s.xbi[rr];
+      } else {
+        pt = pair_tile(s, item);
 #pragma unroll
         for (int c4 = 0; c4 < TN / 32; ++c4) {
           const int c = c4 * 32 + lane;
@@ -409,35 +475,93 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const float cls = !valid ? 3.0f : (qpos < pt.head_new ? 0.0f : (qpos < pt.tail_c ? 1.0f : 2.0f));
           meta[c] = make_float4(s.yn[g], valid ? s.w32[g] : 0.0f, __int_as_float(valid ? s.yi[g] : -2), cls);
         }
-        __syncwarp();
-        const int rloc = q * 32 + lane;
-        const bool rvalid = rloc < pt.rrem;
+        rvalid = rloc < pt.rrem;
         const int64_t p = pt.base + pt.rs + (rvalid ? rloc : 0);
-        const float xn = s.yn[p];
-        const int xi = s.yi[p];
-        const double wp = rvalid ? s.w64[p] : 0.0;
-        const bool ok = mbar_wait(&sh.tfull[buf], bph);
-        if (__any_sync(0xffffffffu, !ok)) {
-          if (lane == 0) atomicOr(s.status, ST_TIMEOUT);
-          break;
-        }
-        tc_fence_after();
-        float fA = 0.0f, fB = 0.0f, fE = 0.0f;
+        xn = s.yn[p];
+        xi = s.yi[p];
+        wp = rvalid ? s.w64[p] : 0.0;
+      }
+      __syncwarp();
+      const bool ok = mbar_wait(&sh.tfull[buf], bph);
+      if (__any_sync(0xffffffffu, !ok)) {
+        if (lane == 0) atomicOr(s.status, ST_TIMEOUT);
+        break;
+      }
+      tc_fence_after();
+      if (!whole) {
+        // spill this part (column-major: for each column the 128 rows are contiguous)
+        float* mine = s.skpart + ((int64_t)blockIdx.x * 2 + (is_first ? 0 : 1)) * (TN * TM);
 #pragma unroll
         for (int ch = 0; ch < TN / 32; ++ch) {
           float g[32];
-          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + buf * TN + ch * 32, g);
+          tmem_ld32(taddr + ch * 32, g);
           if (ch == TN / 32 - 1) {
             tc_fence_before();
             mbar_arrive(&sh.tempty[buf]);
           }
 #pragma unroll
+          for (int i = 0; i < 32; ++i) mine[(ch * 32 + i) * TM + rloc] = g[i];
+        }
+        __threadfence();
+        __syncwarp();
+        int prev = 0;
+        if (lane == 0) prev = atomicAdd(&s.skcnt[(int64_t)item * 4 + q], s1 - s0);
+        prev = __shfl_sync(0xffffffffu, prev, 0);
+        if (prev + (s1 - s0) != nks) continue;    // another CTA's part is still missing
+        if (lane == 0) s.skcnt[(int64_t)item * 4 + q] = 0;
+        __threadfence();
+      }
+      // the CTAs that hold parts of a split (tail) item
+      const int r_tail = item - wk.base;
+      const int c_lo = whole ? 0 : unit_owner(wk.U, (int64_t)r_tail * nks, wk.Gs);
+      const int c_hi = whole ? -1 : unit_owner(wk.U, (int64_t)r_tail * nks + nks - 1, wk.Gs);
+      // column chunk ch of the full Gram tile for this thread's row
+      auto load_chunk = [&](int ch, float (&g)[32]) {
+        if (whole) {
+          tmem_ld32(taddr + ch * 32, g);
+          if (ch == TN / 32 - 1) {
+            tc_fence_before();
+            mbar_arrive(&sh.tempty[buf]);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) g[i] = 0.0f;
+          for (int c = c_lo; c <= c_hi; ++c) {
+            if (unit_start(wk.U, c, wk.Gs) == unit_start(wk.U, c + 1, wk.Gs)) continue;   // no tail units
+            const float* pp = s.skpart + part_slot(wk.U, nks, wk.Gs, c, r_tail) * (TN * TM);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) g[i] += __ldcg(pp + (ch * 32 + i) * TM + rloc);
+          }
+        }
+      };
+      if constexpr (MODE == 0) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int ch = 0; ch < TN / 32; ++ch) {
+          float g[32];
+          load_chunk(ch, g);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int c = ch * 32 + i;
+            const float4 m = meta[c];
+            const float kv = kernel_value<KIND>(g[i], xn, m.x, xi == __float_as_int(m.z), negc, coef0, degree);
+            acc = (c < ncols) ? fmaf(m.y, kv, acc) : acc;
+          }
+        }
+        if (row < rows) s.part[(int64_t)t * s.bpad + row] = acc;
+      } else {
+        float fA = 0.0f, fB = 0.0f, fE = 0.0f;
+#pragma unroll
+        for (int ch = 0; ch < TN / 32; ++ch) {
+          float g[32];
+          load_chunk(ch, g);
+#pragma unroll
           for (int i = 0; i < 32; ++i) {
             const float4 m = meta[ch * 32 + i];
             const float kv = kernel_value<KIND>(g[i], xn, m.x, xi == __float_as_int(m.z), negc, coef0, degree);
-            const float wk = m.y * kv;
-            fA += (m.w < 1.5f) ? wk : 0.0f;
-            fB += (m.w < 0.5f) ? wk : 0.0f;
+            const float wk_ = m.y * kv;
+            fA += (m.w < 1.5f) ? wk_ : 0.0f;
+            fB += (m.w < 0.5f) ? wk_ : 0.0f;
             fE += (m.w > 1.5f && m.w < 2.5f) ? kv : 0.0f;
           }
         }
@@ -456,7 +580,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           sM += __shfl_xor_sync(0xffffffffu, sM, o);
         }
         if (lane == 0) {
-          double* out = s.wpart + ((int64_t)w * 4 + (warp - 2)) * 4;
+          double* out = s.wpart + ((int64_t)item * 4 + q) * 4;
           out[0] = sA; out[1] = sB; out[2] = sE; out[3] = sM;
         }
       }

@@ -130,6 +130,8 @@ struct Dev {
   int32_t* wpair_first; // [k]
   int32_t* wpair_cnt;   // [k]
   double* wpart;     // [max_pairs][4 slots][4 sums]: A, Bdd, E, M partials per tile
+  float* skpart;     // tcgen05 stream-K: [num_sms][2][128 cols][128 rows] partial accumulators
+  int32_t* skcnt;    // tcgen05 stream-K: [items][4] slices delivered per 32-row quadrant
   int64_t* iter;     // [1] next iteration number
   int32_t* status;   // [1] sticky device status bits
   int64_t* stats;    // [3] steps, support rows, tiles

@@ -248,3 +248,33 @@ def test_graph_replay_matches_eager(precision):
         np.testing.assert_array_equal(np.asarray(a[key]), np.asarray(b[key]), err_msg=key)
     for run in runs:
         run.close()
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "bf16"])
+@pytest.mark.parametrize("d", [200, 784])
+def test_teacher_forced_wide_rows_tensor_path(precision, d):
+    """Wide rows give the tcgen05 passes several K-slices per tile (d=784: 13), so the
+    stream-K schedule splits tiles across CTAs. The split parts are merged by the last
+    CTA to deliver, in both the distance pass and the window pass."""
+    X, _ = inputs.image_like(3000, seed=7, d=d, classes=8)
+    p = Pair(X, k=8, b=512, tau=120, precision=precision)
+    batches = inputs.batch_stream(len(X), 512, 6, seed=23)
+    teacher_forced(p, batches, cn_rtol=1e-6 if precision == "bf16x3" else 5e-3)
+    p.close()
+
+
+def test_image_like_full_size_split_bf16():
+    """The MNIST-shaped workload at full size on the tensor-core path (split BF16)."""
+    X, _ = inputs.image_like(70000, seed=12345)
+    p = Pair(X, k=10, b=1024, tau=200, precision="bf16x3")
+    for B in inputs.batch_stream(len(X), 1024, 3, seed=41):
+        rec = p.ora.step(B)
+        d, a, f = p.gpu_step(B)
+        assert dist_rel_err(d, rec.dist) <= DIST_TOL["bf16x3"]
+        ok, _ = near_tie_ok(a, rec, p.abs_tol(rec))
+        assert ok
+        if not np.array_equal(a, rec.assign):
+            return                       # a certified near-tie flipped; trajectories diverge
+        assert abs(f - rec.batch_objective) <= OBJ_TOL * rec.batch_objective
+    compare_states(p.gpu.get_state(), p.ora.state(), cn_rtol=1e-6)
+    p.close()
