@@ -38,6 +38,7 @@ METRIC = "batch-point×center distances/s per iteration on 1 GB300 (BF16 vs FP32
 UNIT = "distances/s"
 PREP_ITERS = 20         # iterations that bring the windows to their steady-state size
 DTYPES = {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}
+OBJ_BAR = 1e-4          # objective relative error a form must meet to count (the metric's bar)
 
 
 def workload_desc(w) -> str:
@@ -111,6 +112,22 @@ def dist_env():
     return world, rank, local
 
 
+def reduce_max(value: float, world: int, device) -> float:
+    """Max over ranks (the slowest replica sets the whole job's time)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(b: int, k: int, steps: int, world: int, max_seconds: float) -> float:
+    """Distances per second of all replicas together: world * b * k * steps / max time."""
+    return world * b * k * steps / max_seconds
+
+
 def make_workload(seed_offset: int = 0):
     X, _ = WORKLOAD.make()
     sigma = inputs.median_sigma(X, seed=1)
@@ -120,19 +137,49 @@ def make_workload(seed_offset: int = 0):
 
 
 # ------------------------------------------------------------------ oracle leg
-def oracle_sample(X, kappa, init, budget_s: float = 20.0, prep: int = 4):
-    """FP64 oracle iterations of the same workload: `prep` untimed iterations
-    from the same start (the support grows towards its steady size), then
-    timed iterations until `budget_s` is spent. Returns (b*k/s median, cores, desc)."""
+def oracle_leg(X, kappa, init, forms, Xd, budget_s: float, prep: int = 4):
+    """The FP64 oracle on the host cores, rank 0 only. It is the CPU baseline
+    and also the accuracy check of every GPU form.
+
+    The oracle runs the workload from the same start on a seeded batch stream.
+    After `prep` iterations its state is loaded into a fresh GPU context of each
+    form (kkm_set_state), and both sides take the next iteration on the same
+    batch. The GPU's f_B and distances are compared with the oracle's
+    (teacher-forced step). The oracle then keeps iterating until `budget_s` of
+    timed iterations is spent; its median b*k per second is the CPU baseline.
+    """
+    import torch
     import oracle
+    from paper_2410_05902_gb300.kkm import KKM
     w = WORKLOAD
-    ora = oracle.MiniBatchKernelKMeans(X, w.k, oracle.Kernel(oracle.GAUSSIAN, kappa), w.b, init, tau=w.tau)
-    batches = inputs.batch_stream(w.n, w.b, 200, seed=77)
+    X64 = X.astype(np.float64)
+    ora = oracle.MiniBatchKernelKMeans(X64, w.k, oracle.Kernel(oracle.GAUSSIAN, kappa), w.b, init, tau=w.tau)
+    batches = inputs.batch_stream(w.n, w.b, 400, seed=77)
     for i in range(prep):
         ora.step(batches[i])
-    times, S = [], []
+    state = ora.state()
+    S_check = int(state["rows_per_center"].sum())
+    t0 = time.perf_counter()
+    rec = ora.step(batches[prep])
+    times = [time.perf_counter() - t0]
+    acc = {}
+    bi = torch.from_numpy(batches[prep].astype(np.int32)).to(Xd.device)
+    fa = torch.from_numpy(rec.assign.astype(np.int32)).to(Xd.device)
+    for form in forms:
+        run = KKM(Xd, w.k, w.b, kernel="gaussian", param=kappa, tau=w.tau, precision=form, init_idx=init)
+        run.set_state(state)
+        dist_out = torch.empty((w.b, w.k), dtype=torch.float32, device=Xd.device)
+        obj = torch.empty(1, dtype=torch.float64, device=Xd.device)
+        run.step(bi, fa, None, dist_out, obj)
+        run.sync()
+        d = dist_out.cpu().numpy().astype(np.float64)
+        f = float(obj.cpu()[0])
+        acc[form] = {"obj_rel_err": abs(f - rec.batch_objective) / abs(rec.batch_objective),
+                     "dist_rel_err": float(np.max(np.abs(d - rec.dist)) / np.max(np.abs(rec.dist)))}
+        run.close()
+    i = prep + 1
     t_start = time.perf_counter()
-    i = prep
+    S = [S_check]
     while time.perf_counter() - t_start < budget_s and i < len(batches):
         S.append(sum(len(ora.center(j).idx) for j in range(w.k)))
         t0 = time.perf_counter()
@@ -142,7 +189,9 @@ def oracle_sample(X, kappa, init, budget_s: float = 20.0, prep: int = 4):
     t = statistics.median(times)
     desc = (f"FP64 oracle, full iterations {prep + 1}-{i} of the same workload from the same start "
             f"(support S {min(S)}-{max(S)} rows), median over {len(times)} iterations")
-    return w.b * w.k / t, oracle.kernels.num_threads(), desc
+    check = (f"teacher-forced iteration {prep + 1} (support S={S_check}): oracle state loaded into each "
+             "GPU form, same batch, f_B and normwise distance error against the FP64 oracle")
+    return w.b * w.k / t, oracle.kernels.num_threads(), desc, acc, check
 
 
 def run_reference(args):
@@ -190,23 +239,15 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------- GPU leg
-def run_ours(args):
+def time_form(form, args, X, Xd, kappa, init, rank, world, dev, barrier):
+    """Timed region, distance-kernel timing and end-to-end pass of one precision form."""
     import torch
     import torch.distributed as dist
-
+    from paper_2410_05902_gb300 import kkm as kb
     from paper_2410_05902_gb300.kkm import KKM
-
-    world, rank, local = dist_env()
-    if world > 1:
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", init_method="env://")
-    dev = torch.device("cuda", local if world > 1 else 0)
-    torch.cuda.set_device(dev)
     w = WORKLOAD
-    X, kappa, init = make_workload(seed_offset=rank)
-    Xd = torch.from_numpy(X).to(dev)
     stream = torch.cuda.current_stream(dev)
-    run = KKM(Xd, w.k, w.b, kernel="gaussian", param=kappa, tau=w.tau, precision=args.precision,
+    run = KKM(Xd, w.k, w.b, kernel="gaussian", param=kappa, tau=w.tau, precision=form,
               seed=1000 + rank, init_idx=init)
     for _ in range(PREP_ITERS):
         run.step()
@@ -216,12 +257,6 @@ def run_ours(args):
     run.sync()
     run.stats(reset=True)
     run.launches(reset=True)
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-
     clocks = Clocks(dev.index) if rank == 0 else None
     barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -234,24 +269,18 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop() if clocks else None
     launches = run.launches(reset=True)
-    steps_done, srows, tiles = run.stats(reset=True)
+    steps_done, srows, _ = run.stats(reset=True)
     # per-launch time of the distance kernel: CUDA events on the context's
     # stream around each launch, over an eager pass of the same workload right
     # after the timed region (events inside a replayed graph keep only the last replay)
     run.timing(True)
     run.timing_read(reset=True)
-    kt_steps = min(args.steps, 500)
-    for _ in range(kt_steps):
+    for _ in range(min(args.steps, 500)):
         run.step()
     n_rec, k_ms = run.timing_read(reset=True)
     run.timing(False)
     run.sync()
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * w.b * w.k * args.steps / (ms / 1e3)
-
+    ms = reduce_max(ms, world, dev)
     # end to end through the public host-buffer call: index upload, step,
     # assignment and objective download, synchronise, every step
     e2e_steps = max(50, min(args.steps, 2000))
@@ -260,67 +289,114 @@ def run_ours(args):
     idx_np = pinned_idx.numpy()
     a_out = torch.empty(w.b, dtype=torch.int32, pin_memory=True).numpy()
     o_out = torch.empty(1, dtype=torch.float64, pin_memory=True).numpy()
-    from paper_2410_05902_gb300 import kkm as kb
-    for s in range(3):
-        kb.kkm_step_host(run.ctx, idx_np[s], a_out, o_out)
+    for s_ in range(3):
+        kb.kkm_step_host(run.ctx, idx_np[s_], a_out, o_out)
     barrier()
     t0 = time.perf_counter()
-    for s in range(e2e_steps):
-        kb.kkm_step_host(run.ctx, idx_np[s], a_out, o_out)
-    t_e2e = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e_value = world * w.b * w.k * e2e_steps / t_e2e
+    for s_ in range(e2e_steps):
+        kb.kkm_step_host(run.ctx, idx_np[s_], a_out, o_out)
+    t_e2e = reduce_max(time.perf_counter() - t0, world, dev)
+    run.close()
+    return {"ms": ms, "value": whole_job_value(w.b, w.k, args.steps, world, ms / 1e3), "clocks": clk,
+            "launches": launches, "S": srows / max(steps_done, 1), "kernel_ms": k_ms / max(n_rec, 1),
+            "kernel_launches": n_rec, "e2e_value": whole_job_value(w.b, w.k, e2e_steps, world, t_e2e),
+            "e2e_steps": e2e_steps}
 
+
+def roofline(form, S, kernel_ms, n_rec):
+    w = WORKLOAD
+    peaks = load_peaks()
+    flops = 2.0 * w.b * S * w.d          # algorithmic Gram flops of one distance-pass launch
+    achieved = flops / (kernel_ms / 1e3) / 1e12
+    if form == "fp32":
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "kernel": "k_dist_simt<FP32> (FP32 FFMA Gram + kernel values + weighted sums)",
+                "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 flop x max SM clock (derived)"}
+    else:
+        peak = peaks["bf16_tflops"]
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "kernel": f"k_dist_tc ({form}: tcgen05 Gram + kernel values + weighted sums)",
+                "peak_source": f"bf16_tflops burst, {peaks['source']}"}
+    roof["traffic"] = measured_traffic(form)
+    roof["flops_per_launch"] = flops
+    roof["avg_launch_ms"] = kernel_ms
+    roof["launches_timed"] = n_rec
+    roof["timing"] = ("CUDA events on the context stream around each distance-pass launch, "
+                      f"{n_rec} eager steps of the same workload right after the timed region")
+    return roof
+
+
+def measured_traffic(form):
+    """DRAM bytes per launch of the distance kernel from the committed ncu
+    summary, when it was taken on the current kernel source (else None)."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic_image_distance_pass.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    src = os.path.join(ROOT, "paper_2410_05902_gb300", "csrc",
+                       "kkm_gram_simt.cu" if form == "fp32" else "kkm_gram_tc.cu")
+    with open(src, "rb") as f:
+        digest = hashlib.sha256(f.read()).hexdigest()
+    e = d.get(form)
+    if not e or e.get("source_sha256") != digest:
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world, rank, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    w = WORKLOAD
+    X, kappa, init = make_workload(seed_offset=rank)
+    Xd = torch.from_numpy(X).to(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    forms = ["fp32", "bf16x3", "bf16"] if args.precision == "auto" else [args.precision]
+    res = {f: time_form(f, args, X, Xd, kappa, init, rank, world, dev, barrier) for f in forms}
     if rank == 0:
-        peaks = load_peaks()
-        S = srows / max(steps_done, 1)
-        avg_ms = k_ms / max(n_rec, 1)
-        flops = 2.0 * w.b * S * w.d          # algorithmic Gram flops of one distance-pass launch
-        achieved = flops / (avg_ms / 1e3) / 1e12
-        if args.precision == "fp32":
-            sms = 152
-            peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None,
-                    "kernel": "k_dist_simt<FP32> (FP32 FFMA Gram + exp + weighted sums)",
-                    "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 x max SM clock (derived)"}
-        else:
-            peak = peaks["bf16_tflops"]
-            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None,
-                    "kernel": "distance pass (tcgen05 Gram + exp + weighted sums)",
-                    "peak_source": f"bf16_tflops burst, {peaks['source']}"}
-        roof["flops_per_launch"] = flops
-        roof["avg_launch_ms"] = avg_ms
-        roof["launches_timed"] = n_rec
-        roof["timing"] = ("CUDA events on the context stream around each distance-pass launch, "
-                          f"{n_rec} eager steps of the same workload right after the timed region")
-        Xs, kappa_s, init_s = X, kappa, init
-        cpu_v, cores, desc = oracle_sample(Xs.astype(np.float64), kappa_s, init_s, budget_s=args.oracle_budget)
+        cpu_v, cores, desc, acc, check = oracle_leg(X, kappa, init, forms, Xd, args.oracle_budget)
+        ok = [f for f in forms if acc[f]["obj_rel_err"] <= OBJ_BAR]
+        chosen = max(ok, key=lambda f: res[f]["value"]) if ok else max(forms, key=lambda f: res[f]["value"])
+        r = res[chosen]
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision],
-            "data": "synthetic",
-            "config": {"workload": workload_desc(w), "precision": args.precision,
-                       "support_rows_S": S, "state_prep_iters": PREP_ITERS,
+            "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[chosen], "data": "synthetic",
+            "config": {"workload": workload_desc(w), "precision": chosen,
+                       "form_rule": f"fastest form with objective error <= {OBJ_BAR} against the FP64 oracle",
+                       "meets_obj_bar": chosen in ok, "support_rows_S": r["S"],
+                       "state_prep_iters": PREP_ITERS,
                        "l2": "inputs larger than L2: X is 220 MB (L2 129 MB); the method's support "
                              "state stays resident between iterations",
                        "parallelism": f"replicas x{world} (independent runs, no collective)",
                        "step_launch": "eager kernel launches" if args.no_graph else "CUDA graph replay"},
-            "roofline": roof,
+            "forms": {f: {"value": res[f]["value"], "ms_per_step": res[f]["ms"] / args.steps,
+                          "dist_kernel_ms": res[f]["kernel_ms"], "e2e": res[f]["e2e_value"], **acc[f]}
+                      for f in forms},
+            "accuracy_check": check,
+            "roofline": roofline(chosen, r["S"], r["kernel_ms"], r["kernel_launches"]),
             "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * w.b,
-                    "d2h_bytes_per_step": 4 * w.b + 8, "steps": e2e_steps,
+            "e2e": {"value": r["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": 4 * w.b,
+                    "d2h_bytes_per_step": 4 * w.b + 8, "steps": r["e2e_steps"],
                     "call": "kkm_step_host (pinned host batch indices in, assignments and f_B out, synchronised)"},
-            "gpu_launches": launches,
-            "clocks": clk,
+            "gpu_launches": r["launches"],
+            "clocks": r["clocks"],
         }
         print(json.dumps(line))
-    run.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -328,10 +404,11 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "bf16", "bf16x3"], default="fp32")
+    ap.add_argument("--precision", choices=["auto", "fp32", "bf16", "bf16x3"], default="auto",
+                    help="auto: time every form, report the fastest that meets the objective bar")
     ap.add_argument("--oracle-budget", type=float, default=20.0)
     ap.add_argument("--no-graph", action="store_true", help="launch every kernel instead of replaying a graph")
     args = ap.parse_args()

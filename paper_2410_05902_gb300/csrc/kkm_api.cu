@@ -41,7 +41,7 @@ struct kkm_ctx {
   std::vector<cudaEvent_t> ev;
   int64_t ev_used = 0;
   int64_t launches = 0;       // kernels launched (host count)
-  alignas(64) unsigned char tmaps[256];   // TMA descriptors of the tensor-core pass
+  alignas(64) unsigned char tmaps[512];   // TMA descriptors of the tensor-core passes (3 x 128 B)
   // CUDA graph of one step (kkm_graph_enable): captured on a private stream
   // per set of kkm_step pointer arguments and launched on `stream`
   bool graph_on = false;
@@ -216,12 +216,13 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
     c->use_tc = (maj == 10 && min == 3) && kkm::tc_available();
   }
   s.tn = c->use_tc ? 128 : 64;
-  s.pair_tile = c->use_tc ? 128 : 64;
-  const int64_t T = s.pair_tile;   // window-pass tile
+  s.pair_rows = c->use_tc ? 128 : 64;
+  s.pair_cols = 64;
+  const int64_t TR = s.pair_rows, TC = s.pair_cols;   // window-pass tile
   s.max_tiles = (int32_t)((int64_t)k * ((wmax + s.tn - 1) / s.tn + 1));
   const int64_t smax = (int64_t)k * wmax;
-  const int64_t p1 = ((smax + T - 1) / T + k) * ((wmax + b + T - 1) / T);
-  const int64_t p2 = ((b + T - 1) / T + k) * ((b + T - 1) / T + k);
+  const int64_t p1 = ((smax + TR - 1) / TR + k) * ((wmax + b + TC - 1) / TC);
+  const int64_t p2 = ((b + TR - 1) / TR + k) * ((b + TC - 1) / TC + k);
   if (p1 + p2 >= (int64_t(1) << 31)) {
     c->err = "window pass would need too many tiles";
     return bail(KKM_EINVAL);
@@ -250,7 +251,7 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
   ALLOC(s.w64, srows);
   ALLOC(s.w32, srows);
   ALLOC(s.head, k); ALLOC(s.tail, k); ALLOC(s.c1, k); ALLOC(s.wsum, k); ALLOC(s.cnorm, k);
-  ALLOC(s.cnorm32, k); ALLOC(s.done_ctr, 1); ALLOC(s.objpart, k);
+  ALLOC(s.cnorm32, k); ALLOC(s.cmpart, (size_t)k * 32);
   ALLOC(s.blk_iter, (size_t)k * s.nbcap); ALLOC(s.blk_cnt, (size_t)k * s.nbcap);
   ALLOC(s.blk_first, k); ALLOC(s.blk_num, k);
   ALLOC(s.assign, s.bpad); ALLOC(s.mind, s.bpad); ALLOC(s.inner_a, s.bpad);
@@ -260,12 +261,7 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
   ALLOC(s.part, (size_t)s.max_tiles * s.bpad);
   ALLOC(s.wpairs, s.max_pairs); ALLOC(s.nwpairs, 1); ALLOC(s.wpair_first, k); ALLOC(s.wpair_cnt, k);
   ALLOC(s.wpart, (size_t)s.max_pairs * 16);
-  if (c->use_tc) {
-    const int64_t max_items = std::max<int64_t>((int64_t)(s.bpad / 128) * s.max_tiles, s.max_pairs);
-    ALLOC(s.skpart, (size_t)s.num_sms * 2 * 128 * 128);
-    ALLOC(s.skcnt, (size_t)max_items * 4);
-  }
-  ALLOC(s.iter, 1); ALLOC(s.status, 1); ALLOC(s.stats, 3); ALLOC(s.obj, 1); ALLOC(s.s_old, 1);
+  ALLOC(s.iter, 1); ALLOC(s.status, 1); ALLOC(s.stats, 3); ALLOC(s.obj, 1);
   ALLOC(c->d_init_idx, k);
   ALLOC(c->d_hbatch, b); ALLOC(c->d_hassign, b); ALLOC(c->d_hobj, 1);
   c->objpart_len = 1024;
@@ -323,11 +319,11 @@ static kkm_status enqueue_step(kkm_ctx* c, cudaStream_t st, const int32_t* batch
     ++c->ev_used;
   }
   KKM_CU(kkm::launch_argmin(s, s.b, forced_assign, assign_out, nullptr, dist_out, true, st), "argmin");
-  KKM_CU(kkm::launch_sort_plan(s, st), "sort/plan");
+  KKM_CU(kkm::launch_sort_plan(s, batch_obj_out, st), "sort/plan");
   KKM_CU(kkm::launch_move(s, st), "row moves");
   if (c->use_tc) KKM_CU(kkm::launch_wgram_tc(s, c->tmaps, st), "window Gram (tcgen05)");
   else KKM_CU(kkm::launch_wgram(s, st), "window Gram");
-  KKM_CU(kkm::launch_finalize(s, batch_obj_out, st), "finalize");
+  KKM_CU(kkm::launch_finalize(s, st), "finalize");
   return KKM_OK;
 }
 

@@ -1,7 +1,9 @@
-// tcgen05 / TMA form of the distance pass (BF16 and split-BF16 Gram products).
+// tcgen05 / TMA form of the two Gram passes (BF16 and split-BF16 products).
 //
-// One persistent CTA per SM walks the work items (128-row batch tile, 128-row
-// support tile of one center). For each item:
+// One persistent CTA per SM walks the work items round-robin. In the distance
+// pass (mode 0) an item is (128-row batch tile, 128-row support tile of one
+// center); in the window pass (mode 1) it is (128 support rows, 64 support
+// rows) of one center. For each item:
 //   G = X_B Y^T           tcgen05.mma kind::f16 (BF16 x BF16 -> FP32 in TMEM),
 //                         operands streamed by TMA through a 6-stage ring of
 //                         128B-swizzled shared-memory slices (64 columns each)
@@ -24,30 +26,31 @@
 namespace kkm {
 namespace {
 
-constexpr int TM = 128;                         // batch rows per tile = TMEM lanes
-constexpr int TN = 128;                         // support rows per tile = accumulator columns
+constexpr int TM = 128;                         // A rows per tile = TMEM lanes
 constexpr int KS = 64;                          // BF16 columns per slice (one 128-byte swizzle row)
-constexpr int A_BYTES = TM * KS * 2;            // 16 KB: one operand tile of one slice
-constexpr int B_BYTES = TN * KS * 2;            // 16 KB
-constexpr int RING_BYTES = 6 * (A_BYTES + B_BYTES);   // 192 KB of shared memory for the operand ring
-constexpr int STAGES = 6;                       // most stages any form uses
-// BF16:   a stage is one 64-column slice (A, B): 32 KB, 6 stages, 4 MMAs.
+constexpr int A_BYTES = TM * KS * 2;            // 16 KB: the A tile of one slice
+constexpr int RING_BYTES = 192 * 1024;          // shared memory for the operand ring
+constexpr int STAGES = 8;                       // most stages any variant uses
+// TNV = support rows per tile (B rows = accumulator columns): 128 or 64.
+// BF16:   a stage is one 64-column slice (A, B): 4 MMAs.
 // BF16X3: a stage is one 64-column slice of all four operand tiles
-//         (A_hi, A_lo, B_hi, B_lo): 64 KB, 3 stages, 12 MMAs (hi.hi, hi.lo, lo.hi),
-//         so hi tiles are fetched once per slice instead of twice.
-template <bool X3> struct Ring {
-  static constexpr int stages = X3 ? 3 : 6;
-  static constexpr int bytes = X3 ? 4 * A_BYTES : A_BYTES + B_BYTES;
+//         (A_hi, A_lo, B_hi, B_lo): 12 MMAs (hi.hi, hi.lo, lo.hi), so the hi
+//         tiles are fetched once per slice instead of twice.
+template <bool X3, int TNV> struct Ring {
+  static constexpr int b_bytes = TNV * KS * 2;
+  static constexpr int bytes = X3 ? 2 * (A_BYTES + b_bytes) : A_BYTES + b_bytes;
+  static constexpr int stages = RING_BYTES / bytes;   // 3, 4, 6 or 8
 };
 constexpr int NTHREADS = 192;
-constexpr uint32_t TMEM_COLS = 2 * TN;
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;   // 2 s per wait
 
 // Instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1),
 // A and B BF16 (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0),
 // N >> 3 in bits 17-22, M >> 4 in bits 24-28.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
-                           ((uint32_t)(TM >> 4) << 24);
+template <int N>
+__host__ __device__ constexpr uint32_t idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
 
 struct Shared {
   uint64_t full[STAGES];
@@ -57,7 +60,7 @@ struct Shared {
   uint64_t mma_done;
   uint32_t tmem_base;
   uint32_t pad;
-  float4 meta[4][TN];                           // per epilogue warp: (||y||^2, w, yi, -)
+  float4 meta[4][128];                          // per epilogue warp: (||y||^2, w, yi, class)
 };
 
 constexpr int SMEM_BYTES = 1024 + RING_BYTES + (int)sizeof(Shared);
@@ -137,11 +140,12 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accum)
+      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
       : "memory");
 }
 
@@ -195,7 +199,8 @@ __device__ __forceinline__ float kernel_value(float g, float xn, float yn, bool 
 
 // A window-pass tile (mode 1): rows of the support store of center j, as
 // positions inside its region. Kind 0 pairs the dropped prefix D with the old
-// window plus the new block; kind 1 pairs the new block with itself.
+// window plus the new block; kind 1 pairs the new block with itself. Row tiles
+// are 128 rows (TM), column tiles TNV rows.
 struct PairTile {
   int64_t base;      // first row of the center's region
   int rs, rrem;      // first row position, rows left in the row range from rs
@@ -203,6 +208,7 @@ struct PairTile {
   int kind, head_new, tail_c;
 };
 
+template <int TNV>
 __device__ __forceinline__ PairTile pair_tile(const Dev& s, int w) {
   const WPair pr = s.wpairs[w];
   const Plan P = s.plan[pr.j];
@@ -213,8 +219,8 @@ __device__ __forceinline__ PairTile pair_tile(const Dev& s, int w) {
   else { r0 = P.tail_c; rn = P.cnt; c0 = P.tail_c; cn = P.cnt; }
   t.rs = r0 + pr.rt * TM;
   t.rrem = rn - pr.rt * TM;
-  t.cs = c0 + pr.ct * TN;
-  t.crem = cn - pr.ct * TN;
+  t.cs = c0 + pr.ct * TNV;
+  t.crem = cn - pr.ct * TNV;
   t.kind = pr.kind;
   t.head_new = P.head_new;
   t.tail_c = P.tail_c;
@@ -223,90 +229,25 @@ __device__ __forceinline__ PairTile pair_tile(const Dev& s, int w) {
 
 // MODE 0: distance pass (A = batch tile, B = support tile, one FP32 partial per row).
 // MODE 1: window pass (A and B = support rows of one center, four FP64 sums per warp).
-// Schedule: data-parallel waves plus stream-K for the tail (Osama et al.,
-// "Stream-K: Work-centric parallel decomposition for dense matrix
-// multiplication", PPoPP 2023). With T items and G CTAs, every CTA first
-// takes floor(T/G) whole items round-robin. The remaining T mod G items are
-// cut into their U = (T mod G) * nks slice units, and the units are split into
-// G contiguous ranges of near-equal length, one per CTA. So every SM gets the
-// same amount of MMA work. An item whose slices span several CTAs ("split") is
-// finished by whichever CTA is the last to deliver its part: every part
-// spills its partial accumulator to global scratch and adds its slice count to
-// the item's arrival counter (one counter per 32-row quadrant, so the four
-// epilogue warps never wait for one another). The warp that completes the
-// count sums all parts and runs the epilogue. Nobody waits on another CTA.
-__device__ __forceinline__ int64_t unit_start(int64_t U, int c, int G) { return U * c / G; }
-
-// The CTA whose stream-K range holds unit u (every such range is non-empty).
-__device__ int unit_owner(int64_t U, int64_t u, int G) {
-  int c = (int)((u * G) / U);
-  while (c + 1 < G && unit_start(U, c + 1, G) <= u) ++c;
-  while (c > 0 && unit_start(U, c, G) > u) --c;
-  return c;
-}
-
-// Partial accumulator slot of CTA c for tail item r (counted from the first
-// tail item): 0 for the first item of the CTA's range, 1 for its last.
-__device__ __forceinline__ int64_t part_slot(int64_t U, int nks, int G, int c, int r) {
-  const int first_r = (int)(unit_start(U, c, G) / nks);
-  return (int64_t)c * 2 + (r == first_r ? 0 : 1);
-}
-
-// The work of one CTA: whole items first, then its stream-K range of tail
-// units. The tail goes to Gs = min(G, tail items * pmax) CTAs, so a tail item
-// is split into at most about pmax parts (pmax = 1: whole items only), which
-// bounds the partial accumulators a merge has to read.
-struct Work {
-  int nks, G, c, full, base, Gs;   // base = first tail item = full * G
-  int64_t U, ub, ue, u;
-  int i;
-  __device__ Work(int total, int nks_, int G_, int c_, int pmax) : nks(nks_), G(G_), c(c_) {
-    full = total / G;
-    base = full * G;
-    const int tail = total - base;
-    Gs = tail * pmax < G ? tail * pmax : G;
-    if (Gs < 1) Gs = 1;
-    U = (int64_t)tail * nks;
-    ub = c < Gs ? unit_start(U, c, Gs) : U;
-    ue = c < Gs ? unit_start(U, c + 1, Gs) : U;
-    u = ub;
-    i = 0;
-  }
-  // next part: item, slice range [s0, s1), and whether it is the range's first tail item
-  __device__ bool next(int& item, int& s0, int& s1, bool& first_tail) {
-    if (i < full) {
-      item = c + i * G;
-      s0 = 0;
-      s1 = nks;
-      first_tail = false;
-      ++i;
-      return true;
-    }
-    if (u >= ue) return false;
-    const int r = (int)(u / nks);
-    item = base + r;
-    s0 = (int)(u - (int64_t)r * nks);
-    const int64_t left = ue - u;
-    s1 = (int64_t)nks < s0 + left ? nks : (int)(s0 + left);
-    first_tail = (u == ub);
-    u += s1 - s0;
-    return true;
-  }
-};
-
-template <int KIND, int MODE, bool X3>
+// Items are dealt round-robin to the persistent CTAs. Splitting a tile along
+// its columns needs no merge because both passes only sum over columns, so
+// narrower tiles (TNV = 64) are how the window pass gets enough items.
+template <int KIND, int MODE, bool X3, int TNV>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_dist_tc(Dev s, int rows, const __grid_constant__ CUtensorMap tmA,
               const __grid_constant__ CUtensorMap tmB) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   Shared& sh = *reinterpret_cast<Shared*>(smem + RING_BYTES);
-  constexpr int NST = Ring<X3>::stages;
-  constexpr int SB = Ring<X3>::bytes;
+  constexpr int NST = Ring<X3, TNV>::stages;
+  constexpr int SB = Ring<X3, TNV>::bytes;
+  constexpr int BB = Ring<X3, TNV>::b_bytes;
+  constexpr uint32_t TMEM_COLS = 2 * TNV;        // two accumulators (double buffering)
+  constexpr uint32_t IDESC = idesc<TNV>();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < STAGES; ++i) {
+    for (int i = 0; i < NST; ++i) {
       mbar_init(&sh.full[i], 1);
       mbar_init(&sh.empty[i], 1);
     }
@@ -332,34 +273,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int R = (rows + TM - 1) / TM;
   const int total = (MODE == 0) ? R * (*s.ntiles) : *s.nwpairs;
   const int nks = s.dp / KS;
-  const int G = gridDim.x;
-  // most parts a tail item is split into: the distance pass has enough items
-  // to keep whole ones, the window pass (few items) splits them in two
-  constexpr int PMAX = (MODE == 0) ? 1 : 2;
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
       bool ok = true;
       uint32_t it = 0;
-      Work wk(total, nks, G, blockIdx.x, PMAX);
-      int item, s0, s1;
-      bool ft;
-      while (ok && wk.next(item, s0, s1, ft)) {
+      for (int item = blockIdx.x; ok && item < total; item += gridDim.x) {
         int ya, yb;
         const CUtensorMap* am;
         if constexpr (MODE == 0) {
-          const int t = item / R, rt = item % R;
-          ya = rt * TM;
-          yb = s.tiles[t].row0;
+          ya = (item % R) * TM;
+          yb = s.tiles[item / R].row0;
           am = &tmA;
         } else {
-          const PairTile pt = pair_tile(s, item);
+          const PairTile pt = pair_tile<TNV>(s, item);
           ya = (int)(pt.base + pt.rs);
           yb = (int)(pt.base + pt.cs);
-          am = &tmB;
+          am = &tmA;   // mode 1 gets the 128-row support map as tmA
         }
-        for (int sl = s0; sl < s1; ++sl, ++it) {
+        for (int sl = 0; sl < nks; ++sl, ++it) {
           const int st = it % NST;
           const uint32_t ph = (it / NST) & 1u;
           if (!mbar_wait(&sh.empty[st], ph ^ 1u)) { ok = false; break; }
@@ -370,7 +303,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             tma_load_2d(a, am, &sh.full[st], x, ya);
             tma_load_2d(a + A_BYTES, am, &sh.full[st], s.dp + x, ya);
             tma_load_2d(a + 2 * A_BYTES, &tmB, &sh.full[st], x, yb);
-            tma_load_2d(a + 3 * A_BYTES, &tmB, &sh.full[st], s.dp + x, yb);
+            tma_load_2d(a + 2 * A_BYTES + BB, &tmB, &sh.full[st], s.dp + x, yb);
           } else {              // stage layout: A | B
             tma_load_2d(a, am, &sh.full[st], x, ya);
             tma_load_2d(a + A_BYTES, &tmB, &sh.full[st], x, yb);
@@ -387,34 +320,30 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (lane == 0) {
       bool ok = true;
       uint32_t it = 0, local = 0;
-      Work wk(total, nks, G, blockIdx.x, PMAX);
-      int item, s0, s1;
-      bool ft;
-      for (; ok && wk.next(item, s0, s1, ft); ++local) {
+      for (int item = blockIdx.x; ok && item < total; item += gridDim.x, ++local) {
         const uint32_t buf = local & 1u, bph = (local >> 1) & 1u;
         if (!mbar_wait(&sh.tempty[buf], bph ^ 1u)) { ok = false; break; }
         tc_fence_after();
-        const uint32_t d = tmem + buf * TN;
-        for (int sl = s0; sl < s1; ++sl, ++it) {
+        const uint32_t d = tmem + buf * TNV;
+        for (int sl = 0; sl < nks; ++sl, ++it) {
           const int st = it % NST;
           const uint32_t ph = (it / NST) & 1u;
           if (!mbar_wait(&sh.full[st], ph)) { ok = false; break; }
           tc_fence_after();
           const uint32_t a0 = smem_u32(smem + st * SB);
-          const uint32_t first = (sl == s0) ? 0u : 1u;
           if constexpr (X3) {
-            const uint32_t alo = a0 + A_BYTES, bhi = a0 + 2 * A_BYTES, blo = a0 + 3 * A_BYTES;
+            const uint32_t alo = a0 + A_BYTES, bhi = a0 + 2 * A_BYTES, blo = bhi + BB;
 #pragma unroll
             for (int k = 0; k < KS / 16; ++k) {
-              mma_bf16(d, sw128_desc(a0 + 32u * k), sw128_desc(bhi + 32u * k), (first | k) != 0 ? 1u : 0u);
-              mma_bf16(d, sw128_desc(a0 + 32u * k), sw128_desc(blo + 32u * k), 1u);
-              mma_bf16(d, sw128_desc(alo + 32u * k), sw128_desc(bhi + 32u * k), 1u);
+              mma_bf16(d, sw128_desc(a0 + 32u * k), sw128_desc(bhi + 32u * k), IDESC, (sl | k) != 0 ? 1u : 0u);
+              mma_bf16(d, sw128_desc(a0 + 32u * k), sw128_desc(blo + 32u * k), IDESC, 1u);
+              mma_bf16(d, sw128_desc(alo + 32u * k), sw128_desc(bhi + 32u * k), IDESC, 1u);
             }
           } else {
             const uint32_t b0 = a0 + A_BYTES;
 #pragma unroll
             for (int k = 0; k < KS / 16; ++k)
-              mma_bf16(d, sw128_desc(a0 + 32u * k), sw128_desc(b0 + 32u * k), (first | k) != 0 ? 1u : 0u);
+              mma_bf16(d, sw128_desc(a0 + 32u * k), sw128_desc(b0 + 32u * k), IDESC, (sl | k) != 0 ? 1u : 0u);
           }
           mma_commit(&sh.empty[st]);
         }
@@ -433,13 +362,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const float negc = s.negc, coef0 = (float)s.coef0;
     const int degree = s.degree;
     uint32_t local = 0;
-    Work wk(total, nks, G, blockIdx.x, PMAX);
-    int item, s0, s1;
-    bool is_first;
-    for (; wk.next(item, s0, s1, is_first); ++local) {
-      const bool whole = (s0 == 0 && s1 == nks);
+    for (int item = blockIdx.x; item < total; item += gridDim.x, ++local) {
       const uint32_t buf = local & 1u, bph = (local >> 1) & 1u;
-      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + buf * TN;
+      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + buf * TNV;
       // column metadata and row data first: their global loads overlap the MMAs
       int t = 0, row = 0, ncols = 0;
       float xn;
@@ -453,7 +378,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const Tile T = s.tiles[t];
         ncols = T.ncols;
 #pragma unroll
-        for (int c4 = 0; c4 < TN / 32; ++c4) {
+        for (int c4 = 0; c4 < TNV / 32; ++c4) {
           const int c = c4 * 32 + lane;
           const bool valid = c < T.ncols;
           const int64_t g = (int64_t)T.row0 + (valid ? c : 0);
@@ -464,9 +389,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         xn = s.xbn[rr];
         xi = s.xbi[rr];
       } else {
-        pt = pair_tile(s, item);
+        pt = pair_tile<TNV>(s, item);
 #pragma unroll
-        for (int c4 = 0; c4 < TN / 32; ++c4) {
+        for (int c4 = 0; c4 < TNV / 32; ++c4) {
           const int c = c4 * 32 + lane;
           const int qpos = pt.cs + c;
           const bool valid = c < pt.crem;
@@ -488,58 +413,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         break;
       }
       tc_fence_after();
-      if (!whole) {
-        // spill this part (column-major: for each column the 128 rows are contiguous)
-        float* mine = s.skpart + ((int64_t)blockIdx.x * 2 + (is_first ? 0 : 1)) * (TN * TM);
-#pragma unroll
-        for (int ch = 0; ch < TN / 32; ++ch) {
-          float g[32];
-          tmem_ld32(taddr + ch * 32, g);
-          if (ch == TN / 32 - 1) {
-            tc_fence_before();
-            mbar_arrive(&sh.tempty[buf]);
-          }
-#pragma unroll
-          for (int i = 0; i < 32; ++i) mine[(ch * 32 + i) * TM + rloc] = g[i];
-        }
-        __threadfence();
-        __syncwarp();
-        int prev = 0;
-        if (lane == 0) prev = atomicAdd(&s.skcnt[(int64_t)item * 4 + q], s1 - s0);
-        prev = __shfl_sync(0xffffffffu, prev, 0);
-        if (prev + (s1 - s0) != nks) continue;    // another CTA's part is still missing
-        if (lane == 0) s.skcnt[(int64_t)item * 4 + q] = 0;
-        __threadfence();
-      }
-      // the CTAs that hold parts of a split (tail) item
-      const int r_tail = item - wk.base;
-      const int c_lo = whole ? 0 : unit_owner(wk.U, (int64_t)r_tail * nks, wk.Gs);
-      const int c_hi = whole ? -1 : unit_owner(wk.U, (int64_t)r_tail * nks + nks - 1, wk.Gs);
-      // column chunk ch of the full Gram tile for this thread's row
-      auto load_chunk = [&](int ch, float (&g)[32]) {
-        if (whole) {
-          tmem_ld32(taddr + ch * 32, g);
-          if (ch == TN / 32 - 1) {
-            tc_fence_before();
-            mbar_arrive(&sh.tempty[buf]);
-          }
-        } else {
-#pragma unroll
-          for (int i = 0; i < 32; ++i) g[i] = 0.0f;
-          for (int c = c_lo; c <= c_hi; ++c) {
-            if (unit_start(wk.U, c, wk.Gs) == unit_start(wk.U, c + 1, wk.Gs)) continue;   // no tail units
-            const float* pp = s.skpart + part_slot(wk.U, nks, wk.Gs, c, r_tail) * (TN * TM);
-#pragma unroll
-            for (int i = 0; i < 32; ++i) g[i] += __ldcg(pp + (ch * 32 + i) * TM + rloc);
-          }
-        }
-      };
       if constexpr (MODE == 0) {
         float acc = 0.0f;
 #pragma unroll
-        for (int ch = 0; ch < TN / 32; ++ch) {
+        for (int ch = 0; ch < TNV / 32; ++ch) {
           float g[32];
-          load_chunk(ch, g);
+          tmem_ld32(taddr + ch * 32, g);
+          if (ch == TNV / 32 - 1) {
+            tc_fence_before();
+            mbar_arrive(&sh.tempty[buf]);
+          }
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
             const int c = ch * 32 + i;
@@ -552,16 +435,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       } else {
         float fA = 0.0f, fB = 0.0f, fE = 0.0f;
 #pragma unroll
-        for (int ch = 0; ch < TN / 32; ++ch) {
+        for (int ch = 0; ch < TNV / 32; ++ch) {
           float g[32];
-          load_chunk(ch, g);
+          tmem_ld32(taddr + ch * 32, g);
+          if (ch == TNV / 32 - 1) {
+            tc_fence_before();
+            mbar_arrive(&sh.tempty[buf]);
+          }
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
             const float4 m = meta[ch * 32 + i];
             const float kv = kernel_value<KIND>(g[i], xn, m.x, xi == __float_as_int(m.z), negc, coef0, degree);
-            const float wk_ = m.y * kv;
-            fA += (m.w < 1.5f) ? wk_ : 0.0f;
-            fB += (m.w < 0.5f) ? wk_ : 0.0f;
+            const float wk = m.y * kv;
+            fA += (m.w < 1.5f) ? wk : 0.0f;
+            fB += (m.w < 0.5f) ? wk : 0.0f;
             fE += (m.w > 1.5f && m.w < 2.5f) ? kv : 0.0f;
           }
         }
@@ -595,32 +482,38 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 }
 
-template <int KIND, int MODE, bool X3>
+template <int KIND, int MODE, bool X3, int TNV>
 cudaError_t launch_form(const Dev& s, const CUtensorMap& a, const CUtensorMap& b, int rows, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_dist_tc<KIND, MODE, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(k_dist_tc<KIND, MODE, X3, TNV>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  return launch_pdl(k_dist_tc<KIND, MODE, X3>, dim3(s.num_sms), dim3(NTHREADS), SMEM_BYTES, st, s, rows, a, b);
+  return launch_pdl(k_dist_tc<KIND, MODE, X3, TNV>, dim3(s.num_sms), dim3(NTHREADS), SMEM_BYTES, st, s, rows, a, b);
 }
 
-template <int KIND, int MODE>
-cudaError_t launch_kind(const Dev& s, const CUtensorMap& a, const CUtensorMap& b, int rows, cudaStream_t st) {
-  return s.form == FORM_BF16X3 ? launch_form<KIND, MODE, true>(s, a, b, rows, st)
-                               : launch_form<KIND, MODE, false>(s, a, b, rows, st);
-}
-
-template <int MODE>
+// maps: [0] batch rows, 128-row boxes; [1] support rows, 128-row boxes; [2] support rows, 64-row boxes
+template <int MODE, int TNV>
 cudaError_t launch_mode(const Dev& s, const void* maps_in, int rows, cudaStream_t st) {
-  const CUtensorMap* maps = static_cast<const CUtensorMap*>(maps_in);
+  const CUtensorMap* m = static_cast<const CUtensorMap*>(maps_in);
+  const CUtensorMap& a = (MODE == 0) ? m[0] : m[1];
+  const CUtensorMap& b = (TNV == 128) ? m[1] : m[2];
+  const bool x3 = s.form == FORM_BF16X3;
   switch (s.kind) {
-    case K_GAUSS: return launch_kind<K_GAUSS, MODE>(s, maps[0], maps[1], rows, st);
-    case K_LAPLACE: return launch_kind<K_LAPLACE, MODE>(s, maps[0], maps[1], rows, st);
-    case K_LINEAR: return launch_kind<K_LINEAR, MODE>(s, maps[0], maps[1], rows, st);
-    default: return launch_kind<K_POLY, MODE>(s, maps[0], maps[1], rows, st);
+    case K_GAUSS:
+      return x3 ? launch_form<K_GAUSS, MODE, true, TNV>(s, a, b, rows, st)
+                : launch_form<K_GAUSS, MODE, false, TNV>(s, a, b, rows, st);
+    case K_LAPLACE:
+      return x3 ? launch_form<K_LAPLACE, MODE, true, TNV>(s, a, b, rows, st)
+                : launch_form<K_LAPLACE, MODE, false, TNV>(s, a, b, rows, st);
+    case K_LINEAR:
+      return x3 ? launch_form<K_LINEAR, MODE, true, TNV>(s, a, b, rows, st)
+                : launch_form<K_LINEAR, MODE, false, TNV>(s, a, b, rows, st);
+    default:
+      return x3 ? launch_form<K_POLY, MODE, true, TNV>(s, a, b, rows, st)
+                : launch_form<K_POLY, MODE, false, TNV>(s, a, b, rows, st);
   }
 }
 
@@ -628,8 +521,8 @@ cudaError_t launch_mode(const Dev& s, const void* maps_in, int rows, cudaStream_
 
 bool tc_available() { return true; }
 
-// Tensor maps of the batch rows (A) and the support store (B): 2-D BF16
-// tensors of ld columns, boxes of 64 columns x 128 rows, 128-byte swizzle.
+// Tensor maps of the batch rows and the support store: 2-D BF16 tensors of ld
+// columns, boxes of 64 columns x 128 (or 64) rows, 128-byte swizzle.
 cudaError_t tc_prepare(Dev& s, void* maps_out) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
@@ -642,9 +535,9 @@ cudaError_t tc_prepare(Dev& s, void* maps_out) {
   }
   CUtensorMap* maps = static_cast<CUtensorMap*>(maps_out);
   const int64_t srows = (int64_t)s.k * s.cap + 256;
-  struct { void* base; uint64_t rows; uint32_t box_rows; } ops[2] = {
-      {s.xbh, (uint64_t)s.bpad, (uint32_t)TM}, {s.ybh, (uint64_t)srows, (uint32_t)TN}};
-  for (int i = 0; i < 2; ++i) {
+  struct { void* base; uint64_t rows; uint32_t box_rows; } ops[3] = {
+      {s.xbh, (uint64_t)s.bpad, 128u}, {s.ybh, (uint64_t)srows, 128u}, {s.ybh, (uint64_t)srows, 64u}};
+  for (int i = 0; i < 3; ++i) {
     cuuint64_t dims[2] = {(cuuint64_t)s.ld, (cuuint64_t)ops[i].rows};
     cuuint64_t strides[1] = {(cuuint64_t)s.ld * 2};
     cuuint32_t box[2] = {(cuuint32_t)KS, ops[i].box_rows};
@@ -659,11 +552,11 @@ cudaError_t tc_prepare(Dev& s, void* maps_out) {
 
 cudaError_t launch_dist_tc(const Dev& s, const void* maps, int rows, cudaStream_t st) {
   if (rows <= 0) return cudaSuccess;
-  return launch_mode<0>(s, maps, rows, st);
+  return launch_mode<0, 128>(s, maps, rows, st);
 }
 
 cudaError_t launch_wgram_tc(const Dev& s, const void* maps, cudaStream_t st) {
-  return launch_mode<1>(s, maps, 0, st);
+  return launch_mode<1, 64>(s, maps, 0, st);
 }
 
 }  // namespace kkm

@@ -80,7 +80,7 @@ struct Dev {
   int32_t num_sms;
   uint64_t seed;
   int32_t tn;        // support rows per distance tile
-  int32_t pair_tile; // rows per side of a window-pass tile (64 SIMT, 128 tcgen05)
+  int32_t pair_rows, pair_cols; // window-pass tile: row and column counts (64x64 SIMT, 128x64 tcgen05)
   int32_t bpad;      // rows of the batch buffers (>= b, multiple of 128)
   int32_t max_tiles, max_pairs;
   const float* X;
@@ -130,15 +130,11 @@ struct Dev {
   int32_t* wpair_first; // [k]
   int32_t* wpair_cnt;   // [k]
   double* wpart;     // [max_pairs][4 slots][4 sums]: A, Bdd, E, M partials per tile
-  float* skpart;     // tcgen05 stream-K: [num_sms][2][128 cols][128 rows] partial accumulators
-  int32_t* skcnt;    // tcgen05 stream-K: [items][4] slices delivered per 32-row quadrant
   int64_t* iter;     // [1] next iteration number
   int32_t* status;   // [1] sticky device status bits
   int64_t* stats;    // [3] steps, support rows, tiles
   double* obj;       // [1] last batch objective
-  double* objpart;   // [k] f_B partial sums, one slice of the batch per finalize warp
-  int32_t* s_old;    // [1] support rows of the current step's distance pass
-  int32_t* done_ctr; // [1] blocks of k_finalize that have finished (reset by the last)
+  float* cmpart;     // [k][32] FP32 lane partials of sum_{x in B_j} <phi(x), C_j>
 };
 
 // Programmatic dependent launch: every step kernel is launched so that it may
@@ -218,10 +214,10 @@ cudaError_t launch_gather_query(const Dev& s, const float* Q, int64_t ldq, int r
 cudaError_t launch_dist_simt(const Dev& s, int rows, cudaStream_t st);
 cudaError_t launch_argmin(const Dev& s, int rows, const int32_t* forced, int32_t* assign_out,
                           float* mind_out, float* dist_out, bool update, cudaStream_t st);
-cudaError_t launch_sort_plan(const Dev& s, cudaStream_t st);
+cudaError_t launch_sort_plan(const Dev& s, double* obj_out, cudaStream_t st);
 cudaError_t launch_move(const Dev& s, cudaStream_t st);
 cudaError_t launch_wgram(const Dev& s, cudaStream_t st);
-cudaError_t launch_finalize(const Dev& s, double* obj_out, cudaStream_t st);
+cudaError_t launch_finalize(const Dev& s, cudaStream_t st);
 cudaError_t launch_build_tiles(const Dev& s, cudaStream_t st);
 cudaError_t launch_init_centers(const Dev& s, const int32_t* init_idx, cudaStream_t st);
 cudaError_t launch_load_rows(const Dev& s, int32_t rows_total, cudaStream_t st);

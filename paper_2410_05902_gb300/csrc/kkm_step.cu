@@ -237,11 +237,13 @@ __global__ void k_argmin(Dev s, int rows, const int32_t* __restrict__ forced,
   }
 }
 
+__device__ void build_tiles_block(const Dev& s, int head, int size);
+
 // Single CTA of 1024 threads. Stable counting sort of the batch by center,
 // alpha_i^j, <C_j, cm(B_j)>, and the per-center window plan: compaction,
 // block push, the drops of Eq. (1), C_1 retirement, and the tile pairs of the
 // norm-recurrence Gram pass.
-__global__ void __launch_bounds__(1024) k_sort_plan(Dev s, int pair_tile) {
+__global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out) {
   KKM_GRID_DEP_WAIT();
   extern __shared__ __align__(16) unsigned char smem[];
   const int k = s.k, b = s.b, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -249,7 +251,8 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, int pair_tile) {
   int32_t* base = cnt + k;                  // [k]
   int32_t* tot = base + k;                  // [k]
   int32_t* coff = tot + k;                  // [k]
-  int16_t* sassign = (int16_t*)(coff + k);  // [b]   assignments (k <= 1024)
+  float* sinner = (float*)(coff + k);       // [b]   <phi(x), C_a> at the used assignment
+  int16_t* sassign = (int16_t*)(sinner + b);// [b]   assignments (k <= 1024)
   int16_t* sperm = sassign + b;             // [b]   batch rows sorted by center (b <= 8192)
   uint16_t* wtab = (uint16_t*)(sperm + b);  // [32][k] per-warp counts / offsets of a chunk
   // per-center window state, loaded up front together with the assignments
@@ -263,7 +266,13 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, int pair_tile) {
     c_nb = s.blk_num[tid];
     c_oldest = s.blk_cnt[(int64_t)tid * s.nbcap + c_first];
   }
-  for (int x = tid; x < b; x += 1024) sassign[x] = (int16_t)s.assign[x];
+  float macc = 0.0f;                        // this thread's share of sum_x min_j Delta
+  for (int x = tid; x < b; x += 1024) {
+    sassign[x] = (int16_t)s.assign[x];
+    sinner[x] = s.inner_a[x];
+    macc += s.mind[x];
+  }
+  const int tiles_used = *s.ntiles;         // tiles of this step's distance pass
   for (int j = tid; j < k; j += 1024) { cnt[j] = 0; base[j] = 0; }
   __syncthreads();
   for (int x = tid; x < b; x += 1024) atomicAdd(&cnt[sassign[x]], 1);
@@ -301,11 +310,35 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, int pair_tile) {
     __syncthreads();
   }
   for (int r = tid; r < b; r += 1024) s.perm[r] = sperm[r];
+  // per center, the 32 lane partials (FP32) of sum_{x in B_j} <phi(x), C_j>;
+  // k_finalize adds them in FP64
+  for (int j = warp; j < k; j += 32) {
+    const int n = cnt[j], o = coff[j];
+    float part = 0.0f;
+    for (int r = lane; r < n; r += 32) part += sinner[sperm[o + r]];
+    s.cmpart[(int64_t)j * 32 + lane] = part;
+  }
+  // f_B(C_i) = (1/b) sum_x min_j Delta(x, C_i^j): FP32 partials, FP64 combine in fixed order
+  {
+    __shared__ float wpartial[32];
+    float v = macc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) wpartial[warp] = v;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < 32; ++w) t += (double)wpartial[w];
+      const double f = t / (double)b;
+      *s.obj = f;
+      if (obj_out) *obj_out = f;
+    }
+  }
   // support rows read by this step's distance pass
   const int sz = tid < k ? c_tail - c_head : 0;
   int s_total = 0;
   block_exclusive_scan_1024(sz, &s_total);
-  if (tid == 0) *s.s_old = s_total;
+
   // window plan, one thread per center
   int npairs = 0, ncomp = 0;
   if (tid < k) {
@@ -364,9 +397,9 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, int pair_tile) {
       s.blk_first[j] = first;
       s.blk_num[j] = nb;
       s.wsum[j] = total;
-      const int T = pair_tile;
+      const int TR = s.pair_rows, TC = s.pair_cols;
       const int nD = P.ndrop, nL = P.tail_new - P.head_c;
-      npairs = ((nD + T - 1) / T) * ((nL + T - 1) / T) + ((n + T - 1) / T) * ((n + T - 1) / T);
+      npairs = ((nD + TR - 1) / TR) * ((nL + TC - 1) / TC) + ((n + TR - 1) / TR) * ((n + TC - 1) / TC);
     }
     s.plan[j] = P;
   }
@@ -375,6 +408,23 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, int pair_tile) {
   const int cfirst = block_exclusive_scan_1024(ncomp, &ctotal);
   if (tid < k) s.comp_off[tid] = cfirst;
   if (tid == 0) *s.comp_total = ctotal;
+  // the next step's tile list, from the windows this update leaves (the
+  // distance pass and argmin of this step have already consumed the current one)
+  {
+    int head = 0, size = 0;
+    if (tid < k) {
+      const Plan P = s.plan[tid];
+      head = P.head_new;
+      size = P.tail_new - P.head_new;
+    }
+    build_tiles_block(s, head, size);
+  }
+  if (tid == 0) {
+    s.stats[0] += 1;
+    s.stats[1] += s_total;
+    s.stats[2] += tiles_used;
+    *s.iter += 1;
+  }
   int ptotal = 0;
   const int pfirst = block_exclusive_scan_1024(npairs, &ptotal);
   if (tid == 0) {
@@ -386,14 +436,15 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, int pair_tile) {
     s.wpair_cnt[tid] = npairs;
     if (npairs > 0 && pfirst + npairs <= s.max_pairs) {
       const Plan P = s.plan[tid];
-      const int T = pair_tile;
+      const int TR = s.pair_rows, TC = s.pair_cols;
       const int nD = P.ndrop, nL = P.tail_new - P.head_c, n = P.cnt;
-      const int rD = (nD + T - 1) / T, cL = (nL + T - 1) / T, tB = (n + T - 1) / T;
+      const int rD = (nD + TR - 1) / TR, cL = (nL + TC - 1) / TC;
+      const int rB = (n + TR - 1) / TR, cB = (n + TC - 1) / TC;
       int e = pfirst;
       for (int rt = 0; rt < rD; ++rt)
         for (int ct = 0; ct < cL; ++ct) s.wpairs[e++] = WPair{tid, 0, rt, ct};
-      for (int rt = 0; rt < tB; ++rt)
-        for (int ct = 0; ct < tB; ++ct) s.wpairs[e++] = WPair{tid, 1, rt, ct};
+      for (int rt = 0; rt < rB; ++rt)
+        for (int ct = 0; ct < cB; ++ct) s.wpairs[e++] = WPair{tid, 1, rt, ct};
     }
   }
 }
@@ -482,138 +533,57 @@ __global__ void __launch_bounds__(1024) k_build_tiles(Dev s) {
   build_tiles_block(s);
 }
 
-// Exclusive scan of one int per lane over a warp; *total receives the sum.
-__device__ __forceinline__ int warp_exclusive_scan(int v, int* total) {
-  const int lane = threadIdx.x & 31;
-  int x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  *total = __shfl_sync(0xffffffffu, x, 31);
-  return x - v;
-}
-
-// Tile list of the distance pass built by one warp (centers in chunks of 32).
-__device__ void build_tiles_warp(const Dev& s) {
-  const int lane = threadIdx.x & 31;
-  int base = 0;
-  for (int j0 = 0; j0 < s.k; j0 += 32) {
-    const int j = j0 + lane;
-    int head = 0, size = 0, nt = 0;
-    if (j < s.k) {
-      head = s.head[j];
-      size = s.tail[j] - head;
-      nt = (size + s.tn - 1) / s.tn;
-    }
-    int chunk = 0;
-    const int first = base + warp_exclusive_scan(nt, &chunk);
-    if (j < s.k) {
-      const bool fits = first + nt <= s.max_tiles;   // never false by the capacity bound
-      s.tile_first[j] = fits ? first : 0;
-      s.tile_cnt[j] = fits ? nt : 0;
-      if (fits)
-        for (int t = 0; t < nt; ++t) {
-          const int c = t * s.tn;
-          s.tiles[first + t] = Tile{j, (int32_t)((int64_t)j * s.cap + head + c), min(s.tn, size - c), 0};
-        }
-    }
-    base += chunk;
-  }
-  if (lane == 0) {
-    *s.ntiles = base <= s.max_tiles ? base : s.max_tiles;
-    if (base > s.max_tiles) atomicOr(s.status, ST_CAPACITY);
-  }
-}
-
-// One warp per center j (block j). For a center that received points, with
-// FP64 where the values accumulate over iterations:
-//   alpha_j = sqrt(b_j / b) (or eta), <C_j, cm(B_j)> = (1/b_j) sum_x <phi(x), C_j>,
-//   the window-pass sums, the Sec. 4 recurrence for ||C_j||^2 corrected for
-//   the rows Eq. (1) drops, and the weights: rows [head_new, tail_c) decay by
-//   (1 - alpha), rows [tail_c, tail_new) get alpha / b_j.
-// The last warp to finish (atomic ticket, no waiting) builds the next tile
-// list, f_B and the iteration counter. GB300 issues FP64 slowly and charges
-// each FP64 warp instruction in full, so the FP64 work is kept to one warp
-// per center, on sums already reduced in FP32 where the terms are FP32.
-__global__ void __launch_bounds__(32) k_finalize(Dev s, double* obj_out) {
+// One warp per center j (block j) that received points, FP64 where the values
+// accumulate over iterations:
+//   alpha_j = sqrt(b_j / b) (or eta), <C_j, cm(B_j)> = (1/b_j) sum_x <phi(x), C_j>
+//   (from k_sort_plan's 32 FP32 lane partials), the window-pass sums, the
+//   Sec. 4 recurrence for ||C_j||^2 corrected for the rows Eq. (1) drops, and
+//   the weights: rows [head_new, tail_c) decay by (1 - alpha), rows
+//   [tail_c, tail_new) get alpha / b_j.
+// GB300 issues FP64 slowly and charges each FP64 warp instruction in full, so
+// the FP64 work stays on one warp per center, on sums already reduced in FP32
+// where the terms are FP32. Every load here depends only on the plan.
+__global__ void __launch_bounds__(32) k_finalize(Dev s) {
   KKM_GRID_DEP_WAIT();
   const int lane = threadIdx.x, j = blockIdx.x;
   const Plan P = s.plan[j];
-  if (P.cnt > 0) {
-    const int n = P.cnt, o = s.coff[j];
-    float part = 0.0f;
-    for (int r = lane; r < n; r += 32) part += s.inner_a[s.perm[o + r]];
-    const double cm_sum = warp_sum((double)part);
-    const int p0 = s.wpair_first[j];
-    const int np = (p0 + s.wpair_cnt[j] <= s.max_pairs) ? s.wpair_cnt[j] : 0;
-    double q[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int e = lane; e < np * 16; e += 32) q[e & 3] += s.wpart[(int64_t)p0 * 16 + e];
-    const double A = warp_sum(q[0]), Bdd = warp_sum(q[1]), E = warp_sum(q[2]), M = warp_sum(q[3]);
-    const double dn = (double)n;
-    const double a = (s.lr == 0) ? sqrt(dn * s.inv_b) : s.eta;
-    const double keep = 1.0 - a, wnew = a / dn;
-    if (lane == 0) {
-      s.alpha[j] = a;
-      const double cmc = cm_sum / dn;
-      s.cmc[j] = cmc;
-      // Sec. 4: ||C'||^2 = (1-a)^2 ||R||^2 + 2a(1-a) <R, m> + a^2 ||m||^2 with
-      // m = cm(B_j) and R = C - D, the part of the old center Eq. (1) keeps
-      const double m2 = M / (dn * dn);
-      const double R2 = s.cnorm[j] - 2.0 * A + Bdd;
-      const double Rm = cmc - E / dn;
-      const double cn = keep * keep * R2 + 2.0 * a * keep * Rm + a * a * m2;
-      s.cnorm[j] = cn;
-      s.cnorm32[j] = (float)cn;
-      s.head[j] = P.head_new;
-      s.tail[j] = P.tail_new;
-      s.c1[j] = P.c1_new;
-    }
-    const float wnew32 = (float)wnew;
-    const int64_t base = (int64_t)j * s.cap;
-    for (int r = P.head_new + lane; r < min(P.tail_c, s.cap); r += 32) {
-      const double w = s.w64[base + r] * keep;
-      s.w64[base + r] = w;
-      s.w32[base + r] = (float)w;
-    }
-    for (int r = P.tail_c + lane; r < min(P.tail_new, s.cap); r += 32) {
-      s.w64[base + r] = wnew;
-      s.w32[base + r] = wnew32;
-    }
-  }
-  // this warp's slice of sum_x min_j Delta(x, C_j) (FP32 lane partials, FP64 combine)
-  {
-    const int chunk = (s.b + gridDim.x - 1) / gridDim.x;
-    const int x0 = j * chunk, x1 = min(s.b, x0 + chunk);
-    float macc = 0.0f;
-    for (int x = x0 + lane; x < x1; x += 32) macc += s.mind[x];
-    const double t = warp_sum((double)macc);
-    if (lane == 0) s.objpart[j] = t;
-  }
-  // the last warp to arrive finishes the step
-  __threadfence();
-  __syncwarp();
-  int last = 0;
-  if (lane == 0) last = (atomicAdd(s.done_ctr, 1) == (int)gridDim.x - 1);
-  last = __shfl_sync(0xffffffffu, last, 0);
-  if (!last) return;
-  __threadfence();
-  const int tiles_used = *s.ntiles;            // tiles of this step's distance pass
-  build_tiles_warp(s);
-  // f_B(C_i): mean of the minimum distances, from the warps' partials in center order
-  double tpart = 0.0;
-  for (int q = lane; q < (int)gridDim.x; q += 32) tpart += s.objpart[q];
-  const double total = warp_sum(tpart);
+  if (P.cnt == 0) return;
+  const int n = P.cnt;
+  const double cm_sum = warp_sum((double)s.cmpart[(int64_t)j * 32 + lane]);
+  const int p0 = s.wpair_first[j];
+  const int np = (p0 + s.wpair_cnt[j] <= s.max_pairs) ? s.wpair_cnt[j] : 0;
+  double q[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int e = lane; e < np * 16; e += 32) q[e & 3] += s.wpart[(int64_t)p0 * 16 + e];
+  const double A = warp_sum(q[0]), Bdd = warp_sum(q[1]), E = warp_sum(q[2]), M = warp_sum(q[3]);
+  const double dn = (double)n;
+  const double a = (s.lr == 0) ? sqrt(dn * s.inv_b) : s.eta;
+  const double keep = 1.0 - a, wnew = a / dn;
   if (lane == 0) {
-    const double f = total / (double)s.b;
-    *s.obj = f;
-    if (obj_out) *obj_out = f;
-    s.stats[0] += 1;
-    s.stats[1] += *s.s_old;
-    s.stats[2] += tiles_used;
-    *s.iter += 1;
-    *s.done_ctr = 0;
+    s.alpha[j] = a;
+    const double cmc = cm_sum / dn;
+    s.cmc[j] = cmc;
+    // Sec. 4: ||C'||^2 = (1-a)^2 ||R||^2 + 2a(1-a) <R, m> + a^2 ||m||^2 with
+    // m = cm(B_j) and R = C - D, the part of the old center Eq. (1) keeps
+    const double m2 = M / (dn * dn);
+    const double R2 = s.cnorm[j] - 2.0 * A + Bdd;
+    const double Rm = cmc - E / dn;
+    const double cn = keep * keep * R2 + 2.0 * a * keep * Rm + a * a * m2;
+    s.cnorm[j] = cn;
+    s.cnorm32[j] = (float)cn;
+    s.head[j] = P.head_new;
+    s.tail[j] = P.tail_new;
+    s.c1[j] = P.c1_new;
+  }
+  const float wnew32 = (float)wnew;
+  const int64_t base = (int64_t)j * s.cap;
+  for (int r = P.head_new + lane; r < min(P.tail_c, s.cap); r += 32) {
+    const double w = s.w64[base + r] * keep;
+    s.w64[base + r] = w;
+    s.w32[base + r] = (float)w;
+  }
+  for (int r = P.tail_c + lane; r < min(P.tail_new, s.cap); r += 32) {
+    s.w64[base + r] = wnew;
+    s.w32[base + r] = wnew32;
   }
 }
 
@@ -711,16 +681,16 @@ cudaError_t launch_argmin(const Dev& s, int rows, const int32_t* forced, int32_t
   return cudaGetLastError();
 }
 
-int sort_plan_smem(int k, int b) { return 4 * k * 4 + b * (2 + 2) + 32 * k * 2; }
+int sort_plan_smem(int k, int b) { return 4 * k * 4 + b * (4 + 2 + 2) + 32 * k * 2; }
 
-cudaError_t launch_sort_plan(const Dev& s, cudaStream_t st) {
+cudaError_t launch_sort_plan(const Dev& s, double* obj_out, cudaStream_t st) {
   const int smem = sort_plan_smem(s.k, s.b);
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_sort_plan, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
-  cudaError_t e = launch_pdl(k_sort_plan, dim3(1), dim3(1024), smem, st, s, s.pair_tile);
+  cudaError_t e = launch_pdl(k_sort_plan, dim3(1), dim3(1024), smem, st, s, obj_out);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
@@ -733,8 +703,8 @@ cudaError_t launch_move(const Dev& s, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const Dev& s, double* obj_out, cudaStream_t st) {
-  cudaError_t e = launch_pdl(k_finalize, dim3(s.k), dim3(32), 0, st, s, obj_out);
+cudaError_t launch_finalize(const Dev& s, cudaStream_t st) {
+  cudaError_t e = launch_pdl(k_finalize, dim3(s.k), dim3(32), 0, st, s);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

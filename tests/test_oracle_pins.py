@@ -7,8 +7,9 @@ oracle against one of the following:
   * a library routine that implements a definition (scipy's cdist),
   * an independent formulation: explicit feature vectors for the linear and
     degree-2 polynomial kernels, and textbook Lloyd,
-  * an identity or bound the paper proves: the Sec. 4 norm recurrence,
-    Lemma 7 (Kanungo et al.), Lemmas 2-3, and the truncation lemma of Sec. 4.1.
+  * an identity or bound the paper proves: the Sec. 4 norm recurrence, the
+    Kanungo et al. lemma and the norm and objective bounds of Sec. 5, and the
+    truncation lemma of Sec. 4.1.
 Each is chosen so that a plausible slip fails it: a dropped C_1 term, a wrong
 decay index, a renormalised truncated center, a sign error in the cross term,
 or a transposed kernel argument.
@@ -259,7 +260,7 @@ def test_norm_recurrence_of_sec4():
             assert r.cnorm_after[j] == pytest.approx(rec, rel=1e-11, abs=1e-13)
 
 
-def test_kanungo_identity_lemma7():
+def test_kanungo_identity():
     """Delta(S, C) = Delta(S, cm(S)) + |S| Delta(C, cm(S)) for C a current center."""
     X, _ = inputs.isotropic_mixture(150, 4, 3, seed=11)
     kern = Kernel(GAUSSIAN, 5.0)
@@ -276,7 +277,7 @@ def test_kanungo_identity_lemma7():
     assert lhs == pytest.approx(d_S_cm + len(S) * diff, rel=1e-10)
 
 
-def test_gaussian_bounds_lemmas_2_3_and_weight_sums():
+def test_gaussian_bounds_and_weight_sums():
     X, _ = inputs.isotropic_mixture(500, 8, 5, seed=12)
     kern = Kernel(GAUSSIAN, 2 * inputs.median_sigma(X, seed=1) ** 2)
     b, k = 64, 5
