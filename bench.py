@@ -41,9 +41,30 @@ DTYPES = {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}
 OBJ_BAR = 1e-4          # objective relative error a form must meet to count (the metric's bar)
 
 
+KERNEL = "gaussian"
+
+
 def workload_desc(w) -> str:
-    return (f"MNIST-shaped synthetic mixture n={w.n} d={w.d} (~80% zeros, Beta(2,2) values, 10 latent "
-            f"classes), k={w.k}, b={w.b}, tau={w.tau}, Gaussian kernel kappa=2*sigma_median^2, beta rate")
+    kern = ("Gaussian kernel kappa=2*sigma_median^2" if KERNEL == "gaussian"
+            else "Laplacian kernel exp(-||x-y||/sigma_median)")
+    if w.kind == "image":
+        return (f"MNIST-shaped synthetic mixture n={w.n} d={w.d} (~80% zeros, Beta(2,2) values, 10 latent "
+                f"classes), k={w.k}, b={w.b}, tau={w.tau}, {kern}, beta rate")
+    shape = ("anisotropic (Haar-random covariances, condition <= 100)" if w.kind == "anisotropic"
+             else "isotropic unit-variance")
+    return (f"{w.name}: synthetic {shape} Gaussian mixture of {w.components} components, n={w.n} d={w.d}, "
+            f"k={w.k}, b={w.b}, tau={w.tau}, {kern}, beta rate")
+
+
+def kernel_param(X) -> float:
+    """kappa = 2 sigma^2 (Gaussian) or sigma (Laplacian), sigma = median pairwise distance."""
+    sigma = inputs.median_sigma(X, seed=1)
+    return 2.0 * sigma * sigma if KERNEL == "gaussian" else sigma
+
+
+def oracle_kernel(param):
+    import oracle
+    return oracle.Kernel(oracle.GAUSSIAN if KERNEL == "gaussian" else oracle.LAPLACIAN, param)
 
 
 def load_peaks() -> dict:
@@ -130,8 +151,7 @@ def whole_job_value(b: int, k: int, steps: int, world: int, max_seconds: float) 
 
 def make_workload(seed_offset: int = 0):
     X, _ = WORKLOAD.make()
-    sigma = inputs.median_sigma(X, seed=1)
-    kappa = 2.0 * sigma * sigma
+    kappa = kernel_param(X)
     init = inputs.init_indices(WORKLOAD.n, WORKLOAD.k, seed=3 + seed_offset)
     return X, kappa, init
 
@@ -153,7 +173,7 @@ def oracle_leg(X, kappa, init, forms, Xd, budget_s: float, prep: int = 4):
     from paper_2410_05902_gb300.kkm import KKM
     w = WORKLOAD
     X64 = X.astype(np.float64)
-    ora = oracle.MiniBatchKernelKMeans(X64, w.k, oracle.Kernel(oracle.GAUSSIAN, kappa), w.b, init, tau=w.tau)
+    ora = oracle.MiniBatchKernelKMeans(X64, w.k, oracle_kernel(kappa), w.b, init, tau=w.tau)
     batches = inputs.batch_stream(w.n, w.b, 400, seed=77)
     for i in range(prep):
         ora.step(batches[i])
@@ -166,7 +186,7 @@ def oracle_leg(X, kappa, init, forms, Xd, budget_s: float, prep: int = 4):
     bi = torch.from_numpy(batches[prep].astype(np.int32)).to(Xd.device)
     fa = torch.from_numpy(rec.assign.astype(np.int32)).to(Xd.device)
     for form in forms:
-        run = KKM(Xd, w.k, w.b, kernel="gaussian", param=kappa, tau=w.tau, precision=form, init_idx=init)
+        run = KKM(Xd, w.k, w.b, kernel=KERNEL, param=kappa, tau=w.tau, precision=form, init_idx=init)
         run.set_state(state)
         dist_out = torch.empty((w.b, w.k), dtype=torch.float32, device=Xd.device)
         obj = torch.empty(1, dtype=torch.float64, device=Xd.device)
@@ -202,7 +222,7 @@ def run_reference(args):
     import oracle
     w = WORKLOAD
     X, kappa, init = make_workload()
-    ora = oracle.MiniBatchKernelKMeans(X, w.k, oracle.Kernel(oracle.GAUSSIAN, kappa), w.b, init, tau=w.tau)
+    ora = oracle.MiniBatchKernelKMeans(X, w.k, oracle_kernel(kappa), w.b, init, tau=w.tau)
     batches = inputs.batch_stream(w.n, w.b, 200, seed=77)
     for i in range(4):
         ora.step(batches[i])
@@ -247,7 +267,7 @@ def time_form(form, args, X, Xd, kappa, init, rank, world, dev, barrier):
     from paper_2410_05902_gb300.kkm import KKM
     w = WORKLOAD
     stream = torch.cuda.current_stream(dev)
-    run = KKM(Xd, w.k, w.b, kernel="gaussian", param=kappa, tau=w.tau, precision=form,
+    run = KKM(Xd, w.k, w.b, kernel=KERNEL, param=kappa, tau=w.tau, precision=form,
               seed=1000 + rank, init_idx=init)
     for _ in range(PREP_ITERS):
         run.step()
@@ -380,8 +400,8 @@ def run_ours(args):
                        "form_rule": f"fastest form with objective error <= {OBJ_BAR} against the FP64 oracle",
                        "meets_obj_bar": chosen in ok, "support_rows_S": r["S"],
                        "state_prep_iters": PREP_ITERS,
-                       "l2": "inputs larger than L2: X is 220 MB (L2 129 MB); the method's support "
-                             "state stays resident between iterations",
+                       "l2": f"inputs larger than L2: X is {X.nbytes / 1e6:.0f} MB (L2 129 MB); the "
+                             "method's support state stays resident between iterations",
                        "parallelism": f"replicas x{world} (independent runs, no collective)",
                        "step_launch": "eager kernel launches" if args.no_graph else "CUDA graph replay"},
             "forms": {f: {"value": res[f]["value"], "ms_per_step": res[f]["ms"] / args.steps,
@@ -411,7 +431,13 @@ def main():
                     help="auto: time every form, report the fastest that meets the objective bar")
     ap.add_argument("--oracle-budget", type=float, default=20.0)
     ap.add_argument("--no-graph", action="store_true", help="launch every kernel instead of replaying a graph")
+    ap.add_argument("--workload", choices=sorted(inputs.WORKLOADS), default="image",
+                    help="image (default) is the headline workload; the others are secondary measurements")
+    ap.add_argument("--kernel", choices=["gaussian", "laplacian"], default="gaussian")
     args = ap.parse_args()
+    global WORKLOAD, KERNEL
+    WORKLOAD = inputs.WORKLOADS[args.workload]
+    KERNEL = args.kernel
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -167,8 +167,8 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
         return fail(nullptr, KKM_EINVAL, "init_idx entry out of [0, n)");
 
   const int64_t wmax = cfg->tau > 0 ? (int64_t)cfg->tau + b : 1 + (int64_t)cfg->max_iters * b;
-  const int64_t cap = cfg->tau > 0 ? kkm::round_up(2LL * cfg->tau + 4LL * b + 8, 8)
-                                   : kkm::round_up(wmax, 8);
+  const int64_t cap = (cfg->tau > 0 ? kkm::round_up(2LL * cfg->tau + 4LL * b + 8, 8)
+                                    : kkm::round_up(wmax, 8)) + kkm::REGION_PAD;
   const int64_t srows = (int64_t)k * cap + 256;
   if (srows >= (int64_t(1) << 31)) return fail(nullptr, KKM_EINVAL, "support store too large (k*cap)");
 
@@ -260,7 +260,8 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
   ALLOC(s.tiles, s.max_tiles); ALLOC(s.ntiles, 1); ALLOC(s.tile_first, k); ALLOC(s.tile_cnt, k);
   ALLOC(s.part, (size_t)s.max_tiles * s.bpad);
   ALLOC(s.wpairs, s.max_pairs); ALLOC(s.nwpairs, 1); ALLOC(s.wpair_first, k); ALLOC(s.wpair_cnt, k);
-  ALLOC(s.wpart, (size_t)s.max_pairs * 16);
+  s.wslots = c->use_tc ? 8 : 4;
+  ALLOC(s.wpart, (size_t)s.max_pairs * s.wslots * 4);
   ALLOC(s.iter, 1); ALLOC(s.status, 1); ALLOC(s.stats, 3); ALLOC(s.obj, 1);
   ALLOC(c->d_init_idx, k);
   ALLOC(c->d_hbatch, b); ALLOC(c->d_hassign, b); ALLOC(c->d_hobj, 1);
@@ -594,6 +595,9 @@ KKM_API kkm_status kkm_set_state(kkm_ctx* c, int64_t iteration, const int32_t* r
     bo += nblk;
   }
   KKM_CU(cudaStreamSynchronize(c->stream), "stream synchronize");
+  // weights are 0 outside the windows
+  KKM_CU(cudaMemset(s.w64, 0, ((size_t)k * s.cap + 256) * sizeof(double)), "state write");
+  KKM_CU(cudaMemset(s.w32, 0, ((size_t)k * s.cap + 256) * sizeof(float)), "state write");
   std::vector<int32_t> head(k, 0), tail(k), c1(k), wsum(k), bf(k, 0), bn(k);
   std::vector<int32_t> bi((size_t)k * s.nbcap, 0), bc((size_t)k * s.nbcap, 0);
   ro = 0; bo = 0;

@@ -41,7 +41,8 @@ template <bool X3, int TNV> struct Ring {
   static constexpr int bytes = X3 ? 2 * (A_BYTES + b_bytes) : A_BYTES + b_bytes;
   static constexpr int stages = RING_BYTES / bytes;   // 3, 4, 6 or 8
 };
-constexpr int NTHREADS = 192;
+constexpr int NEPI = 8;                          // epilogue warps (two per TMEM lane quadrant)
+constexpr int NTHREADS = 64 + 32 * NEPI;        // + one TMA warp and one MMA warp
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;   // 2 s per wait
 
 // Instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1),
@@ -52,15 +53,31 @@ __host__ __device__ constexpr uint32_t idesc() {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 }
 
+constexpr int MS = 4;                           // metadata ring slots (items in flight)
+
+// Distance-pass metadata of one item, copied by the producer: col[0] =
+// ||y||^2, col[1] = w, col[2] = data index of the 128 support rows; row[0] =
+// ||x||^2, row[1] = data index of the 128 batch rows.
+struct MetaSlot {
+  float col[3][128];
+  float row[2][128];
+};
+
 struct Shared {
   uint64_t full[STAGES];
   uint64_t empty[STAGES];
   uint64_t tfull[2];
   uint64_t tempty[2];
+  uint64_t mfull[MS];
+  uint64_t mempty[MS];
   uint64_t mma_done;
   uint32_t tmem_base;
   uint32_t pad;
-  float4 meta[4][128];                          // per epilogue warp: (||y||^2, w, yi, class)
+  union alignas(16) {
+    MetaSlot ring[MS];                          // distance pass
+    float warp[NEPI][5][64];                    // window pass: per epilogue warp (load_pair_meta)
+  } meta;
+  float red[2][4][32];                          // distance pass: second-half row sums (item parity, quadrant)
 };
 
 constexpr int SMEM_BYTES = 1024 + RING_BYTES + (int)sizeof(Shared);
@@ -179,22 +196,41 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Kernel values of one row against two columns from their Gram entries g.
+// Gaussian: rc = ||x||^2 * negc and cc = ||y||^2 * negc (negc = -log2(e)/kappa),
+//           K = 2^min(rc + cc - 2 negc g, 0).
+// Laplacian: rc = ||x||^2, cc = ||y||^2, K = 2^(negc * sqrt(max(D^2, 0))).
+// Both give exactly 1 when the two rows are the same data point (K(x,x) = 1).
+// Linear and polynomial values of padding columns (yi = -2) are zeroed, as
+// those kernels are unbounded.
 template <int KIND>
-__device__ __forceinline__ float kernel_value(float g, float xn, float yn, bool same, float negc,
+__device__ __forceinline__ float2 kernel_pair(float2 g, float rc, float2 cc, int xi, int2 yi, float negc,
                                               float coef0, int degree) {
-  if constexpr (KIND == K_GAUSS || KIND == K_LAPLACE) {
-    float d2 = fmaxf(fmaf(-2.0f, g, xn + yn), 0.0f);
-    d2 = same ? 0.0f : d2;
-    const float arg = (KIND == K_GAUSS) ? d2 : sqrtf(d2);
-    return ex2_approx(arg * negc);
+  float2 k;
+  if constexpr (KIND == K_GAUSS) {
+    const float2 a = __ffma2_rn(g, make_float2(-2.0f * negc, -2.0f * negc), __fadd2_rn(make_float2(rc, rc), cc));
+    k.x = xi == yi.x ? 1.0f : ex2_approx(fminf(a.x, 0.0f));
+    k.y = xi == yi.y ? 1.0f : ex2_approx(fminf(a.y, 0.0f));
+  } else if constexpr (KIND == K_LAPLACE) {
+    const float2 d2 = __ffma2_rn(g, make_float2(-2.0f, -2.0f), __fadd2_rn(make_float2(rc, rc), cc));
+    k.x = xi == yi.x ? 1.0f : ex2_approx(sqrt_approx(fmaxf(d2.x, 0.0f)) * negc);
+    k.y = xi == yi.y ? 1.0f : ex2_approx(sqrt_approx(fmaxf(d2.y, 0.0f)) * negc);
   } else if constexpr (KIND == K_LINEAR) {
-    return g;
+    k.x = yi.x == -2 ? 0.0f : g.x;
+    k.y = yi.y == -2 ? 0.0f : g.y;
   } else {
-    const float base = g + coef0;
-    float r = 1.0f;
-    for (int p = 0; p < degree; ++p) r *= base;
-    return r;
+    float rx = 1.0f, ry = 1.0f;
+    for (int p = 0; p < degree; ++p) { rx *= g.x + coef0; ry *= g.y + coef0; }
+    k.x = yi.x == -2 ? 0.0f : rx;
+    k.y = yi.y == -2 ? 0.0f : ry;
   }
+  return k;
 }
 
 // A window-pass tile (mode 1): rows of the support store of center j, as
@@ -227,11 +263,52 @@ __device__ __forceinline__ PairTile pair_tile(const Dev& s, int w) {
   return t;
 }
 
+// Window-pass column metadata of one epilogue warp (C columns of its half
+// tile): col[0] = ||y||^2 (times negc for the Gaussian), col[1] = w on the
+// old window (A), col[2] = data index (-2 on padding columns), col[3] = w on
+// the dropped rows (Bdd), col[4] = 1 on the new block (E).
+template <int KIND, int TNV>
+__device__ __forceinline__ void load_pair_meta(const Dev& s, const PairTile& pt, int cbase, float (*m)[64],
+                                               int lane) {
+  constexpr int C = TNV / 2;
+  const float sc = (KIND == K_GAUSS) ? s.negc : 1.0f;
+#pragma unroll
+  for (int c = lane; c < C; c += 32) {
+    const int col = cbase + c;
+    const int qpos = pt.cs + col;
+    const bool valid = col < pt.crem;
+    const int64_t gi = pt.base + (valid ? qpos : pt.cs);
+    const float w = valid ? s.w32[gi] : 0.0f;
+    const bool in_d = qpos < pt.head_new, in_old = qpos < pt.tail_c;
+    m[0][c] = s.yn[gi] * sc;
+    m[1][c] = in_old ? w : 0.0f;
+    m[2][c] = __int_as_float(valid ? s.yi[gi] : -2);
+    m[3][c] = in_d ? w : 0.0f;
+    m[4][c] = (valid && !in_old) ? 1.0f : 0.0f;
+  }
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // MODE 0: distance pass (A = batch tile, B = support tile, one FP32 partial per row).
-// MODE 1: window pass (A and B = support rows of one center, four FP64 sums per warp).
+// MODE 1: window pass (A and B = support rows of one center, four FP32 sums per warp,
+//         added up in FP64 by the finalize kernel).
 // Items are dealt round-robin to the persistent CTAs. Splitting a tile along
 // its columns needs no merge because both passes only sum over columns, so
 // narrower tiles (TNV = 64) are how the window pass gets enough items.
+//
+// Distance pass metadata: a tile starts on a multiple of 4 support rows and
+// support weights are 0 outside the windows, so the column metadata of an
+// item (||y||^2, w, data index) and its row metadata (||x||^2, data index)
+// are plain contiguous ranges. The producer copies them with bulk async
+// copies into a 4-slot ring next to the operand ring; nothing on the
+// epilogue's path waits on a global load. The tile descriptors themselves are
+// fetched 32 items at a time, one per producer lane.
 template <int KIND, int MODE, bool X3, int TNV>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_dist_tc(Dev s, int rows, const __grid_constant__ CUtensorMap tmA,
@@ -244,6 +321,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   constexpr int BB = Ring<X3, TNV>::b_bytes;
   constexpr uint32_t TMEM_COLS = 2 * TNV;        // two accumulators (double buffering)
   constexpr uint32_t IDESC = idesc<TNV>();
+  constexpr uint32_t META_BYTES = 3 * TNV * 4 + 2 * TM * 4;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
@@ -253,7 +331,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&sh.tfull[i], 1);
-      mbar_init(&sh.tempty[i], 128);
+      mbar_init(&sh.tempty[i], NEPI);
+    }
+    for (int i = 0; i < MS; ++i) {
+      mbar_init(&sh.mfull[i], 1);
+      mbar_init(&sh.mempty[i], NEPI);
     }
     mbar_init(&sh.mma_done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -275,24 +357,42 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int nks = s.dp / KS;
 
   if (warp == 0) {
-    // ------------------------------------------------------------ TMA producer
-    if (lane == 0) {
-      bool ok = true;
-      uint32_t it = 0;
-      for (int item = blockIdx.x; ok && item < total; item += gridDim.x) {
-        int ya, yb;
-        const CUtensorMap* am;
-        if constexpr (MODE == 0) {
-          ya = (item % R) * TM;
-          yb = s.tiles[item / R].row0;
-          am = &tmA;
-        } else {
-          const PairTile pt = pair_tile<TNV>(s, item);
-          ya = (int)(pt.base + pt.rs);
-          yb = (int)(pt.base + pt.cs);
-          am = &tmA;   // mode 1 gets the 128-row support map as tmA
+    // ------------------------------------------------------- producer (one warp)
+    bool ok = true;
+    uint32_t it = 0, local = 0, mi = 0;          // fills issued, items visited, metadata copies issued
+    int pya = 0, pyb = 0;                        // this lane's prefetched item: A and B row
+    for (int item = blockIdx.x; item < total; item += gridDim.x, ++local) {
+      if ((local & 31u) == 0) {                  // descriptors of the next 32 items
+        const int mine = item + lane * gridDim.x;
+        if (mine < total) {
+          if constexpr (MODE == 0) {
+            pya = (mine % R) * TM;
+            pyb = s.tiles[mine / R].row0;
+          } else {
+            const PairTile pt = pair_tile<TNV>(s, mine);
+            pya = (int)(pt.base + pt.rs);
+            pyb = (int)(pt.base + pt.cs);
+          }
         }
-        for (int sl = 0; sl < nks; ++sl, ++it) {
+      }
+      const int ya = __shfl_sync(0xffffffffu, pya, local & 31u);
+      const int yb = __shfl_sync(0xffffffffu, pyb, local & 31u);
+      if (lane == 0) {
+        if constexpr (MODE == 0) {
+          const int ms = local % MS;
+          if (!mbar_wait(&sh.mempty[ms], ((local / MS) & 1u) ^ 1u)) ok = false;
+          if (ok) {
+            MetaSlot& m = sh.meta.ring[ms];
+            mbar_expect_tx(&sh.mfull[ms], META_BYTES);
+            bulk_load(m.col[0], s.yn + yb, TNV * 4, &sh.mfull[ms]);
+            bulk_load(m.col[1], s.w32 + yb, TNV * 4, &sh.mfull[ms]);
+            bulk_load(m.col[2], s.yi + yb, TNV * 4, &sh.mfull[ms]);
+            bulk_load(m.row[0], s.xbn + ya, TM * 4, &sh.mfull[ms]);
+            bulk_load(m.row[1], s.xbi + ya, TM * 4, &sh.mfull[ms]);
+            ++mi;
+          }
+        }
+        for (int sl = 0; ok && sl < nks; ++sl, ++it) {
           const int st = it % NST;
           const uint32_t ph = (it / NST) & 1u;
           if (!mbar_wait(&sh.empty[st], ph ^ 1u)) { ok = false; break; }
@@ -300,19 +400,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           uint8_t* a = smem + st * SB;
           mbar_expect_tx(&sh.full[st], SB);
           if constexpr (X3) {   // stage layout: A_hi | A_lo | B_hi | B_lo
-            tma_load_2d(a, am, &sh.full[st], x, ya);
-            tma_load_2d(a + A_BYTES, am, &sh.full[st], s.dp + x, ya);
+            tma_load_2d(a, &tmA, &sh.full[st], x, ya);
+            tma_load_2d(a + A_BYTES, &tmA, &sh.full[st], s.dp + x, ya);
             tma_load_2d(a + 2 * A_BYTES, &tmB, &sh.full[st], x, yb);
             tma_load_2d(a + 2 * A_BYTES + BB, &tmB, &sh.full[st], s.dp + x, yb);
           } else {              // stage layout: A | B
-            tma_load_2d(a, am, &sh.full[st], x, ya);
+            tma_load_2d(a, &tmA, &sh.full[st], x, ya);
             tma_load_2d(a + A_BYTES, &tmB, &sh.full[st], x, yb);
           }
         }
       }
-      // the last fill of every stage must land before the CTA may exit
+      if (!__shfl_sync(0xffffffffu, (int)ok, 0)) break;
+    }
+    if (lane == 0) {
+      // the copies in flight must land before the CTA may exit: the last fill
+      // of every stage, and the metadata of the last MS items
       for (uint32_t q = (it > (uint32_t)NST ? it - NST : 0u); q < it; ++q)
         if (!mbar_wait(&sh.full[q % NST], (q / NST) & 1u)) ok = false;
+      if constexpr (MODE == 0)
+        for (uint32_t q = (mi > (uint32_t)MS ? mi - MS : 0u); q < mi; ++q)
+          if (!mbar_wait(&sh.mfull[q % MS], (q / MS) & 1u)) ok = false;
       if (!ok) atomicOr(s.status, ST_TIMEOUT);
     }
   } else if (warp == 1) {
@@ -356,108 +463,119 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   } else {
     // ---------------------------------------------------------------- epilogue
-    const int q = warp & 3;                      // TMEM lane quadrant of this warp
+    // Eight warps, two per TMEM lane quadrant: warp e = warp - 2 reads lanes
+    // 32*(warp % 4).. (the rows of quadrant q) and columns [h*C, h*C + C) of the
+    // accumulator, h = e / 4.
+    const int e = warp - 2;
+    const int q = warp & 3;
+    const int h = e >> 2;
+    constexpr int C = TNV / 2;
+    const int cbase = h * C;
     const int rloc = q * 32 + lane;              // this thread's row inside the tile
-    float4* meta = sh.meta[warp - 2];
-    const float negc = s.negc, coef0 = (float)s.coef0;
+    const float negc = s.negc;
+    const float coef0 = (float)s.coef0;
     const int degree = s.degree;
+    bool dead = false;                           // a wait ran out: skip the work, keep the barriers
     uint32_t local = 0;
     for (int item = blockIdx.x; item < total; item += gridDim.x, ++local) {
       const uint32_t buf = local & 1u, bph = (local >> 1) & 1u;
-      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + buf * TNV;
-      // column metadata and row data first: their global loads overlap the MMAs
-      int t = 0, row = 0, ncols = 0;
-      float xn;
-      int xi;
-      PairTile pt;
-      double wp = 0.0;
-      bool rvalid = true;
-      __syncwarp();
+      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + buf * TNV + cbase;
       if constexpr (MODE == 0) {
-        t = item / R;
-        const Tile T = s.tiles[t];
-        ncols = T.ncols;
-#pragma unroll
-        for (int c4 = 0; c4 < TNV / 32; ++c4) {
-          const int c = c4 * 32 + lane;
-          const bool valid = c < T.ncols;
-          const int64_t g = (int64_t)T.row0 + (valid ? c : 0);
-          meta[c] = make_float4(s.yn[g], valid ? s.w32[g] : 0.0f, __int_as_float(valid ? s.yi[g] : -2), 0.0f);
+        const int ms = local % MS;
+        const MetaSlot& m = sh.meta.ring[ms];
+        const bool ok = dead || (mbar_wait(&sh.mfull[ms], (local / MS) & 1u) && mbar_wait(&sh.tfull[buf], bph));
+        if (__any_sync(0xffffffffu, !ok)) {
+          if (lane == 0 && !dead) atomicOr(s.status, ST_TIMEOUT);
+          dead = true;
         }
-        row = (item % R) * TM + rloc;
-        const int rr = row < rows ? row : 0;
-        xn = s.xbn[rr];
-        xi = s.xbi[rr];
+        float f0 = 0.0f;
+        if (!dead) {
+          tc_fence_after();
+          const float xn = m.row[0][rloc];
+          const int xi = __float_as_int(m.row[1][rloc]);
+          const float rc = (KIND == K_GAUSS) ? xn * negc : xn;
+          float2 a0 = make_float2(0.0f, 0.0f), a1 = a0;
+#pragma unroll
+          for (int ch = 0; ch < C / 32; ++ch) {
+            float g[32];
+            tmem_ld32(taddr + ch * 32, g);
+            if (ch == C / 32 - 1) {   // the accumulator is free for the next item's MMAs
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&sh.tempty[buf]);
+            }
+#pragma unroll
+            for (int i = 0; i < 32; i += 2) {
+              const int c = cbase + ch * 32 + i;
+              const float2 yn = *reinterpret_cast<const float2*>(&m.col[0][c]);
+              const float2 w = *reinterpret_cast<const float2*>(&m.col[1][c]);
+              const int2 yi = *reinterpret_cast<const int2*>(&m.col[2][c]);
+              const float2 cc = (KIND == K_GAUSS) ? __fmul2_rn(yn, make_float2(negc, negc)) : yn;
+              const float2 kv = kernel_pair<KIND>(make_float2(g[i], g[i + 1]), rc, cc, xi, yi, negc, coef0, degree);
+              if ((i & 2) == 0) a0 = __ffma2_rn(w, kv, a0);
+              else a1 = __ffma2_rn(w, kv, a1);
+            }
+          }
+          f0 = (a0.x + a0.y) + (a1.x + a1.y);
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sh.mempty[ms]);   // this warp is done with the slot
+        }
+        // the two column halves of a row meet in shared memory (slot by item parity)
+        float* red = sh.red[local & 1u][q];
+        if (h == 1) red[lane] = f0;
+        asm volatile("bar.sync %0, 64;" ::"r"(1 + q) : "memory");
+        const int row = (item % R) * TM + rloc;
+        if (h == 0 && !dead && row < rows) s.part[(int64_t)(item / R) * s.bpad + row] = f0 + red[lane];
       } else {
-        pt = pair_tile<TNV>(s, item);
-#pragma unroll
-        for (int c4 = 0; c4 < TNV / 32; ++c4) {
-          const int c = c4 * 32 + lane;
-          const int qpos = pt.cs + c;
-          const bool valid = c < pt.crem;
-          const int64_t g = pt.base + (valid ? qpos : pt.cs);
-          // column class: 0 dropped (in D and the old window), 1 old window, 2 new block, 3 none
-          const float cls = !valid ? 3.0f : (qpos < pt.head_new ? 0.0f : (qpos < pt.tail_c ? 1.0f : 2.0f));
-          meta[c] = make_float4(s.yn[g], valid ? s.w32[g] : 0.0f, __int_as_float(valid ? s.yi[g] : -2), cls);
-        }
-        rvalid = rloc < pt.rrem;
+        // window pass: this warp loads its own metadata; the loads overlap the MMAs
+        float (*mw)[64] = sh.meta.warp[e];
+        __syncwarp();
+        const PairTile pt = pair_tile<TNV>(s, item);
+        load_pair_meta<KIND, TNV>(s, pt, cbase, mw, lane);
+        const bool rvalid = rloc < pt.rrem;
         const int64_t p = pt.base + pt.rs + (rvalid ? rloc : 0);
-        xn = s.yn[p];
-        xi = s.yi[p];
-        wp = rvalid ? s.w64[p] : 0.0;
-      }
-      __syncwarp();
-      const bool ok = mbar_wait(&sh.tfull[buf], bph);
-      if (__any_sync(0xffffffffu, !ok)) {
-        if (lane == 0) atomicOr(s.status, ST_TIMEOUT);
-        break;
-      }
-      tc_fence_after();
-      if constexpr (MODE == 0) {
-        float acc = 0.0f;
-#pragma unroll
-        for (int ch = 0; ch < TNV / 32; ++ch) {
-          float g[32];
-          tmem_ld32(taddr + ch * 32, g);
-          if (ch == TNV / 32 - 1) {
-            tc_fence_before();
-            mbar_arrive(&sh.tempty[buf]);
-          }
-#pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const int c = ch * 32 + i;
-            const float4 m = meta[c];
-            const float kv = kernel_value<KIND>(g[i], xn, m.x, xi == __float_as_int(m.z), negc, coef0, degree);
-            acc = (c < ncols) ? fmaf(m.y, kv, acc) : acc;
-          }
+        const float xn = s.yn[p];
+        const int xi = s.yi[p];
+        const float wp = rvalid ? s.w32[p] : 0.0f;
+        __syncwarp();
+        const bool ok = dead || mbar_wait(&sh.tfull[buf], bph);
+        if (__any_sync(0xffffffffu, !ok)) {
+          if (lane == 0 && !dead) atomicOr(s.status, ST_TIMEOUT);
+          dead = true;
         }
-        if (row < rows) s.part[(int64_t)t * s.bpad + row] = acc;
-      } else {
-        float fA = 0.0f, fB = 0.0f, fE = 0.0f;
+        if (dead) continue;
+        tc_fence_after();
+        const float rc = (KIND == K_GAUSS) ? xn * negc : xn;
+        float2 a0 = make_float2(0.0f, 0.0f), a1 = a0, a2 = a0;
 #pragma unroll
-        for (int ch = 0; ch < TNV / 32; ++ch) {
+        for (int ch = 0; ch < C / 32; ++ch) {
           float g[32];
           tmem_ld32(taddr + ch * 32, g);
-          if (ch == TNV / 32 - 1) {
+          if (ch == C / 32 - 1) {
             tc_fence_before();
-            mbar_arrive(&sh.tempty[buf]);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh.tempty[buf]);
           }
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const float4 m = meta[ch * 32 + i];
-            const float kv = kernel_value<KIND>(g[i], xn, m.x, xi == __float_as_int(m.z), negc, coef0, degree);
-            const float wk = m.y * kv;
-            fA += (m.w < 1.5f) ? wk : 0.0f;
-            fB += (m.w < 0.5f) ? wk : 0.0f;
-            fE += (m.w > 1.5f && m.w < 2.5f) ? kv : 0.0f;
+          for (int i = 0; i < 32; i += 2) {
+            const int c = ch * 32 + i;
+            const float2 cc = *reinterpret_cast<const float2*>(&mw[0][c]);
+            const float2 wa = *reinterpret_cast<const float2*>(&mw[1][c]);
+            const int2 yi = *reinterpret_cast<const int2*>(&mw[2][c]);
+            const float2 wb = *reinterpret_cast<const float2*>(&mw[3][c]);
+            const float2 we = *reinterpret_cast<const float2*>(&mw[4][c]);
+            const float2 kv = kernel_pair<KIND>(make_float2(g[i], g[i + 1]), rc, cc, xi, yi, negc, coef0, degree);
+            a0 = __ffma2_rn(wa, kv, a0);
+            a1 = __ffma2_rn(wb, kv, a1);
+            a2 = __ffma2_rn(we, kv, a2);
           }
         }
         // kind 0: A = w_p sum_{q in W} w_q K, Bdd = w_p sum_{q in D} w_q K, E = w_p sum_{q in B} K
         // kind 1: M = sum_{q in B} K (every valid column of a kind-1 tile is in B)
-        double sA = 0.0, sB = 0.0, sE = 0.0, sM = 0.0;
+        float sA = 0.0f, sB = 0.0f, sE = 0.0f, sM = 0.0f;
         if (rvalid) {
-          if (pt.kind == 0) { sA = wp * (double)fA; sB = wp * (double)fB; sE = wp * (double)fE; }
-          else sM = (double)fE;
+          if (pt.kind == 0) { sA = wp * (a0.x + a0.y); sB = wp * (a1.x + a1.y); sE = wp * (a2.x + a2.y); }
+          else sM = a2.x + a2.y;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -467,7 +585,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           sM += __shfl_xor_sync(0xffffffffu, sM, o);
         }
         if (lane == 0) {
-          double* out = s.wpart + ((int64_t)item * 4 + q) * 4;
+          double* out = s.wpart + ((int64_t)item * NEPI + e) * 4;
           out[0] = sA; out[1] = sB; out[2] = sE; out[3] = sM;
         }
       }

@@ -9,16 +9,21 @@
 //                  each block in batch order. Appends go at tail. Drops advance
 //                  head. When an append would pass the region's end, the
 //                  window is first copied down to row 0 ("compaction"). With
-//                  cap = 2*tau + 4*b + 8 the source and destination rows of
-//                  that copy never overlap, because a window holds at most
-//                  tau + b rows.
+//                  cap - REGION_PAD = 2*tau + 4*b + 8 usable rows the source
+//                  and destination rows of that copy never overlap, because a
+//                  window holds at most tau + b rows. The last REGION_PAD rows
+//                  of a region are never used, so a tile that starts inside
+//                  the window never reaches the next region.
 //   row data       FP32 form: FP32 rows, ld = round_up(d, 16), zero padded.
 //                  BF16 forms: BF16 rows [hi(0..dp) | lo(0..dp)], dp =
 //                  round_up(d, 64), zero padded; ld = 2*dp.
 //   yn             FP32 ||y||^2 of the values the Gram product actually uses
 //   yi             int32 data index of the row (the key that forces K(x,x)=1
 //                  when a batch point meets its own support copy)
-//   w64 / w32      FP64 master weight and its FP32 copy for the distance kernel
+//   w64 / w32      FP64 master weight and its FP32 copy for the distance kernel.
+//                  Invariant: both are 0 on every row outside its window, so a
+//                  tile may cover rows on either side of a window and read
+//                  their weights as they are.
 //
 // Per-center block ring: (iteration, count) of the window's blocks, oldest
 // first, at most tau + 2 entries. C_1 is not in the ring; c1[j] flags it.
@@ -37,6 +42,8 @@ constexpr int ST_BAD_BATCH_INDEX = 1;
 constexpr int ST_BAD_ASSIGN = 2;
 constexpr int ST_CAPACITY = 4;
 constexpr int ST_TIMEOUT = 8;
+
+constexpr int REGION_PAD = 128;   // unused rows at the end of each support region
 
 // Column tile of the distance pass: support rows [row0, row0 + ncols) of center j.
 struct Tile {
@@ -129,7 +136,8 @@ struct Dev {
   int32_t* nwpairs;  // [1]
   int32_t* wpair_first; // [k]
   int32_t* wpair_cnt;   // [k]
-  double* wpart;     // [max_pairs][4 slots][4 sums]: A, Bdd, E, M partials per tile
+  double* wpart;     // [max_pairs][wslots][4 sums]: A, Bdd, E, M partials per tile
+  int32_t wslots;    // partial slots per window-pass tile (4 SIMT, 8 tcgen05)
   int64_t* iter;     // [1] next iteration number
   int32_t* status;   // [1] sticky device status bits
   int64_t* stats;    // [3] steps, support rows, tiles

@@ -354,14 +354,14 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out) {
     P.ndrop = 0;
     P.c1_new = c_c1;
     if (n > 0) {
-      if (P.tail_c + n > s.cap) {       // compaction: move the window down to row 0
+      if (P.tail_c + n > s.cap - REGION_PAD) {   // compaction: move the window down to row 0
         P.src_head = P.head_c;
         P.tail_c = P.tail_c - P.head_c;
         P.head_c = 0;
         ncomp = P.tail_c;
       }
       P.tail_new = P.tail_c + n;
-      if (P.tail_new > s.cap) atomicOr(s.status, ST_CAPACITY);
+      if (P.tail_new > s.cap - REGION_PAD) atomicOr(s.status, ST_CAPACITY);
       int first = c_first, nb = c_nb;
       int32_t* bi = s.blk_iter + (int64_t)j * s.nbcap;
       int32_t* bc = s.blk_cnt + (int64_t)j * s.nbcap;
@@ -466,7 +466,7 @@ __global__ void k_move(Dev s) {
       const int j = s.assign[x];
       const Plan P = s.plan[j];
       const int pos = P.tail_c + (w - s.coff[j]);
-      if (pos >= s.cap) continue;                   // flagged ST_CAPACITY in the plan
+      if (pos >= s.cap - REGION_PAD) continue;      // flagged ST_CAPACITY in the plan
       const int64_t dst = (int64_t)j * s.cap + pos;
       warp_copy_row(s, false, x, dst);
       if (lane == 0) {
@@ -496,9 +496,15 @@ __global__ void k_move(Dev s) {
 }
 
 // Tile list of the distance pass (block of 1024, k <= 1024). Thread j < k
-// passes the window [head, head + size) of center j.
+// passes the window [head, head + size) of center j. Tiles start at head
+// rounded down to a multiple of 4 rows (16-byte aligned metadata); the rows
+// before head that this adds carry weight 0.
 __device__ void build_tiles_block(const Dev& s, int head, int size) {
   const int tid = threadIdx.x;
+  if (size > 0) {
+    size += head & 3;
+    head &= ~3;
+  }
   const int nt = tid < s.k ? (size + s.tn - 1) / s.tn : 0;
   int total = 0;
   const int first = block_exclusive_scan_1024(nt, &total);
@@ -553,7 +559,8 @@ __global__ void __launch_bounds__(32) k_finalize(Dev s) {
   const int p0 = s.wpair_first[j];
   const int np = (p0 + s.wpair_cnt[j] <= s.max_pairs) ? s.wpair_cnt[j] : 0;
   double q[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int e = lane; e < np * 16; e += 32) q[e & 3] += s.wpart[(int64_t)p0 * 16 + e];
+  const int per = s.wslots * 4;
+  for (int e = lane; e < np * per; e += 32) q[e & 3] += s.wpart[(int64_t)p0 * per + e];
   const double A = warp_sum(q[0]), Bdd = warp_sum(q[1]), E = warp_sum(q[2]), M = warp_sum(q[3]);
   const double dn = (double)n;
   const double a = (s.lr == 0) ? sqrt(dn * s.inv_b) : s.eta;
@@ -576,6 +583,17 @@ __global__ void __launch_bounds__(32) k_finalize(Dev s) {
   }
   const float wnew32 = (float)wnew;
   const int64_t base = (int64_t)j * s.cap;
+  // rows that leave the window get weight 0: the dropped prefix and, after a
+  // compaction, the old copies of the moved rows
+  for (int r = P.head_c + lane; r < P.head_new; r += 32) {
+    s.w64[base + r] = 0.0;
+    s.w32[base + r] = 0.0f;
+  }
+  if (P.src_head >= 0)
+    for (int r = P.src_head + lane; r < P.src_head + (P.tail_c - P.head_c); r += 32) {
+      s.w64[base + r] = 0.0;
+      s.w32[base + r] = 0.0f;
+    }
   for (int r = P.head_new + lane; r < min(P.tail_c, s.cap); r += 32) {
     const double w = s.w64[base + r] * keep;
     s.w64[base + r] = w;
