@@ -78,6 +78,7 @@ struct Shared {
     float warp[NEPI][5][64];                    // window pass: per epilogue warp (load_pair_meta)
   } meta;
   float red[2][4][32];                          // distance pass: second-half row sums (item parity, quadrant)
+  float wred[2][NEPI][4];                       // window pass: per-warp sums (item parity, warp, sum)
 };
 
 constexpr int SMEM_BYTES = 1024 + RING_BYTES + (int)sizeof(Shared);
@@ -296,8 +297,8 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 }
 
 // MODE 0: distance pass (A = batch tile, B = support tile, one FP32 partial per row).
-// MODE 1: window pass (A and B = support rows of one center, four FP32 sums per warp,
-//         added up in FP64 by the finalize kernel).
+// MODE 1: window pass (A and B = support rows of one center; four sums per item:
+//         FP32 within a warp, FP64 across the eight epilogue warps).
 // Items are dealt round-robin to the persistent CTAs. Splitting a tile along
 // its columns needs no merge because both passes only sum over columns, so
 // narrower tiles (TNV = 64) are how the window pass gets enough items.
@@ -543,50 +544,58 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (lane == 0 && !dead) atomicOr(s.status, ST_TIMEOUT);
           dead = true;
         }
-        if (dead) continue;
-        tc_fence_after();
-        const float rc = (KIND == K_GAUSS) ? xn * negc : xn;
-        float2 a0 = make_float2(0.0f, 0.0f), a1 = a0, a2 = a0;
-#pragma unroll
-        for (int ch = 0; ch < C / 32; ++ch) {
-          float g[32];
-          tmem_ld32(taddr + ch * 32, g);
-          if (ch == C / 32 - 1) {
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&sh.tempty[buf]);
-          }
-#pragma unroll
-          for (int i = 0; i < 32; i += 2) {
-            const int c = ch * 32 + i;
-            const float2 cc = *reinterpret_cast<const float2*>(&mw[0][c]);
-            const float2 wa = *reinterpret_cast<const float2*>(&mw[1][c]);
-            const int2 yi = *reinterpret_cast<const int2*>(&mw[2][c]);
-            const float2 wb = *reinterpret_cast<const float2*>(&mw[3][c]);
-            const float2 we = *reinterpret_cast<const float2*>(&mw[4][c]);
-            const float2 kv = kernel_pair<KIND>(make_float2(g[i], g[i + 1]), rc, cc, xi, yi, negc, coef0, degree);
-            a0 = __ffma2_rn(wa, kv, a0);
-            a1 = __ffma2_rn(wb, kv, a1);
-            a2 = __ffma2_rn(we, kv, a2);
-          }
-        }
-        // kind 0: A = w_p sum_{q in W} w_q K, Bdd = w_p sum_{q in D} w_q K, E = w_p sum_{q in B} K
-        // kind 1: M = sum_{q in B} K (every valid column of a kind-1 tile is in B)
         float sA = 0.0f, sB = 0.0f, sE = 0.0f, sM = 0.0f;
-        if (rvalid) {
-          if (pt.kind == 0) { sA = wp * (a0.x + a0.y); sB = wp * (a1.x + a1.y); sE = wp * (a2.x + a2.y); }
-          else sM = a2.x + a2.y;
-        }
+        if (!dead) {
+          tc_fence_after();
+          const float rc = (KIND == K_GAUSS) ? xn * negc : xn;
+          float2 a0 = make_float2(0.0f, 0.0f), a1 = a0, a2 = a0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          sA += __shfl_xor_sync(0xffffffffu, sA, o);
-          sB += __shfl_xor_sync(0xffffffffu, sB, o);
-          sE += __shfl_xor_sync(0xffffffffu, sE, o);
-          sM += __shfl_xor_sync(0xffffffffu, sM, o);
+          for (int ch = 0; ch < C / 32; ++ch) {
+            float g[32];
+            tmem_ld32(taddr + ch * 32, g);
+            if (ch == C / 32 - 1) {
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&sh.tempty[buf]);
+            }
+#pragma unroll
+            for (int i = 0; i < 32; i += 2) {
+              const int c = ch * 32 + i;
+              const float2 cc = *reinterpret_cast<const float2*>(&mw[0][c]);
+              const float2 wa = *reinterpret_cast<const float2*>(&mw[1][c]);
+              const int2 yi = *reinterpret_cast<const int2*>(&mw[2][c]);
+              const float2 wb = *reinterpret_cast<const float2*>(&mw[3][c]);
+              const float2 we = *reinterpret_cast<const float2*>(&mw[4][c]);
+              const float2 kv = kernel_pair<KIND>(make_float2(g[i], g[i + 1]), rc, cc, xi, yi, negc, coef0, degree);
+              a0 = __ffma2_rn(wa, kv, a0);
+              a1 = __ffma2_rn(wb, kv, a1);
+              a2 = __ffma2_rn(we, kv, a2);
+            }
+          }
+          // kind 0: A = w_p sum_{q in W} w_q K, Bdd = w_p sum_{q in D} w_q K, E = w_p sum_{q in B} K
+          // kind 1: M = sum_{q in B} K (every valid column of a kind-1 tile is in B)
+          if (rvalid) {
+            if (pt.kind == 0) { sA = wp * (a0.x + a0.y); sB = wp * (a1.x + a1.y); sE = wp * (a2.x + a2.y); }
+            else sM = a2.x + a2.y;
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            sA += __shfl_xor_sync(0xffffffffu, sA, o);
+            sB += __shfl_xor_sync(0xffffffffu, sB, o);
+            sE += __shfl_xor_sync(0xffffffffu, sE, o);
+            sM += __shfl_xor_sync(0xffffffffu, sM, o);
+          }
         }
-        if (lane == 0) {
-          double* out = s.wpart + ((int64_t)item * NEPI + e) * 4;
-          out[0] = sA; out[1] = sB; out[2] = sE; out[3] = sM;
+        // the eight warps' sums meet in shared memory (slot by item parity);
+        // one thread per sum adds them in a fixed order and writes the item's four sums
+        float (*red)[4] = sh.wred[local & 1u];
+        if (lane == 0) { red[e][0] = sA; red[e][1] = sB; red[e][2] = sE; red[e][3] = sM; }
+        asm volatile("bar.sync 5, %0;" ::"n"(32 * NEPI) : "memory");
+        if (e == 0 && lane < 4 && !dead) {
+          double v = 0.0;
+#pragma unroll
+          for (int w = 0; w < NEPI; ++w) v += (double)red[w][lane];
+          s.wpart[(int64_t)item * 4 + lane] = v;
         }
       }
     }

@@ -137,7 +137,7 @@ struct Dev {
   int32_t* wpair_first; // [k]
   int32_t* wpair_cnt;   // [k]
   double* wpart;     // [max_pairs][wslots][4 sums]: A, Bdd, E, M partials per tile
-  int32_t wslots;    // partial slots per window-pass tile (4 SIMT, 8 tcgen05)
+  int32_t wslots;    // partial slots per window-pass tile (4 SIMT, 1 tcgen05)
   int64_t* iter;     // [1] next iteration number
   int32_t* status;   // [1] sticky device status bits
   int64_t* stats;    // [3] steps, support rows, tiles

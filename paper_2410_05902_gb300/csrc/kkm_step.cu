@@ -539,35 +539,51 @@ __global__ void __launch_bounds__(1024) k_build_tiles(Dev s) {
   build_tiles_block(s);
 }
 
-// One warp per center j (block j) that received points, FP64 where the values
-// accumulate over iterations:
+// One block of 256 threads per center j that received points, FP64 where the
+// values accumulate over iterations:
 //   alpha_j = sqrt(b_j / b) (or eta), <C_j, cm(B_j)> = (1/b_j) sum_x <phi(x), C_j>
 //   (from k_sort_plan's 32 FP32 lane partials), the window-pass sums, the
 //   Sec. 4 recurrence for ||C_j||^2 corrected for the rows Eq. (1) drops, and
 //   the weights: rows [head_new, tail_c) decay by (1 - alpha), rows
-//   [tail_c, tail_new) get alpha / b_j.
-// GB300 issues FP64 slowly and charges each FP64 warp instruction in full, so
-// the FP64 work stays on one warp per center, on sums already reduced in FP32
-// where the terms are FP32. Every load here depends only on the plan.
-__global__ void __launch_bounds__(32) k_finalize(Dev s) {
+//   [tail_c, tail_new) get alpha / b_j, rows that left the window get 0.
+// GB300 issues FP64 slowly, so the scalar FP64 work runs on one thread and the
+// per-row work is spread over the block, with independent loads in flight.
+__global__ void __launch_bounds__(256) k_finalize(Dev s) {
   KKM_GRID_DEP_WAIT();
-  const int lane = threadIdx.x, j = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, j = blockIdx.x;
   const Plan P = s.plan[j];
   if (P.cnt == 0) return;
-  const int n = P.cnt;
-  const double cm_sum = warp_sum((double)s.cmpart[(int64_t)j * 32 + lane]);
+  __shared__ double red[8][4];
+  __shared__ double cm_s;
+  __shared__ double keep_s, wnew_s;
+  // window-pass sums: element e of a tile's partials is sum e & 3 (A, Bdd, E, M);
+  // with a stride of 256 every thread stays on sum tid & 3
+  const int per = s.wslots * 4;
   const int p0 = s.wpair_first[j];
   const int np = (p0 + s.wpair_cnt[j] <= s.max_pairs) ? s.wpair_cnt[j] : 0;
-  double q[4] = {0.0, 0.0, 0.0, 0.0};
-  const int per = s.wslots * 4;
-  for (int e = lane; e < np * per; e += 32) q[e & 3] += s.wpart[(int64_t)p0 * per + e];
-  const double A = warp_sum(q[0]), Bdd = warp_sum(q[1]), E = warp_sum(q[2]), M = warp_sum(q[3]);
-  const double dn = (double)n;
-  const double a = (s.lr == 0) ? sqrt(dn * s.inv_b) : s.eta;
-  const double keep = 1.0 - a, wnew = a / dn;
-  if (lane == 0) {
+  const double* wp = s.wpart + (int64_t)p0 * per;
+  double acc = 0.0;
+#pragma unroll 4
+  for (int e = tid; e < np * per; e += 256) acc += wp[e];
+#pragma unroll
+  for (int o = 4; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane < 4) red[warp][lane] = acc;
+  if (warp == 0) {
+    const double v = warp_sum((double)s.cmpart[(int64_t)j * 32 + lane]);
+    if (lane == 0) cm_s = v;
+  }
+  __syncthreads();
+  const int n = P.cnt;
+  if (tid == 0) {
+    double q[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int w = 0; w < 8; ++w)
+      for (int t = 0; t < 4; ++t) q[t] += red[w][t];
+    const double A = q[0], Bdd = q[1], E = q[2], M = q[3];
+    const double dn = (double)n;
+    const double a = (s.lr == 0) ? sqrt(dn * s.inv_b) : s.eta;
+    const double keep = 1.0 - a;
     s.alpha[j] = a;
-    const double cmc = cm_sum / dn;
+    const double cmc = cm_s / dn;
     s.cmc[j] = cmc;
     // Sec. 4: ||C'||^2 = (1-a)^2 ||R||^2 + 2a(1-a) <R, m> + a^2 ||m||^2 with
     // m = cm(B_j) and R = C - D, the part of the old center Eq. (1) keeps
@@ -580,26 +596,31 @@ __global__ void __launch_bounds__(32) k_finalize(Dev s) {
     s.head[j] = P.head_new;
     s.tail[j] = P.tail_new;
     s.c1[j] = P.c1_new;
+    keep_s = keep;
+    wnew_s = a / dn;
   }
+  __syncthreads();
+  const double keep = keep_s, wnew = wnew_s;
   const float wnew32 = (float)wnew;
   const int64_t base = (int64_t)j * s.cap;
   // rows that leave the window get weight 0: the dropped prefix and, after a
   // compaction, the old copies of the moved rows
-  for (int r = P.head_c + lane; r < P.head_new; r += 32) {
+  for (int r = P.head_c + tid; r < P.head_new; r += 256) {
     s.w64[base + r] = 0.0;
     s.w32[base + r] = 0.0f;
   }
   if (P.src_head >= 0)
-    for (int r = P.src_head + lane; r < P.src_head + (P.tail_c - P.head_c); r += 32) {
+    for (int r = P.src_head + tid; r < P.src_head + (P.tail_c - P.head_c); r += 256) {
       s.w64[base + r] = 0.0;
       s.w32[base + r] = 0.0f;
     }
-  for (int r = P.head_new + lane; r < min(P.tail_c, s.cap); r += 32) {
+#pragma unroll 4
+  for (int r = P.head_new + tid; r < min(P.tail_c, s.cap); r += 256) {
     const double w = s.w64[base + r] * keep;
     s.w64[base + r] = w;
     s.w32[base + r] = (float)w;
   }
-  for (int r = P.tail_c + lane; r < min(P.tail_new, s.cap); r += 32) {
+  for (int r = P.tail_c + tid; r < min(P.tail_new, s.cap); r += 256) {
     s.w64[base + r] = wnew;
     s.w32[base + r] = wnew32;
   }
@@ -722,7 +743,7 @@ cudaError_t launch_move(const Dev& s, cudaStream_t st) {
 }
 
 cudaError_t launch_finalize(const Dev& s, cudaStream_t st) {
-  cudaError_t e = launch_pdl(k_finalize, dim3(s.k), dim3(32), 0, st, s);
+  cudaError_t e = launch_pdl(k_finalize, dim3(s.k), dim3(256), 0, st, s);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
