@@ -11,8 +11,6 @@ namespace kkm {
 
 namespace {
 
-constexpr int kWarp = 32;
-
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -183,41 +181,82 @@ __global__ void k_gather_query(Dev s, const float* __restrict__ Q, int64_t ldq, 
   }
 }
 
-// One warp per batch row, one lane per center (lane j handles centers j,
-// j+32, ...): <phi(x), C_j> is the sum of center j's per-tile partials (its
+// Block of 16 warps per 32 batch rows: lane = row, warp w handles centers
+// w, w+16, ... so every load of the per-tile partials is one coalesced
+// 128-byte line. <phi(x), C_j> is the sum of center j's per-tile partials (its
 // tiles are the consecutive list entries tile_first[j] ..), then
-// Delta(x, C_j) = K(x,x) - 2 <phi(x), C_j> + ||C_j||^2 in FP64, and a warp
-// argmin with ties to the lowest j. Every lane's loads are independent, so a
-// row costs a few memory latencies whatever k is.
-__global__ void k_argmin(Dev s, int rows, const int32_t* __restrict__ forced,
-                         int32_t* __restrict__ assign_out, float* __restrict__ mind_out,
-                         float* __restrict__ dist_out, int update) {
+// Delta(x, C_j) = K(x,x) - 2 <phi(x), C_j> + ||C_j||^2 in FP32, and the argmin
+// with ties to the lowest j, across the warps in shared memory. A warp takes
+// four centers at a time and issues the loads of their first four tiles
+// before it adds anything, so a row costs a few memory latencies.
+constexpr int AM_WARPS = 16;
+
+__global__ void __launch_bounds__(32 * AM_WARPS) k_argmin(Dev s, int rows, const int32_t* __restrict__ forced,
+                                                          int32_t* __restrict__ assign_out,
+                                                          float* __restrict__ mind_out,
+                                                          float* __restrict__ dist_out, int update) {
   KKM_GRID_DEP_WAIT();
-  const int x = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (x >= rows) return;
-  const float kxx = (float)kernel_self(s.kind, (double)s.xbn[x], s.coef0, s.degree);
-  const int fa = forced ? forced[x] : -1;
+  __shared__ float r_best[AM_WARPS][32], r_inner[AM_WARPS][32], r_f[AM_WARPS][32];
+  __shared__ int r_j[AM_WARPS][32];
+  __shared__ int c_first[1024], c_cnt[1024];
+  __shared__ float c_norm[1024];
+  for (int j = threadIdx.x; j < s.k; j += 32 * AM_WARPS) {
+    c_first[j] = s.tile_first[j];
+    c_cnt[j] = s.tile_cnt[j];
+    c_norm[j] = s.cnorm32[j];
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int x = blockIdx.x * 32 + lane;
+  const bool live = x < rows;
+  const int xr = live ? x : 0;
+  const float kxx = (float)kernel_self(s.kind, (double)s.xbn[xr], s.coef0, s.degree);
+  const int fa = forced ? forced[xr] : -1;
+  __syncthreads();
   float best = 3.0e38f, best_inner = 0.0f, f_inner = 0.0f;
   int bj = 0x7fffffff;
-  for (int j = lane; j < s.k; j += 32) {
-    const int t0 = s.tile_first[j], nt = s.tile_cnt[j];
-    float inner = 0.0f;
-    for (int t = 0; t < nt; ++t) inner += s.part[(int64_t)(t0 + t) * s.bpad + x];
-    const float dist = fmaf(-2.0f, inner, kxx + s.cnorm32[j]);
-    if (dist_out) dist_out[(int64_t)x * s.k + j] = (float)dist;
-    if (dist < best) { best = dist; bj = j; best_inner = inner; }   // j increases: ties keep the lowest
-    if (j == fa) f_inner = inner;
-  }
+  const float* part = s.part + xr;
+  const int64_t ld = s.bpad;
+  for (int j0 = w; j0 < s.k; j0 += 4 * AM_WARPS) {
+    float v[4][4];
+    int t0[4], nt[4];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-    const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
-    const float oi = __shfl_xor_sync(0xffffffffu, best_inner, o);
-    if (ob < best || (ob == best && oj < bj)) { best = ob; bj = oj; best_inner = oi; }
-    f_inner += __shfl_xor_sync(0xffffffffu, f_inner, o);   // only the lane owning fa is non-zero
+    for (int u = 0; u < 4; ++u) {
+      const int j = j0 + u * AM_WARPS;
+      t0[u] = j < s.k ? c_first[j] : 0;
+      nt[u] = j < s.k ? c_cnt[j] : 0;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) v[u][t] = t < nt[u] ? part[(int64_t)(t0[u] + t) * ld] : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = j0 + u * AM_WARPS;
+      if (j >= s.k) break;
+      float i0 = v[u][0], i1 = v[u][1], i2 = v[u][2], i3 = v[u][3];
+      for (int t = 4; t < nt[u]; t += 4) {
+        i0 += part[(int64_t)(t0[u] + t) * ld];
+        if (t + 1 < nt[u]) i1 += part[(int64_t)(t0[u] + t + 1) * ld];
+        if (t + 2 < nt[u]) i2 += part[(int64_t)(t0[u] + t + 2) * ld];
+        if (t + 3 < nt[u]) i3 += part[(int64_t)(t0[u] + t + 3) * ld];
+      }
+      const float inner = (i0 + i1) + (i2 + i3);
+      const float dist = fmaf(-2.0f, inner, kxx + c_norm[j]);
+      if (dist_out && live) dist_out[(int64_t)x * s.k + j] = dist;
+      if (dist < best) { best = dist; bj = j; best_inner = inner; }   // j increases: ties keep the lowest
+      if (j == fa) f_inner = inner;
+    }
   }
-  if (lane != 0) return;
+  r_best[w][lane] = best;
+  r_j[w][lane] = bj;
+  r_inner[w][lane] = best_inner;
+  r_f[w][lane] = f_inner;
+  __syncthreads();
+  if (w != 0 || !live) return;
+  for (int o = 1; o < AM_WARPS; ++o) {
+    const float ob = r_best[o][lane];
+    const int oj = r_j[o][lane];
+    if (ob < best || (ob == best && oj < bj)) { best = ob; bj = oj; best_inner = r_inner[o][lane]; }
+    f_inner += r_f[o][lane];   // only the warp owning fa is non-zero
+  }
   int a = bj;
   float a_inner = best_inner;
   if (forced) {
@@ -247,7 +286,8 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out) {
   KKM_GRID_DEP_WAIT();
   extern __shared__ __align__(16) unsigned char smem[];
   const int k = s.k, b = s.b, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  int32_t* cnt = (int32_t*)smem;            // [k]
+  Plan* splan = (Plan*)smem;                // [k]   this step's window plans
+  int32_t* cnt = (int32_t*)(splan + k);     // [k]
   int32_t* base = cnt + k;                  // [k]
   int32_t* tot = base + k;                  // [k]
   int32_t* coff = tot + k;                  // [k]
@@ -294,14 +334,17 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out) {
     const int rank = __popc(peers & ((1u << lane) - 1u));
     if (j >= 0 && rank == 0) wtab[warp * k + j] = (uint16_t)__popc(peers);
     __syncthreads();
-    for (int jj = tid; jj < k; jj += 1024) {
-      int run = 0;
-      for (int w = 0; w < 32; ++w) {
-        const int v = wtab[w * k + jj];
-        wtab[w * k + jj] = (uint16_t)run;
-        run += v;
+    // exclusive prefix of each center's per-warp counts over the 32 warps: one warp per center
+    for (int jj = warp; jj < k; jj += 32) {
+      const int v = wtab[lane * k + jj];
+      int x = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
       }
-      tot[jj] = run;
+      wtab[lane * k + jj] = (uint16_t)(x - v);
+      if (lane == 31) tot[jj] = x;
     }
     __syncthreads();
     if (j >= 0) sperm[coff[j] + base[j] + wtab[warp * k + j] + rank] = (int16_t)x;
@@ -326,12 +369,13 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) wpartial[warp] = v;
     __syncthreads();
-    if (tid == 0) {
-      double t = 0.0;
-      for (int w = 0; w < 32; ++w) t += (double)wpartial[w];
-      const double f = t / (double)b;
-      *s.obj = f;
-      if (obj_out) *obj_out = f;
+    if (warp == 0) {
+      const double t = warp_sum((double)wpartial[lane]);
+      if (lane == 0) {
+        const double f = t * s.inv_b;
+        *s.obj = f;
+        if (obj_out) *obj_out = f;
+      }
     }
   }
   // support rows read by this step's distance pass
@@ -402,6 +446,7 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out) {
       npairs = ((nD + TR - 1) / TR) * ((nL + TC - 1) / TC) + ((n + TR - 1) / TR) * ((n + TC - 1) / TC);
     }
     s.plan[j] = P;
+    splan[j] = P;
   }
   __syncthreads();
   int ctotal = 0;
@@ -413,9 +458,8 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out) {
   {
     int head = 0, size = 0;
     if (tid < k) {
-      const Plan P = s.plan[tid];
-      head = P.head_new;
-      size = P.tail_new - P.head_new;
+      head = splan[tid].head_new;
+      size = splan[tid].tail_new - head;
     }
     build_tiles_block(s, head, size);
   }
@@ -434,17 +478,22 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out) {
   if (tid < k) {
     s.wpair_first[tid] = pfirst;
     s.wpair_cnt[tid] = npairs;
-    if (npairs > 0 && pfirst + npairs <= s.max_pairs) {
-      const Plan P = s.plan[tid];
-      const int TR = s.pair_rows, TC = s.pair_cols;
-      const int nD = P.ndrop, nL = P.tail_new - P.head_c, n = P.cnt;
-      const int rD = (nD + TR - 1) / TR, cL = (nL + TC - 1) / TC;
-      const int rB = (n + TR - 1) / TR, cB = (n + TC - 1) / TC;
-      int e = pfirst;
-      for (int rt = 0; rt < rD; ++rt)
-        for (int ct = 0; ct < cL; ++ct) s.wpairs[e++] = WPair{tid, 0, rt, ct};
-      for (int rt = 0; rt < rB; ++rt)
-        for (int ct = 0; ct < cB; ++ct) s.wpairs[e++] = WPair{tid, 1, rt, ct};
+    base[tid] = pfirst;
+    tot[tid] = npairs;
+  }
+  __syncthreads();
+  // the window-pass tile list: one warp per center, a lane per tile
+  for (int j = warp; j < k; j += 32) {
+    const int np = tot[j], pf = base[j];
+    if (np == 0 || pf + np > s.max_pairs) continue;
+    const Plan P = splan[j];
+    const int TR = s.pair_rows, TC = s.pair_cols;
+    const int nD = P.ndrop, nL = P.tail_new - P.head_c, n = P.cnt;
+    const int cL = (nL + TC - 1) / TC, cB = (n + TC - 1) / TC;
+    const int n0 = ((nD + TR - 1) / TR) * cL;
+    for (int e = lane; e < np; e += 32) {
+      const int f = e - n0;
+      s.wpairs[pf + e] = e < n0 ? WPair{j, 0, e / cL, e % cL} : WPair{j, 1, f / cB, f % cB};
     }
   }
 }
@@ -500,7 +549,8 @@ __global__ void k_move(Dev s) {
 // rounded down to a multiple of 4 rows (16-byte aligned metadata); the rows
 // before head that this adds carry weight 0.
 __device__ void build_tiles_block(const Dev& s, int head, int size) {
-  const int tid = threadIdx.x;
+  __shared__ int t_first[1024], t_nt[1024], t_head[1024], t_size[1024];
+  const int tid = threadIdx.x, lane = tid & 31;
   if (size > 0) {
     size += head & 3;
     head &= ~3;
@@ -516,13 +566,18 @@ __device__ void build_tiles_block(const Dev& s, int head, int size) {
     const bool fits = first + nt <= s.max_tiles;   // never false by the capacity bound
     s.tile_first[tid] = fits ? first : 0;
     s.tile_cnt[tid] = fits ? nt : 0;
-    if (fits)
-      for (int t = 0; t < nt; ++t) {
-        const int c = t * s.tn;
-        s.tiles[first + t] = Tile{tid, (int32_t)((int64_t)tid * s.cap + head + c),
-                                  min(s.tn, size - c), 0};
-      }
+    t_first[tid] = first;
+    t_nt[tid] = fits ? nt : 0;
+    t_head[tid] = head;
+    t_size[tid] = size;
   }
+  __syncthreads();
+  // one warp per center, a lane per tile
+  for (int j = tid >> 5; j < s.k; j += 32)
+    for (int t = lane; t < t_nt[j]; t += 32) {
+      const int c = t * s.tn;
+      s.tiles[t_first[j] + t] = Tile{j, (int32_t)((int64_t)j * s.cap + t_head[j] + c), min(s.tn, t_size[j] - c), 0};
+    }
 }
 
 __device__ void build_tiles_block(const Dev& s) {
@@ -714,19 +769,20 @@ cudaError_t launch_gather_query(const Dev& s, const float* Q, int64_t ldq, int r
 cudaError_t launch_argmin(const Dev& s, int rows, const int32_t* forced, int32_t* assign_out,
                           float* mind_out, float* dist_out, bool update, cudaStream_t st) {
   if (rows <= 0) return cudaSuccess;
-  cudaError_t e = launch_pdl(k_argmin, dim3((rows * 32 + 127) / 128), dim3(128), 0, st, s, rows, forced,
+  cudaError_t e = launch_pdl(k_argmin, dim3((rows + 31) / 32), dim3(32 * AM_WARPS), 0, st, s, rows, forced,
                              assign_out, mind_out, dist_out, update ? 1 : 0);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
-int sort_plan_smem(int k, int b) { return 4 * k * 4 + b * (4 + 2 + 2) + 32 * k * 2; }
+int sort_plan_smem(int k, int b) { return k * (int)sizeof(Plan) + 4 * k * 4 + b * (4 + 2 + 2) + 32 * k * 2; }
 
 cudaError_t launch_sort_plan(const Dev& s, double* obj_out, cudaStream_t st) {
   const int smem = sort_plan_smem(s.k, s.b);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_sort_plan, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    const cudaError_t e = cudaFuncSetAttribute(k_sort_plan, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
     attr_set = true;
   }
   cudaError_t e = launch_pdl(k_sort_plan, dim3(1), dim3(1024), smem, st, s, obj_out);
