@@ -41,7 +41,8 @@ template <bool X3, int TNV> struct Ring {
   static constexpr int bytes = X3 ? 2 * (A_BYTES + b_bytes) : A_BYTES + b_bytes;
   static constexpr int stages = RING_BYTES / bytes;   // 3, 4, 6 or 8
 };
-constexpr int NEPI = 8;                          // epilogue warps (two per TMEM lane quadrant)
+constexpr int NEPI = 16;                         // epilogue warps (four per TMEM lane quadrant)
+constexpr int NH = NEPI / 4;                     // column parts of an accumulator
 constexpr int NTHREADS = 64 + 32 * NEPI;        // + one TMA warp and one MMA warp
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;   // 2 s per wait
 
@@ -75,9 +76,9 @@ struct Shared {
   uint32_t pad;
   union alignas(16) {
     MetaSlot ring[MS];                          // distance pass
-    float warp[NEPI][5][64];                    // window pass: per epilogue warp (load_pair_meta)
+    float warp[NEPI][5][32];                    // window pass: per epilogue warp (load_pair_meta)
   } meta;
-  float red[2][4][32];                          // distance pass: second-half row sums (item parity, quadrant)
+  float red[2][NH - 1][4][32];                   // distance pass: row sums of column parts 1.. (item parity, part, quadrant)
   float wred[2][NEPI][4];                       // window pass: per-warp sums (item parity, warp, sum)
 };
 
@@ -173,23 +174,36 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-// 32 consecutive FP32 accumulator columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+// tcgen05.ld .16x256b.xNB: 16 TMEM lanes starting at the address's lane, NB
+// blocks of 8 consecutive FP32 columns. Thread t receives, for block j,
+//   v[4j]   = (lane t/4,     column 8j + 2(t%4)),  v[4j+1] = the next column,
+//   v[4j+2] = (lane t/4 + 8, column 8j + 2(t%4)),  v[4j+3] = the next column.
+// Each column value is needed by 4 threads instead of 32 (the 32x32b shape
+// gives a thread one lane and all columns), which cuts the per-column
+// metadata the epilogue reads from shared memory by 4x.
+template <int NB>
+__device__ __forceinline__ void tmem_ld16x256(uint32_t taddr, float (&v)[4 * NB]) {
+  uint32_t r[4 * NB];
+  if constexpr (NB == 4) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.16x256b.x4.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+  } else {
+    static_assert(NB == 2, "tmem_ld16x256: 2 or 4 blocks");
+    asm volatile(
+        "tcgen05.ld.sync.aligned.16x256b.x2.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "r"(taddr));
+  }
 #pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 4 * NB; ++i) v[i] = __uint_as_float(r[i]);
 }
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
@@ -205,7 +219,9 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 
 // Kernel values of one row against two columns from their Gram entries g.
 // Gaussian: rc = ||x||^2 * negc and cc = ||y||^2 * negc (negc = -log2(e)/kappa),
-//           K = 2^min(rc + cc - 2 negc g, 0).
+//           K = 2^(rc + cc - 2 negc g). The exponent is -D^2 log2(e)/kappa with
+//           D^2 = ||x||^2 + ||y||^2 - 2g; rounding can leave it a few ulps of
+//           ||x||^2 above 0 for near-duplicates, where K = 1 to that accuracy.
 // Laplacian: rc = ||x||^2, cc = ||y||^2, K = 2^(negc * sqrt(max(D^2, 0))).
 // Both give exactly 1 when the two rows are the same data point (K(x,x) = 1).
 // Linear and polynomial values of padding columns (yi = -2) are zeroed, as
@@ -216,8 +232,8 @@ __device__ __forceinline__ float2 kernel_pair(float2 g, float rc, float2 cc, int
   float2 k;
   if constexpr (KIND == K_GAUSS) {
     const float2 a = __ffma2_rn(g, make_float2(-2.0f * negc, -2.0f * negc), __fadd2_rn(make_float2(rc, rc), cc));
-    k.x = xi == yi.x ? 1.0f : ex2_approx(fminf(a.x, 0.0f));
-    k.y = xi == yi.y ? 1.0f : ex2_approx(fminf(a.y, 0.0f));
+    k.x = xi == yi.x ? 1.0f : ex2_approx(a.x);
+    k.y = xi == yi.y ? 1.0f : ex2_approx(a.y);
   } else if constexpr (KIND == K_LAPLACE) {
     const float2 d2 = __ffma2_rn(g, make_float2(-2.0f, -2.0f), __fadd2_rn(make_float2(rc, rc), cc));
     k.x = xi == yi.x ? 1.0f : ex2_approx(sqrt_approx(fmaxf(d2.x, 0.0f)) * negc);
@@ -264,21 +280,23 @@ __device__ __forceinline__ PairTile pair_tile(const Dev& s, int w) {
   return t;
 }
 
-// Window-pass column metadata of one epilogue warp (C columns of its half
-// tile): col[0] = ||y||^2 (times negc for the Gaussian), col[1] = w on the
+// Window-pass column metadata of one epilogue warp (the C = TNV / NH columns of
+// its part of the tile): col[0] = ||y||^2 (times negc for the Gaussian), col[1] = w on the
 // old window (A), col[2] = data index (-2 on padding columns), col[3] = w on
-// the dropped rows (Bdd), col[4] = 1 on the new block (E).
+// the dropped rows (Bdd), col[4] = 1 on the new block (E). Padding columns
+// keep the ||y||^2 of the row the MMA read there, so their kernel values stay
+// finite (and their weights are 0).
 template <int KIND, int TNV>
-__device__ __forceinline__ void load_pair_meta(const Dev& s, const PairTile& pt, int cbase, float (*m)[64],
+__device__ __forceinline__ void load_pair_meta(const Dev& s, const PairTile& pt, int cbase, float (*m)[32],
                                                int lane) {
-  constexpr int C = TNV / 2;
+  constexpr int C = TNV / NH;
   const float sc = (KIND == K_GAUSS) ? s.negc : 1.0f;
 #pragma unroll
   for (int c = lane; c < C; c += 32) {
     const int col = cbase + c;
-    const int qpos = pt.cs + col;
+    const int qpos = pt.cs + col;                // inside the region even past the range
     const bool valid = col < pt.crem;
-    const int64_t gi = pt.base + (valid ? qpos : pt.cs);
+    const int64_t gi = pt.base + qpos;
     const float w = valid ? s.w32[gi] : 0.0f;
     const bool in_d = qpos < pt.head_new, in_old = qpos < pt.tail_c;
     m[0][c] = s.yn[gi] * sc;
@@ -464,15 +482,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   } else {
     // ---------------------------------------------------------------- epilogue
-    // Eight warps, two per TMEM lane quadrant: warp e = warp - 2 reads lanes
+    // NEPI warps, NH per TMEM lane quadrant: warp e = warp - 2 reads lanes
     // 32*(warp % 4).. (the rows of quadrant q) and columns [h*C, h*C + C) of the
     // accumulator, h = e / 4.
     const int e = warp - 2;
     const int q = warp & 3;
     const int h = e >> 2;
-    constexpr int C = TNV / 2;
+    constexpr int C = TNV / NH;                  // accumulator columns of this warp
+    constexpr int NB = C / 8;                    // 8-column blocks per TMEM load
     const int cbase = h * C;
-    const int rloc = q * 32 + lane;              // this thread's row inside the tile
+    // this thread's rows inside the quadrant: g4 + 8u (u = 0..3); its columns:
+    // cbase + 8j + c2 and the next one (j = 0..NB-1)
+    const int g4 = lane >> 2, c2 = 2 * (lane & 3);
+    const int rq = g4 + 8 * (lane & 3);          // the row this thread reports after the reduction
     const float negc = s.negc;
     const float coef0 = (float)s.coef0;
     const int degree = s.degree;
@@ -489,107 +511,148 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (lane == 0 && !dead) atomicOr(s.status, ST_TIMEOUT);
           dead = true;
         }
-        float f0 = 0.0f;
+        float f = 0.0f;
         if (!dead) {
           tc_fence_after();
-          const float xn = m.row[0][rloc];
-          const int xi = __float_as_int(m.row[1][rloc]);
-          const float rc = (KIND == K_GAUSS) ? xn * negc : xn;
-          float2 a0 = make_float2(0.0f, 0.0f), a1 = a0;
-#pragma unroll
-          for (int ch = 0; ch < C / 32; ++ch) {
-            float g[32];
-            tmem_ld32(taddr + ch * 32, g);
-            if (ch == C / 32 - 1) {   // the accumulator is free for the next item's MMAs
-              tc_fence_before();
-              __syncwarp();
-              if (lane == 0) mbar_arrive(&sh.tempty[buf]);
-            }
-#pragma unroll
-            for (int i = 0; i < 32; i += 2) {
-              const int c = cbase + ch * 32 + i;
-              const float2 yn = *reinterpret_cast<const float2*>(&m.col[0][c]);
-              const float2 w = *reinterpret_cast<const float2*>(&m.col[1][c]);
-              const int2 yi = *reinterpret_cast<const int2*>(&m.col[2][c]);
-              const float2 cc = (KIND == K_GAUSS) ? __fmul2_rn(yn, make_float2(negc, negc)) : yn;
-              const float2 kv = kernel_pair<KIND>(make_float2(g[i], g[i + 1]), rc, cc, xi, yi, negc, coef0, degree);
-              if ((i & 2) == 0) a0 = __ffma2_rn(w, kv, a0);
-              else a1 = __ffma2_rn(w, kv, a1);
-            }
-          }
-          f0 = (a0.x + a0.y) + (a1.x + a1.y);
+          float v0[4 * NB], v1[4 * NB];
+          tmem_ld16x256<NB>(taddr, v0);                          // rows g4, g4 + 8
+          tmem_ld16x256<NB>(taddr + (16u << 16), v1);            // rows g4 + 16, g4 + 24
+          tmem_wait_ld();
+          tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(&sh.mempty[ms]);   // this warp is done with the slot
+          if (lane == 0) mbar_arrive(&sh.tempty[buf]);           // the accumulator is free again
+          float rc[4];
+          int xi[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int r = q * 32 + g4 + 8 * u;
+            rc[u] = (KIND == K_GAUSS) ? m.row[0][r] * negc : m.row[0][r];
+            xi[u] = __float_as_int(m.row[1][r]);
+          }
+          float2 acc[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acc[u] = make_float2(0.0f, 0.0f);
+#pragma unroll
+          for (int j = 0; j < NB; ++j) {
+            const int c = cbase + 8 * j + c2;
+            const float2 yn = *reinterpret_cast<const float2*>(&m.col[0][c]);
+            const float2 w = *reinterpret_cast<const float2*>(&m.col[1][c]);
+            const int2 yi = *reinterpret_cast<const int2*>(&m.col[2][c]);
+            const float2 cc = (KIND == K_GAUSS) ? __fmul2_rn(yn, make_float2(negc, negc)) : yn;
+            acc[0] = __ffma2_rn(w, kernel_pair<KIND>(make_float2(v0[4 * j], v0[4 * j + 1]), rc[0], cc, xi[0], yi,
+                                                     negc, coef0, degree), acc[0]);
+            acc[1] = __ffma2_rn(w, kernel_pair<KIND>(make_float2(v0[4 * j + 2], v0[4 * j + 3]), rc[1], cc, xi[1], yi,
+                                                     negc, coef0, degree), acc[1]);
+            acc[2] = __ffma2_rn(w, kernel_pair<KIND>(make_float2(v1[4 * j], v1[4 * j + 1]), rc[2], cc, xi[2], yi,
+                                                     negc, coef0, degree), acc[2]);
+            acc[3] = __ffma2_rn(w, kernel_pair<KIND>(make_float2(v1[4 * j + 2], v1[4 * j + 3]), rc[3], cc, xi[3], yi,
+                                                     negc, coef0, degree), acc[3]);
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sh.mempty[ms]);           // this warp is done with the slot
+          // row sums: the four lanes of a group hold the same rows, different columns
+          float fr[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            fr[u] = acc[u].x + acc[u].y;
+            fr[u] += __shfl_xor_sync(0xffffffffu, fr[u], 1);
+            fr[u] += __shfl_xor_sync(0xffffffffu, fr[u], 2);
+          }
+          const int us = lane & 3;
+          f = us == 0 ? fr[0] : (us == 1 ? fr[1] : (us == 2 ? fr[2] : fr[3]));   // row rq
         }
-        // the two column halves of a row meet in shared memory (slot by item parity)
-        float* red = sh.red[local & 1u][q];
-        if (h == 1) red[lane] = f0;
-        asm volatile("bar.sync %0, 64;" ::"r"(1 + q) : "memory");
-        const int row = (item % R) * TM + rloc;
-        if (h == 0 && !dead && row < rows) s.part[(int64_t)(item / R) * s.bpad + row] = f0 + red[lane];
+        // the NH column parts of a row meet in shared memory (slot by item parity)
+        float (*red)[4][32] = sh.red[local & 1u];
+        if (h > 0) red[h - 1][q][rq] = f;
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + q), "n"(32 * NH) : "memory");
+        const int row = (item % R) * TM + q * 32 + rq;
+        if (h == 0 && !dead && row < rows) {
+#pragma unroll
+          for (int v = 0; v < NH - 1; ++v) f += red[v][q][rq];
+          s.part[(int64_t)(item / R) * s.bpad + row] = f;
+        }
       } else {
         // window pass: this warp loads its own metadata; the loads overlap the MMAs
-        float (*mw)[64] = sh.meta.warp[e];
+        float (*mw)[32] = sh.meta.warp[e];
         __syncwarp();
         const PairTile pt = pair_tile<TNV>(s, item);
         load_pair_meta<KIND, TNV>(s, pt, cbase, mw, lane);
-        const bool rvalid = rloc < pt.rrem;
-        const int64_t p = pt.base + pt.rs + (rvalid ? rloc : 0);
-        const float xn = s.yn[p];
-        const int xi = s.yi[p];
-        const float wp = rvalid ? s.w32[p] : 0.0f;
+        // rows past the range are still rows of the region: their ||y||^2 matches
+        // the operand the MMA read, so every kernel value stays finite
+        float rc[4], wp[4];
+        int xi[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int r = q * 32 + g4 + 8 * u;
+          const int64_t p = pt.base + pt.rs + r;
+          rc[u] = (KIND == K_GAUSS) ? s.yn[p] * negc : s.yn[p];
+          xi[u] = s.yi[p];
+          // kind 0 rows carry their weight, kind 1 rows count once (0 past the range)
+          wp[u] = r < pt.rrem ? (pt.kind == 0 ? s.w32[p] : 1.0f) : 0.0f;
+        }
         __syncwarp();
         const bool ok = dead || mbar_wait(&sh.tfull[buf], bph);
         if (__any_sync(0xffffffffu, !ok)) {
           if (lane == 0 && !dead) atomicOr(s.status, ST_TIMEOUT);
           dead = true;
         }
-        float sA = 0.0f, sB = 0.0f, sE = 0.0f, sM = 0.0f;
+        float sA = 0.0f, sB = 0.0f, sE = 0.0f;
         if (!dead) {
           tc_fence_after();
-          const float rc = (KIND == K_GAUSS) ? xn * negc : xn;
-          float2 a0 = make_float2(0.0f, 0.0f), a1 = a0, a2 = a0;
+          float v0[4 * NB], v1[4 * NB];
+          tmem_ld16x256<NB>(taddr, v0);
+          tmem_ld16x256<NB>(taddr + (16u << 16), v1);
+          tmem_wait_ld();
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sh.tempty[buf]);
+          float2 aA[4], aB[4], aE[4];
 #pragma unroll
-          for (int ch = 0; ch < C / 32; ++ch) {
-            float g[32];
-            tmem_ld32(taddr + ch * 32, g);
-            if (ch == C / 32 - 1) {
-              tc_fence_before();
-              __syncwarp();
-              if (lane == 0) mbar_arrive(&sh.tempty[buf]);
-            }
+          for (int u = 0; u < 4; ++u) aA[u] = aB[u] = aE[u] = make_float2(0.0f, 0.0f);
 #pragma unroll
-            for (int i = 0; i < 32; i += 2) {
-              const int c = ch * 32 + i;
-              const float2 cc = *reinterpret_cast<const float2*>(&mw[0][c]);
-              const float2 wa = *reinterpret_cast<const float2*>(&mw[1][c]);
-              const int2 yi = *reinterpret_cast<const int2*>(&mw[2][c]);
-              const float2 wb = *reinterpret_cast<const float2*>(&mw[3][c]);
-              const float2 we = *reinterpret_cast<const float2*>(&mw[4][c]);
-              const float2 kv = kernel_pair<KIND>(make_float2(g[i], g[i + 1]), rc, cc, xi, yi, negc, coef0, degree);
-              a0 = __ffma2_rn(wa, kv, a0);
-              a1 = __ffma2_rn(wb, kv, a1);
-              a2 = __ffma2_rn(we, kv, a2);
+          for (int j = 0; j < NB; ++j) {
+            const int c = 8 * j + c2;
+            const float2 cc = *reinterpret_cast<const float2*>(&mw[0][c]);
+            const float2 wa = *reinterpret_cast<const float2*>(&mw[1][c]);
+            const int2 yi = *reinterpret_cast<const int2*>(&mw[2][c]);
+            const float2 wb = *reinterpret_cast<const float2*>(&mw[3][c]);
+            const float2 we = *reinterpret_cast<const float2*>(&mw[4][c]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const float* vv = (u < 2) ? v0 : v1;
+              const int o = 4 * j + 2 * (u & 1);
+              const float2 kv = kernel_pair<KIND>(make_float2(vv[o], vv[o + 1]), rc[u], cc, xi[u], yi, negc,
+                                                  coef0, degree);
+              aA[u] = __ffma2_rn(wa, kv, aA[u]);
+              aB[u] = __ffma2_rn(wb, kv, aB[u]);
+              aE[u] = __ffma2_rn(we, kv, aE[u]);
             }
           }
           // kind 0: A = w_p sum_{q in W} w_q K, Bdd = w_p sum_{q in D} w_q K, E = w_p sum_{q in B} K
-          // kind 1: M = sum_{q in B} K (every valid column of a kind-1 tile is in B)
-          if (rvalid) {
-            if (pt.kind == 0) { sA = wp * (a0.x + a0.y); sB = wp * (a1.x + a1.y); sE = wp * (a2.x + a2.y); }
-            else sM = a2.x + a2.y;
+          // kind 1: M = sum_{q in B} K (every valid column of a kind-1 tile is in B), kept in sE
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            sA = fmaf(wp[u], aA[u].x + aA[u].y, sA);
+            sB = fmaf(wp[u], aB[u].x + aB[u].y, sB);
+            sE = fmaf(wp[u], aE[u].x + aE[u].y, sE);
           }
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) {
             sA += __shfl_xor_sync(0xffffffffu, sA, o);
             sB += __shfl_xor_sync(0xffffffffu, sB, o);
             sE += __shfl_xor_sync(0xffffffffu, sE, o);
-            sM += __shfl_xor_sync(0xffffffffu, sM, o);
           }
         }
-        // the eight warps' sums meet in shared memory (slot by item parity);
-        // one thread per sum adds them in a fixed order and writes the item's four sums
+        // the warps' sums meet in shared memory (slot by item parity); one
+        // thread per sum adds them in a fixed order and writes the item's four sums
         float (*red)[4] = sh.wred[local & 1u];
-        if (lane == 0) { red[e][0] = sA; red[e][1] = sB; red[e][2] = sE; red[e][3] = sM; }
+        if (lane == 0) {
+          const bool k0 = pt.kind == 0;
+          red[e][0] = k0 ? sA : 0.0f;
+          red[e][1] = k0 ? sB : 0.0f;
+          red[e][2] = k0 ? sE : 0.0f;
+          red[e][3] = k0 ? 0.0f : sE;
+        }
         asm volatile("bar.sync 5, %0;" ::"n"(32 * NEPI) : "memory");
         if (e == 0 && lane < 4 && !dead) {
           double v = 0.0;
