@@ -12,6 +12,8 @@ Contents:
               the full history every iteration, no recurrences
   rng.py      SplitMix64 counter sampler for batch indices
   init.py     kernel k-means++ seeding (D^2 sampling in feature space)
+  grad.py     batch objective at fixed assignments and its gradient with
+              respect to the query rows and s = log sigma
 
 Every function is pinned by the ``-m "not gpu"`` tests in
 tests/test_oracle_*.py against closed forms, special cases that reduce to
@@ -22,9 +24,10 @@ from .kkm import (CenterRep, MiniBatchKernelKMeans, StepRecord, combination_norm
                   distance_to_combination)
 from .rng import batch_indices, index_below, splitmix64
 from .init import kmeanspp
+from . import grad
 
 __all__ = [
     "GAUSSIAN", "LAPLACIAN", "LINEAR", "POLY", "Kernel", "kernel_diag", "kernel_matrix",
     "kernel_wsum", "CenterRep", "combination_norm2", "distance_to_combination", "MiniBatchKernelKMeans", "StepRecord", "batch_indices",
-    "index_below", "splitmix64", "kmeanspp",
+    "index_below", "splitmix64", "kmeanspp", "grad",
 ]
