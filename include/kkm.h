@@ -180,6 +180,32 @@ kkm_status kkm_assign(kkm_ctx* ctx, const float* Q, int64_t m, int64_t ldq, int3
  * *out (host). */
 kkm_status kkm_objective(kkm_ctx* ctx, const float* Q, int64_t m, int64_t ldq, double* out);
 
+/* kkm_objective_fwd / kkm_objective_bwd -- the batch objective of Sec. 1,
+ * f_A(C) = (1/|A|) sum_a Delta(a, C_{assign(a)}), at GIVEN assignments, as a
+ * differentiable function of the query rows and of the bandwidth, and its
+ * adjoint. The centers (support rows, weights) are held fixed and the
+ * bandwidth is parameterised by s = log_sigma: Gaussian kappa = 2 e^{2s},
+ * Laplacian sigma = e^s (the context's own kernel parameter is not used or
+ * changed). Only the Gaussian and Laplacian kernels qualify (KKM_ENOTSUP
+ * otherwise), with d <= 1024.
+ *   Q        : device, m x d FP32, leading dimension ldq >= d; m >= 1.
+ *   assign   : device, m int32 centers in [0, k) (an index outside sets the
+ *              device status; the next synchronising call returns KKM_EINVAL).
+ *   loss_out : device, 1 double: the objective.
+ *   delta_out: device, m FP32 Delta(q, C_{assign(q)}), or NULL.
+ * The adjoint recomputes every kernel value (nothing is kept between calls):
+ *   grad_loss      : device, 1 double, dObjective of the caller's loss.
+ *   grad_q         : device, m x d FP32 (leading dimension ldg >= d):
+ *                    grad_loss * d objective / d Q. Support rows are constants.
+ *   grad_log_sigma : device, 1 double: grad_loss * d objective / d s.
+ * Both calls are asynchronous on the context's stream and allocate a
+ * workspace that grows with m and lives until kkm_destroy. */
+kkm_status kkm_objective_fwd(kkm_ctx* ctx, const float* Q, int64_t m, int64_t ldq, const int32_t* assign,
+                             double log_sigma, double* loss_out, float* delta_out);
+kkm_status kkm_objective_bwd(kkm_ctx* ctx, const float* Q, int64_t m, int64_t ldq, const int32_t* assign,
+                             double log_sigma, const double* grad_loss, float* grad_q, int64_t ldg,
+                             double* grad_log_sigma);
+
 /* kkm_sync -- synchronises the context's stream and reports device-side faults. */
 kkm_status kkm_sync(kkm_ctx* ctx);
 

@@ -49,6 +49,9 @@ struct kkm_ctx {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
   const void* gkey[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  // workspace of kkm_objective_fwd / _bwd (grows with m, freed with the context)
+  double* gws = nullptr;
+  size_t gws_len = 0;
 };
 
 namespace {
@@ -83,6 +86,9 @@ void free_all(kkm_ctx* c) {
   c->cap_stream = nullptr;
   for (void* p : c->allocs) cudaFree(p);
   c->allocs.clear();
+  if (c->gws) cudaFree(c->gws);
+  c->gws = nullptr;
+  c->gws_len = 0;
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   c->ev.clear();
 }
@@ -462,6 +468,54 @@ KKM_API kkm_status kkm_objective(kkm_ctx* c, const float* Q, int64_t m, int64_t 
   if (st != KKM_OK) return st;
   *out = total / (double)m;
   return KKM_OK;
+}
+
+namespace {
+
+kkm_status objective_call(kkm_ctx* c, const float* Q, int64_t m, int64_t ldq, const int32_t* assign,
+                          double log_sigma, double* loss, float* delta, const double* grad_loss, float* grad_q,
+                          int64_t ldg, double* grad_s) {
+  const kkm::Dev& s = c->s;
+  if (s.kind != kkm::K_GAUSS && s.kind != kkm::K_LAPLACE)
+    return fail(c, KKM_ENOTSUP, "the bandwidth objective needs the Gaussian or Laplacian kernel");
+  if (s.d > 1024) return fail(c, KKM_ENOTSUP, "the bandwidth objective supports d <= 1024");
+  if (m < 1 || !Q || ldq < s.d || !assign) return fail(c, KKM_EINVAL, "bad query rows or assignments");
+  if (!std::isfinite(log_sigma)) return fail(c, KKM_EINVAL, "log_sigma must be finite");
+  const size_t need = kkm::grad_workspace_doubles(s, m);
+  if (need > c->gws_len) {
+    if (c->gws) KKM_CU(cudaFree(c->gws), "workspace free");
+    c->gws = nullptr;
+    c->gws_len = 0;
+    void* p = nullptr;
+    const cudaError_t e = cudaMalloc(&p, need * sizeof(double));
+    if (e != cudaSuccess) return fail(c, KKM_ENOMEM, std::string("workspace: ") + cudaGetErrorString(e));
+    c->gws = static_cast<double*>(p);
+    c->gws_len = need;
+  }
+  KKM_CU(kkm::launch_objective(s, log_sigma, Q, m, ldq, assign, loss, delta, grad_loss, grad_q, ldg, grad_s,
+                               c->gws, c->stream), "objective kernels");
+  c->launches += 4;
+  return KKM_OK;
+}
+
+}  // namespace
+
+KKM_API kkm_status kkm_objective_fwd(kkm_ctx* c, const float* Q, int64_t m, int64_t ldq, const int32_t* assign,
+                                     double log_sigma, double* loss_out, float* delta_out) {
+  kkm_status st = check_usable(c);
+  if (st != KKM_OK) return st;
+  if (!loss_out) return fail(c, KKM_EINVAL, "loss_out is NULL");
+  return objective_call(c, Q, m, ldq, assign, log_sigma, loss_out, delta_out, nullptr, nullptr, 0, nullptr);
+}
+
+KKM_API kkm_status kkm_objective_bwd(kkm_ctx* c, const float* Q, int64_t m, int64_t ldq, const int32_t* assign,
+                                     double log_sigma, const double* grad_loss, float* grad_q, int64_t ldg,
+                                     double* grad_log_sigma) {
+  kkm_status st = check_usable(c);
+  if (st != KKM_OK) return st;
+  if (!grad_loss || !grad_q || !grad_log_sigma || ldg < c->s.d)
+    return fail(c, KKM_EINVAL, "grad_loss, grad_q (ldg >= d) and grad_log_sigma are required");
+  return objective_call(c, Q, m, ldq, assign, log_sigma, nullptr, nullptr, grad_loss, grad_q, ldg, grad_log_sigma);
 }
 
 KKM_API kkm_status kkm_sync(kkm_ctx* c) {

@@ -226,6 +226,13 @@ cudaError_t launch_sort_plan(const Dev& s, double* obj_out, cudaStream_t st);
 cudaError_t launch_move(const Dev& s, cudaStream_t st);
 cudaError_t launch_wgram(const Dev& s, cudaStream_t st);
 cudaError_t launch_finalize(const Dev& s, cudaStream_t st);
+// batch objective at fixed assignments and its adjoint (kkm_grad.cu); ws holds
+// grad_workspace_doubles(s, m) doubles. With grad_q == NULL only the forward
+// runs (loss, delta); otherwise the adjoint (grad_q, grad_s).
+size_t grad_workspace_doubles(const Dev& s, int64_t m);
+cudaError_t launch_objective(const Dev& s, double log_sigma, const float* Q, int64_t m, int64_t ldq,
+                             const int32_t* assign, double* loss, float* delta, const double* grad_loss,
+                             float* grad_q, int64_t ldg, double* grad_s, double* ws, cudaStream_t st);
 cudaError_t launch_build_tiles(const Dev& s, cudaStream_t st);
 cudaError_t launch_init_centers(const Dev& s, const int32_t* init_idx, cudaStream_t st);
 cudaError_t launch_load_rows(const Dev& s, int32_t rows_total, cudaStream_t st);

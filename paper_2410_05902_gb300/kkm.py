@@ -66,6 +66,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "kkm_step_host": ([_P, _P, _P, _P], c_int32),
         "kkm_assign": ([_P, _P, c_int64, c_int64, _P, _P, _P], c_int32),
         "kkm_objective": ([_P, _P, c_int64, c_int64, POINTER(c_double)], c_int32),
+        "kkm_objective_fwd": ([_P, _P, c_int64, c_int64, _P, c_double, _P, _P], c_int32),
+        "kkm_objective_bwd": ([_P, _P, c_int64, c_int64, _P, c_double, _P, _P, c_int64, _P], c_int32),
         "kkm_sync": ([_P], c_int32),
         "kkm_get_state_sizes": ([_P, POINTER(c_int64), POINTER(c_int64)], c_int32),
         "kkm_get_state": ([_P, POINTER(c_int64), _P, _P, _P, _P, _P, _P, _P, _P], c_int32),
@@ -134,6 +136,17 @@ def kkm_objective(ctx, Q: int | None, m: int, ldq: int) -> float:
     out = c_double()
     _check(load().kkm_objective(ctx, Q, m, ldq, ctypes.byref(out)), ctx)
     return out.value
+
+
+def kkm_objective_fwd(ctx, Q: int, m: int, ldq: int, assign: int, log_sigma: float, loss_out: int,
+                      delta_out: int | None) -> None:
+    _check(load().kkm_objective_fwd(ctx, Q, m, ldq, assign, float(log_sigma), loss_out, delta_out), ctx)
+
+
+def kkm_objective_bwd(ctx, Q: int, m: int, ldq: int, assign: int, log_sigma: float, grad_loss: int,
+                      grad_q: int, ldg: int, grad_log_sigma: int) -> None:
+    _check(load().kkm_objective_bwd(ctx, Q, m, ldq, assign, float(log_sigma), grad_loss, grad_q, ldg,
+                                    grad_log_sigma), ctx)
 
 
 def kkm_sync(ctx) -> None:
@@ -267,6 +280,24 @@ class KKM:
         if Q is None:
             return kkm_objective(self.ctx, None, 0, 0)
         return kkm_objective(self.ctx, Q.data_ptr(), Q.shape[0], Q.stride(0))
+
+    def objective_fwd(self, Q, assign, log_sigma: float, want_delta: bool = False):
+        """Batch objective at fixed assignments (device scalar) and optionally Delta per row."""
+        torch = self._torch
+        loss = torch.empty(1, dtype=torch.float64, device=Q.device)
+        delta = torch.empty(Q.shape[0], dtype=torch.float32, device=Q.device) if want_delta else None
+        kkm_objective_fwd(self.ctx, Q.data_ptr(), Q.shape[0], Q.stride(0), assign.data_ptr(), log_sigma,
+                          loss.data_ptr(), self._ptr(delta))
+        return loss, delta
+
+    def objective_bwd(self, Q, assign, log_sigma: float, grad_loss):
+        """(grad Q, grad log_sigma) of grad_loss * objective (grad_loss: 1-element float64 CUDA tensor)."""
+        torch = self._torch
+        gq = torch.empty(Q.shape, dtype=torch.float32, device=Q.device)
+        gs = torch.empty(1, dtype=torch.float64, device=Q.device)
+        kkm_objective_bwd(self.ctx, Q.data_ptr(), Q.shape[0], Q.stride(0), assign.data_ptr(), log_sigma,
+                          grad_loss.data_ptr(), gq.data_ptr(), gq.stride(0), gs.data_ptr())
+        return gq, gs
 
     def sync(self):
         kkm_sync(self.ctx)
