@@ -421,6 +421,132 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------- secondary measurements
+def run_batching(args):
+    """The batched sweep: 64 independent runs (n, d, k, b drawn with seed 777),
+    variants picked per (d, b) class by the autotuner, one group step = one
+    iteration of every run as one CUDA graph launch. Metric: sum over runs of
+    b*k distances per second."""
+    import torch
+    from paper_2410_05902_gb300.group import Group, autotune
+    from paper_2410_05902_gb300.kkm import KKM
+    world, rank, _ = dist_env()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    specs = inputs.batching_specs(64, seed=777)
+    data = []
+    for i, sp in enumerate(specs):
+        X, _ = sp.make()
+        sigma = inputs.median_sigma(X, seed=1)
+        data.append((torch.from_numpy(X).to(dev), 2.0 * sigma * sigma, inputs.init_indices(sp.n, sp.k, seed=100 + i)))
+        del X
+    # autotune once per (d, b) class on its median-k run
+    classes = {}
+    for i, sp in enumerate(specs):
+        classes.setdefault((sp.d, sp.b), []).append(i)
+    choice, tune = {}, {}
+    for key, idx in sorted(classes.items()):
+        rep = sorted(idx, key=lambda i: specs[i].k)[len(idx) // 2]
+        sp = specs[rep]
+        Xd, kappa, init = data[rep]
+        best, times = autotune(Xd, sp.k, sp.b, "gaussian", kappa, 200, init, warm=args.warmup + 12, iters=8)
+        choice[key] = best
+        tune[f"d={key[0]},b={key[1]}"] = {"choice": f"{best[0]}/tile{best[1] or 'default'}",
+                                          "ms_per_step": {f"{p}/tile{t or 'default'}": round(v, 4)
+                                                          for (p, t), v in times.items()}}
+    runs = []
+    for i, sp in enumerate(specs):
+        prec, tile = choice[(sp.d, sp.b)]
+        Xd, kappa, init = data[i]
+        runs.append(KKM(Xd, sp.k, sp.b, kernel="gaussian", param=kappa, tau=200, precision=prec,
+                        dist_tile=tile, seed=1000 + i, init_idx=init))
+    g = Group(runs)
+    for _ in range(PREP_ITERS + args.warmup):
+        g.step()
+    g.sync()
+    stream = torch.cuda.current_stream(dev)
+    clocks = Clocks(0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # the group orders its work on a stream of its own: bracket it with syncs
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        g.step()
+    g.sync()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    per_step = sum(sp.b * sp.k for sp in specs)
+    value = per_step * args.steps / wall
+    print(json.dumps({
+        "metric": "batched sweep: sum over 64 runs of b*k batch-point x center distances/s per iteration on 1 GB300",
+        "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "mixed (autotuned per class: f32 / bf16x3)", "data": "synthetic",
+        "config": {"workload": "batching: 64 runs, n ~ U[5000, 200000], d in {16, 64, 256}, k ~ U[5, 200], "
+                               "b in {256, 512, 1024, 2048} (seed 777), isotropic mixtures with k_true = k, "
+                               "Gaussian kernel kappa = 2 sigma_median^2 per run, tau = 200, beta rate",
+                   "timing": "host wall clock around the timed group steps with a device sync on both sides "
+                             "(every iteration of all runs is one CUDA graph launch on the group's stream)",
+                   "distances_per_step": per_step, "state_prep_iters": PREP_ITERS,
+                   "l2": "inputs larger than L2 (the 64 datasets hold about "
+                         f"{sum(int(d[0].numel()) for d in data) * 4 / 1e9:.1f} GB)"},
+        "autotune": tune, "gpu_launches": 7 * len(runs) * args.steps, "clocks": clk,
+    }))
+    g.close()
+    for r in runs:
+        r.close()
+
+
+def run_objective_grad(args):
+    """The differentiation workload: after 50 iterations, the objective at the
+    argmin assignments and its adjoint (query rows and log sigma) for one
+    batch, timed with CUDA events."""
+    import torch
+    from paper_2410_05902_gb300.kkm import KKM
+    w = inputs.WORKLOADS["differentiation"]
+    dev = torch.device("cuda", 0)
+    X, _ = w.make()
+    sigma = inputs.median_sigma(X, seed=1)
+    Xd = torch.from_numpy(X).to(dev)
+    run = KKM(Xd, w.k, w.b, kernel="gaussian", param=2 * sigma * sigma, tau=w.tau, precision="fp32",
+              init_idx=inputs.init_indices(w.n, w.k, seed=3))
+    run.graph(True)
+    for _ in range(50):
+        run.step()
+    batch = torch.from_numpy(inputs.batch_stream(w.n, w.b, 1, seed=77)[0]).to(dev)
+    Q = Xd[batch].contiguous()
+    a = run.assign(Q)[0]
+    s = float(np.log(sigma))
+    g1 = torch.ones(1, dtype=torch.float64, device=dev)
+    stream = run.stream
+    for _ in range(args.warmup):
+        run.objective_fwd(Q, a, s)
+        run.objective_bwd(Q, a, s, g1)
+    run.sync()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        run.objective_fwd(Q, a, s)
+    ev[1].record(stream)
+    for _ in range(args.steps):
+        run.objective_bwd(Q, a, s, g1)
+    ev[2].record(stream)
+    run.sync()
+    fwd = ev[0].elapsed_time(ev[1]) / args.steps
+    bwd = ev[1].elapsed_time(ev[2]) / args.steps
+    steps, srows, _ = run.stats()
+    print(json.dumps({
+        "metric": "objective + adjoint at fixed assignments (query rows and log sigma), ms per batch",
+        "value": fwd + bwd, "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": fwd + bwd, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "differentiation: 2e5 x 64 isotropic mixture of 50 components, k=50, b=2048, "
+                               "tau=200, Gaussian kernel, after 50 iterations", "fwd_ms": fwd, "bwd_ms": bwd,
+                   "support_rows_S": srows / max(steps, 1)},
+    }))
+    run.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -431,15 +557,23 @@ def main():
                     help="auto: time every form, report the fastest that meets the objective bar")
     ap.add_argument("--oracle-budget", type=float, default=20.0)
     ap.add_argument("--no-graph", action="store_true", help="launch every kernel instead of replaying a graph")
-    ap.add_argument("--workload", choices=sorted(inputs.WORKLOADS), default="image",
+    ap.add_argument("--workload", choices=sorted(inputs.WORKLOADS) + ["batching"], default="image",
                     help="image (default) is the headline workload; the others are secondary measurements")
+    ap.add_argument("--objective-grad", action="store_true",
+                    help="time the objective and its adjoint on the differentiation workload")
     ap.add_argument("--kernel", choices=["gaussian", "laplacian"], default="gaussian")
     args = ap.parse_args()
-    global WORKLOAD, KERNEL
-    WORKLOAD = inputs.WORKLOADS[args.workload]
-    KERNEL = args.kernel
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    global WORKLOAD, KERNEL
+    if args.workload == "batching":
+        run_batching(args)
+        return
+    if args.objective_grad:
+        run_objective_grad(args)
+        return
+    WORKLOAD = inputs.WORKLOADS[args.workload]
+    KERNEL = args.kernel
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define KKM_ABI_VERSION 1
+#define KKM_ABI_VERSION 2
 
 typedef enum kkm_status {
   KKM_OK = 0,
@@ -94,6 +94,8 @@ typedef struct kkm_config {
   int32_t precision; /* kkm_precision */
   int32_t max_iters; /* untruncated runs only: iterations the support store must hold (>= 1) */
   uint64_t seed;     /* SplitMix64 seed of the built-in batch sampler */
+  int32_t dist_tile; /* tensor-core forms: support rows per distance-pass tile, 64 or 128; 0 = 128 */
+  int32_t reserved;  /* must be 0 */
 } kkm_config;
 
 typedef struct kkm_ctx kkm_ctx;
@@ -180,7 +182,7 @@ kkm_status kkm_assign(kkm_ctx* ctx, const float* Q, int64_t m, int64_t ldq, int3
  * *out (host). */
 kkm_status kkm_objective(kkm_ctx* ctx, const float* Q, int64_t m, int64_t ldq, double* out);
 
-/* kkm_objective_fwd / kkm_objective_bwd -- the batch objective of Sec. 1,
+/* kkm_objective_fwd / kkm_objective_bwd -- the batch objective of Sec. 3,
  * f_A(C) = (1/|A|) sum_a Delta(a, C_{assign(a)}), at GIVEN assignments, as a
  * differentiable function of the query rows and of the bandwidth, and its
  * adjoint. The centers (support rows, weights) are held fixed and the
@@ -313,6 +315,25 @@ const char* kkm_noalloc_last_error(void);
 
 /* Frees everything the context allocated. NULL is accepted. It synchronises first. */
 kkm_status kkm_destroy(kkm_ctx* ctx);
+
+/* Run groups: many independent runs (restarts, bandwidth or k sweeps, runs
+ * of different n, d, k, b) stepped together.
+ * kkm_group_create -- groups n distinct contexts of one device. stream (a
+ *   cudaStream_t, or NULL for a stream of the group's own) orders the
+ *   group's work. The runs' own streams are synchronised once here; while
+ *   grouped, a run must not be stepped on its own, and kkm_group_sync must
+ *   precede any other call on a run. The group does not own the runs.
+ * kkm_group_step -- one iteration of every run (each with its built-in
+ *   sampler), asynchronous. From the second call on, the whole iteration of
+ *   all runs is one CUDA graph launch whose per-run branches run concurrently.
+ * kkm_group_sync -- synchronises and reports each run's device status.
+ * kkm_group_last_error(NULL) gives the calling thread's last create failure. */
+typedef struct kkm_group kkm_group;
+kkm_status kkm_group_create(kkm_group** out, kkm_ctx* const* runs, int32_t n, void* stream);
+kkm_status kkm_group_step(kkm_group* group);
+kkm_status kkm_group_sync(kkm_group* group);
+const char* kkm_group_last_error(kkm_group* group);
+kkm_status kkm_group_destroy(kkm_group* group);
 
 /* Message of the last failure (see the conventions above). Never NULL. */
 const char* kkm_last_error(const kkm_ctx* ctx);

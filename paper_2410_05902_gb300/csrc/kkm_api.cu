@@ -162,6 +162,9 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
     return fail(nullptr, KKM_EINVAL, "unknown learning rate");
   if (cfg->lr == KKM_LR_CONST && !(cfg->eta > 0.0 && cfg->eta <= 1.0))
     return fail(nullptr, KKM_EINVAL, "eta must be in (0, 1]");
+  if (cfg->dist_tile != 0 && cfg->dist_tile != 64 && cfg->dist_tile != 128)
+    return fail(nullptr, KKM_EINVAL, "dist_tile must be 0, 64 or 128");
+  if (cfg->reserved != 0) return fail(nullptr, KKM_EINVAL, "reserved must be 0");
   if (cfg->precision < KKM_PREC_FP32 || cfg->precision > KKM_PREC_BF16X3)
     return fail(nullptr, KKM_EINVAL, "unknown precision");
   if (cfg->tau > 1000000) return fail(nullptr, KKM_EINVAL, "tau must be <= 1e6");
@@ -221,7 +224,7 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
     cudaDeviceGetAttribute(&min, cudaDevAttrComputeCapabilityMinor, c->device);
     c->use_tc = (maj == 10 && min == 3) && kkm::tc_available();
   }
-  s.tn = c->use_tc ? 128 : 64;
+  s.tn = c->use_tc ? (cfg->dist_tile == 64 ? 64 : 128) : 64;
   s.pair_rows = c->use_tc ? 128 : 64;
   s.pair_cols = 64;
   const int64_t TR = s.pair_rows, TC = s.pair_cols;   // window-pass tile
@@ -742,6 +745,171 @@ KKM_API kkm_status kkm_launches(kkm_ctx* c, int64_t* launches, int32_t reset) {
   if (!c) return fail(nullptr, KKM_EINVAL, "null context");
   if (launches) *launches = c->launches;
   if (reset) c->launches = 0;
+  return KKM_OK;
+}
+
+// ------------------------------------------------------------ run groups
+// Many independent runs stepped together: one step of every run is one CUDA
+// graph launch. The graph forks from a root stream into one branch per run,
+// each branch holding that run's kernel sequence, and joins back, so the
+// runs' kernels run concurrently on the GPU. The first group step runs
+// eagerly through the same branches; the graph is captured on the second.
+struct kkm_group {
+  int device = 0;
+  std::vector<kkm_ctx*> runs;
+  cudaStream_t stream = nullptr;   // where the group's work is ordered
+  bool own_stream = false;
+  cudaStream_t root = nullptr;     // capture root
+  std::vector<cudaStream_t> branch;
+  std::vector<cudaEvent_t> ev;     // [0] fork, [1 + i] join of run i
+  cudaGraphExec_t gexec = nullptr;
+  int64_t steps = 0;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_group_error;
+
+kkm_status gfail(kkm_group* g, kkm_status st, const std::string& msg) {
+  if (g) g->err = msg; else g_group_error = msg;
+  return st;
+}
+
+void group_free(kkm_group* g) {
+  if (g->gexec) cudaGraphExecDestroy(g->gexec);
+  for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
+  for (cudaStream_t b : g->branch) cudaStreamDestroy(b);
+  if (g->root) cudaStreamDestroy(g->root);
+  if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
+}
+
+// Fork from `from`, queue one step of every run on its branch, join back.
+kkm_status group_enqueue(kkm_group* g, cudaStream_t from) {
+  if (cudaEventRecord(g->ev[0], from) != cudaSuccess) return gfail(g, KKM_ECUDA, "fork event");
+  for (size_t i = 0; i < g->runs.size(); ++i) {
+    kkm_ctx* c = g->runs[i];
+    if (cudaStreamWaitEvent(g->branch[i], g->ev[0], 0) != cudaSuccess) return gfail(g, KKM_ECUDA, "fork wait");
+    const kkm_status st = enqueue_step(c, g->branch[i], nullptr, nullptr, nullptr, nullptr, nullptr, false);
+    if (st != KKM_OK) return gfail(g, st, "run " + std::to_string(i) + ": " + c->err);
+    if (cudaEventRecord(g->ev[1 + i], g->branch[i]) != cudaSuccess) return gfail(g, KKM_ECUDA, "join event");
+    if (cudaStreamWaitEvent(from, g->ev[1 + i], 0) != cudaSuccess) return gfail(g, KKM_ECUDA, "join wait");
+  }
+  return KKM_OK;
+}
+
+}  // namespace
+
+KKM_API kkm_status kkm_group_create(kkm_group** out, kkm_ctx* const* runs, int32_t n, void* stream) {
+  if (!out) return gfail(nullptr, KKM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || !runs) return gfail(nullptr, KKM_EINVAL, "a group needs n >= 1 runs");
+  for (int32_t i = 0; i < n; ++i) {
+    if (!runs[i]) return gfail(nullptr, KKM_EINVAL, "null run");
+    if (runs[i]->poisoned) return gfail(nullptr, KKM_ESTATE, "a run is poisoned");
+    if (runs[i]->device != runs[0]->device) return gfail(nullptr, KKM_EINVAL, "runs on different devices");
+    for (int32_t q = 0; q < i; ++q)
+      if (runs[q] == runs[i]) return gfail(nullptr, KKM_EINVAL, "a run appears twice");
+  }
+  kkm_group* g = new (std::nothrow) kkm_group();
+  if (!g) return gfail(nullptr, KKM_ENOMEM, "out of host memory");
+  g->device = runs[0]->device;
+  g->runs.assign(runs, runs + n);
+  auto bail = [&](const char* what, cudaError_t e) {
+    g_group_error = std::string(what) + ": " + cudaGetErrorString(e);
+    group_free(g);
+    delete g;
+    return KKM_ECUDA;
+  };
+  cudaError_t e = cudaSetDevice(g->device);
+  if (e != cudaSuccess) return bail("cudaSetDevice", e);
+  for (kkm_ctx* c : g->runs) {
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return bail("run stream synchronize", e);
+  }
+  if (stream) {
+    g->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail("stream", e);
+    g->own_stream = true;
+  }
+  e = cudaStreamCreateWithFlags(&g->root, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return bail("stream", e);
+  g->branch.resize(n, nullptr);
+  for (int32_t i = 0; i < n; ++i) {
+    e = cudaStreamCreateWithFlags(&g->branch[i], cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail("stream", e);
+  }
+  g->ev.resize(n + 1, nullptr);
+  for (auto& ev : g->ev) {
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return bail("event", e);
+  }
+  *out = g;
+  return KKM_OK;
+}
+
+KKM_API kkm_status kkm_group_step(kkm_group* g) {
+  if (!g) return gfail(nullptr, KKM_EINVAL, "null group");
+  if (cudaSetDevice(g->device) != cudaSuccess) return gfail(g, KKM_ECUDA, "cudaSetDevice failed");
+  for (kkm_ctx* c : g->runs) {
+    if (c->poisoned) return gfail(g, KKM_ESTATE, "a run is poisoned");
+    if (c->s.tau == 0 && c->iteration > c->max_iters)
+      return gfail(g, KKM_ESTATE, "an untruncated run has done max_iters iterations");
+  }
+  if (g->steps == 0) {
+    const kkm_status st = group_enqueue(g, g->stream);
+    if (st != KKM_OK) return st;
+  } else {
+    if (!g->gexec) {
+      if (cudaStreamBeginCapture(g->root, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return gfail(g, KKM_ECUDA, "begin capture");
+      const kkm_status st = group_enqueue(g, g->root);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(g->root, &graph);
+      if (st != KKM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+      }
+      if (e != cudaSuccess) return gfail(g, KKM_ECUDA, std::string("end capture: ") + cudaGetErrorString(e));
+      const cudaError_t ei = cudaGraphInstantiate(&g->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ei != cudaSuccess) return gfail(g, KKM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+    }
+    const cudaError_t e = cudaGraphLaunch(g->gexec, g->stream);
+    if (e != cudaSuccess) return gfail(g, KKM_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+  }
+  for (kkm_ctx* c : g->runs) {
+    c->launches += 7;
+    ++c->iteration;
+  }
+  ++g->steps;
+  return KKM_OK;
+}
+
+KKM_API kkm_status kkm_group_sync(kkm_group* g) {
+  if (!g) return gfail(nullptr, KKM_EINVAL, "null group");
+  if (cudaSetDevice(g->device) != cudaSuccess) return gfail(g, KKM_ECUDA, "cudaSetDevice failed");
+  const cudaError_t e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) return gfail(g, KKM_ECUDA, std::string("stream synchronize: ") + cudaGetErrorString(e));
+  for (size_t i = 0; i < g->runs.size(); ++i) {
+    const kkm_status st = sync_and_check(g->runs[i]);
+    if (st != KKM_OK) return gfail(g, st, "run " + std::to_string(i) + ": " + g->runs[i]->err);
+  }
+  return KKM_OK;
+}
+
+KKM_API const char* kkm_group_last_error(kkm_group* g) {
+  return g ? g->err.c_str() : g_group_error.c_str();
+}
+
+KKM_API kkm_status kkm_group_destroy(kkm_group* g) {
+  if (!g) return KKM_OK;
+  cudaSetDevice(g->device);
+  cudaStreamSynchronize(g->stream);
+  group_free(g);
+  delete g;
   return KKM_OK;
 }
 

@@ -5,7 +5,7 @@
 //   Delta(x, C) = 1 - 2 sum_t w_t K(x, y_t) + N_C,  N_C = sum_{t,u} w_t w_u K(y_t, y_u)
 //
 // with the assignments, support rows and weights held fixed (the f_B
-// objective of Sec. 1 at given assignments) and the bandwidth parameterised
+// objective of Sec. 3 at given assignments) and the bandwidth parameterised
 // by s = log sigma: Gaussian kappa = 2 e^{2s}, Laplacian sigma = e^s. Both
 // kernels have K(x,x) = 1. The support rows are constants, so the query
 // gradient flows through the cross term only:

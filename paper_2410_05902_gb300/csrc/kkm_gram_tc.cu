@@ -681,7 +681,11 @@ cudaError_t launch_form(const Dev& s, const CUtensorMap& a, const CUtensorMap& b
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  return launch_pdl(k_dist_tc<KIND, MODE, X3, TNV>, dim3(s.num_sms), dim3(NTHREADS), SMEM_BYTES, st, s, rows, a, b);
+  // one CTA per SM, but never more CTAs than the most items this launch can
+  // have: small runs then leave SMs free for the kernels of other runs
+  const int64_t most = MODE == 0 ? (int64_t)((rows + TM - 1) / TM) * s.max_tiles : (int64_t)s.max_pairs;
+  const int grid = (int)(most < s.num_sms ? (most > 0 ? most : 1) : s.num_sms);
+  return launch_pdl(k_dist_tc<KIND, MODE, X3, TNV>, dim3(grid), dim3(NTHREADS), SMEM_BYTES, st, s, rows, a, b);
 }
 
 // maps: [0] batch rows, 128-row boxes; [1] support rows, 128-row boxes; [2] support rows, 64-row boxes
@@ -742,7 +746,7 @@ cudaError_t tc_prepare(Dev& s, void* maps_out) {
 
 cudaError_t launch_dist_tc(const Dev& s, const void* maps, int rows, cudaStream_t st) {
   if (rows <= 0) return cudaSuccess;
-  return launch_mode<0, 128>(s, maps, rows, st);
+  return s.tn == 64 ? launch_mode<0, 64>(s, maps, rows, st) : launch_mode<0, 128>(s, maps, rows, st);
 }
 
 cudaError_t launch_wgram_tc(const Dev& s, const void* maps, cudaStream_t st) {

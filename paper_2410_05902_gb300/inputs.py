@@ -151,3 +151,34 @@ WORKLOADS = {
     "differentiation": Workload("differentiation", n=200_000, d=64, k=50, b=2048, tau=200,
                                 iters=200, kind="isotropic", components=50),
 }
+
+
+@dataclass(frozen=True)
+class RunSpec:
+    """One independent clustering run of a batched sweep."""
+
+    n: int
+    d: int
+    k: int
+    b: int
+    data_seed: int
+
+    def make(self):
+        """Isotropic mixture with k_true = k components."""
+        return isotropic_mixture(self.n, self.d, self.k, self.data_seed)
+
+
+def batching_specs(count: int = 64, seed: int = 777, n_range=(5000, 200000), dims=(16, 64, 256),
+                   k_range=(5, 200), batches=(256, 512, 1024, 2048), n_scale: float = 1.0):
+    """The batched-sweep workload: ``count`` runs with n uniform in n_range
+    (times n_scale), d from dims, k uniform in k_range, b from batches, all
+    drawn from one seeded generator."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        d = int(rng.choice(dims))
+        k = int(rng.integers(k_range[0], k_range[1] + 1))
+        b = int(rng.choice(batches))
+        out.append(RunSpec(max(int(n * n_scale), k), d, k, b, data_seed=seed * 1000 + i))
+    return out

@@ -35,7 +35,7 @@ class kkm_kernel(ctypes.Structure):
 
 class kkm_config(ctypes.Structure):
     _fields_ = [("tau", c_int32), ("lr", c_int32), ("eta", c_double), ("precision", c_int32),
-                ("max_iters", c_int32), ("seed", c_uint64)]
+                ("max_iters", c_int32), ("seed", c_uint64), ("dist_tile", c_int32), ("reserved", c_int32)]
 
 
 class KKMError(RuntimeError):
@@ -81,6 +81,11 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                    c_int32, POINTER(kkm_kernel), _P, _P, _P], c_int32),
         "kkm_noalloc_last_error": ([], ctypes.c_char_p),
         "kkm_destroy": ([_P], c_int32),
+        "kkm_group_create": ([POINTER(_P), _P, c_int32, _P], c_int32),
+        "kkm_group_step": ([_P], c_int32),
+        "kkm_group_sync": ([_P], c_int32),
+        "kkm_group_last_error": ([_P], ctypes.c_char_p),
+        "kkm_group_destroy": ([_P], c_int32),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -232,7 +237,7 @@ class KKM:
     def __init__(self, X, k: int, b: int, kernel: str = "gaussian", param: float = 1.0,
                  coef0: float = 0.0, degree: int = 2, tau: int = 200, lr: str = "beta",
                  eta: float = 0.0, precision: str = "fp32", seed: int = 0, init_idx=None,
-                 max_iters: int = 0, stream=None):
+                 max_iters: int = 0, stream=None, dist_tile: int = 0):
         import torch
         if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float32 and X.dim() == 2):
             raise TypeError("X must be a 2-D float32 CUDA tensor")
@@ -245,7 +250,7 @@ class KKM:
         self.stream = stream if stream is not None else torch.cuda.current_stream(X.device)
         kern = kkm_kernel(KERNELS[kernel], float(param), float(coef0), int(degree))
         cfg = kkm_config(int(tau), KKM_LR_BETA if lr == "beta" else KKM_LR_CONST, float(eta),
-                         PRECISIONS[precision], int(max_iters), int(seed) & ((1 << 64) - 1))
+                         PRECISIONS[precision], int(max_iters), int(seed) & ((1 << 64) - 1), int(dist_tile), 0)
         with torch.cuda.device(X.device):
             self.ctx = kkm_init(X.data_ptr(), self.n, self.d, X.stride(0), self.k, kern, self.b, cfg,
                                 None if init_idx is None else np.asarray(init_idx), self.stream.cuda_stream)

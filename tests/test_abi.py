@@ -45,7 +45,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_version(lib):
-    assert lib.kkm_version() == 1
+    assert lib.kkm_version() == 2
 
 
 def _init(lib, **over):
@@ -75,6 +75,8 @@ def _init(lib, **over):
     (dict(cfg=kkm.kkm_config(50, kkm.KKM_LR_CONST, 1.5, 0, 0, 0)), "eta"),
     (dict(cfg=kkm.kkm_config(50, 0, 0.0, 9, 0, 0)), "precision"),
     (dict(cfg=kkm.kkm_config(0, 0, 0.0, 0, 0, 0)), "max_iters"),
+    (dict(cfg=kkm.kkm_config(50, 0, 0.0, 0, 0, 0, 96, 0)), "dist_tile"),
+    (dict(cfg=kkm.kkm_config(50, 0, 0.0, 0, 0, 0, 0, 1)), "reserved"),
 ])
 def test_init_rejects_invalid_arguments_on_host(lib, over, needle):
     st, ctx = _init(lib, **over)
@@ -89,6 +91,18 @@ def test_null_context_calls(lib):
     assert lib.kkm_sync(None) == kkm.KKM_EINVAL
     out = ctypes.c_double()
     assert lib.kkm_objective(None, None, 0, 0, ctypes.byref(out)) == kkm.KKM_EINVAL
+
+
+def test_group_create_validates_on_host(lib):
+    g = ctypes.c_void_p()
+    assert lib.kkm_group_create(None, None, 1, None) == kkm.KKM_EINVAL
+    assert lib.kkm_group_create(ctypes.byref(g), None, 0, None) == kkm.KKM_EINVAL
+    assert not g.value
+    arr = (ctypes.c_void_p * 1)(None)
+    assert lib.kkm_group_create(ctypes.byref(g), arr, 1, None) == kkm.KKM_EINVAL
+    assert b"null run" in lib.kkm_group_last_error(None)
+    assert lib.kkm_group_step(None) == kkm.KKM_EINVAL
+    assert lib.kkm_group_destroy(None) == kkm.KKM_OK
 
 
 def test_binding_fails_loudly_without_library(tmp_path):
