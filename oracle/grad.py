@@ -1,7 +1,7 @@
 """FP64 oracle of the batch objective with fixed assignments, and its gradient
 (test infrastructure only).
 
-The objective is the mini-batch objective of Sec. 1 (f_A(C), a mean of
+The objective is the mini-batch objective of Sec. 3 (f_A(C), a mean of
 feature-space distances) evaluated at given assignments:
 
     L(Q, s) = (1/m) sum_x Delta(x, C_{a(x)}),

@@ -98,8 +98,8 @@ class MiniBatchKernelKMeans:
         self.init_idx = np.asarray(init_idx, dtype=np.int64).copy()
         if self.init_idx.shape != (self.k,):
             raise ValueError("one initial point per center")
-        if lr not in ("beta", "const"):
-            raise ValueError("lr must be 'beta' or 'const'")
+        if lr not in ("beta", "const", "sklearn"):
+            raise ValueError("lr must be 'beta', 'const' or 'sklearn'")
         if lr == "const" and eta is None:
             raise ValueError("the constant rate needs eta")
         self.lr, self.eta = lr, eta
@@ -203,10 +203,26 @@ class MiniBatchKernelKMeans:
         return float(np.mean(np.min(self.distances(Q), axis=1)))
 
     # -------------------------------------------------------------- iteration
+    def cumulative_counts(self) -> np.ndarray:
+        """N^j: points assigned to center j over all iterations so far."""
+        return np.array([sum(len(B) for B in self.blocks[j]) for j in range(self.k)], dtype=np.int64)
+
     def learning_rate(self, counts: np.ndarray) -> np.ndarray:
+        """alpha_i^j for this iteration's counts b_i^j (0 for an empty cluster).
+
+        beta:    sqrt(b_i^j / b) (Sec. 4.1);
+        const:   eta;
+        sklearn: b_i^j / N^j with N^j the cumulative count including this
+                 batch, the running-mean rate of mini-batch k-means as
+                 scikit-learn implements it (the "sklearn" learning rate the
+                 experiments of Sec. 6 compare with).
+        """
         counts = np.asarray(counts, dtype=np.float64)
         if self.lr == "beta":
             return np.sqrt(counts / self.b)
+        if self.lr == "sklearn":
+            total = self.cumulative_counts() + counts
+            return np.where(counts > 0, counts / np.where(total > 0, total, 1.0), 0.0)
         return np.where(counts > 0, float(self.eta), 0.0)
 
     def step(self, batch, forced_assign=None) -> StepRecord:
@@ -253,4 +269,5 @@ class MiniBatchKernelKMeans:
             "block_count": np.array([bk[1] for r in reps for bk in r.blocks], dtype=np.int64),
             "c1_kept": np.array([r.c1_kept for r in reps], dtype=bool),
             "cnorm": self.center_norms(),
+            "cum_counts": self.cumulative_counts(),
         }

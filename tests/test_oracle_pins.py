@@ -166,6 +166,30 @@ def test_linear_kernel_equals_explicit_minibatch_kmeans():
         np.testing.assert_allclose(rep.w @ X[rep.idx], C[j], rtol=1e-10, atol=1e-12)
 
 
+def test_sklearn_rate_is_the_running_mean():
+    """With the sklearn rate b_i^j / N^j (N^j cumulative) and the linear
+    kernel, an untruncated center is the plain mean of every point ever
+    assigned to it (the init point until the first assignment) -- computed
+    here directly from the assignments, with no weights."""
+    X, _ = inputs.isotropic_mixture(300, 3, 4, seed=8)
+    X = X.astype(np.float64)
+    k, b = 4, 24
+    init = inputs.init_indices(len(X), k, seed=2)
+    m = MiniBatchKernelKMeans(X, k, Kernel(LINEAR), b, init, tau=None, lr="sklearn")
+    members = [[] for _ in range(k)]
+    for B in inputs.batch_stream(len(X), b, 10, seed=3):
+        centers = np.array([X[members[j]].mean(axis=0) if members[j] else X[init[j]] for j in range(k)])
+        r = m.step(B)
+        expect = ((X[B][:, None, :] - centers[None, :, :]) ** 2).sum(axis=2)
+        np.testing.assert_allclose(r.dist, expect, rtol=1e-9, atol=1e-9)
+        for x, a in zip(B, r.assign):
+            members[a].append(x)
+        np.testing.assert_array_equal(m.cumulative_counts(), [len(v) for v in members])
+    for j in range(k):
+        rep = m.center(j)
+        np.testing.assert_allclose(rep.w @ X[rep.idx], X[members[j]].mean(axis=0), rtol=1e-10, atol=1e-12)
+
+
 def test_truncated_distances_equal_explicit_vectors():
     """With finite tau the oracle's kernel-trick distances equal explicit ones to sum_s w_s x_s."""
     X, _ = inputs.isotropic_mixture(300, 4, 3, seed=6)
