@@ -74,9 +74,12 @@ typedef struct kkm_kernel {
 
 /* Learning rates. KKM_LR_BETA is alpha_i^j = sqrt(b_i^j / b), the rate of
  * Schwartzman (2023) that the truncation lemma's proof in Sec. 4.1 uses.
- * KKM_LR_CONST is alpha = eta. Either way an empty cluster (b_i^j = 0) gets
- * alpha = 0 and its center does not change. */
-typedef enum kkm_lr { KKM_LR_BETA = 0, KKM_LR_CONST = 1 } kkm_lr;
+ * KKM_LR_CONST is alpha = eta. KKM_LR_SKLEARN is alpha_i^j = b_i^j / N^j with
+ * N^j the points assigned to center j over all iterations, this batch
+ * included (the running-mean rate Sec. 6 compares against; N^j is part of
+ * the state, see kkm_get_cum_counts). Every rate gives an empty cluster
+ * (b_i^j = 0) alpha = 0, so its center does not change. */
+typedef enum kkm_lr { KKM_LR_BETA = 0, KKM_LR_CONST = 1, KKM_LR_SKLEARN = 2 } kkm_lr;
 
 /* Arithmetic of the batch-by-support Gram products x.y (Sec. 4.1, "Algorithm
  * implementation and runtime"). Norms, kernel values and weighted sums are
@@ -148,6 +151,26 @@ kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d, int64_t
  * An index out of range is found on the device, and it poisons the context. */
 kkm_status kkm_step(kkm_ctx* ctx, const int32_t* batch_idx, const int32_t* forced_assign,
                     int32_t* assign_out, float* dist_out, double* batch_obj_out);
+
+/* kkm_step_eval -- kkm_step (device sampler when batch_idx is NULL) that
+ * also evaluates the updated centers on the same batch: obj_before_dev
+ * receives f_{B_i}(C_i) and obj_after_dev f_{B_i}(C_{i+1}) (device doubles,
+ * both required). Their difference is the improvement the early-stopping
+ * rule of Sec. 5 tests. Asynchronous. */
+kkm_status kkm_step_eval(kkm_ctx* ctx, const int32_t* batch_idx, double* obj_before_dev, double* obj_after_dev);
+
+/* kkm_fit -- up to max_iters iterations with early stopping (Sec. 5): it
+ * stops after the first iteration whose improvement
+ * f_{B_i}(C_i) - f_{B_i}(C_{i+1}) is below eps. Writes the iterations done
+ * and the last improvement (host; either may be NULL). Synchronises every
+ * iteration. */
+kkm_status kkm_fit(kkm_ctx* ctx, int64_t max_iters, double eps, int64_t* iters_done, double* last_improvement);
+
+/* kkm_get_cum_counts / kkm_set_cum_counts -- the cumulative counts N^j of
+ * the sklearn rate (k int64, host). Part of a checkpoint of such a run;
+ * kkm_init starts them at 0. Both synchronise. */
+kkm_status kkm_get_cum_counts(kkm_ctx* ctx, int64_t* counts);
+kkm_status kkm_set_cum_counts(kkm_ctx* ctx, const int64_t* counts);
 
 /* kkm_graph_enable -- with enable != 0, kkm_step captures its kernel sequence
  * in a CUDA graph and replays that graph. The graph is built once for each

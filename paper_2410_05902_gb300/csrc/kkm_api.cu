@@ -36,6 +36,7 @@ struct kkm_ctx {
   int32_t* d_hassign = nullptr;
   double* d_hobj = nullptr;
   double* d_objpart = nullptr;
+  double* d_obj2 = nullptr;   // kkm_fit: f_B before and after the update
   int32_t objpart_len = 0;
   bool timing = false;
   std::vector<cudaEvent_t> ev;
@@ -158,7 +159,7 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
   if (kernel->kind == KKM_POLY &&
       (kernel->degree < 1 || kernel->degree > 8 || !std::isfinite(kernel->coef0)))
     return fail(nullptr, KKM_EINVAL, "polynomial degree must be in [1, 8] with a finite coef0");
-  if (cfg->lr != KKM_LR_BETA && cfg->lr != KKM_LR_CONST)
+  if (cfg->lr != KKM_LR_BETA && cfg->lr != KKM_LR_CONST && cfg->lr != KKM_LR_SKLEARN)
     return fail(nullptr, KKM_EINVAL, "unknown learning rate");
   if (cfg->lr == KKM_LR_CONST && !(cfg->eta > 0.0 && cfg->eta <= 1.0))
     return fail(nullptr, KKM_EINVAL, "eta must be in (0, 1]");
@@ -265,7 +266,7 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
   ALLOC(s.blk_first, k); ALLOC(s.blk_num, k);
   ALLOC(s.assign, s.bpad); ALLOC(s.mind, s.bpad); ALLOC(s.inner_a, s.bpad);
   ALLOC(s.counts, k); ALLOC(s.alpha, k); ALLOC(s.coff, k + 1); ALLOC(s.perm, s.bpad);
-  ALLOC(s.cmc, k); ALLOC(s.plan, k); ALLOC(s.comp_off, k); ALLOC(s.comp_total, 1);
+  ALLOC(s.cmc, k); ALLOC(s.ncum, k); ALLOC(c->d_obj2, 2); ALLOC(s.plan, k); ALLOC(s.comp_off, k); ALLOC(s.comp_total, 1);
   ALLOC(s.tiles, s.max_tiles); ALLOC(s.ntiles, 1); ALLOC(s.tile_first, k); ALLOC(s.tile_cnt, k);
   ALLOC(s.part, (size_t)s.max_tiles * s.bpad);
   ALLOC(s.wpairs, s.max_pairs); ALLOC(s.nwpairs, 1); ALLOC(s.wpair_first, k); ALLOC(s.wpair_cnt, k);
@@ -435,7 +436,7 @@ static kkm_status assign_chunks(kkm_ctx* c, const float* Q, int64_t m, int64_t l
       if (mind_out)
         KKM_CU(cudaMemcpyAsync(mind_out + r0, s.mind, rows * sizeof(float), cudaMemcpyDeviceToDevice,
                                c->stream), "mind copy");
-      KKM_CU(kkm::launch_mind_sum(s, rows, c->d_objpart + pending, c->stream), "objective sum");
+      KKM_CU(kkm::launch_mind_sum(s, rows, 1.0, c->d_objpart + pending, c->stream), "objective sum");
       if (++pending == c->objpart_len || r0 + s.b >= m) {
         partials.resize(pending);
         KKM_CU(cudaMemcpyAsync(partials.data(), c->d_objpart, pending * sizeof(double),
@@ -519,6 +520,74 @@ KKM_API kkm_status kkm_objective_bwd(kkm_ctx* c, const float* Q, int64_t m, int6
   if (!grad_loss || !grad_q || !grad_log_sigma || ldg < c->s.d)
     return fail(c, KKM_EINVAL, "grad_loss, grad_q (ldg >= d) and grad_log_sigma are required");
   return objective_call(c, Q, m, ldq, assign, log_sigma, nullptr, nullptr, grad_loss, grad_q, ldg, grad_log_sigma);
+}
+
+KKM_API kkm_status kkm_step_eval(kkm_ctx* c, const int32_t* batch_idx, double* obj_before_dev,
+                                 double* obj_after_dev) {
+  kkm_status st = check_usable(c);
+  if (st != KKM_OK) return st;
+  if (!obj_before_dev || !obj_after_dev) return fail(c, KKM_EINVAL, "obj_before_dev and obj_after_dev are required");
+  st = kkm_step(c, batch_idx, nullptr, nullptr, nullptr, obj_before_dev);
+  if (st != KKM_OK) return st;
+  // f_{B_i}(C_{i+1}): the distance pass and argmin again on the same batch
+  // rows, against the windows, weights and norms the step just wrote
+  const Dev& s = c->s;
+  if (c->use_tc) KKM_CU(kkm::launch_dist_tc(s, c->tmaps, s.b, c->stream), "distance kernel (tcgen05)");
+  else KKM_CU(kkm::launch_dist_simt(s, s.b, c->stream), "distance kernel");
+  KKM_CU(kkm::launch_argmin(s, s.b, nullptr, nullptr, s.mind, nullptr, false, c->stream), "argmin");
+  KKM_CU(kkm::launch_mind_sum(s, s.b, s.inv_b, obj_after_dev, c->stream), "objective sum");
+  c->launches += 3;
+  return KKM_OK;
+}
+
+KKM_API kkm_status kkm_fit(kkm_ctx* c, int64_t max_iters, double eps, int64_t* iters_done,
+                           double* last_improvement) {
+  kkm_status st = check_usable(c);
+  if (st != KKM_OK) return st;
+  if (max_iters < 0 || std::isnan(eps)) return fail(c, KKM_EINVAL, "max_iters >= 0 and a non-NaN eps required");
+  int64_t done = 0;
+  double imp = 0.0;
+  for (; done < max_iters;) {
+    st = kkm_step_eval(c, nullptr, c->d_obj2, c->d_obj2 + 1);
+    if (st != KKM_OK) return st;
+    ++done;
+    st = sync_and_check(c);
+    if (st != KKM_OK) return st;
+    double h[2];
+    KKM_CU(cudaMemcpy(h, c->d_obj2, sizeof(h), cudaMemcpyDeviceToHost), "objective read");
+    imp = h[0] - h[1];   // the improvement on the batch (Sec. 5)
+    if (imp < eps) break;
+  }
+  if (iters_done) *iters_done = done;
+  if (last_improvement) *last_improvement = imp;
+  return KKM_OK;
+}
+
+KKM_API kkm_status kkm_get_cum_counts(kkm_ctx* c, int64_t* counts) {
+  kkm_status st = check_usable(c);
+  if (st != KKM_OK) return st;
+  if (!counts) return fail(c, KKM_EINVAL, "counts is NULL");
+  st = sync_and_check(c);
+  if (st != KKM_OK) return st;
+  std::vector<double> h(c->s.k);
+  KKM_CU(cudaMemcpy(h.data(), c->s.ncum, h.size() * sizeof(double), cudaMemcpyDeviceToHost), "state read");
+  for (int j = 0; j < c->s.k; ++j) counts[j] = (int64_t)h[j];
+  return KKM_OK;
+}
+
+KKM_API kkm_status kkm_set_cum_counts(kkm_ctx* c, const int64_t* counts) {
+  kkm_status st = check_usable(c);
+  if (st != KKM_OK) return st;
+  if (!counts) return fail(c, KKM_EINVAL, "counts is NULL");
+  std::vector<double> h(c->s.k);
+  for (int j = 0; j < c->s.k; ++j) {
+    if (counts[j] < 0 || counts[j] > (int64_t(1) << 53)) return fail(c, KKM_EINVAL, "counts out of range");
+    h[j] = (double)counts[j];
+  }
+  st = sync_and_check(c);
+  if (st != KKM_OK) return st;
+  KKM_CU(cudaMemcpy(c->s.ncum, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice), "state write");
+  return KKM_OK;
 }
 
 KKM_API kkm_status kkm_sync(kkm_ctx* c) {

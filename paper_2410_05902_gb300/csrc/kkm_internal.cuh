@@ -136,6 +136,7 @@ struct Dev {
   int32_t* nwpairs;  // [1]
   int32_t* wpair_first; // [k]
   int32_t* wpair_cnt;   // [k]
+  double* ncum;      // [k] points assigned to each center so far (N^j of the sklearn rate)
   double* wpart;     // [max_pairs][wslots][4 sums]: A, Bdd, E, M partials per tile
   int32_t wslots;    // partial slots per window-pass tile (4 SIMT, 1 tcgen05)
   int64_t* iter;     // [1] next iteration number
@@ -236,7 +237,7 @@ cudaError_t launch_objective(const Dev& s, double log_sigma, const float* Q, int
 cudaError_t launch_build_tiles(const Dev& s, cudaStream_t st);
 cudaError_t launch_init_centers(const Dev& s, const int32_t* init_idx, cudaStream_t st);
 cudaError_t launch_load_rows(const Dev& s, int32_t rows_total, cudaStream_t st);
-cudaError_t launch_mind_sum(const Dev& s, int rows, double* out, cudaStream_t st);
+cudaError_t launch_mind_sum(const Dev& s, int rows, double scale, double* out, cudaStream_t st);  // scale * sum of mind
 
 // tensor-core distance pass (BF16 forms); returns cudaErrorNotSupported when unavailable
 // maps: 256 bytes, 64-byte aligned, holding the two CUtensorMap of the pass

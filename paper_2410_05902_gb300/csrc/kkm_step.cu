@@ -635,7 +635,12 @@ __global__ void __launch_bounds__(256) k_finalize(Dev s) {
       for (int t = 0; t < 4; ++t) q[t] += red[w][t];
     const double A = q[0], Bdd = q[1], E = q[2], M = q[3];
     const double dn = (double)n;
-    const double a = (s.lr == 0) ? sqrt(dn * s.inv_b) : s.eta;
+    const double N = s.ncum[j] + dn;   // points assigned to j so far, this batch included
+    s.ncum[j] = N;
+    double a;
+    if (s.lr == 0) a = sqrt(dn * s.inv_b);
+    else if (s.lr == 2) a = dn / N;        // sklearn: the running-mean rate
+    else a = s.eta;
     const double keep = 1.0 - a;
     s.alpha[j] = a;
     const double cmc = cm_s / dn;
@@ -730,8 +735,8 @@ __global__ void k_load_rows(Dev s) {
   }
 }
 
-// FP64 sum of mind[0..rows) into *out (single CTA, fixed order).
-__global__ void __launch_bounds__(1024) k_mind_sum(Dev s, int rows, double* out) {
+// scale * (FP64 sum of mind[0..rows)) into *out (single CTA, fixed order).
+__global__ void __launch_bounds__(1024) k_mind_sum(Dev s, int rows, double scale, double* out) {
   KKM_GRID_DEP_WAIT();
   __shared__ double red[1024];
   double acc = 0.0;
@@ -742,7 +747,7 @@ __global__ void __launch_bounds__(1024) k_mind_sum(Dev s, int rows, double* out)
     if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *out = red[0];
+  if (threadIdx.x == 0) *out = red[0] * scale;
 }
 
 }  // namespace
@@ -819,8 +824,8 @@ cudaError_t launch_load_rows(const Dev& s, int32_t, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_mind_sum(const Dev& s, int rows, double* out, cudaStream_t st) {
-  cudaError_t e = launch_pdl(k_mind_sum, dim3(1), dim3(1024), 0, st, s, rows, out);
+cudaError_t launch_mind_sum(const Dev& s, int rows, double scale, double* out, cudaStream_t st) {
+  cudaError_t e = launch_pdl(k_mind_sum, dim3(1), dim3(1024), 0, st, s, rows, scale, out);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

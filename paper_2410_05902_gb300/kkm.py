@@ -20,7 +20,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libkkm.so")
 
 KKM_OK, KKM_EINVAL, KKM_ENOMEM, KKM_ECUDA, KKM_ETIMEOUT, KKM_ESTATE, KKM_ENOTSUP = range(7)
 KKM_GAUSSIAN, KKM_LAPLACIAN, KKM_LINEAR, KKM_POLY = range(4)
-KKM_LR_BETA, KKM_LR_CONST = 0, 1
+KKM_LR_BETA, KKM_LR_CONST, KKM_LR_SKLEARN = 0, 1, 2
+LEARNING_RATES = {"beta": KKM_LR_BETA, "const": KKM_LR_CONST, "sklearn": KKM_LR_SKLEARN}
 KKM_PREC_FP32, KKM_PREC_BF16, KKM_PREC_BF16X3 = 0, 1, 2
 PRECISIONS = {"fp32": KKM_PREC_FP32, "bf16": KKM_PREC_BF16, "bf16x3": KKM_PREC_BF16X3}
 KERNELS = {"gaussian": KKM_GAUSSIAN, "laplacian": KKM_LAPLACIAN, "linear": KKM_LINEAR,
@@ -81,6 +82,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                    c_int32, POINTER(kkm_kernel), _P, _P, _P], c_int32),
         "kkm_noalloc_last_error": ([], ctypes.c_char_p),
         "kkm_destroy": ([_P], c_int32),
+        "kkm_step_eval": ([_P, _P, _P, _P], c_int32),
+        "kkm_fit": ([_P, c_int64, c_double, POINTER(c_int64), POINTER(c_double)], c_int32),
+        "kkm_get_cum_counts": ([_P, _P], c_int32),
+        "kkm_set_cum_counts": ([_P, _P], c_int32),
         "kkm_group_create": ([POINTER(_P), _P, c_int32, _P], c_int32),
         "kkm_group_step": ([_P], c_int32),
         "kkm_group_sync": ([_P], c_int32),
@@ -209,6 +214,8 @@ def kkm_get_state(ctx, k: int) -> dict:
         "rows_per_center", "row_idx", "row_w", "blocks_per_center", "block_iter", "block_count",
         "c1_kept", "cnorm")]), ctx)
     out["iteration"] = it.value
+    out["cum_counts"] = np.zeros(k, np.int64)
+    _check(load().kkm_get_cum_counts(ctx, _np_ptr(out["cum_counts"])), ctx)
     return out
 
 
@@ -218,6 +225,19 @@ def kkm_set_state(ctx, state: dict) -> None:
         ("blocks_per_center", np.int32), ("block_iter", np.int64), ("block_count", np.int32),
         ("c1_kept", np.uint8), ("cnorm", np.float64))]
     _check(load().kkm_set_state(ctx, int(state["iteration"]), *[_np_ptr(a) for a in arrs]), ctx)
+    if "cum_counts" in state:
+        cc = np.ascontiguousarray(state["cum_counts"], dtype=np.int64)
+        _check(load().kkm_set_cum_counts(ctx, _np_ptr(cc)), ctx)
+
+
+def kkm_step_eval(ctx, batch_idx: int | None, obj_before: int, obj_after: int) -> None:
+    _check(load().kkm_step_eval(ctx, batch_idx, obj_before, obj_after), ctx)
+
+
+def kkm_fit(ctx, max_iters: int, eps: float) -> tuple[int, float]:
+    done, imp = c_int64(), c_double()
+    _check(load().kkm_fit(ctx, int(max_iters), float(eps), ctypes.byref(done), ctypes.byref(imp)), ctx)
+    return done.value, imp.value
 
 
 def kkm_destroy(ctx) -> None:
@@ -249,7 +269,7 @@ class KKM:
         self.k, self.b = int(k), int(b)
         self.stream = stream if stream is not None else torch.cuda.current_stream(X.device)
         kern = kkm_kernel(KERNELS[kernel], float(param), float(coef0), int(degree))
-        cfg = kkm_config(int(tau), KKM_LR_BETA if lr == "beta" else KKM_LR_CONST, float(eta),
+        cfg = kkm_config(int(tau), LEARNING_RATES[lr], float(eta),
                          PRECISIONS[precision], int(max_iters), int(seed) & ((1 << 64) - 1), int(dist_tile), 0)
         with torch.cuda.device(X.device):
             self.ctx = kkm_init(X.data_ptr(), self.n, self.d, X.stride(0), self.k, kern, self.b, cfg,
@@ -303,6 +323,18 @@ class KKM:
         kkm_objective_bwd(self.ctx, Q.data_ptr(), Q.shape[0], Q.stride(0), assign.data_ptr(), log_sigma,
                           grad_loss.data_ptr(), gq.data_ptr(), gq.stride(0), gs.data_ptr())
         return gq, gs
+
+    def step_eval(self, batch_idx=None):
+        """One iteration plus f_B before and after the update on the same batch (device scalars)."""
+        torch = self._torch
+        before = torch.empty(1, dtype=torch.float64, device=self.X.device)
+        after = torch.empty(1, dtype=torch.float64, device=self.X.device)
+        kkm_step_eval(self.ctx, self._ptr(batch_idx), before.data_ptr(), after.data_ptr())
+        return before, after
+
+    def fit(self, max_iters: int, eps: float):
+        """Iterate until the batch improvement drops below eps (Sec. 5); (iterations, last improvement)."""
+        return kkm_fit(self.ctx, max_iters, eps)
 
     def sync(self):
         kkm_sync(self.ctx)

@@ -99,4 +99,6 @@ def compare_states(gpu_state, ora_state, w_rtol=1e-12, cn_rtol=1e-6):
     np.testing.assert_array_equal(gpu_state["c1_kept"].astype(bool), ora_state["c1_kept"])
     np.testing.assert_allclose(gpu_state["row_w"], ora_state["row_w"], rtol=w_rtol, atol=1e-300)
     np.testing.assert_allclose(gpu_state["cnorm"], ora_state["cnorm"], rtol=cn_rtol, atol=cn_rtol)
+    if "cum_counts" in gpu_state and "cum_counts" in ora_state:
+        np.testing.assert_array_equal(gpu_state["cum_counts"], ora_state["cum_counts"])
     assert gpu_state["iteration"] == ora_state["iteration"]

@@ -278,3 +278,72 @@ def test_image_like_full_size_split_bf16():
         assert abs(f - rec.batch_objective) <= OBJ_TOL * rec.batch_objective
     compare_states(p.gpu.get_state(), p.ora.state(), cn_rtol=1e-6)
     p.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_sklearn_rate_teacher_forced(precision):
+    """The sklearn rate b_i^j / N^j with N^j carried in the state (kkm_get/set_cum_counts)."""
+    X = small_data(n=1500, d=12, c=6)
+    p = Pair(X, k=6, b=128, tau=80, lr="sklearn", precision=precision)
+    teacher_forced(p, inputs.batch_stream(len(X), 128, 8, seed=41))
+    p.close()
+
+
+def test_sklearn_rate_free_running():
+    X = small_data(n=1200, d=8, c=5)
+    p = Pair(X, k=5, b=96, tau=60, lr="sklearn")
+    for B in inputs.batch_stream(len(X), 96, 20, seed=42):
+        rec = p.ora.step(B)
+        d, a, f = p.gpu_step(B)
+        assert dist_rel_err(d, rec.dist) <= DIST_TOL["fp32"]
+        assert abs(f - rec.batch_objective) <= OBJ_TOL * rec.batch_objective
+        if not np.array_equal(a, rec.assign):
+            assert near_tie_ok(a, rec, p.abs_tol(rec))[0]
+            break
+    compare_states(p.gpu.get_state(), p.ora.state())
+    p.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_step_eval_objectives(precision):
+    """f_{B_i}(C_i) and f_{B_i}(C_{i+1}) of kkm_step_eval against the oracle's
+    batch objective before the update and its objective on the same batch after."""
+    X = small_data()
+    p = Pair(X, k=10, b=256, tau=200, precision=precision)
+    torch = p.torch
+    for B in inputs.batch_stream(len(X), 256, 6, seed=23):
+        p.gpu.set_state(p.ora.state())
+        rec = p.ora.step(B)
+        after_ref = p.ora.objective(X[B].astype(np.float64))
+        before, after = p.gpu.step_eval(torch.from_numpy(B.astype(np.int32)).cuda())
+        p.gpu.sync()
+        assert abs(float(before.cpu()[0]) - rec.batch_objective) <= OBJ_TOL * rec.batch_objective
+        assert abs(float(after.cpu()[0]) - after_ref) <= OBJ_TOL * after_ref
+    p.close()
+
+
+def test_fit_stops_at_the_first_small_improvement():
+    """kkm_fit stops after the first iteration whose improvement
+    f_{B_i}(C_i) - f_{B_i}(C_{i+1}) is below eps (Sec. 5); a twin run stepped
+    with kkm_step_eval (same built-in sampler, same kernels) shows the same
+    improvements."""
+    torch = torch_cuda()
+    from paper_2410_05902_gb300.kkm import KKM
+    X = small_data()
+    sigma = inputs.median_sigma(X, seed=1)
+    Xd = torch.from_numpy(X).cuda()
+    init = inputs.init_indices(len(X), 10, seed=3)
+    mk = lambda: KKM(Xd, 10, 256, kernel="gaussian", param=2 * sigma * sigma, tau=200, seed=5, init_idx=init)
+    eps = 2e-3
+    a, b = mk(), mk()
+    done, last = a.fit(100, eps)
+    imps = []
+    for _ in range(done):
+        before, after = b.step_eval()
+        imps.append(float(before.cpu()[0]) - float(after.cpu()[0]))
+    assert 1 <= done <= 100
+    assert imps[-1] == last
+    assert all(v >= eps for v in imps[:-1])
+    assert done == 100 or last < eps
+    a.close()
+    b.close()
