@@ -268,7 +268,7 @@ def time_form(form, args, X, Xd, kappa, init, rank, world, dev, barrier):
     w = WORKLOAD
     stream = torch.cuda.current_stream(dev)
     run = KKM(Xd, w.k, w.b, kernel=KERNEL, param=kappa, tau=w.tau, precision=form,
-              seed=1000 + rank, init_idx=init)
+              seed=1000 + rank, init_idx=init, dist_tile=args.dist_tile)
     for _ in range(PREP_ITERS):
         run.step()
     run.graph(not args.no_graph)          # the step replays as one captured CUDA graph
@@ -562,6 +562,8 @@ def main():
     ap.add_argument("--objective-grad", action="store_true",
                     help="time the objective and its adjoint on the differentiation workload")
     ap.add_argument("--kernel", choices=["gaussian", "laplacian"], default="gaussian")
+    ap.add_argument("--dist-tile", type=int, choices=[0, 64, 128, 256], default=0,
+                    help="support rows per tensor-core distance tile (0: the library default)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

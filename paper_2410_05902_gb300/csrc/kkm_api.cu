@@ -42,7 +42,7 @@ struct kkm_ctx {
   std::vector<cudaEvent_t> ev;
   int64_t ev_used = 0;
   int64_t launches = 0;       // kernels launched (host count)
-  alignas(64) unsigned char tmaps[512];   // TMA descriptors of the tensor-core passes (3 x 128 B)
+  alignas(64) unsigned char tmaps[512];   // TMA descriptors of the tensor-core passes (4 x 128 B)
   // CUDA graph of one step (kkm_graph_enable): captured on a private stream
   // per set of kkm_step pointer arguments and launched on `stream`
   bool graph_on = false;
@@ -163,8 +163,8 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
     return fail(nullptr, KKM_EINVAL, "unknown learning rate");
   if (cfg->lr == KKM_LR_CONST && !(cfg->eta > 0.0 && cfg->eta <= 1.0))
     return fail(nullptr, KKM_EINVAL, "eta must be in (0, 1]");
-  if (cfg->dist_tile != 0 && cfg->dist_tile != 64 && cfg->dist_tile != 128)
-    return fail(nullptr, KKM_EINVAL, "dist_tile must be 0, 64 or 128");
+  if (cfg->dist_tile != 0 && cfg->dist_tile != 64 && cfg->dist_tile != 128 && cfg->dist_tile != 256)
+    return fail(nullptr, KKM_EINVAL, "dist_tile must be 0, 64, 128 or 256");
   if (cfg->reserved != 0) return fail(nullptr, KKM_EINVAL, "reserved must be 0");
   if (cfg->precision < KKM_PREC_FP32 || cfg->precision > KKM_PREC_BF16X3)
     return fail(nullptr, KKM_EINVAL, "unknown precision");
@@ -225,7 +225,7 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
     cudaDeviceGetAttribute(&min, cudaDevAttrComputeCapabilityMinor, c->device);
     c->use_tc = (maj == 10 && min == 3) && kkm::tc_available();
   }
-  s.tn = c->use_tc ? (cfg->dist_tile == 64 ? 64 : 128) : 64;
+  s.tn = c->use_tc ? (cfg->dist_tile == 0 ? 256 : cfg->dist_tile) : 64;
   s.pair_rows = c->use_tc ? 128 : 64;
   s.pair_cols = 64;
   const int64_t TR = s.pair_rows, TC = s.pair_cols;   // window-pass tile

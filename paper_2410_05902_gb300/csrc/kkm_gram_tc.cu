@@ -60,7 +60,7 @@ constexpr int MS = 4;                           // metadata ring slots (items in
 // ||y||^2, col[1] = w, col[2] = data index of the 128 support rows; row[0] =
 // ||x||^2, row[1] = data index of the 128 batch rows.
 struct MetaSlot {
-  float col[3][128];
+  float col[3][256];
   float row[2][128];
 };
 
@@ -184,7 +184,18 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 template <int NB>
 __device__ __forceinline__ void tmem_ld16x256(uint32_t taddr, float (&v)[4 * NB]) {
   uint32_t r[4 * NB];
-  if constexpr (NB == 4) {
+  if constexpr (NB == 8) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.16x256b.x8.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+          "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+          "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+  } else if constexpr (NB == 4) {
     asm volatile(
         "tcgen05.ld.sync.aligned.16x256b.x4.b32 "
         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -193,7 +204,7 @@ __device__ __forceinline__ void tmem_ld16x256(uint32_t taddr, float (&v)[4 * NB]
           "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
   } else {
-    static_assert(NB == 2, "tmem_ld16x256: 2 or 4 blocks");
+    static_assert(NB == 2, "tmem_ld16x256: 2, 4 or 8 blocks");
     asm volatile(
         "tcgen05.ld.sync.aligned.16x256b.x2.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
@@ -688,12 +699,12 @@ cudaError_t launch_form(const Dev& s, const CUtensorMap& a, const CUtensorMap& b
   return launch_pdl(k_dist_tc<KIND, MODE, X3, TNV>, dim3(grid), dim3(NTHREADS), SMEM_BYTES, st, s, rows, a, b);
 }
 
-// maps: [0] batch rows, 128-row boxes; [1] support rows, 128-row boxes; [2] support rows, 64-row boxes
+// maps: [0] batch rows, 128-row boxes; support rows with [1] 128-row, [2] 64-row, [3] 256-row boxes
 template <int MODE, int TNV>
 cudaError_t launch_mode(const Dev& s, const void* maps_in, int rows, cudaStream_t st) {
   const CUtensorMap* m = static_cast<const CUtensorMap*>(maps_in);
   const CUtensorMap& a = (MODE == 0) ? m[0] : m[1];
-  const CUtensorMap& b = (TNV == 128) ? m[1] : m[2];
+  const CUtensorMap& b = (TNV == 256) ? m[3] : (TNV == 128) ? m[1] : m[2];
   const bool x3 = s.form == FORM_BF16X3;
   switch (s.kind) {
     case K_GAUSS:
@@ -716,7 +727,7 @@ cudaError_t launch_mode(const Dev& s, const void* maps_in, int rows, cudaStream_
 bool tc_available() { return true; }
 
 // Tensor maps of the batch rows and the support store: 2-D BF16 tensors of ld
-// columns, boxes of 64 columns x 128 (or 64) rows, 128-byte swizzle.
+// columns, boxes of 64 columns x 128 (64, 256) rows, 128-byte swizzle.
 cudaError_t tc_prepare(Dev& s, void* maps_out) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
@@ -729,9 +740,10 @@ cudaError_t tc_prepare(Dev& s, void* maps_out) {
   }
   CUtensorMap* maps = static_cast<CUtensorMap*>(maps_out);
   const int64_t srows = (int64_t)s.k * s.cap + 256;
-  struct { void* base; uint64_t rows; uint32_t box_rows; } ops[3] = {
-      {s.xbh, (uint64_t)s.bpad, 128u}, {s.ybh, (uint64_t)srows, 128u}, {s.ybh, (uint64_t)srows, 64u}};
-  for (int i = 0; i < 3; ++i) {
+  struct { void* base; uint64_t rows; uint32_t box_rows; } ops[4] = {
+      {s.xbh, (uint64_t)s.bpad, 128u}, {s.ybh, (uint64_t)srows, 128u}, {s.ybh, (uint64_t)srows, 64u},
+      {s.ybh, (uint64_t)srows, 256u}};
+  for (int i = 0; i < 4; ++i) {
     cuuint64_t dims[2] = {(cuuint64_t)s.ld, (cuuint64_t)ops[i].rows};
     cuuint64_t strides[1] = {(cuuint64_t)s.ld * 2};
     cuuint32_t box[2] = {(cuuint32_t)KS, ops[i].box_rows};
@@ -746,7 +758,9 @@ cudaError_t tc_prepare(Dev& s, void* maps_out) {
 
 cudaError_t launch_dist_tc(const Dev& s, const void* maps, int rows, cudaStream_t st) {
   if (rows <= 0) return cudaSuccess;
-  return s.tn == 64 ? launch_mode<0, 64>(s, maps, rows, st) : launch_mode<0, 128>(s, maps, rows, st);
+  if (s.tn == 64) return launch_mode<0, 64>(s, maps, rows, st);
+  if (s.tn == 256) return launch_mode<0, 256>(s, maps, rows, st);
+  return launch_mode<0, 128>(s, maps, rows, st);
 }
 
 cudaError_t launch_wgram_tc(const Dev& s, const void* maps, cudaStream_t st) {

@@ -12,8 +12,8 @@
 //                  cap - REGION_PAD = 2*tau + 4*b + 8 usable rows the source
 //                  and destination rows of that copy never overlap, because a
 //                  window holds at most tau + b rows. The last REGION_PAD rows
-//                  of a region are never used, so a tile that starts inside
-//                  the window never reaches the next region.
+//                  of a region are never used, so a tile (at most 256 rows)
+//                  that starts inside the window never reaches the next region.
 //   row data       FP32 form: FP32 rows, ld = round_up(d, 16), zero padded.
 //                  BF16 forms: BF16 rows [hi(0..dp) | lo(0..dp)], dp =
 //                  round_up(d, 64), zero padded; ld = 2*dp.
@@ -43,7 +43,7 @@ constexpr int ST_BAD_ASSIGN = 2;
 constexpr int ST_CAPACITY = 4;
 constexpr int ST_TIMEOUT = 8;
 
-constexpr int REGION_PAD = 128;   // unused rows at the end of each support region
+constexpr int REGION_PAD = 256;   // unused rows at the end of each support region (the widest tile)
 
 // Column tile of the distance pass: support rows [row0, row0 + ncols) of center j.
 struct Tile {

@@ -16,7 +16,7 @@ from ctypes import c_void_p
 from .kkm import KKM, KKMError, load
 
 # (precision, distance-pass tile width); 0 = the form's default
-DEFAULT_CANDIDATES = (("fp32", 0), ("bf16x3", 64), ("bf16x3", 128))
+DEFAULT_CANDIDATES = (("fp32", 0), ("bf16x3", 64), ("bf16x3", 128), ("bf16x3", 256))
 
 
 class Group:

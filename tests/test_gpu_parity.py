@@ -250,14 +250,13 @@ def test_graph_replay_matches_eager(precision):
         run.close()
 
 
-@pytest.mark.parametrize("precision", ["bf16x3", "bf16"])
-@pytest.mark.parametrize("d", [200, 784])
-def test_teacher_forced_wide_rows_tensor_path(precision, d):
-    """Wide rows give the tcgen05 passes several K-slices per tile (d=784: 13), so the
-    stream-K schedule splits tiles across CTAs. The split parts are merged by the last
-    CTA to deliver, in both the distance pass and the window pass."""
+@pytest.mark.parametrize("precision,d,tile", [("bf16x3", 200, 128), ("bf16", 200, 64), ("bf16x3", 784, 128),
+                                              ("bf16", 784, 256), ("bf16x3", 784, 256), ("bf16x3", 96, 64)])
+def test_teacher_forced_wide_rows_tensor_path(precision, d, tile):
+    """Wide rows give the tcgen05 passes several K-slices per tile (d=784: 13), with
+    64-, 128- and 256-row support tiles in the distance pass."""
     X, _ = inputs.image_like(3000, seed=7, d=d, classes=8)
-    p = Pair(X, k=8, b=512, tau=120, precision=precision)
+    p = Pair(X, k=8, b=512, tau=120, precision=precision, dist_tile=tile)
     batches = inputs.batch_stream(len(X), 512, 6, seed=23)
     teacher_forced(p, batches, cn_rtol=1e-6 if precision == "bf16x3" else 5e-3)
     p.close()
