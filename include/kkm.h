@@ -106,6 +106,23 @@ typedef struct kkm_ctx kkm_ctx;
 /* ABI version of the loaded library (KKM_ABI_VERSION). */
 int32_t kkm_version(void);
 
+/* kkm_kmeanspp -- kernel k-means++ seeding (D^2 sampling in feature space,
+ * the initialisation of Secs. 1 and 5): k data indices, the first uniform,
+ * each later one with probability proportional to min over the chosen c of
+ * Delta(x, c) = K(x,x) - 2K(x,c) + K(c,c), evaluated in FP64. Draw t uses
+ * output t of SplitMix64 seeded with `seed`: the first as an index by
+ * Lemire's multiply-high, the others as u = (h >> 11) 2^-53, picking the first
+ * x whose running sum of D^2 exceeds u times the total.
+ *   X       : device, n x d FP32, leading dimension ldx >= d.
+ *   k       : 1 <= k <= n.
+ *   kernel  : host; as for kkm_init.
+ *   out_idx : host, k int64 (the indices kkm_init's init_idx takes).
+ *   stream  : cudaStream_t or NULL. The call allocates n + n/8 + k words of
+ *             device scratch, frees it, and synchronises the stream.
+ * kkm_last_error(NULL) reports failures. */
+kkm_status kkm_kmeanspp(const float* X, int64_t n, int32_t d, int64_t ldx, int32_t k, const kkm_kernel* kernel,
+                        uint64_t seed, int64_t* out_idx, void* stream);
+
 /* kkm_init -- creates a run (the inputs of Algorithms 1/2).
  *   out        : host; receives the new context, or NULL on failure.
  *   X          : device, n x d FP32 dataset, leading dimension ldx >= d.

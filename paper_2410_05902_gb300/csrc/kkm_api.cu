@@ -140,6 +140,41 @@ KKM_API const char* kkm_last_error(const kkm_ctx* ctx) {
   return ctx ? ctx->err.c_str() : g_init_error.c_str();
 }
 
+KKM_API kkm_status kkm_kmeanspp(const float* X, int64_t n, int32_t d, int64_t ldx, int32_t k,
+                                const kkm_kernel* kernel, uint64_t seed, int64_t* out_idx, void* stream) {
+  if (!X || !kernel || !out_idx) return fail(nullptr, KKM_EINVAL, "X, kernel and out_idx are required");
+  if (n < 1 || n >= (int64_t(1) << 31)) return fail(nullptr, KKM_EINVAL, "n must be in [1, 2^31)");
+  if (d < 1 || d > 4096) return fail(nullptr, KKM_EINVAL, "d must be in [1, 4096]");
+  if (ldx < d) return fail(nullptr, KKM_EINVAL, "ldx must be >= d");
+  if (k < 1 || k > n) return fail(nullptr, KKM_EINVAL, "k must be in [1, n]");
+  if (kernel->kind < KKM_GAUSSIAN || kernel->kind > KKM_POLY)
+    return fail(nullptr, KKM_EINVAL, "unknown kernel kind");
+  if ((kernel->kind == KKM_GAUSSIAN || kernel->kind == KKM_LAPLACIAN) &&
+      !(std::isfinite(kernel->param) && kernel->param > 0.0))
+    return fail(nullptr, KKM_EINVAL, "kernel param (kappa or sigma) must be finite and > 0");
+  if (kernel->kind == KKM_POLY &&
+      (kernel->degree < 1 || kernel->degree > 8 || !std::isfinite(kernel->coef0)))
+    return fail(nullptr, KKM_EINVAL, "polynomial degree must be in [1, 8] with a finite coef0");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double* d2 = nullptr;
+  double* part = nullptr;
+  int64_t* chosen = nullptr;
+  const int64_t nblk = (n + 7) / 8;
+  cudaError_t e = cudaMalloc(&d2, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&part, nblk * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&chosen, k * sizeof(int64_t));
+  if (e == cudaSuccess)
+    e = kkm::launch_kmeanspp(X, n, d, ldx, k, kernel->kind, kernel->param, kernel->coef0, kernel->degree, seed, d2,
+                             part, chosen, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out_idx, chosen, k * sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d2);
+  cudaFree(part);
+  cudaFree(chosen);
+  if (e != cudaSuccess) return fail(nullptr, KKM_ECUDA, std::string("k-means++: ") + cudaGetErrorString(e));
+  return KKM_OK;
+}
+
 KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d, int64_t ldx,
                             int32_t k, const kkm_kernel* kernel, int32_t b, const kkm_config* cfg,
                             const int64_t* init_idx, void* stream) {

@@ -230,6 +230,11 @@ cudaError_t launch_finalize(const Dev& s, cudaStream_t st);
 // batch objective at fixed assignments and its adjoint (kkm_grad.cu); ws holds
 // grad_workspace_doubles(s, m) doubles. With grad_q == NULL only the forward
 // runs (loss, delta); otherwise the adjoint (grad_q, grad_s).
+// kernel k-means++ seeding (kkm_seed.cu): chosen[0..k) on the device;
+// d2 holds n doubles, part ceil(n/8) doubles
+cudaError_t launch_kmeanspp(const float* X, int64_t n, int d, int64_t ldx, int k, int kind, double param,
+                            double coef0, int degree, uint64_t seed, double* d2, double* part, int64_t* chosen,
+                            cudaStream_t st);
 size_t grad_workspace_doubles(const Dev& s, int64_t m);
 cudaError_t launch_objective(const Dev& s, double log_sigma, const float* Q, int64_t m, int64_t ldq,
                              const int32_t* assign, double* loss, float* delta, const double* grad_loss,

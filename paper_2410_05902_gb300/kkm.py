@@ -83,6 +83,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "kkm_noalloc_last_error": ([], ctypes.c_char_p),
         "kkm_destroy": ([_P], c_int32),
         "kkm_step_eval": ([_P, _P, _P, _P], c_int32),
+        "kkm_kmeanspp": ([_P, c_int64, c_int32, c_int64, c_int32, POINTER(kkm_kernel), c_uint64, _P, _P], c_int32),
         "kkm_fit": ([_P, c_int64, c_double, POINTER(c_int64), POINTER(c_double)], c_int32),
         "kkm_get_cum_counts": ([_P, _P], c_int32),
         "kkm_set_cum_counts": ([_P, _P], c_int32),
@@ -157,6 +158,27 @@ def kkm_objective_bwd(ctx, Q: int, m: int, ldq: int, assign: int, log_sigma: flo
                       grad_q: int, ldg: int, grad_log_sigma: int) -> None:
     _check(load().kkm_objective_bwd(ctx, Q, m, ldq, assign, float(log_sigma), grad_loss, grad_q, ldg,
                                     grad_log_sigma), ctx)
+
+
+def kkm_kmeanspp(X_ptr: int, n: int, d: int, ldx: int, k: int, kernel: kkm_kernel, seed: int,
+                 stream: int | None) -> np.ndarray:
+    out = np.zeros(k, np.int64)
+    _check(load().kkm_kmeanspp(X_ptr, n, d, ldx, k, ctypes.byref(kernel), int(seed) & ((1 << 64) - 1),
+                               _np_ptr(out), stream), None)
+    return out
+
+
+def kmeanspp(X, k: int, kernel: str = "gaussian", param: float = 1.0, coef0: float = 0.0, degree: int = 2,
+             seed: int = 0, stream=None) -> np.ndarray:
+    """Kernel k-means++ seeding on the GPU: k data indices of the CUDA float32 tensor X."""
+    import torch
+    if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float32 and X.dim() == 2
+            and X.stride(1) == 1):
+        raise TypeError("X must be a row-contiguous 2-D float32 CUDA tensor")
+    st = stream if stream is not None else torch.cuda.current_stream(X.device)
+    kern = kkm_kernel(KERNELS[kernel], float(param), float(coef0), int(degree))
+    with torch.cuda.device(X.device):
+        return kkm_kmeanspp(X.data_ptr(), X.shape[0], X.shape[1], X.stride(0), int(k), kern, seed, st.cuda_stream)
 
 
 def kkm_sync(ctx) -> None:
@@ -271,6 +293,10 @@ class KKM:
         kern = kkm_kernel(KERNELS[kernel], float(param), float(coef0), int(degree))
         cfg = kkm_config(int(tau), LEARNING_RATES[lr], float(eta),
                          PRECISIONS[precision], int(max_iters), int(seed) & ((1 << 64) - 1), int(dist_tile), 0)
+        if isinstance(init_idx, str):
+            if init_idx != "kmeans++":
+                raise ValueError("init_idx: indices, None, or 'kmeans++'")
+            init_idx = kmeanspp(X, self.k, kernel, param, coef0, degree, seed=seed, stream=self.stream)
         with torch.cuda.device(X.device):
             self.ctx = kkm_init(X.data_ptr(), self.n, self.d, X.stride(0), self.k, kern, self.b, cfg,
                                 None if init_idx is None else np.asarray(init_idx), self.stream.cuda_stream)

@@ -5,6 +5,8 @@ exports every function include/kkm.h declares, and it rejects invalid
 arguments on the host before any CUDA call. No compute call is made here.
 """
 import ctypes
+
+import numpy as np
 import os
 import re
 import shutil
@@ -103,6 +105,17 @@ def test_group_create_validates_on_host(lib):
     assert b"null run" in lib.kkm_group_last_error(None)
     assert lib.kkm_group_step(None) == kkm.KKM_EINVAL
     assert lib.kkm_group_destroy(None) == kkm.KKM_OK
+
+
+def test_kmeanspp_validates_on_host(lib):
+    out = np.zeros(4, np.int64)
+    kern = kkm.kkm_kernel(kkm.KKM_GAUSSIAN, 1.0, 0.0, 2)
+    ptr = out.ctypes.data_as(ctypes.c_void_p)
+    assert lib.kkm_kmeanspp(None, 10, 3, 3, 4, ctypes.byref(kern), 0, ptr, None) == kkm.KKM_EINVAL
+    assert lib.kkm_kmeanspp(ctypes.c_void_p(16), 3, 3, 3, 4, ctypes.byref(kern), 0, ptr, None) == kkm.KKM_EINVAL
+    assert b"k must be" in lib.kkm_last_error(None)
+    bad = kkm.kkm_kernel(kkm.KKM_GAUSSIAN, -1.0, 0.0, 2)
+    assert lib.kkm_kmeanspp(ctypes.c_void_p(16), 10, 3, 3, 4, ctypes.byref(bad), 0, ptr, None) == kkm.KKM_EINVAL
 
 
 def test_binding_fails_loudly_without_library(tmp_path):
