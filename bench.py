@@ -37,7 +37,7 @@ WORKLOAD = inputs.WORKLOADS["image"]
 METRIC = "batch-point×center distances/s per iteration on 1 GB300 (BF16 vs FP32) at ≤1e-4 obj err"
 UNIT = "distances/s"
 PREP_ITERS = 20         # iterations that bring the windows to their steady-state size
-DTYPES = {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}
+DTYPES = {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3", "tf32": "tf32"}
 OBJ_BAR = 1e-4          # objective relative error a form must meet to count (the metric's bar)
 
 
@@ -333,6 +333,12 @@ def roofline(form, S, kernel_ms, n_rec):
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "kernel": "k_dist_simt<FP32> (FP32 FFMA Gram + kernel values + weighted sums)",
                 "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 flop x max SM clock (derived)"}
+    elif form == "tf32":
+        # TF32 dense: the measured BF16 burst times the nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s)
+        peak = peaks["bf16_tflops"] * 1.1 / 2.25
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "kernel": "k_dist_tc (tf32: tcgen05 kind::tf32 Gram + kernel values + weighted sums)",
+                "peak_source": f"bf16_tflops burst ({peaks['source']}) x 1.1/2.25 nominal TF32/BF16 ratio"}
     else:
         peak = peaks["bf16_tflops"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -385,7 +391,7 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    forms = ["fp32", "bf16x3", "bf16"] if args.precision == "auto" else [args.precision]
+    forms = ["fp32", "bf16x3", "tf32", "bf16"] if args.precision == "auto" else [args.precision]
     res = {f: time_form(f, args, X, Xd, kappa, init, rank, world, dev, barrier) for f in forms}
     if rank == 0:
         cpu_v, cores, desc, acc, check = oracle_leg(X, kappa, init, forms, Xd, args.oracle_budget)
@@ -553,7 +559,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["auto", "fp32", "bf16", "bf16x3"], default="auto",
+    ap.add_argument("--precision", choices=["auto", "fp32", "bf16", "bf16x3", "tf32"], default="auto",
                     help="auto: time every form, report the fastest that meets the objective bar")
     ap.add_argument("--oracle-budget", type=float, default=20.0)
     ap.add_argument("--no-graph", action="store_true", help="launch every kernel instead of replaying a graph")

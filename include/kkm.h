@@ -87,8 +87,18 @@ typedef enum kkm_lr { KKM_LR_BETA = 0, KKM_LR_CONST = 1, KKM_LR_SKLEARN = 2 } kk
  *   FP32   : CUDA-core FP32 FMA products.
  *   BF16   : tcgen05 tensor cores, BF16 operands, FP32 accumulation.
  *   BF16X3 : tcgen05, split operands x = hi + lo (both BF16); the product is
- *            hi.hi + hi.lo + lo.hi, accumulated in FP32. */
-typedef enum kkm_precision { KKM_PREC_FP32 = 0, KKM_PREC_BF16 = 1, KKM_PREC_BF16X3 = 2 } kkm_precision;
+ *            hi.hi + hi.lo + lo.hi, accumulated in FP32.
+ *   TF32   : tcgen05 kind::tf32, operands rounded to TF32 (10 explicit
+ *            mantissa bits, round to nearest with ties away), FP32
+ *            accumulation.
+ * The tensor-core forms need a compute capability 10.3 device (KKM_ENOTSUP
+ * for TF32 elsewhere; BF16 and BF16X3 fall back to CUDA-core products). */
+typedef enum kkm_precision {
+  KKM_PREC_FP32 = 0,
+  KKM_PREC_BF16 = 1,
+  KKM_PREC_BF16X3 = 2,
+  KKM_PREC_TF32 = 3
+} kkm_precision;
 
 typedef struct kkm_config {
   int32_t tau;       /* truncation parameter tau of Sec. 4.1; <= 0 runs Algorithm 1 untruncated */

@@ -201,7 +201,7 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
   if (cfg->dist_tile != 0 && cfg->dist_tile != 64 && cfg->dist_tile != 128 && cfg->dist_tile != 256)
     return fail(nullptr, KKM_EINVAL, "dist_tile must be 0, 64, 128 or 256");
   if (cfg->reserved != 0) return fail(nullptr, KKM_EINVAL, "reserved must be 0");
-  if (cfg->precision < KKM_PREC_FP32 || cfg->precision > KKM_PREC_BF16X3)
+  if (cfg->precision < KKM_PREC_FP32 || cfg->precision > KKM_PREC_TF32)
     return fail(nullptr, KKM_EINVAL, "unknown precision");
   if (cfg->tau > 1000000) return fail(nullptr, KKM_EINVAL, "tau must be <= 1e6");
   if (cfg->tau <= 0 && cfg->max_iters < 1)
@@ -249,6 +249,7 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
   s.num_sms = sms > 0 ? sms : 148;
   s.seed = cfg->seed;
   if (s.form == kkm::FORM_FP32) { s.dp = 0; s.ld = (int32_t)kkm::round_up(d, 16); }
+  else if (s.form == kkm::FORM_TF32) { s.dp = (int32_t)kkm::round_up(d, 32); s.ld = s.dp; }
   else { s.dp = (int32_t)kkm::round_up(d, 64); s.ld = 2 * s.dp; }
   s.bpad = (int32_t)kkm::round_up(b, 128);
 
@@ -259,6 +260,10 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
     cudaDeviceGetAttribute(&maj, cudaDevAttrComputeCapabilityMajor, c->device);
     cudaDeviceGetAttribute(&min, cudaDevAttrComputeCapabilityMinor, c->device);
     c->use_tc = (maj == 10 && min == 3) && kkm::tc_available();
+  }
+  if (s.form == kkm::FORM_TF32 && !c->use_tc) {
+    c->err = "the TF32 form needs a compute capability 10.3 device";
+    return bail(KKM_ENOTSUP);
   }
   s.tn = c->use_tc ? (cfg->dist_tile == 0 ? 256 : cfg->dist_tile) : 64;
   s.pair_rows = c->use_tc ? 128 : 64;
@@ -274,7 +279,7 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
   }
   s.max_pairs = (int32_t)(p1 + p2);
 
-  const int esz = s.form == kkm::FORM_FP32 ? 4 : 2;
+  const int esz = kkm::f32_rows(s.form) ? 4 : 2;
   cudaError_t e = cudaSuccess;
 #define ALLOC(ptr, count)                                        \
   do {                                                           \

@@ -1,20 +1,22 @@
-// tcgen05 / TMA form of the two Gram passes (BF16 and split-BF16 products).
+// tcgen05 / TMA form of the two Gram passes (BF16, split-BF16 and TF32 products).
 //
 // One persistent CTA per SM walks the work items round-robin. In the distance
-// pass (mode 0) an item is (128-row batch tile, 128-row support tile of one
-// center); in the window pass (mode 1) it is (128 support rows, 64 support
-// rows) of one center. For each item:
-//   G = X_B Y^T           tcgen05.mma kind::f16 (BF16 x BF16 -> FP32 in TMEM),
-//                         operands streamed by TMA through a 6-stage ring of
-//                         128B-swizzled shared-memory slices (64 columns each)
+// pass (mode 0) an item is (128-row batch tile, TNV-row support tile of one
+// center; TNV = 256 by default, 64 or 128 on request); in the window pass
+// (mode 1) it is (128 support rows, 64 support rows) of one center. For each
+// item:
+//   G = X_B Y^T           tcgen05.mma kind::f16 (BF16) or kind::tf32 (TF32),
+//                         FP32 in TMEM; operands streamed by TMA through a
+//                         192 KB ring of 128B-swizzled shared-memory slices
 //   K = kernel(||x||^2 + ||y||^2 - 2G)     in registers after tcgen05.ld
 //   part[tile][x] = sum_y w_y K(x, y)      one partial per row and tile
 // The split form (x = hi + lo) runs the K loop three times over the slice
 // pairs (hi,hi), (hi,lo), (lo,hi) into the same accumulator.
 //
-// Roles: warp 0 issues TMA loads, warp 1 issues the MMAs (one elected lane)
-// and owns the TMEM allocation (2 accumulators x 128 columns), warps 2-5 are
-// the epilogue (one TMEM lane = one batch row per thread). Every mbarrier wait
+// Roles: warp 0 issues TMA loads (and stages each item's metadata), warp 1
+// issues the MMAs (one elected lane) and owns the TMEM allocation (2
+// accumulators x TNV columns), warps 2-17 are the epilogue (four per TMEM lane
+// quadrant, each on a quarter of the columns). Every mbarrier wait
 // is bounded. A wait that runs out sets ST_TIMEOUT and makes the role stop. On
 // the way out the producer waits for its last copies to land and the MMA warp
 // waits for its last MMAs, so TMEM is freed only once nothing is in flight.
@@ -29,6 +31,9 @@ namespace {
 constexpr int TM = 128;                         // A rows per tile = TMEM lanes
 constexpr int KS = 64;                          // BF16 columns per slice (one 128-byte swizzle row)
 constexpr int A_BYTES = TM * KS * 2;            // 16 KB: the A tile of one slice
+// operand formats: BF16 (one product), split BF16 (hi.hi + hi.lo + lo.hi), TF32
+// (FP32 rows rounded to TF32; a 128-byte slice row holds 32 of them)
+constexpr int OP_BF16 = 0, OP_X3 = 1, OP_TF32 = 2;
 constexpr int RING_BYTES = 192 * 1024;          // shared memory for the operand ring
 constexpr int STAGES = 8;                       // most stages any variant uses
 // TNV = support rows per tile (B rows = accumulator columns): 128 or 64.
@@ -46,12 +51,14 @@ constexpr int NH = NEPI / 4;                     // column parts of an accumulat
 constexpr int NTHREADS = 64 + 32 * NEPI;        // + one TMA warp and one MMA warp
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;   // 2 s per wait
 
-// Instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1),
-// A and B BF16 (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0),
-// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
-template <int N>
+// Instruction descriptor of tcgen05.mma kind::f16 / kind::tf32: D FP32
+// (bits 4-5 = 1), A and B BF16 (type 1) or TF32 (type 2) in bits 7-9 and
+// 10-12, both K-major (bits 15, 16 = 0), N >> 3 in bits 17-22, M >> 4 in
+// bits 24-28.
+template <int N, int OP>
 __host__ __device__ constexpr uint32_t idesc() {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+  constexpr uint32_t t = OP == OP_TF32 ? 2u : 1u;
+  return (1u << 4) | (t << 7) | (t << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 }
 
 constexpr int MS = 4;                           // metadata ring slots (items in flight)
@@ -159,13 +166,24 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accum) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
-      : "memory");
+// One MMA on a 32-byte K step of the 128-byte swizzled rows: K = 16 BF16
+// values (kind::f16) or K = 8 TF32 values (kind::tf32).
+template <int OP>
+__device__ __forceinline__ void mma_op(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accum) {
+  if constexpr (OP == OP_TF32) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+  }
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -339,10 +357,12 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 // copies into a 4-slot ring next to the operand ring; nothing on the
 // epilogue's path waits on a global load. The tile descriptors themselves are
 // fetched 32 items at a time, one per producer lane.
-template <int KIND, int MODE, bool X3, int TNV>
+template <int KIND, int MODE, int OP, int TNV>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_dist_tc(Dev s, int rows, const __grid_constant__ CUtensorMap tmA,
               const __grid_constant__ CUtensorMap tmB) {
+  constexpr bool X3 = OP == OP_X3;
+  constexpr int KSE = OP == OP_TF32 ? 32 : KS;   // operand elements per slice row
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   Shared& sh = *reinterpret_cast<Shared*>(smem + RING_BYTES);
@@ -350,7 +370,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   constexpr int SB = Ring<X3, TNV>::bytes;
   constexpr int BB = Ring<X3, TNV>::b_bytes;
   constexpr uint32_t TMEM_COLS = 2 * TNV;        // two accumulators (double buffering)
-  constexpr uint32_t IDESC = idesc<TNV>();
+  constexpr uint32_t IDESC = idesc<TNV, OP>();
   constexpr uint32_t META_BYTES = 3 * TNV * 4 + 2 * TM * 4;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -384,7 +404,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   const int R = (rows + TM - 1) / TM;
   const int total = (MODE == 0) ? R * (*s.ntiles) : *s.nwpairs;
-  const int nks = s.dp / KS;
+  const int nks = s.dp / KSE;
 
   if (warp == 0) {
     // ------------------------------------------------------- producer (one warp)
@@ -426,7 +446,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int st = it % NST;
           const uint32_t ph = (it / NST) & 1u;
           if (!mbar_wait(&sh.empty[st], ph ^ 1u)) { ok = false; break; }
-          const int x = sl * KS;
+          const int x = sl * KSE;
           uint8_t* a = smem + st * SB;
           mbar_expect_tx(&sh.full[st], SB);
           if constexpr (X3) {   // stage layout: A_hi | A_lo | B_hi | B_lo
@@ -471,16 +491,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if constexpr (X3) {
             const uint32_t alo = a0 + A_BYTES, bhi = a0 + 2 * A_BYTES, blo = bhi + BB;
 #pragma unroll
-            for (int k = 0; k < KS / 16; ++k) {
-              mma_bf16(d, sw128_desc(a0 + 32u * k), sw128_desc(bhi + 32u * k), IDESC, (sl | k) != 0 ? 1u : 0u);
-              mma_bf16(d, sw128_desc(a0 + 32u * k), sw128_desc(blo + 32u * k), IDESC, 1u);
-              mma_bf16(d, sw128_desc(alo + 32u * k), sw128_desc(bhi + 32u * k), IDESC, 1u);
+            for (int k = 0; k < 4; ++k) {
+              mma_op<OP>(d, sw128_desc(a0 + 32u * k), sw128_desc(bhi + 32u * k), IDESC, (sl | k) != 0 ? 1u : 0u);
+              mma_op<OP>(d, sw128_desc(a0 + 32u * k), sw128_desc(blo + 32u * k), IDESC, 1u);
+              mma_op<OP>(d, sw128_desc(alo + 32u * k), sw128_desc(bhi + 32u * k), IDESC, 1u);
             }
           } else {
             const uint32_t b0 = a0 + A_BYTES;
 #pragma unroll
-            for (int k = 0; k < KS / 16; ++k)
-              mma_bf16(d, sw128_desc(a0 + 32u * k), sw128_desc(b0 + 32u * k), IDESC, (sl | k) != 0 ? 1u : 0u);
+            for (int k = 0; k < 4; ++k)   // four 32-byte K steps per 128-byte slice row
+              mma_op<OP>(d, sw128_desc(a0 + 32u * k), sw128_desc(b0 + 32u * k), IDESC, (sl | k) != 0 ? 1u : 0u);
           }
           mma_commit(&sh.empty[st]);
         }
@@ -683,11 +703,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 }
 
-template <int KIND, int MODE, bool X3, int TNV>
+template <int KIND, int MODE, int OP, int TNV>
 cudaError_t launch_form(const Dev& s, const CUtensorMap& a, const CUtensorMap& b, int rows, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_dist_tc<KIND, MODE, X3, TNV>,
+    cudaError_t e = cudaFuncSetAttribute(k_dist_tc<KIND, MODE, OP, TNV>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
     attr = true;
@@ -696,7 +716,17 @@ cudaError_t launch_form(const Dev& s, const CUtensorMap& a, const CUtensorMap& b
   // have: small runs then leave SMs free for the kernels of other runs
   const int64_t most = MODE == 0 ? (int64_t)((rows + TM - 1) / TM) * s.max_tiles : (int64_t)s.max_pairs;
   const int grid = (int)(most < s.num_sms ? (most > 0 ? most : 1) : s.num_sms);
-  return launch_pdl(k_dist_tc<KIND, MODE, X3, TNV>, dim3(grid), dim3(NTHREADS), SMEM_BYTES, st, s, rows, a, b);
+  return launch_pdl(k_dist_tc<KIND, MODE, OP, TNV>, dim3(grid), dim3(NTHREADS), SMEM_BYTES, st, s, rows, a, b);
+}
+
+template <int MODE, int OP, int TNV>
+cudaError_t launch_kind(const Dev& s, const CUtensorMap& a, const CUtensorMap& b, int rows, cudaStream_t st) {
+  switch (s.kind) {
+    case K_GAUSS: return launch_form<K_GAUSS, MODE, OP, TNV>(s, a, b, rows, st);
+    case K_LAPLACE: return launch_form<K_LAPLACE, MODE, OP, TNV>(s, a, b, rows, st);
+    case K_LINEAR: return launch_form<K_LINEAR, MODE, OP, TNV>(s, a, b, rows, st);
+    default: return launch_form<K_POLY, MODE, OP, TNV>(s, a, b, rows, st);
+  }
 }
 
 // maps: [0] batch rows, 128-row boxes; support rows with [1] 128-row, [2] 64-row, [3] 256-row boxes
@@ -705,20 +735,10 @@ cudaError_t launch_mode(const Dev& s, const void* maps_in, int rows, cudaStream_
   const CUtensorMap* m = static_cast<const CUtensorMap*>(maps_in);
   const CUtensorMap& a = (MODE == 0) ? m[0] : m[1];
   const CUtensorMap& b = (TNV == 256) ? m[3] : (TNV == 128) ? m[1] : m[2];
-  const bool x3 = s.form == FORM_BF16X3;
-  switch (s.kind) {
-    case K_GAUSS:
-      return x3 ? launch_form<K_GAUSS, MODE, true, TNV>(s, a, b, rows, st)
-                : launch_form<K_GAUSS, MODE, false, TNV>(s, a, b, rows, st);
-    case K_LAPLACE:
-      return x3 ? launch_form<K_LAPLACE, MODE, true, TNV>(s, a, b, rows, st)
-                : launch_form<K_LAPLACE, MODE, false, TNV>(s, a, b, rows, st);
-    case K_LINEAR:
-      return x3 ? launch_form<K_LINEAR, MODE, true, TNV>(s, a, b, rows, st)
-                : launch_form<K_LINEAR, MODE, false, TNV>(s, a, b, rows, st);
-    default:
-      return x3 ? launch_form<K_POLY, MODE, true, TNV>(s, a, b, rows, st)
-                : launch_form<K_POLY, MODE, false, TNV>(s, a, b, rows, st);
+  switch (s.form) {
+    case FORM_BF16X3: return launch_kind<MODE, OP_X3, TNV>(s, a, b, rows, st);
+    case FORM_TF32: return launch_kind<MODE, OP_TF32, TNV>(s, a, b, rows, st);
+    default: return launch_kind<MODE, OP_BF16, TNV>(s, a, b, rows, st);
   }
 }
 
@@ -726,8 +746,9 @@ cudaError_t launch_mode(const Dev& s, const void* maps_in, int rows, cudaStream_
 
 bool tc_available() { return true; }
 
-// Tensor maps of the batch rows and the support store: 2-D BF16 tensors of ld
-// columns, boxes of 64 columns x 128 (64, 256) rows, 128-byte swizzle.
+// Tensor maps of the batch rows and the support store: 2-D tensors of ld
+// columns (BF16, or FP32 for the TF32 form), boxes of one 128-byte row of
+// columns (64 BF16 or 32 FP32) x 128 (64, 256) rows, 128-byte swizzle.
 cudaError_t tc_prepare(Dev& s, void* maps_out) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
@@ -740,15 +761,20 @@ cudaError_t tc_prepare(Dev& s, void* maps_out) {
   }
   CUtensorMap* maps = static_cast<CUtensorMap*>(maps_out);
   const int64_t srows = (int64_t)s.k * s.cap + 256;
+  const bool f32 = s.form == FORM_TF32;
+  void* xb = f32 ? (void*)s.xb32 : (void*)s.xbh;
+  void* yb = f32 ? (void*)s.y32 : (void*)s.ybh;
+  const int esz = f32 ? 4 : 2;
   struct { void* base; uint64_t rows; uint32_t box_rows; } ops[4] = {
-      {s.xbh, (uint64_t)s.bpad, 128u}, {s.ybh, (uint64_t)srows, 128u}, {s.ybh, (uint64_t)srows, 64u},
-      {s.ybh, (uint64_t)srows, 256u}};
+      {xb, (uint64_t)s.bpad, 128u}, {yb, (uint64_t)srows, 128u}, {yb, (uint64_t)srows, 64u},
+      {yb, (uint64_t)srows, 256u}};
   for (int i = 0; i < 4; ++i) {
     cuuint64_t dims[2] = {(cuuint64_t)s.ld, (cuuint64_t)ops[i].rows};
-    cuuint64_t strides[1] = {(cuuint64_t)s.ld * 2};
-    cuuint32_t box[2] = {(cuuint32_t)KS, ops[i].box_rows};
+    cuuint64_t strides[1] = {(cuuint64_t)s.ld * esz};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / esz), ops[i].box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = encode(&maps[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ops[i].base, dims, strides, box, estr,
+    CUresult r = encode(&maps[i], f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                        ops[i].base, dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;

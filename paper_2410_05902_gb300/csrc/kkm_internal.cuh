@@ -15,6 +15,7 @@
 //                  of a region are never used, so a tile (at most 256 rows)
 //                  that starts inside the window never reaches the next region.
 //   row data       FP32 form: FP32 rows, ld = round_up(d, 16), zero padded.
+//                  TF32 form: FP32 rows rounded to TF32, ld = dp = round_up(d, 32).
 //                  BF16 forms: BF16 rows [hi(0..dp) | lo(0..dp)], dp =
 //                  round_up(d, 64), zero padded; ld = 2*dp.
 //   yn             FP32 ||y||^2 of the values the Gram product actually uses
@@ -34,7 +35,10 @@
 
 namespace kkm {
 
-enum Form : int { FORM_FP32 = 0, FORM_BF16 = 1, FORM_BF16X3 = 2 };
+enum Form : int { FORM_FP32 = 0, FORM_BF16 = 1, FORM_BF16X3 = 2, FORM_TF32 = 3 };
+
+// forms whose row buffers hold FP32 values (xb32 / y32)
+__host__ __device__ inline bool f32_rows(int form) { return form == FORM_FP32 || form == FORM_TF32; }
 enum KernelKind : int { K_GAUSS = 0, K_LAPLACE = 1, K_LINEAR = 2, K_POLY = 3 };
 
 // device status bits (sticky until the context is destroyed)

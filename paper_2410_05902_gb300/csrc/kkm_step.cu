@@ -48,10 +48,19 @@ __device__ int block_exclusive_scan_1024(int v, int* total) {
 
 // Stores four consecutive source values at column c of a batch/support row in
 // the run's form and returns their contribution to ||row||^2 (the values the
-// Gram product will use: FP32, BF16 hi, or BF16 hi + lo). Per-element work
+// Gram product will use: FP32, TF32, BF16 hi, or BF16 hi + lo). Per-element work
 // stays in FP32: FP64 throughput on GB300 is a small fraction of FP32's.
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
 __device__ __forceinline__ float store4(const Dev& s, int64_t dst_row, bool to_support, int c, float4 v) {
-  if (s.form == FORM_FP32) {
+  if (s.form == FORM_TF32) {   // the values the TF32 product uses: rounded to nearest, ties away
+    v = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
+  }
+  if (f32_rows(s.form)) {
     float* dst = (to_support ? s.y32 : s.xb32) + dst_row * s.ld + c;
     *reinterpret_cast<float4*>(dst) = v;
     return fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, v.w * v.w)));
@@ -113,11 +122,12 @@ __device__ double warp_store_row(const Dev& s, const float* src, int64_t dst_row
 // loads first (up to eight 16-byte loads per lane in flight), then stores.
 __device__ void warp_copy_row(const Dev& s, bool src_support, int64_t src_row, int64_t dst_row) {
   const int lane = threadIdx.x & 31;
-  const int elem = (s.form == FORM_FP32) ? 4 : 2;
+  const bool f32 = f32_rows(s.form);
+  const int elem = f32 ? 4 : 2;
   const int n16 = s.ld * elem / 16;
-  const char* src = (const char*)(src_support ? (s.form == FORM_FP32 ? (void*)s.y32 : (void*)s.ybh)
-                                              : (s.form == FORM_FP32 ? (void*)s.xb32 : (void*)s.xbh));
-  char* dst = (char*)(s.form == FORM_FP32 ? (void*)s.y32 : (void*)s.ybh);
+  const char* src = (const char*)(src_support ? (f32 ? (void*)s.y32 : (void*)s.ybh)
+                                              : (f32 ? (void*)s.xb32 : (void*)s.xbh));
+  char* dst = (char*)(f32 ? (void*)s.y32 : (void*)s.ybh);
   const int4* sp = (const int4*)(src + src_row * (int64_t)s.ld * elem);
   int4* dp = (int4*)(dst + dst_row * (int64_t)s.ld * elem);
   for (int c0 = 0; c0 < n16; c0 += 32 * 8) {

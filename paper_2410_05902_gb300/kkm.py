@@ -22,8 +22,8 @@ KKM_OK, KKM_EINVAL, KKM_ENOMEM, KKM_ECUDA, KKM_ETIMEOUT, KKM_ESTATE, KKM_ENOTSUP
 KKM_GAUSSIAN, KKM_LAPLACIAN, KKM_LINEAR, KKM_POLY = range(4)
 KKM_LR_BETA, KKM_LR_CONST, KKM_LR_SKLEARN = 0, 1, 2
 LEARNING_RATES = {"beta": KKM_LR_BETA, "const": KKM_LR_CONST, "sklearn": KKM_LR_SKLEARN}
-KKM_PREC_FP32, KKM_PREC_BF16, KKM_PREC_BF16X3 = 0, 1, 2
-PRECISIONS = {"fp32": KKM_PREC_FP32, "bf16": KKM_PREC_BF16, "bf16x3": KKM_PREC_BF16X3}
+KKM_PREC_FP32, KKM_PREC_BF16, KKM_PREC_BF16X3, KKM_PREC_TF32 = 0, 1, 2, 3
+PRECISIONS = {"fp32": KKM_PREC_FP32, "bf16": KKM_PREC_BF16, "bf16x3": KKM_PREC_BF16X3, "tf32": KKM_PREC_TF32}
 KERNELS = {"gaussian": KKM_GAUSSIAN, "laplacian": KKM_LAPLACIAN, "linear": KKM_LINEAR,
            "poly": KKM_POLY}
 _STATUS = {0: "KKM_OK", 1: "KKM_EINVAL", 2: "KKM_ENOMEM", 3: "KKM_ECUDA", 4: "KKM_ETIMEOUT",

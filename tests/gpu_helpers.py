@@ -15,12 +15,15 @@ from paper_2410_05902_gb300 import inputs
 # to 2e-3. The objective is held to 1e-4 relative. Assignments must match
 # except on rows whose FP64 oracle gap d_(2) - d_(1) lies within the form's
 # absolute error bound, tol * max |d|.
-DIST_TOL = {"fp32": 1e-5, "bf16x3": 1e-5, "bf16": 2e-3}
+# TF32 operands carry 11 significant bits to BF16's 8, so its bound is BF16's / 8.
+DIST_TOL = {"fp32": 1e-5, "bf16x3": 1e-5, "bf16": 2e-3, "tf32": 2.5e-4}
 OBJ_TOL = 1e-4
 # BF16 operands carry 8 significant bits: its f_B error is of the order of its
 # distance error, so it is held to that here (the benchmark reports whether the
 # BF16 form reaches the 1e-4 objective bar on its workload).
-OBJ_TOL_FORM = {"fp32": OBJ_TOL, "bf16x3": OBJ_TOL, "bf16": 2e-3}
+OBJ_TOL_FORM = {"fp32": OBJ_TOL, "bf16x3": OBJ_TOL, "bf16": 2e-3, "tf32": 2.5e-4}
+# center norms after one teacher-forced step (the Gram error enters the recurrence's sums)
+CN_RTOL = {"fp32": 1e-6, "bf16x3": 1e-6, "bf16": 5e-3, "tf32": 1e-3}
 KIND = {"gaussian": oracle.GAUSSIAN, "laplacian": oracle.LAPLACIAN, "linear": oracle.LINEAR,
         "poly": oracle.POLY}
 

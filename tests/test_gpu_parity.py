@@ -16,7 +16,8 @@ import pytest
 
 import oracle
 from paper_2410_05902_gb300 import inputs
-from gpu_helpers import DIST_TOL, OBJ_TOL, OBJ_TOL_FORM, Pair, compare_states, dist_rel_err, near_tie_ok, torch_cuda
+from gpu_helpers import (CN_RTOL, DIST_TOL, OBJ_TOL, OBJ_TOL_FORM, Pair, compare_states, dist_rel_err,
+                         near_tie_ok, torch_cuda)
 
 pytestmark = pytest.mark.gpu
 
@@ -45,13 +46,12 @@ def teacher_forced(pair, batches, w_rtol=1e-12, cn_rtol=1e-6, check_assign=True)
     return worst
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16x3", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3", "bf16", "tf32"])
 def test_teacher_forced_small(precision):
     X = small_data()
     p = Pair(X, k=10, b=256, tau=200, precision=precision)
     batches = inputs.batch_stream(len(X), 256, 12, seed=21)
-    cn_rtol = 1e-6 if precision != "bf16" else 5e-3
-    teacher_forced(p, batches, cn_rtol=cn_rtol)
+    teacher_forced(p, batches, cn_rtol=CN_RTOL[precision])
     p.close()
 
 
@@ -251,14 +251,15 @@ def test_graph_replay_matches_eager(precision):
 
 
 @pytest.mark.parametrize("precision,d,tile", [("bf16x3", 200, 128), ("bf16", 200, 64), ("bf16x3", 784, 128),
-                                              ("bf16", 784, 256), ("bf16x3", 784, 256), ("bf16x3", 96, 64)])
+                                              ("bf16", 784, 256), ("bf16x3", 784, 256), ("bf16x3", 96, 64),
+                                              ("tf32", 200, 128), ("tf32", 784, 256), ("tf32", 40, 64)])
 def test_teacher_forced_wide_rows_tensor_path(precision, d, tile):
     """Wide rows give the tcgen05 passes several K-slices per tile (d=784: 13), with
     64-, 128- and 256-row support tiles in the distance pass."""
     X, _ = inputs.image_like(3000, seed=7, d=d, classes=8)
     p = Pair(X, k=8, b=512, tau=120, precision=precision, dist_tile=tile)
     batches = inputs.batch_stream(len(X), 512, 6, seed=23)
-    teacher_forced(p, batches, cn_rtol=1e-6 if precision == "bf16x3" else 5e-3)
+    teacher_forced(p, batches, cn_rtol=CN_RTOL[precision])
     p.close()
 
 
