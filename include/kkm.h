@@ -100,6 +100,19 @@ typedef enum kkm_precision {
   KKM_PREC_TF32 = 3
 } kkm_precision;
 
+/* How the centers are held.
+ *   KKM_ALGO_WINDOWS : as weighted support rows (the truncated centers of
+ *                      Eq. (1); with tau <= 0 every block is kept).
+ *   KKM_ALGO_TABLE   : Algorithm 1 (untruncated; tau must be <= 0) through the
+ *                      table <phi(x), C_j> for every x in X and every j, the
+ *                      O(n(b+k))-per-iteration scheme of Appendix A: each step
+ *                      is an n x b Gram pass against the center-sorted batch
+ *                      and a table update. Needs n*k FP32 of table; support
+ *                      rows are never stored, so kkm_get_state / set_state,
+ *                      kkm_assign of arbitrary rows and the objective adjoint
+ *                      return KKM_ENOTSUP (kkm_objective over X works). */
+typedef enum kkm_algo { KKM_ALGO_WINDOWS = 0, KKM_ALGO_TABLE = 1 } kkm_algo;
+
 typedef struct kkm_config {
   int32_t tau;       /* truncation parameter tau of Sec. 4.1; <= 0 runs Algorithm 1 untruncated */
   int32_t lr;        /* kkm_lr */
@@ -108,7 +121,7 @@ typedef struct kkm_config {
   int32_t max_iters; /* untruncated runs only: iterations the support store must hold (>= 1) */
   uint64_t seed;     /* SplitMix64 seed of the built-in batch sampler */
   int32_t dist_tile; /* tensor-core forms: support rows per distance-pass tile, 64, 128 or 256; 0 = 256 */
-  int32_t reserved;  /* must be 0 */
+  int32_t algo;      /* kkm_algo */
 } kkm_config;
 
 typedef struct kkm_ctx kkm_ctx;

@@ -50,6 +50,13 @@ struct kkm_ctx {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
   const void* gkey[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  // table form of Algorithm 1 (kkm_config.algo = KKM_ALGO_TABLE)
+  bool tab = false;
+  kkm::TabBuf tb{};
+  kkm::Dev g{};                              // Gram view: A = every row of X, B = the support buffer
+  alignas(64) unsigned char gmaps[512];      // its TMA descriptors
+  double* d_tabblk = nullptr;
+  int32_t tabblk_n = 0;
   // workspace of kkm_objective_fwd / _bwd (grows with m, freed with the context)
   double* gws = nullptr;
   size_t gws_len = 0;
@@ -200,20 +207,29 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
     return fail(nullptr, KKM_EINVAL, "eta must be in (0, 1]");
   if (cfg->dist_tile != 0 && cfg->dist_tile != 64 && cfg->dist_tile != 128 && cfg->dist_tile != 256)
     return fail(nullptr, KKM_EINVAL, "dist_tile must be 0, 64, 128 or 256");
-  if (cfg->reserved != 0) return fail(nullptr, KKM_EINVAL, "reserved must be 0");
+  if (cfg->algo != KKM_ALGO_WINDOWS && cfg->algo != KKM_ALGO_TABLE)
+    return fail(nullptr, KKM_EINVAL, "unknown algo");
+  const bool tab = cfg->algo == KKM_ALGO_TABLE;
+  if (tab && cfg->tau > 0)
+    return fail(nullptr, KKM_EINVAL, "the table form runs Algorithm 1: tau must be <= 0");
+  if (tab && (int64_t)n * k >= (int64_t(1) << 40)) return fail(nullptr, KKM_EINVAL, "n*k too large for the table");
   if (cfg->precision < KKM_PREC_FP32 || cfg->precision > KKM_PREC_TF32)
     return fail(nullptr, KKM_EINVAL, "unknown precision");
   if (cfg->tau > 1000000) return fail(nullptr, KKM_EINVAL, "tau must be <= 1e6");
-  if (cfg->tau <= 0 && cfg->max_iters < 1)
+  if (cfg->tau <= 0 && cfg->max_iters < 1 && !tab)
     return fail(nullptr, KKM_EINVAL, "an untruncated run needs max_iters >= 1");
   if (init_idx)
     for (int j = 0; j < k; ++j)
       if (init_idx[j] < 0 || init_idx[j] >= n)
         return fail(nullptr, KKM_EINVAL, "init_idx entry out of [0, n)");
 
-  const int64_t wmax = cfg->tau > 0 ? (int64_t)cfg->tau + b : 1 + (int64_t)cfg->max_iters * b;
-  const int64_t cap = (cfg->tau > 0 ? kkm::round_up(2LL * cfg->tau + 4LL * b + 8, 8)
-                                    : kkm::round_up(wmax, 8)) + kkm::REGION_PAD;
+  // table form: the support store is one buffer of the center-sorted batch
+  // (b rows in blocks of whole tiles, at most 256 rows each, plus slack),
+  // sized as k regions
+  const int64_t wmax = tab ? b : cfg->tau > 0 ? (int64_t)cfg->tau + b : 1 + (int64_t)cfg->max_iters * b;
+  const int64_t cap = tab ? kkm::round_up((b + 256LL * k + 512 + k - 1) / k, 8)
+                          : (cfg->tau > 0 ? kkm::round_up(2LL * cfg->tau + 4LL * b + 8, 8)
+                                          : kkm::round_up(wmax, 8)) + kkm::REGION_PAD;
   const int64_t srows = (int64_t)k * cap + 256;
   if (srows >= (int64_t(1) << 31)) return fail(nullptr, KKM_EINVAL, "support store too large (k*cap)");
 
@@ -239,7 +255,8 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
   s.n = n; s.d = d; s.k = k; s.b = b; s.ldx = ldx; s.X = X;
   s.tau = cfg->tau > 0 ? cfg->tau : 0;
   s.cap = (int32_t)cap;
-  s.nbcap = cfg->tau > 0 ? cfg->tau + 2 : cfg->max_iters + 2;
+  s.nbcap = tab ? 2 : cfg->tau > 0 ? cfg->tau + 2 : cfg->max_iters + 2;
+  c->tab = tab;
   s.form = cfg->precision;
   s.kind = kernel->kind; s.degree = kernel->degree; s.lr = cfg->lr;
   s.param = kernel->param; s.coef0 = kernel->coef0; s.eta = cfg->eta;
@@ -265,11 +282,12 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
     c->err = "the TF32 form needs a compute capability 10.3 device";
     return bail(KKM_ENOTSUP);
   }
-  s.tn = c->use_tc ? (cfg->dist_tile == 0 ? 256 : cfg->dist_tile) : 64;
+  s.tn = c->use_tc ? (cfg->dist_tile == 0 ? (tab ? 64 : 256) : cfg->dist_tile) : 64;
   s.pair_rows = c->use_tc ? 128 : 64;
   s.pair_cols = 64;
   const int64_t TR = s.pair_rows, TC = s.pair_cols;   // window-pass tile
-  s.max_tiles = (int32_t)((int64_t)k * ((wmax + s.tn - 1) / s.tn + 1));
+  s.max_tiles = tab ? (int32_t)(k + (b + s.tn - 1) / s.tn + 1)
+                    : (int32_t)((int64_t)k * ((wmax + s.tn - 1) / s.tn + 1));
   const int64_t smax = (int64_t)k * wmax;
   const int64_t p1 = ((smax + TR - 1) / TR + k) * ((wmax + b + TC - 1) / TC);
   const int64_t p2 = ((b + TR - 1) / TR + k) * ((b + TC - 1) / TC + k);
@@ -317,6 +335,27 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
   ALLOC(c->d_hbatch, b); ALLOC(c->d_hassign, b); ALLOC(c->d_hobj, 1);
   c->objpart_len = 1024;
   ALLOC(c->d_objpart, c->objpart_len);
+  if (tab) {
+    // the Gram view: A = every row of X in the operand form
+    const int64_t npad = kkm::round_up(n, 128);
+    kkm::Dev& g = c->g;
+    g = s;
+    g.xb32 = nullptr;
+    g.xbh = nullptr;
+    if (esz == 4) ALLOC(g.xb32, (size_t)npad * s.ld);
+    else ALLOC(g.xbh, (size_t)npad * s.ld);
+    ALLOC(g.xbn, npad);
+    ALLOC(g.xbi, npad);
+    g.bpad = (int32_t)npad;
+    ALLOC(g.part, (size_t)s.max_tiles * npad);
+    ALLOC(c->tb.T, (size_t)k * n);
+    ALLOC(c->tb.bs_off, k + 1);
+    c->tb.part = g.part;
+    c->tb.npad = npad;
+    c->tb.bs_rows = (int32_t)srows;
+    c->tabblk_n = (int32_t)std::min<int64_t>(4 * s.num_sms, (n + 255) / 256);
+    ALLOC(c->d_tabblk, c->tabblk_n);
+  }
 #undef ALLOC
 
   // initial centers: caller's indices, or k distinct ones from SplitMix64
@@ -337,9 +376,19 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
   const int64_t one = 1;
   e = cudaMemcpyAsync(c->d_init_idx, h_init.data(), k * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(s.iter, &one, sizeof(one), cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess) e = kkm::launch_init_centers(s, c->d_init_idx, c->stream);
-  if (e == cudaSuccess && c->use_tc) e = kkm::tc_prepare(s, c->tmaps);
-  if (e == cudaSuccess) e = kkm::launch_build_tiles(s, c->stream);
+  if (tab) {
+    // T[j][x] = K(x, x_init_j): the Gram pass against the k initial rows, then T = S
+    if (e == cudaSuccess) e = kkm::launch_tab_init(s, c->g, c->tb, c->d_init_idx, c->stream);
+    if (e == cudaSuccess && c->use_tc) e = kkm::tc_prepare(c->g, c->gmaps);
+    if (e == cudaSuccess)
+      e = c->use_tc ? kkm::launch_dist_tc(c->g, c->gmaps, (int)n, c->stream)
+                    : kkm::launch_dist_simt(c->g, (int)n, c->stream);
+    if (e == cudaSuccess) e = kkm::launch_tab_update(s, c->tb, true, c->stream);
+  } else {
+    if (e == cudaSuccess) e = kkm::launch_init_centers(s, c->d_init_idx, c->stream);
+    if (e == cudaSuccess && c->use_tc) e = kkm::tc_prepare(s, c->tmaps);
+    if (e == cudaSuccess) e = kkm::launch_build_tiles(s, c->stream);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
     c->err = std::string("initialisation: ") + cudaGetErrorString(e);
@@ -360,6 +409,25 @@ static kkm_status enqueue_step(kkm_ctx* c, cudaStream_t st, const int32_t* batch
                                const int32_t* forced_assign, int32_t* assign_out, float* dist_out,
                                double* batch_obj_out, bool timed) {
   const Dev& s = c->s;
+  if (c->tab) {
+    // table form (Appendix A): distances off the table, sort, lay out the batch,
+    // the n x b Gram pass, the norm recurrence, the table update
+    KKM_CU(kkm::launch_gather_batch(s, batch_idx, st), "batch gather");
+    KKM_CU(kkm::launch_tab_batch_dist(s, c->tb, s.b, forced_assign, assign_out, nullptr, dist_out, true, st),
+           "table distances");
+    KKM_CU(kkm::launch_tab_plan(s, c->tb, batch_obj_out, st), "sort/layout");
+    KKM_CU(kkm::launch_tab_fill(s, c->tb, st), "batch layout");
+    if (timed) KKM_CU(cudaEventRecord(c->ev[2 * c->ev_used], st), "timing event");
+    if (c->use_tc) KKM_CU(kkm::launch_dist_tc(c->g, c->gmaps, (int)s.n, st), "Gram pass (tcgen05)");
+    else KKM_CU(kkm::launch_dist_simt(c->g, (int)s.n, st), "Gram pass");
+    if (timed) {
+      KKM_CU(cudaEventRecord(c->ev[2 * c->ev_used + 1], st), "timing event");
+      ++c->ev_used;
+    }
+    KKM_CU(kkm::launch_tab_center(s, c->tb, st), "norm recurrence");
+    KKM_CU(kkm::launch_tab_update(s, c->tb, false, st), "table update");
+    return KKM_OK;
+  }
   // with batch_idx NULL the gather draws the indices itself (SplitMix64)
   KKM_CU(kkm::launch_gather_batch(s, batch_idx, st), "batch gather");
   if (timed) KKM_CU(cudaEventRecord(c->ev[2 * c->ev_used], st), "timing event");
@@ -382,7 +450,7 @@ KKM_API kkm_status kkm_step(kkm_ctx* c, const int32_t* batch_idx, const int32_t*
                             int32_t* assign_out, float* dist_out, double* batch_obj_out) {
   kkm_status st = check_usable(c);
   if (st != KKM_OK) return st;
-  if (c->s.tau == 0 && c->iteration > c->max_iters)
+  if (c->s.tau == 0 && !c->tab && c->iteration > c->max_iters)
     return fail(c, KKM_ESTATE, "untruncated run: max_iters iterations already done");
   const bool timed = c->timing && c->ev_used < (int64_t)c->ev.size() / 2;
   if (c->graph_on && !timed && c->eager_steps > 0) {
@@ -495,6 +563,7 @@ KKM_API kkm_status kkm_assign(kkm_ctx* c, const float* Q, int64_t m, int64_t ldq
                               float* mind_out, float* dist_out) {
   kkm_status st = check_usable(c);
   if (st != KKM_OK) return st;
+  if (c->tab) return fail(c, KKM_ENOTSUP, "the table form scores only the rows of X (kkm_objective)");
   if (m < 0 || (m > 0 && (!Q || ldq < c->s.d))) return fail(c, KKM_EINVAL, "bad query matrix");
   return assign_chunks(c, Q, m, ldq, assign_out, mind_out, dist_out, nullptr);
 }
@@ -503,6 +572,18 @@ KKM_API kkm_status kkm_objective(kkm_ctx* c, const float* Q, int64_t m, int64_t 
   kkm_status st = check_usable(c);
   if (st != KKM_OK) return st;
   if (!out) return fail(c, KKM_EINVAL, "out is NULL");
+  if (c->tab) {
+    if (Q) return fail(c, KKM_ENOTSUP, "the table form scores only the rows of X (Q = NULL)");
+    KKM_CU(kkm::launch_tab_objective(c->s, c->tb, c->g.xbn, c->d_tabblk, c->tabblk_n, c->stream), "objective");
+    st = sync_and_check(c);
+    if (st != KKM_OK) return st;
+    std::vector<double> h(c->tabblk_n);
+    KKM_CU(cudaMemcpy(h.data(), c->d_tabblk, h.size() * sizeof(double), cudaMemcpyDeviceToHost), "objective read");
+    double total = 0.0;
+    for (double v : h) total += v;
+    *out = total / (double)c->s.n;
+    return KKM_OK;
+  }
   if (!Q) { Q = c->s.X; m = c->s.n; ldq = c->s.ldx; }
   if (m < 1 || ldq < c->s.d) return fail(c, KKM_EINVAL, "bad query matrix");
   double total = 0.0;
@@ -520,6 +601,7 @@ kkm_status objective_call(kkm_ctx* c, const float* Q, int64_t m, int64_t ldq, co
                           double log_sigma, double* loss, float* delta, const double* grad_loss, float* grad_q,
                           int64_t ldg, double* grad_s) {
   const kkm::Dev& s = c->s;
+  if (c->tab) return fail(c, KKM_ENOTSUP, "the table form keeps no support rows");
   if (s.kind != kkm::K_GAUSS && s.kind != kkm::K_LAPLACE)
     return fail(c, KKM_ENOTSUP, "the bandwidth objective needs the Gaussian or Laplacian kernel");
   if (s.d > 1024) return fail(c, KKM_ENOTSUP, "the bandwidth objective supports d <= 1024");
@@ -572,9 +654,14 @@ KKM_API kkm_status kkm_step_eval(kkm_ctx* c, const int32_t* batch_idx, double* o
   // f_{B_i}(C_{i+1}): the distance pass and argmin again on the same batch
   // rows, against the windows, weights and norms the step just wrote
   const Dev& s = c->s;
-  if (c->use_tc) KKM_CU(kkm::launch_dist_tc(s, c->tmaps, s.b, c->stream), "distance kernel (tcgen05)");
-  else KKM_CU(kkm::launch_dist_simt(s, s.b, c->stream), "distance kernel");
-  KKM_CU(kkm::launch_argmin(s, s.b, nullptr, nullptr, s.mind, nullptr, false, c->stream), "argmin");
+  if (c->tab) {
+    KKM_CU(kkm::launch_tab_batch_dist(s, c->tb, s.b, nullptr, nullptr, s.mind, nullptr, false, c->stream),
+           "table distances");
+  } else {
+    if (c->use_tc) KKM_CU(kkm::launch_dist_tc(s, c->tmaps, s.b, c->stream), "distance kernel (tcgen05)");
+    else KKM_CU(kkm::launch_dist_simt(s, s.b, c->stream), "distance kernel");
+    KKM_CU(kkm::launch_argmin(s, s.b, nullptr, nullptr, s.mind, nullptr, false, c->stream), "argmin");
+  }
   KKM_CU(kkm::launch_mind_sum(s, s.b, s.inv_b, obj_after_dev, c->stream), "objective sum");
   c->launches += 3;
   return KKM_OK;
@@ -639,6 +726,7 @@ KKM_API kkm_status kkm_sync(kkm_ctx* c) {
 KKM_API kkm_status kkm_get_state_sizes(kkm_ctx* c, int64_t* total_rows, int64_t* total_blocks) {
   kkm_status st = check_usable(c);
   if (st != KKM_OK) return st;
+  if (c->tab) return fail(c, KKM_ENOTSUP, "the table form keeps no support rows");
   st = sync_and_check(c);
   if (st != KKM_OK) return st;
   const int k = c->s.k;
@@ -660,6 +748,7 @@ KKM_API kkm_status kkm_get_state(kkm_ctx* c, int64_t* iteration, int32_t* rows_p
                                  double* cnorm) {
   kkm_status st = check_usable(c);
   if (st != KKM_OK) return st;
+  if (c->tab) return fail(c, KKM_ENOTSUP, "the table form keeps no support rows");
   st = sync_and_check(c);
   if (st != KKM_OK) return st;
   const Dev& s = c->s;
@@ -721,6 +810,7 @@ KKM_API kkm_status kkm_set_state(kkm_ctx* c, int64_t iteration, const int32_t* r
                                  const double* cnorm) {
   kkm_status st = check_usable(c);
   if (st != KKM_OK) return st;
+  if (c->tab) return fail(c, KKM_ENOTSUP, "the table form keeps no support rows");
   const Dev& s = c->s;
   const int k = s.k;
   if (!rows_per_center || !row_idx || !row_w || !blocks_per_center || !block_iter || !block_count ||
@@ -964,7 +1054,7 @@ KKM_API kkm_status kkm_group_step(kkm_group* g) {
   if (cudaSetDevice(g->device) != cudaSuccess) return gfail(g, KKM_ECUDA, "cudaSetDevice failed");
   for (kkm_ctx* c : g->runs) {
     if (c->poisoned) return gfail(g, KKM_ESTATE, "a run is poisoned");
-    if (c->s.tau == 0 && c->iteration > c->max_iters)
+    if (c->s.tau == 0 && !c->tab && c->iteration > c->max_iters)
       return gfail(g, KKM_ESTATE, "an untruncated run has done max_iters iterations");
   }
   if (g->steps == 0) {

@@ -219,6 +219,15 @@ __host__ __device__ inline double kernel_self(int kind, double xn, double coef0,
   return r;
 }
 
+// Table form of Algorithm 1 (kkm_config.algo = KKM_ALGO_TABLE).
+struct TabBuf {
+  float* T;            // [k][n] <phi(x), C_j>, center-major
+  int32_t* bs_off;     // [k+1] start of each center's rows in the support buffer (whole tiles)
+  const float* part;   // the Gram view's per-tile partials, [tiles][npad]
+  int64_t npad;        // row stride of part (round_up(n, 128))
+  int32_t bs_rows;     // rows of the support buffer (k * cap + 256)
+};
+
 // ------------------------------------------------------------ launchers
 // All return cudaGetLastError() of their launches.
 cudaError_t launch_sample(const Dev& s, cudaStream_t st);
@@ -246,6 +255,15 @@ cudaError_t launch_objective(const Dev& s, double log_sigma, const float* Q, int
 cudaError_t launch_build_tiles(const Dev& s, cudaStream_t st);
 cudaError_t launch_init_centers(const Dev& s, const int32_t* init_idx, cudaStream_t st);
 cudaError_t launch_load_rows(const Dev& s, int32_t rows_total, cudaStream_t st);
+cudaError_t launch_tab_batch_dist(const Dev& s, const TabBuf& q, int rows, const int32_t* forced,
+                                  int32_t* assign_out, float* mind_out, float* dist_out, bool update, cudaStream_t st);
+cudaError_t launch_tab_plan(const Dev& s, const TabBuf& q, double* obj_out, cudaStream_t st);
+cudaError_t launch_tab_fill(const Dev& s, const TabBuf& q, cudaStream_t st);
+cudaError_t launch_tab_center(const Dev& s, const TabBuf& q, cudaStream_t st);
+cudaError_t launch_tab_update(const Dev& s, const TabBuf& q, bool init, cudaStream_t st);
+cudaError_t launch_tab_init(const Dev& s, const Dev& g, const TabBuf& q, const int32_t* init_idx, cudaStream_t st);
+cudaError_t launch_tab_objective(const Dev& s, const TabBuf& q, const float* xn, double* blk, int nblk,
+                                 cudaStream_t st);
 cudaError_t launch_mind_sum(const Dev& s, int rows, double scale, double* out, cudaStream_t st);  // scale * sum of mind
 
 // tensor-core distance pass (BF16 forms); returns cudaErrorNotSupported when unavailable

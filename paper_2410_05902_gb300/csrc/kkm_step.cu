@@ -760,6 +760,291 @@ __global__ void __launch_bounds__(1024) k_mind_sum(Dev s, int rows, double scale
   if (threadIdx.x == 0) *out = red[0] * scale;
 }
 
+// ------------------------------------------------------------------------
+// Table form of Algorithm 1 (Appendix A, "Runtime analysis of Algorithm 1"):
+// the run keeps T[j][x] = <phi(x), C_j> for every x in X and ||C_j||^2. An
+// iteration reads the batch distances off the table, sorts the batch by
+// center, lays the batch rows out center by center in the support buffer
+// (blocks of whole tiles, weight 1/b_j), runs the n x b Gram pass against them
+// (S[j][x] = <phi(x), cm(B_j)>), and updates
+//   T[j][x] <- (1 - alpha_j) T[j][x] + alpha_j S[j][x],
+//   ||C'||^2 = (1-a)^2 ||C||^2 + 2a(1-a) <C, cm(B_j)> + a^2 ||cm(B_j)||^2,
+// with <C, cm(B_j)> = (1/b_j) sum_{y in B_j} T[j][y] (old table) and
+// ||cm(B_j)||^2 = (1/b_j) sum_{y in B_j} S[j][y].
+
+// Batch distances from the table: a warp per batch row, lanes over centers.
+// Same outputs and tie rule as k_argmin.
+__global__ void k_tab_batch_dist(Dev s, TabBuf q, int rows, const int32_t* __restrict__ forced,
+                                 int32_t* __restrict__ assign_out, float* __restrict__ mind_out,
+                                 float* __restrict__ dist_out, int update) {
+  KKM_GRID_DEP_WAIT();
+  const int x = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (x >= rows) return;
+  const int64_t i = s.xbi[x];
+  const float kxx = (float)kernel_self(s.kind, (double)s.xbn[x], s.coef0, s.degree);
+  const int fa = forced ? forced[x] : -1;
+  float best = 3.0e38f, best_inner = 0.0f, f_inner = 0.0f;
+  int bj = 0x7fffffff;
+  for (int j = lane; j < s.k; j += 32) {
+    const float inner = q.T[(int64_t)j * s.n + i];
+    const float dist = fmaf(-2.0f, inner, kxx + s.cnorm32[j]);
+    if (dist_out) dist_out[(int64_t)x * s.k + j] = dist;
+    if (dist < best) { best = dist; bj = j; best_inner = inner; }
+    if (j == fa) f_inner = inner;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+    const float oi = __shfl_xor_sync(0xffffffffu, best_inner, o);
+    if (ob < best || (ob == best && oj < bj)) { best = ob; bj = oj; best_inner = oi; }
+    f_inner += __shfl_xor_sync(0xffffffffu, f_inner, o);
+  }
+  if (lane != 0) return;
+  int a = bj;
+  float a_inner = best_inner;
+  if (forced) {
+    if (fa < 0 || fa >= s.k) atomicOr(s.status, ST_BAD_ASSIGN);
+    else { a = fa; a_inner = f_inner; }
+  }
+  if (assign_out) assign_out[x] = bj;
+  if (mind_out) mind_out[x] = best;
+  if (update) {
+    s.assign[x] = a;
+    s.mind[x] = best;
+    s.inner_a[x] = a_inner;
+  }
+}
+
+// Single CTA: stable counting sort of the batch by center, <C_j, cm(B_j)>,
+// f_B, the support-buffer layout (center j at bs_off[j], blocks of whole
+// tiles) and its tile list, weights of every buffer row cleared (k_tab_fill
+// sets the used ones).
+__global__ void __launch_bounds__(1024) k_tab_plan(Dev s, TabBuf q, double* obj_out) {
+  KKM_GRID_DEP_WAIT();
+  __shared__ int cnt[1024], coff[1024];
+  __shared__ int16_t sassign[8192];
+  __shared__ float wpartial[32];
+  const int k = s.k, b = s.b, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid < k) cnt[tid] = 0;
+  float macc = 0.0f;
+  for (int x = tid; x < b; x += 1024) {
+    macc += s.mind[x];
+    sassign[x] = (int16_t)s.assign[x];
+  }
+  __syncthreads();
+  for (int x = tid; x < b; x += 1024) atomicAdd(&cnt[sassign[x]], 1);
+  __syncthreads();
+  const int my = tid < k ? cnt[tid] : 0;
+  int total = 0;
+  const int off = block_exclusive_scan_1024(my, &total);
+  if (tid < k) { coff[tid] = off; s.coff[tid] = off; s.counts[tid] = my; }
+  if (tid == 0) s.coff[k] = total;
+  __syncthreads();
+  // stable order: row x goes to coff[a] + (rows before x with the same center);
+  // one warp per center walks the batch in order (b is small)
+  for (int j = warp; j < k; j += 32) {
+    int base = coff[j];
+    for (int x0 = 0; x0 < b; x0 += 32) {
+      const int x = x0 + lane;
+      const bool mine = x < b && sassign[x] == j;
+      const unsigned m = __ballot_sync(0xffffffffu, mine);
+      if (mine) s.perm[base + __popc(m & ((1u << lane) - 1u))] = x;
+      base += __popc(m);
+    }
+    // <C_j, cm(B_j)>: FP32 lane sums of the assigned rows' table entries, FP64 combine
+    float part = 0.0f;
+    for (int r = coff[j] + lane; r < coff[j] + cnt[j]; r += 32) part += s.inner_a[s.perm[r]];
+    const double sum = warp_sum((double)part);
+    if (lane == 0) s.cmc[j] = cnt[j] > 0 ? sum / (double)cnt[j] : 0.0;
+  }
+  // f_B(C_i)
+  float v = macc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) wpartial[warp] = v;
+  // support-buffer layout and tiles: every center's block is padded to whole
+  // tiles, so a tile never reaches the next center's rows (the padding rows
+  // carry weight 0)
+  const int rowsT = tid < k ? (my + s.tn - 1) / s.tn * s.tn : 0;
+  int used = 0;
+  const int bo = block_exclusive_scan_1024(rowsT, &used);
+  const int nt = tid < k ? (my + s.tn - 1) / s.tn : 0;
+  int ntot = 0;
+  const int tf = block_exclusive_scan_1024(nt, &ntot);
+  if (tid < k) {
+    q.bs_off[tid] = bo;
+    s.tile_first[tid] = tf;
+    s.tile_cnt[tid] = nt;
+    for (int t = 0; t < nt; ++t)
+      s.tiles[tf + t] = Tile{tid, (int32_t)((int64_t)bo + t * s.tn), min(s.tn, my - t * s.tn), 0};
+  }
+  if (tid == 0) {
+    q.bs_off[k] = used;
+    *s.ntiles = ntot;
+  }
+  for (int r = tid; r < q.bs_rows; r += 1024) {
+    s.w32[r] = 0.0f;
+    s.w64[r] = 0.0;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const double t = warp_sum((double)wpartial[lane]);
+    if (lane == 0) {
+      const double f = t * s.inv_b;
+      *s.obj = f;
+      if (obj_out) *obj_out = f;
+      s.stats[0] += 1;
+      *s.iter += 1;
+    }
+  }
+}
+
+// The batch rows into the support buffer, center by center (a warp per row),
+// with weight 1/b_j.
+__global__ void k_tab_fill(Dev s, TabBuf q) {
+  KKM_GRID_DEP_WAIT();
+  const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (p >= s.b) return;
+  const int x = s.perm[p];
+  const int j = s.assign[x];
+  const int dst = q.bs_off[j] + (p - s.coff[j]);
+  warp_copy_row(s, false, x, dst);
+  if ((threadIdx.x & 31) == 0) {
+    const double w = 1.0 / (double)s.counts[j];
+    s.yn[dst] = s.xbn[x];
+    s.yi[dst] = s.xbi[x];
+    s.w64[dst] = w;
+    s.w32[dst] = (float)w;
+  }
+}
+
+// Per center with points: ||cm(B_j)||^2 from S at the batch rows, the rate,
+// and the FP64 norm recurrence (block of 256 per center).
+__global__ void __launch_bounds__(256) k_tab_center(Dev s, TabBuf q) {
+  KKM_GRID_DEP_WAIT();
+  __shared__ double red[8];
+  const int j = blockIdx.x, tid = threadIdx.x;
+  const int n = s.counts[j];
+  if (n == 0) {
+    if (tid == 0) s.alpha[j] = 0.0;
+    return;
+  }
+  const int t0 = s.tile_first[j], nt = s.tile_cnt[j];
+  float acc = 0.0f;
+  for (int p = s.coff[j] + tid; p < s.coff[j] + n; p += 256) {
+    const int64_t i = s.xbi[s.perm[p]];
+    float sv = 0.0f;
+    for (int t = 0; t < nt; ++t) sv += q.part[(int64_t)(t0 + t) * q.npad + i];
+    acc += sv;
+  }
+  const double w = warp_sum((double)acc);
+  if ((tid & 31) == 0) red[tid >> 5] = w;
+  __syncthreads();
+  if (tid == 0) {
+    double m2 = 0.0;
+    for (int v = 0; v < 8; ++v) m2 += red[v];
+    const double dn = (double)n;
+    m2 /= dn;
+    const double N = s.ncum[j] + dn;
+    s.ncum[j] = N;
+    double a;
+    if (s.lr == 0) a = sqrt(dn * s.inv_b);
+    else if (s.lr == 2) a = dn / N;
+    else a = s.eta;
+    const double keep = 1.0 - a;
+    const double cn = keep * keep * s.cnorm[j] + 2.0 * a * keep * s.cmc[j] + a * a * m2;
+    s.alpha[j] = a;
+    s.cnorm[j] = cn;
+    s.cnorm32[j] = (float)cn;
+  }
+}
+
+// T[j][x] <- (1 - alpha_j) T[j][x] + alpha_j S[j][x] for the centers with
+// points (grid: x in blocks of 1024, y = center). init: T = S for every center.
+__global__ void __launch_bounds__(256) k_tab_update(Dev s, TabBuf q, int init) {
+  KKM_GRID_DEP_WAIT();
+  const int j = blockIdx.y;
+  if (!init && s.counts[j] == 0) return;
+  const double a = init ? 1.0 : s.alpha[j];
+  const float af = (float)a, kf = (float)(1.0 - a);
+  const int t0 = s.tile_first[j], nt = s.tile_cnt[j];
+  float* T = q.T + (int64_t)j * s.n;
+#pragma unroll 4
+  for (int64_t x = (int64_t)blockIdx.x * 1024 + threadIdx.x; x < min((int64_t)(blockIdx.x + 1) * 1024, s.n);
+       x += 256) {
+    float sv = 0.0f;
+    for (int t = 0; t < nt; ++t) sv += q.part[(int64_t)(t0 + t) * q.npad + x];
+    T[x] = init ? sv : fmaf(kf, T[x], af * sv);
+  }
+}
+
+// The initial centers C_1^j = phi(x_init_j) as the support buffer (row j*tn,
+// weight 1, one tile each), and ||C_1^j||^2 = K(x, x).
+__global__ void k_tab_init_rows(Dev s, TabBuf q, const int32_t* __restrict__ init_idx) {
+  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (j >= s.k) return;
+  const int lane = threadIdx.x & 31;
+  int64_t i = init_idx[j];
+  if (i < 0 || i >= s.n) {
+    if (lane == 0) atomicOr(s.status, ST_BAD_BATCH_INDEX);
+    i = 0;
+  }
+  const int64_t row = (int64_t)j * s.tn;
+  const float* src = s.X + i * s.ldx;
+  const double nrm = warp_store_row(s, src, row, true);
+  double exact = 0.0;
+  for (int c = lane; c < s.d; c += 32) exact += (double)src[c] * (double)src[c];
+  exact = warp_sum(exact);
+  if (lane == 0) {
+    s.yn[row] = (float)nrm;
+    s.yi[row] = (int32_t)i;
+    s.w64[row] = 1.0;
+    s.w32[row] = 1.0f;
+    s.tiles[j] = Tile{j, (int32_t)row, 1, 0};
+    s.tile_first[j] = j;
+    s.tile_cnt[j] = 1;
+    s.cnorm[j] = kernel_self(s.kind, exact, s.coef0, s.degree);
+    s.cnorm32[j] = (float)s.cnorm[j];
+    if (j == 0) *s.ntiles = s.k;
+  }
+}
+
+// Every row of X into the run's operand form (the Gram view's A rows), with
+// its norm and its own index (a warp per row).
+__global__ void k_tab_convert(Dev g) {
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (r >= g.n) return;
+  const double nrm = warp_store_row(g, g.X + r * g.ldx, r, false);
+  if ((threadIdx.x & 31) == 0) {
+    g.xbn[r] = (float)nrm;
+    g.xbi[r] = (int32_t)r;
+  }
+}
+
+// f_X = (1/n) sum_x min_j Delta(x, C_j) from the table: FP32 per row, FP64 block sums.
+__global__ void __launch_bounds__(256) k_tab_objective(Dev s, TabBuf q, const float* __restrict__ xn,
+                                                       double* __restrict__ blk) {
+  __shared__ double red[8];
+  double acc = 0.0;
+  for (int64_t x = (int64_t)blockIdx.x * 256 + threadIdx.x; x < s.n; x += (int64_t)gridDim.x * 256) {
+    const float kxx = (float)kernel_self(s.kind, (double)xn[x], s.coef0, s.degree);
+    float best = 3.0e38f;
+    for (int j = 0; j < s.k; ++j)
+      best = fminf(best, fmaf(-2.0f, q.T[(int64_t)j * s.n + x], kxx + s.cnorm32[j]));
+    acc += (double)best;
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int v = 0; v < 8; ++v) t += red[v];
+    blk[blockIdx.x] = t;
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
@@ -837,6 +1122,57 @@ cudaError_t launch_load_rows(const Dev& s, int32_t, cudaStream_t st) {
 cudaError_t launch_mind_sum(const Dev& s, int rows, double scale, double* out, cudaStream_t st) {
   cudaError_t e = launch_pdl(k_mind_sum, dim3(1), dim3(1024), 0, st, s, rows, scale, out);
   if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+
+// ------------------------------------------------------------- table form
+cudaError_t launch_tab_batch_dist(const Dev& s, const TabBuf& q, int rows, const int32_t* forced,
+                                  int32_t* assign_out, float* mind_out, float* dist_out, bool update,
+                                  cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+  cudaError_t e = launch_pdl(k_tab_batch_dist, dim3((rows * 32 + 255) / 256), dim3(256), 0, st, s, q, rows, forced,
+                             assign_out, mind_out, dist_out, update ? 1 : 0);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tab_plan(const Dev& s, const TabBuf& q, double* obj_out, cudaStream_t st) {
+  cudaError_t e = launch_pdl(k_tab_plan, dim3(1), dim3(1024), 0, st, s, q, obj_out);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tab_fill(const Dev& s, const TabBuf& q, cudaStream_t st) {
+  cudaError_t e = launch_pdl(k_tab_fill, dim3((s.b * 32 + 255) / 256), dim3(256), 0, st, s, q);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tab_center(const Dev& s, const TabBuf& q, cudaStream_t st) {
+  cudaError_t e = launch_pdl(k_tab_center, dim3(s.k), dim3(256), 0, st, s, q);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tab_update(const Dev& s, const TabBuf& q, bool init, cudaStream_t st) {
+  const dim3 grid((unsigned)((s.n + 1023) / 1024), (unsigned)s.k);
+  cudaError_t e = launch_pdl(k_tab_update, grid, dim3(256), 0, st, s, q, init ? 1 : 0);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tab_init(const Dev& s, const Dev& g, const TabBuf& q, const int32_t* init_idx, cudaStream_t st) {
+  k_tab_convert<<<(unsigned)((g.n * 32 + 255) / 256), 256, 0, st>>>(g);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_tab_init_rows<<<(s.k * 32 + 255) / 256, 256, 0, st>>>(s, q, init_idx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tab_objective(const Dev& s, const TabBuf& q, const float* xn, double* blk, int nblk,
+                                 cudaStream_t st) {
+  k_tab_objective<<<nblk, 256, 0, st>>>(s, q, xn, blk);
   return cudaGetLastError();
 }
 

@@ -22,6 +22,8 @@ KKM_OK, KKM_EINVAL, KKM_ENOMEM, KKM_ECUDA, KKM_ETIMEOUT, KKM_ESTATE, KKM_ENOTSUP
 KKM_GAUSSIAN, KKM_LAPLACIAN, KKM_LINEAR, KKM_POLY = range(4)
 KKM_LR_BETA, KKM_LR_CONST, KKM_LR_SKLEARN = 0, 1, 2
 LEARNING_RATES = {"beta": KKM_LR_BETA, "const": KKM_LR_CONST, "sklearn": KKM_LR_SKLEARN}
+KKM_ALGO_WINDOWS, KKM_ALGO_TABLE = 0, 1
+ALGOS = {"windows": KKM_ALGO_WINDOWS, "table": KKM_ALGO_TABLE}
 KKM_PREC_FP32, KKM_PREC_BF16, KKM_PREC_BF16X3, KKM_PREC_TF32 = 0, 1, 2, 3
 PRECISIONS = {"fp32": KKM_PREC_FP32, "bf16": KKM_PREC_BF16, "bf16x3": KKM_PREC_BF16X3, "tf32": KKM_PREC_TF32}
 KERNELS = {"gaussian": KKM_GAUSSIAN, "laplacian": KKM_LAPLACIAN, "linear": KKM_LINEAR,
@@ -36,7 +38,7 @@ class kkm_kernel(ctypes.Structure):
 
 class kkm_config(ctypes.Structure):
     _fields_ = [("tau", c_int32), ("lr", c_int32), ("eta", c_double), ("precision", c_int32),
-                ("max_iters", c_int32), ("seed", c_uint64), ("dist_tile", c_int32), ("reserved", c_int32)]
+                ("max_iters", c_int32), ("seed", c_uint64), ("dist_tile", c_int32), ("algo", c_int32)]
 
 
 class KKMError(RuntimeError):
@@ -279,7 +281,7 @@ class KKM:
     def __init__(self, X, k: int, b: int, kernel: str = "gaussian", param: float = 1.0,
                  coef0: float = 0.0, degree: int = 2, tau: int = 200, lr: str = "beta",
                  eta: float = 0.0, precision: str = "fp32", seed: int = 0, init_idx=None,
-                 max_iters: int = 0, stream=None, dist_tile: int = 0):
+                 max_iters: int = 0, stream=None, dist_tile: int = 0, algo: str = "windows"):
         import torch
         if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float32 and X.dim() == 2):
             raise TypeError("X must be a 2-D float32 CUDA tensor")
@@ -292,7 +294,8 @@ class KKM:
         self.stream = stream if stream is not None else torch.cuda.current_stream(X.device)
         kern = kkm_kernel(KERNELS[kernel], float(param), float(coef0), int(degree))
         cfg = kkm_config(int(tau), LEARNING_RATES[lr], float(eta),
-                         PRECISIONS[precision], int(max_iters), int(seed) & ((1 << 64) - 1), int(dist_tile), 0)
+                         PRECISIONS[precision], int(max_iters), int(seed) & ((1 << 64) - 1), int(dist_tile),
+                         ALGOS[algo])
         if isinstance(init_idx, str):
             if init_idx != "kmeans++":
                 raise ValueError("init_idx: indices, None, or 'kmeans++'")

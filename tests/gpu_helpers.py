@@ -56,7 +56,8 @@ class Pair:
     """An oracle run and a GPU run on the same data, kernel and initial centers."""
 
     def __init__(self, X, k, b, kernel="gaussian", param=None, tau=200, precision="fp32",
-                 init=None, lr="beta", eta=None, max_iters=0, coef0=0.0, degree=2, seed=0, dist_tile=0):
+                 init=None, lr="beta", eta=None, max_iters=0, coef0=0.0, degree=2, seed=0, dist_tile=0,
+                 algo="windows"):
         torch = torch_cuda()
         from paper_2410_05902_gb300.kkm import KKM
         self.torch = torch
@@ -74,7 +75,7 @@ class Pair:
         self.Xd = torch.from_numpy(self.X).cuda()
         self.gpu = KKM(self.Xd, k, b, kernel=kernel, param=self.param, coef0=coef0, degree=degree,
                        tau=tau, lr=lr, eta=eta or 0.0, precision=precision, seed=seed,
-                       init_idx=self.init, max_iters=max_iters, dist_tile=dist_tile)
+                       init_idx=self.init, max_iters=max_iters, dist_tile=dist_tile, algo=algo)
         self.dist = torch.empty((b, k), dtype=torch.float32, device="cuda")
         self.assign = torch.empty(b, dtype=torch.int32, device="cuda")
         self.obj = torch.empty(1, dtype=torch.float64, device="cuda")

@@ -78,7 +78,8 @@ def _init(lib, **over):
     (dict(cfg=kkm.kkm_config(50, 0, 0.0, 9, 0, 0)), "precision"),
     (dict(cfg=kkm.kkm_config(0, 0, 0.0, 0, 0, 0)), "max_iters"),
     (dict(cfg=kkm.kkm_config(50, 0, 0.0, 0, 0, 0, 96, 0)), "dist_tile"),
-    (dict(cfg=kkm.kkm_config(50, 0, 0.0, 0, 0, 0, 0, 1)), "reserved"),
+    (dict(cfg=kkm.kkm_config(50, 0, 0.0, 0, 0, 0, 0, 7)), "algo"),
+    (dict(cfg=kkm.kkm_config(50, 0, 0.0, 0, 0, 0, 0, 1)), "tau"),
 ])
 def test_init_rejects_invalid_arguments_on_host(lib, over, needle):
     st, ctx = _init(lib, **over)
