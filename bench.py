@@ -42,11 +42,14 @@ OBJ_BAR = 1e-4          # objective relative error a form must meet to count (th
 
 
 KERNEL = "gaussian"
+ALGO = "windows"
 
 
 def workload_desc(w) -> str:
     kern = ("Gaussian kernel kappa=2*sigma_median^2" if KERNEL == "gaussian"
             else "Laplacian kernel exp(-||x-y||/sigma_median)")
+    if ALGO == "table":
+        kern += ", untruncated Algorithm 1 through the n x k table (Appendix A)"
     if w.kind == "image":
         return (f"MNIST-shaped synthetic mixture n={w.n} d={w.d} (~80% zeros, Beta(2,2) values, 10 latent "
                 f"classes), k={w.k}, b={w.b}, tau={w.tau}, {kern}, beta rate")
@@ -173,10 +176,10 @@ def oracle_leg(X, kappa, init, forms, Xd, budget_s: float, prep: int = 4):
     from paper_2410_05902_gb300.kkm import KKM
     w = WORKLOAD
     X64 = X.astype(np.float64)
-    ora = oracle.MiniBatchKernelKMeans(X64, w.k, oracle_kernel(kappa), w.b, init, tau=w.tau)
+    ora = oracle.MiniBatchKernelKMeans(X64, w.k, oracle_kernel(kappa), w.b, init,
+                                       tau=None if ALGO == "table" else w.tau)
     batches = inputs.batch_stream(w.n, w.b, 400, seed=77)
-    for i in range(prep):
-        ora.step(batches[i])
+    recs = [ora.step(batches[i]) for i in range(prep)]
     state = ora.state()
     S_check = int(state["rows_per_center"].sum())
     t0 = time.perf_counter()
@@ -186,8 +189,15 @@ def oracle_leg(X, kappa, init, forms, Xd, budget_s: float, prep: int = 4):
     bi = torch.from_numpy(batches[prep].astype(np.int32)).to(Xd.device)
     fa = torch.from_numpy(rec.assign.astype(np.int32)).to(Xd.device)
     for form in forms:
-        run = KKM(Xd, w.k, w.b, kernel=KERNEL, param=kappa, tau=w.tau, precision=form, init_idx=init)
-        run.set_state(state)
+        run = KKM(Xd, w.k, w.b, kernel=KERNEL, param=kappa, tau=0 if ALGO == "table" else w.tau,
+                  precision=form, init_idx=init, algo=ALGO)
+        if ALGO == "table":
+            # no checkpoint of the table: replay the oracle's forced trajectory instead
+            for r in recs:
+                run.step(torch.from_numpy(r.batch.astype(np.int32)).to(Xd.device),
+                         torch.from_numpy(r.assign.astype(np.int32)).to(Xd.device))
+        else:
+            run.set_state(state)
         dist_out = torch.empty((w.b, w.k), dtype=torch.float32, device=Xd.device)
         obj = torch.empty(1, dtype=torch.float64, device=Xd.device)
         run.step(bi, fa, None, dist_out, obj)
@@ -211,6 +221,9 @@ def oracle_leg(X, kappa, init, forms, Xd, budget_s: float, prep: int = 4):
             f"(support S {min(S)}-{max(S)} rows), median over {len(times)} iterations")
     check = (f"teacher-forced iteration {prep + 1} (support S={S_check}): oracle state loaded into each "
              "GPU form, same batch, f_B and normwise distance error against the FP64 oracle")
+    if ALGO == "table":
+        check = (f"iteration {prep + 1} after {prep} iterations forced along the untruncated FP64 oracle's "
+                 "trajectory (same batches and assignments): f_B and normwise distance error")
     return w.b * w.k / t, oracle.kernels.num_threads(), desc, acc, check
 
 
@@ -267,8 +280,8 @@ def time_form(form, args, X, Xd, kappa, init, rank, world, dev, barrier):
     from paper_2410_05902_gb300.kkm import KKM
     w = WORKLOAD
     stream = torch.cuda.current_stream(dev)
-    run = KKM(Xd, w.k, w.b, kernel=KERNEL, param=kappa, tau=w.tau, precision=form,
-              seed=1000 + rank, init_idx=init, dist_tile=args.dist_tile)
+    run = KKM(Xd, w.k, w.b, kernel=KERNEL, param=kappa, tau=0 if ALGO == "table" else w.tau, precision=form,
+              seed=1000 + rank, init_idx=init, dist_tile=args.dist_tile, algo=ALGO)
     for _ in range(PREP_ITERS):
         run.step()
     run.graph(not args.no_graph)          # the step replays as one captured CUDA graph
@@ -326,7 +339,9 @@ def time_form(form, args, X, Xd, kappa, init, rank, world, dev, barrier):
 def roofline(form, S, kernel_ms, n_rec):
     w = WORKLOAD
     peaks = load_peaks()
-    flops = 2.0 * w.b * S * w.d          # algorithmic Gram flops of one distance-pass launch
+    # algorithmic Gram flops of one distance-pass launch: 2 b S d (windows) or
+    # 2 n b d (table form: every row of X against the batch)
+    flops = 2.0 * w.n * w.b * w.d if ALGO == "table" else 2.0 * w.b * S * w.d
     achieved = flops / (kernel_ms / 1e3) / 1e12
     if form == "fp32":
         peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
@@ -568,6 +583,8 @@ def main():
     ap.add_argument("--objective-grad", action="store_true",
                     help="time the objective and its adjoint on the differentiation workload")
     ap.add_argument("--kernel", choices=["gaussian", "laplacian"], default="gaussian")
+    ap.add_argument("--algo", choices=["windows", "table"], default="windows",
+                    help="table: Algorithm 1 through the n x k table (untruncated; secondary measurement)")
     ap.add_argument("--dist-tile", type=int, choices=[0, 64, 128, 256], default=0,
                     help="support rows per tensor-core distance tile (0: the library default)")
     args = ap.parse_args()
@@ -580,8 +597,10 @@ def main():
     if args.objective_grad:
         run_objective_grad(args)
         return
+    global ALGO
     WORKLOAD = inputs.WORKLOADS[args.workload]
     KERNEL = args.kernel
+    ALGO = args.algo
     if args.impl == "reference":
         run_reference(args)
     else:
