@@ -82,15 +82,24 @@ def load_peaks() -> dict:
 
 
 class Clocks:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region.
+
+    The sampler starts before the region and a reader thread stamps every
+    line with the host clock; only samples between start() and stop() count.
+    The caller waits for the first line (ready()) so that nvidia-smi's own
+    start-up does not fall inside a short region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
+        import threading
         self.proc = None
         self.gpu = gpu_index
+        self.lines = []
+        self.t0 = self.t1 = None
+        self.first = threading.Event()
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}",
@@ -98,17 +107,37 @@ class Clocks:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
+            self.first.set()
+            return
+        self.reader = threading.Thread(target=self._read, daemon=True)
+        self.reader.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.perf_counter(), line))
+            self.first.set()
+        self.first.set()
+
+    def ready(self, timeout: float = 10.0):
+        self.first.wait(timeout)
+        return self
+
+    def start(self):
+        self.t0 = time.perf_counter()
 
     def stop(self):
+        self.t1 = time.perf_counter()
         if self.proc is None:
             return None
         self.proc.terminate()
         try:
-            out, _ = self.proc.communicate(timeout=5)
+            self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-            out, _ = self.proc.communicate()
-        rows = [r.split(",") for r in out.strip().splitlines() if r.strip()]
+            self.proc.wait()
+        self.reader.join(timeout=5)
+        t0 = self.t0 if self.t0 is not None else float("-inf")
+        rows = [l.split(",") for t, l in self.lines if t0 <= t <= self.t1 and l.strip()]
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
@@ -290,8 +319,10 @@ def time_form(form, args, X, Xd, kappa, init, rank, world, dev, barrier):
     run.sync()
     run.stats(reset=True)
     run.launches(reset=True)
-    clocks = Clocks(dev.index) if rank == 0 else None
+    clocks = Clocks(dev.index).ready() if rank == 0 else None
     barrier()
+    if clocks:
+        clocks.start()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -486,10 +517,11 @@ def run_batching(args):
         g.step()
     g.sync()
     stream = torch.cuda.current_stream(dev)
-    clocks = Clocks(0)
+    clocks = Clocks(0).ready()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     # the group orders its work on a stream of its own: bracket it with syncs
     torch.cuda.synchronize(dev)
+    clocks.start()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         g.step()
@@ -611,7 +643,7 @@ def run_compare_fullbatch(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["auto", "fp32", "bf16", "bf16x3", "tf32"], default="auto",
