@@ -314,10 +314,15 @@ kkm_status kkm_stats(kkm_ctx* ctx, int64_t* steps, int64_t* support_rows, int64_
                      int32_t reset);
 
 /* kkm_timing -- CUDA-event timing of the distance kernel (the b x S Gram
- * product with its kernel and weighted-sum epilogue). While it is enabled,
- * every kkm_step records a pair of events on the context's stream around
- * that kernel's launch, for up to 4096 steps. kkm_timing_read synchronises
- * and writes the launches recorded and their summed milliseconds (host).
+ * product with its kernel and weighted-sum epilogue). While it is enabled
+ * (enable != 0), every eager kkm_step records a pair of events on the
+ * context's stream around that kernel, for up to 4096 steps. With enable = R
+ * > 1 the step launches the kernel R times back to back between the two
+ * events (it is idempotent: it rewrites the same partial sums from the same
+ * inputs) and the record is the average, which leaves out the launch gap
+ * that a single launch between two events includes. enable must be in
+ * [0, 1000] (KKM_EINVAL otherwise). kkm_timing_read synchronises and writes
+ * the launches recorded and the sum of their per-launch milliseconds (host).
  * reset != 0 clears the record. */
 kkm_status kkm_timing_enable(kkm_ctx* ctx, int32_t enable);
 kkm_status kkm_timing_read(kkm_ctx* ctx, int64_t* launches, double* total_ms, int32_t reset);

@@ -16,7 +16,8 @@
 // Roles: warp 0 issues TMA loads (and stages each item's metadata), warp 1
 // issues the MMAs (one elected lane) and owns the TMEM allocation (2
 // accumulators x TNV columns), warps 2-17 are the epilogue (four per TMEM lane
-// quadrant, each on a quarter of the columns). Every mbarrier wait
+// quadrant). In the distance pass they form two groups that take alternate
+// items; in the window pass all sixteen share each item. Every mbarrier wait
 // is bounded. A wait that runs out sets ST_TIMEOUT and makes the role stop. On
 // the way out the producer waits for its last copies to land and the MMA warp
 // waits for its last MMAs, so TMEM is freed only once nothing is in flight.
@@ -85,7 +86,7 @@ struct Shared {
     MetaSlot ring[MS];                          // distance pass
     float warp[NEPI][5][32];                    // window pass: per epilogue warp (load_pair_meta)
   } meta;
-  float red[2][NH - 1][4][32];                   // distance pass: row sums of column parts 1.. (item parity, part, quadrant)
+  float red[768];                                // distance pass: row sums of column parts (dist_epilogue)
   float wred[2][NEPI][4];                       // window pass: per-warp sums (item parity, warp, sum)
 };
 
@@ -246,6 +247,36 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   return y;
 }
 
+// 2^x on the FMA pipe, for two values at once (FP32, x >= -127 after the
+// clamp; the exponents here are <= 0 up to rounding). Cody-Waite range
+// reduction x = j + f, j = round(x) (adding 1.5 * 2^23 rounds to an integer
+// held in the low mantissa bits), f in [-1/2, 1/2]; 2^f is a degree-5
+// polynomial whose coefficients minimise the relative error on [-1/2, 1/2]
+// (minimax, from exp2_poly.py: 7.4e-8 exact, 2.1e-7 evaluated in FP32), and
+// 2^j is added to its exponent bits. Where x clamps to -127 the result is 0 or
+// a denormal of that size, as negligible as the 0 that ex2.approx.ftz gives.
+// The epilogue sends a quarter of its exponentials here and the rest to the
+// MUFU, whose 16 results per clock and SM otherwise bound it; the split of
+// exponentials between the two pipes follows FlashAttention-4 (Dao et al.).
+__device__ __forceinline__ float2 exp2_fma2(float2 x) {
+  constexpr float C0 = 1.0000001192092896f, C1 = 0.6931469440460205f, C2 = 0.24022120237350464f,
+                  C3 = 0.0555071160197258f, C4 = 0.009675559587776661f, C5 = 0.001327692880295217f;
+  constexpr float MAGIC = 12582912.0f;          // 1.5 * 2^23
+  x.x = fmaxf(x.x, -127.0f);
+  x.y = fmaxf(x.y, -127.0f);
+  const float2 t = __fadd2_rn(x, make_float2(MAGIC, MAGIC));
+  const float2 j = __fadd2_rn(t, make_float2(-MAGIC, -MAGIC));
+  const float2 f = __ffma2_rn(j, make_float2(-1.0f, -1.0f), x);
+  float2 p = __ffma2_rn(make_float2(C5, C5), f, make_float2(C4, C4));
+  p = __ffma2_rn(p, f, make_float2(C3, C3));
+  p = __ffma2_rn(p, f, make_float2(C2, C2));
+  p = __ffma2_rn(p, f, make_float2(C1, C1));
+  p = __ffma2_rn(p, f, make_float2(C0, C0));
+  // the low bits of t hold j + 2^22: shifted by 23 they leave j << 23 (mod 2^32)
+  return make_float2(__int_as_float(__float_as_int(p.x) + (__float_as_int(t.x) << 23)),
+                     __int_as_float(__float_as_int(p.y) + (__float_as_int(t.y) << 23)));
+}
+
 // Kernel values of one row against two columns from their Gram entries g.
 // Gaussian: rc = ||x||^2 * negc and cc = ||y||^2 * negc (negc = -log2(e)/kappa),
 //           K = 2^(rc + cc - 2 negc g). The exponent is -D^2 log2(e)/kappa with
@@ -254,19 +285,32 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 // Laplacian: rc = ||x||^2, cc = ||y||^2, K = 2^(negc * sqrt(max(D^2, 0))).
 // Both give exactly 1 when the two rows are the same data point (K(x,x) = 1).
 // Linear and polynomial values of padding columns (yi = -2) are zeroed, as
-// those kernels are unbounded.
-template <int KIND>
+// those kernels are unbounded. POLY takes the exponential on the FMA pipe.
+template <int KIND, bool POLY = false>
 __device__ __forceinline__ float2 kernel_pair(float2 g, float rc, float2 cc, int xi, int2 yi, float negc,
                                               float coef0, int degree) {
   float2 k;
   if constexpr (KIND == K_GAUSS) {
     const float2 a = __ffma2_rn(g, make_float2(-2.0f * negc, -2.0f * negc), __fadd2_rn(make_float2(rc, rc), cc));
-    k.x = xi == yi.x ? 1.0f : ex2_approx(a.x);
-    k.y = xi == yi.y ? 1.0f : ex2_approx(a.y);
+    if constexpr (POLY) {
+      const float2 p = exp2_fma2(a);
+      k.x = xi == yi.x ? 1.0f : p.x;
+      k.y = xi == yi.y ? 1.0f : p.y;
+    } else {
+      k.x = xi == yi.x ? 1.0f : ex2_approx(a.x);
+      k.y = xi == yi.y ? 1.0f : ex2_approx(a.y);
+    }
   } else if constexpr (KIND == K_LAPLACE) {
     const float2 d2 = __ffma2_rn(g, make_float2(-2.0f, -2.0f), __fadd2_rn(make_float2(rc, rc), cc));
-    k.x = xi == yi.x ? 1.0f : ex2_approx(sqrt_approx(fmaxf(d2.x, 0.0f)) * negc);
-    k.y = xi == yi.y ? 1.0f : ex2_approx(sqrt_approx(fmaxf(d2.y, 0.0f)) * negc);
+    const float2 a = make_float2(sqrt_approx(fmaxf(d2.x, 0.0f)) * negc, sqrt_approx(fmaxf(d2.y, 0.0f)) * negc);
+    if constexpr (POLY) {
+      const float2 p = exp2_fma2(a);
+      k.x = xi == yi.x ? 1.0f : p.x;
+      k.y = xi == yi.y ? 1.0f : p.y;
+    } else {
+      k.x = xi == yi.x ? 1.0f : ex2_approx(a.x);
+      k.y = xi == yi.y ? 1.0f : ex2_approx(a.y);
+    }
   } else if constexpr (KIND == K_LINEAR) {
     k.x = yi.x == -2 ? 0.0f : g.x;
     k.y = yi.y == -2 ? 0.0f : g.y;
@@ -343,6 +387,145 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
       : "memory");
 }
 
+// Distance-pass epilogue pieces. A chunk is CW accumulator columns of the
+// warp's 32 rows: chunk_load reads it from TMEM (two 16-lane loads), and
+// chunk_math adds w_y K(x, y) over its columns into the row sums acc[u] (rows
+// g4 + 8u of the quadrant, two columns per lane and 8-column block). Every
+// fourth block takes its exponentials on the FMA pipe.
+template <int NB>
+__device__ __forceinline__ void chunk_load(uint32_t taddr, float (&v0)[4 * NB], float (&v1)[4 * NB]) {
+  tmem_ld16x256<NB>(taddr, v0);                 // rows g4, g4 + 8
+  tmem_ld16x256<NB>(taddr + (16u << 16), v1);   // rows g4 + 16, g4 + 24
+  tmem_wait_ld();
+}
+
+template <int KIND, bool POLY, int NB>
+__device__ __forceinline__ void block_math(const float (&v0)[4 * NB], const float (&v1)[4 * NB], int j, float2 w,
+                                           float2 cc, int2 yi, const float (&rc)[4], const int (&xi)[4], float negc,
+                                           float coef0, int degree, float2 (&acc)[4]) {
+  acc[0] = __ffma2_rn(w, kernel_pair<KIND, POLY>(make_float2(v0[4 * j], v0[4 * j + 1]), rc[0], cc, xi[0], yi, negc,
+                                                 coef0, degree), acc[0]);
+  acc[1] = __ffma2_rn(w, kernel_pair<KIND, POLY>(make_float2(v0[4 * j + 2], v0[4 * j + 3]), rc[1], cc, xi[1], yi,
+                                                 negc, coef0, degree), acc[1]);
+  acc[2] = __ffma2_rn(w, kernel_pair<KIND, POLY>(make_float2(v1[4 * j], v1[4 * j + 1]), rc[2], cc, xi[2], yi, negc,
+                                                 coef0, degree), acc[2]);
+  acc[3] = __ffma2_rn(w, kernel_pair<KIND, POLY>(make_float2(v1[4 * j + 2], v1[4 * j + 3]), rc[3], cc, xi[3], yi,
+                                                 negc, coef0, degree), acc[3]);
+}
+
+template <int KIND, int NB>
+__device__ __forceinline__ void chunk_math(const float (&v0)[4 * NB], const float (&v1)[4 * NB], const MetaSlot& m,
+                                           int c0, const float (&rc)[4], const int (&xi)[4], float negc, float coef0,
+                                           int degree, float2 (&acc)[4]) {
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    const int c = c0 + 8 * j;
+    const float2 yn = *reinterpret_cast<const float2*>(&m.col[0][c]);
+    const float2 w = *reinterpret_cast<const float2*>(&m.col[1][c]);
+    const int2 yi = *reinterpret_cast<const int2*>(&m.col[2][c]);
+    const float2 cc = (KIND == K_GAUSS) ? __fmul2_rn(yn, make_float2(negc, negc)) : yn;
+    if ((j & 3) == 3) block_math<KIND, true, NB>(v0, v1, j, w, cc, yi, rc, xi, negc, coef0, degree, acc);
+    else block_math<KIND, false, NB>(v0, v1, j, w, cc, yi, rc, xi, negc, coef0, degree, acc);
+  }
+}
+
+// Distance-pass epilogue (warps 2-17): two groups of eight warps, two per TMEM
+// lane quadrant. Group g = (warp - 2) / 8 takes this CTA's items of parity g
+// (accumulator buffer g, and the metadata slots of those items), so one
+// group's TMEM loads, combine and stores overlap the other group's
+// arithmetic. Warp part h covers its quadrant's 32 rows and columns
+// [h TNV/2, (h+1) TNV/2) in chunks of CW (at most 32, to keep the values in
+// registers); it frees the accumulator once the last chunk is in registers.
+// A CTA with a single item runs it on both groups instead, each warp on a
+// quarter of the columns (part 2g + h). The parts of a row meet in shared
+// memory (by the group's item parity), and part 0 writes part[tile][row].
+template <int KIND, int TNV>
+__device__ __forceinline__ void dist_epilogue(const Dev& s, Shared& sh, uint32_t tmem, int total, int R, int rows,
+                                              int warp, int lane) {
+  constexpr int CW = TNV / 4 < 32 ? TNV / 4 : 32;   // columns per chunk
+  constexpr int NB = CW / 8;                    // 8-column blocks per TMEM load
+  const int e = warp - 2, g = e >> 3, h = (e >> 2) & 1, q = warp & 3;
+  const int g4 = lane >> 2, c2 = 2 * (lane & 3);
+  const int rq = g4 + 8 * (lane & 3);           // the row this thread reports after the lane reduction
+  const float negc = s.negc;
+  const float coef0 = (float)s.coef0;
+  const int degree = s.degree;
+  const int mine = total > (int)blockIdx.x ? (total - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+  const bool solo = mine == 1;
+  bool dead = false;                            // a wait ran out: skip the work, keep the barriers
+  uint32_t local = 0;
+  for (int item = blockIdx.x; item < total; item += gridDim.x, ++local) {
+    if (!solo && (int)(local & 1u) != g) continue;
+    const uint32_t buf = local & 1u, bph = (local >> 1) & 1u;
+    const int ms = local % MS;
+    const MetaSlot& m = sh.meta.ring[ms];
+    const bool ok = dead || (mbar_wait(&sh.mfull[ms], (local / MS) & 1u) && mbar_wait(&sh.tfull[buf], bph));
+    if (__any_sync(0xffffffffu, !ok)) {
+      if (lane == 0 && !dead) atomicOr(s.status, ST_TIMEOUT);
+      dead = true;
+    }
+    float f = 0.0f;
+    if (!dead) {
+      tc_fence_after();
+      float rc[4];
+      int xi[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = q * 32 + g4 + 8 * u;
+        rc[u] = (KIND == K_GAUSS) ? m.row[0][r] * negc : m.row[0][r];
+        xi[u] = __float_as_int(m.row[1][r]);
+      }
+      float2 acc[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] = make_float2(0.0f, 0.0f);
+      const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16) + buf * TNV;
+      const int pc0 = solo ? (2 * g + h) * (TNV / 4) : h * (TNV / 2);   // first column of this part
+      const int nch = (solo ? TNV / 4 : TNV / 2) / CW;
+      float v0[4 * NB], v1[4 * NB];
+      for (int ch = 0; ch < nch; ++ch) {
+        chunk_load<NB>(tq + pc0 + ch * CW, v0, v1);
+        if (!solo && ch == nch - 1) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sh.tempty[buf]);     // the accumulator is free again
+        }
+        chunk_math<KIND, NB>(v0, v1, m, pc0 + ch * CW + c2, rc, xi, negc, coef0, degree, acc);
+      }
+      if (!solo) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sh.mempty[ms]);        // this warp is done with the slot
+      }
+      // row sums: the four lanes of a group hold the same rows, different columns
+      float fr[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        fr[u] = acc[u].x + acc[u].y;
+        fr[u] += __shfl_xor_sync(0xffffffffu, fr[u], 1);
+        fr[u] += __shfl_xor_sync(0xffffffffu, fr[u], 2);
+      }
+      const int us = lane & 3;
+      f = us == 0 ? fr[0] : (us == 1 ? fr[1] : (us == 2 ? fr[2] : fr[3]));   // row rq
+    }
+    const int row = (item % R) * TM + q * 32 + rq;
+    if (solo) {
+      const int P = 2 * g + h;
+      if (P > 0) sh.red[((P - 1) * 4 + q) * 32 + rq] = f;
+      asm volatile("bar.sync %0, 128;" ::"r"(9 + q) : "memory");
+      if (P == 0 && !dead && row < rows) {
+        f += sh.red[(0 * 4 + q) * 32 + rq];
+        f += sh.red[(1 * 4 + q) * 32 + rq];
+        f += sh.red[(2 * 4 + q) * 32 + rq];
+        s.part[(int64_t)(item / R) * s.bpad + row] = f;
+      }
+    } else {
+      float* slot = sh.red + ((g * 2 + (int)((local >> 1) & 1u)) * 4 + q) * 32;
+      if (h == 1) slot[rq] = f;
+      asm volatile("bar.sync %0, 64;" ::"r"(1 + g * 4 + q) : "memory");
+      if (h == 0 && !dead && row < rows) s.part[(int64_t)(item / R) * s.bpad + row] = f + slot[rq];
+    }
+  }
+}
+
 // MODE 0: distance pass (A = batch tile, B = support tile, one FP32 partial per row).
 // MODE 1: window pass (A and B = support rows of one center; four sums per item:
 //         FP32 within a warp, FP64 across the eight epilogue warps).
@@ -381,11 +564,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&sh.tfull[i], 1);
-      mbar_init(&sh.tempty[i], NEPI);
+      mbar_init(&sh.tempty[i], MODE == 0 ? NEPI / 2 : NEPI);   // distance pass: one group per buffer
     }
     for (int i = 0; i < MS; ++i) {
       mbar_init(&sh.mfull[i], 1);
-      mbar_init(&sh.mempty[i], NEPI);
+      mbar_init(&sh.mempty[i], NEPI / 2);
     }
     mbar_init(&sh.mma_done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -400,11 +583,42 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = sh.tmem_base;
-  KKM_GRID_DEP_WAIT();   // everything above touches only this CTA's shared memory and TMEM
-
   const int R = (rows + TM - 1) / TM;
-  const int total = (MODE == 0) ? R * (*s.ntiles) : *s.nwpairs;
   const int nks = s.dp / KSE;
+
+  // Distance pass with s.pre_b: the producer stages the B tiles of its first
+  // item's first stages and that item's column metadata before the
+  // grid-dependency wait, while the batch gather still runs. They come from
+  // earlier steps; the batch rows and their metadata follow after the wait.
+  int npre = 0;                                  // first-item stages whose B tile is already on its way
+  if constexpr (MODE == 0) {
+    if (warp == 0 && s.pre_b) {
+      if (lane == 0 && (int)blockIdx.x < R * (*s.ntiles)) {
+        const int yb0 = s.tiles[blockIdx.x / R].row0;
+        MetaSlot& m = sh.meta.ring[0];
+        mbar_expect_tx(&sh.mfull[0], META_BYTES);   // covers the row metadata issued after the wait
+        bulk_load(m.col[0], s.yn + yb0, TNV * 4, &sh.mfull[0]);
+        bulk_load(m.col[1], s.w32 + yb0, TNV * 4, &sh.mfull[0]);
+        bulk_load(m.col[2], s.yi + yb0, TNV * 4, &sh.mfull[0]);
+        npre = nks < NST ? nks : NST;
+        for (int sl = 0; sl < npre; ++sl) {
+          uint8_t* a = smem + sl * SB;
+          mbar_expect_tx(&sh.full[sl], SB);         // covers the A tile issued after the wait
+          if constexpr (X3) {
+            tma_load_2d(a + 2 * A_BYTES, &tmB, &sh.full[sl], sl * KSE, yb0);
+            tma_load_2d(a + 2 * A_BYTES + BB, &tmB, &sh.full[sl], s.dp + sl * KSE, yb0);
+          } else {
+            tma_load_2d(a + A_BYTES, &tmB, &sh.full[sl], sl * KSE, yb0);
+          }
+        }
+      }
+      npre = __shfl_sync(0xffffffffu, npre, 0);
+    }
+  }
+  KKM_GRID_DEP_WAIT();   // everything above reads only data of earlier steps
+
+
+  const int total = (MODE == 0) ? R * (*s.ntiles) : *s.nwpairs;
 
   if (warp == 0) {
     // ------------------------------------------------------- producer (one warp)
@@ -433,10 +647,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (!mbar_wait(&sh.mempty[ms], ((local / MS) & 1u) ^ 1u)) ok = false;
           if (ok) {
             MetaSlot& m = sh.meta.ring[ms];
-            mbar_expect_tx(&sh.mfull[ms], META_BYTES);
-            bulk_load(m.col[0], s.yn + yb, TNV * 4, &sh.mfull[ms]);
-            bulk_load(m.col[1], s.w32 + yb, TNV * 4, &sh.mfull[ms]);
-            bulk_load(m.col[2], s.yi + yb, TNV * 4, &sh.mfull[ms]);
+            if (local != 0 || npre == 0) {             // else staged before the wait
+              mbar_expect_tx(&sh.mfull[ms], META_BYTES);
+              bulk_load(m.col[0], s.yn + yb, TNV * 4, &sh.mfull[ms]);
+              bulk_load(m.col[1], s.w32 + yb, TNV * 4, &sh.mfull[ms]);
+              bulk_load(m.col[2], s.yi + yb, TNV * 4, &sh.mfull[ms]);
+            }
             bulk_load(m.row[0], s.xbn + ya, TM * 4, &sh.mfull[ms]);
             bulk_load(m.row[1], s.xbi + ya, TM * 4, &sh.mfull[ms]);
             ++mi;
@@ -448,15 +664,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (!mbar_wait(&sh.empty[st], ph ^ 1u)) { ok = false; break; }
           const int x = sl * KSE;
           uint8_t* a = smem + st * SB;
-          mbar_expect_tx(&sh.full[st], SB);
+          const bool pre = local == 0 && sl < npre;   // B tile and expected bytes issued before the wait
+          if (!pre) mbar_expect_tx(&sh.full[st], SB);
           if constexpr (X3) {   // stage layout: A_hi | A_lo | B_hi | B_lo
             tma_load_2d(a, &tmA, &sh.full[st], x, ya);
             tma_load_2d(a + A_BYTES, &tmA, &sh.full[st], s.dp + x, ya);
-            tma_load_2d(a + 2 * A_BYTES, &tmB, &sh.full[st], x, yb);
-            tma_load_2d(a + 2 * A_BYTES + BB, &tmB, &sh.full[st], s.dp + x, yb);
+            if (!pre) {
+              tma_load_2d(a + 2 * A_BYTES, &tmB, &sh.full[st], x, yb);
+              tma_load_2d(a + 2 * A_BYTES + BB, &tmB, &sh.full[st], s.dp + x, yb);
+            }
           } else {              // stage layout: A | B
             tma_load_2d(a, &tmA, &sh.full[st], x, ya);
-            tma_load_2d(a + A_BYTES, &tmB, &sh.full[st], x, yb);
+            if (!pre) tma_load_2d(a + A_BYTES, &tmB, &sh.full[st], x, yb);
           }
         }
       }
@@ -511,6 +730,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (!mbar_wait(&sh.mma_done, 0)) ok = false;
       if (!ok) atomicOr(s.status, ST_TIMEOUT);
     }
+  } else if constexpr (MODE == 0) {
+    // ---------------------------------------------------------------- epilogue
+    dist_epilogue<KIND, TNV>(s, sh, tmem, total, R, rows, warp, lane);
   } else {
     // ---------------------------------------------------------------- epilogue
     // NEPI warps, NH per TMEM lane quadrant: warp e = warp - 2 reads lanes
@@ -525,7 +747,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // this thread's rows inside the quadrant: g4 + 8u (u = 0..3); its columns:
     // cbase + 8j + c2 and the next one (j = 0..NB-1)
     const int g4 = lane >> 2, c2 = 2 * (lane & 3);
-    const int rq = g4 + 8 * (lane & 3);          // the row this thread reports after the reduction
     const float negc = s.negc;
     const float coef0 = (float)s.coef0;
     const int degree = s.degree;
@@ -534,75 +755,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int item = blockIdx.x; item < total; item += gridDim.x, ++local) {
       const uint32_t buf = local & 1u, bph = (local >> 1) & 1u;
       const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + buf * TNV + cbase;
-      if constexpr (MODE == 0) {
-        const int ms = local % MS;
-        const MetaSlot& m = sh.meta.ring[ms];
-        const bool ok = dead || (mbar_wait(&sh.mfull[ms], (local / MS) & 1u) && mbar_wait(&sh.tfull[buf], bph));
-        if (__any_sync(0xffffffffu, !ok)) {
-          if (lane == 0 && !dead) atomicOr(s.status, ST_TIMEOUT);
-          dead = true;
-        }
-        float f = 0.0f;
-        if (!dead) {
-          tc_fence_after();
-          float v0[4 * NB], v1[4 * NB];
-          tmem_ld16x256<NB>(taddr, v0);                          // rows g4, g4 + 8
-          tmem_ld16x256<NB>(taddr + (16u << 16), v1);            // rows g4 + 16, g4 + 24
-          tmem_wait_ld();
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&sh.tempty[buf]);           // the accumulator is free again
-          float rc[4];
-          int xi[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int r = q * 32 + g4 + 8 * u;
-            rc[u] = (KIND == K_GAUSS) ? m.row[0][r] * negc : m.row[0][r];
-            xi[u] = __float_as_int(m.row[1][r]);
-          }
-          float2 acc[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) acc[u] = make_float2(0.0f, 0.0f);
-#pragma unroll
-          for (int j = 0; j < NB; ++j) {
-            const int c = cbase + 8 * j + c2;
-            const float2 yn = *reinterpret_cast<const float2*>(&m.col[0][c]);
-            const float2 w = *reinterpret_cast<const float2*>(&m.col[1][c]);
-            const int2 yi = *reinterpret_cast<const int2*>(&m.col[2][c]);
-            const float2 cc = (KIND == K_GAUSS) ? __fmul2_rn(yn, make_float2(negc, negc)) : yn;
-            acc[0] = __ffma2_rn(w, kernel_pair<KIND>(make_float2(v0[4 * j], v0[4 * j + 1]), rc[0], cc, xi[0], yi,
-                                                     negc, coef0, degree), acc[0]);
-            acc[1] = __ffma2_rn(w, kernel_pair<KIND>(make_float2(v0[4 * j + 2], v0[4 * j + 3]), rc[1], cc, xi[1], yi,
-                                                     negc, coef0, degree), acc[1]);
-            acc[2] = __ffma2_rn(w, kernel_pair<KIND>(make_float2(v1[4 * j], v1[4 * j + 1]), rc[2], cc, xi[2], yi,
-                                                     negc, coef0, degree), acc[2]);
-            acc[3] = __ffma2_rn(w, kernel_pair<KIND>(make_float2(v1[4 * j + 2], v1[4 * j + 3]), rc[3], cc, xi[3], yi,
-                                                     negc, coef0, degree), acc[3]);
-          }
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&sh.mempty[ms]);           // this warp is done with the slot
-          // row sums: the four lanes of a group hold the same rows, different columns
-          float fr[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            fr[u] = acc[u].x + acc[u].y;
-            fr[u] += __shfl_xor_sync(0xffffffffu, fr[u], 1);
-            fr[u] += __shfl_xor_sync(0xffffffffu, fr[u], 2);
-          }
-          const int us = lane & 3;
-          f = us == 0 ? fr[0] : (us == 1 ? fr[1] : (us == 2 ? fr[2] : fr[3]));   // row rq
-        }
-        // the NH column parts of a row meet in shared memory (slot by item parity)
-        float (*red)[4][32] = sh.red[local & 1u];
-        if (h > 0) red[h - 1][q][rq] = f;
-        asm volatile("bar.sync %0, %1;" ::"r"(1 + q), "n"(32 * NH) : "memory");
-        const int row = (item % R) * TM + q * 32 + rq;
-        if (h == 0 && !dead && row < rows) {
-#pragma unroll
-          for (int v = 0; v < NH - 1; ++v) f += red[v][q][rq];
-          s.part[(int64_t)(item / R) * s.bpad + row] = f;
-        }
-      } else {
+      {
         // window pass: this warp loads its own metadata; the loads overlap the MMAs
         float (*mw)[32] = sh.meta.warp[e];
         __syncwarp();

@@ -91,6 +91,8 @@ struct Dev {
   int32_t num_sms;
   uint64_t seed;
   int32_t tn;        // support rows per distance tile
+  int32_t pre_b;     // distance pass: the support operand, its metadata and the tile list come from
+                     // kernels before the one just ahead, so they may be read before the grid-dependency wait
   int32_t pair_rows, pair_cols; // window-pass tile: row and column counts (64x64 SIMT, 128x64 tcgen05)
   int32_t bpad;      // rows of the batch buffers (>= b, multiple of 128)
   int32_t max_tiles, max_pairs;
@@ -154,6 +156,9 @@ struct Dev {
 // be scheduled while its predecessor drains. It must wait here before it reads
 // anything the predecessor writes (a no-op when launched without the attribute).
 #define KKM_GRID_DEP_WAIT() asm volatile("griddepcontrol.wait;" ::: "memory")
+// Lets the next kernel in the stream start its pre-wait part. Issued only after
+// this kernel's own wait, so every kernel before it has completed by then.
+#define KKM_LAUNCH_DEPENDENTS() asm volatile("griddepcontrol.launch_dependents;" ::: "memory")
 
 // Launches `kern` with the programmatic-stream-serialization attribute.
 template <typename... Params, typename... Args>

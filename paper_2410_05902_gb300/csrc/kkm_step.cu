@@ -158,6 +158,9 @@ __global__ void k_sample(Dev s) {
 // NULL the slot's index is drawn here: SplitMix64 output (i-1)*b + slot.
 __global__ void k_gather_batch(Dev s, const int32_t* __restrict__ idx) {
   KKM_GRID_DEP_WAIT();
+  // the distance pass may now stage what it reads from earlier steps (the
+  // support tiles, their metadata, the tile list); this kernel writes none of it
+  KKM_LAUNCH_DEPENDENTS();
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (warp >= s.b) return;
   int64_t i;

@@ -193,7 +193,8 @@ def kkm_stats(ctx, reset: bool = False) -> tuple[int, int, int]:
     return a.value, b_.value, c.value
 
 
-def kkm_timing_enable(ctx, enable: bool) -> None:
+def kkm_timing_enable(ctx, enable) -> None:
+    """enable: False/0 off, True/1 one launch per record, R > 1: R back-to-back launches."""
     _check(load().kkm_timing_enable(ctx, int(enable)), ctx)
 
 
@@ -377,7 +378,7 @@ class KKM:
     def stats(self, reset: bool = False):
         return kkm_stats(self.ctx, reset)
 
-    def timing(self, enable: bool):
+    def timing(self, enable):
         kkm_timing_enable(self.ctx, enable)
 
     def graph(self, enable: bool):

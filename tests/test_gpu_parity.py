@@ -347,3 +347,20 @@ def test_fit_stops_at_the_first_small_improvement():
     assert done == 100 or last < eps
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision,tile,kernel", [("bf16", 256, "gaussian"), ("bf16x3", 128, "gaussian"),
+                                                   ("tf32", 256, "laplacian"), ("bf16x3", 64, "laplacian")])
+def test_teacher_forced_many_items_per_cta(precision, tile, kernel):
+    """More distance-pass items than SMs, so each CTA runs several and the two
+    epilogue groups alternate (one item per CTA runs both groups on it)."""
+    torch = torch_cuda()
+    X = small_data(n=12000, d=48, c=40, seed=77)
+    p = Pair(X, k=40, b=2048, kernel=kernel, tau=60, precision=precision, dist_tile=tile)
+    batches = inputs.batch_stream(len(X), 2048, 4, seed=78)
+    p.gpu.stats(reset=True)
+    teacher_forced(p, batches, cn_rtol=CN_RTOL[precision])
+    steps, _, tiles = p.gpu.stats(reset=True)
+    items = (2048 // 128) * tiles / steps
+    assert items > 2 * torch.cuda.get_device_properties(0).multi_processor_count
+    p.close()
