@@ -233,45 +233,6 @@ __device__ __forceinline__ void tmem_ld16x256(uint32_t taddr, float (&v)[4 * NB]
   for (int i = 0; i < 4 * NB; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Issue-only forms of the 16x256b load for the pipelined distance epilogue:
-// the destination registers are valid only after tmem_wait_regs, which takes
-// them as read-write operands so that no use can be scheduled before it.
-template <int NB>
-__device__ __forceinline__ void tmem_issue16x256(uint32_t taddr, uint32_t (&r)[4 * NB]) {
-  if constexpr (NB == 4) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.16x256b.x4.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-  } else {
-    static_assert(NB == 2, "tmem_issue16x256: 2 or 4 blocks");
-    asm volatile(
-        "tcgen05.ld.sync.aligned.16x256b.x2.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-        : "r"(taddr));
-  }
-}
-
-// tcgen05.wait::ld tied to the registers of the loads it completes.
-template <int N>
-__device__ __forceinline__ void tmem_wait_regs(uint32_t (&a)[N], uint32_t (&b)[N]) {
-  if constexpr (N == 16) {
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]), "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11]), "+r"(a[12]), "+r"(a[13]), "+r"(a[14]), "+r"(a[15]), "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7]), "+r"(b[8]), "+r"(b[9]), "+r"(b[10]), "+r"(b[11]), "+r"(b[12]), "+r"(b[13]), "+r"(b[14]), "+r"(b[15])
-                 :
-                 : "memory");
-  } else {
-    static_assert(N == 8, "tmem_wait_regs: 8 or 16 registers per load");
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]), "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7])
-                 :
-                 : "memory");
-  }
-}
-
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -427,31 +388,33 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 }
 
 // Distance-pass epilogue pieces. A chunk is CW accumulator columns of the
-// warp's 32 rows, read from TMEM by two 16-lane loads (v0: rows g4, g4 + 8;
-// v1: rows g4 + 16, g4 + 24). chunk_math adds w_y K(x, y) over its columns
-// into the row sums acc[u] (rows g4 + 8u of the quadrant, two columns per lane
-// and 8-column block). Block POLYJ of the chunk (if any) takes its exponentials
-// on the FMA pipe; the caller picks it so that a quarter of the blocks do.
-__device__ __forceinline__ float2 f2(uint32_t a, uint32_t b) {
-  return make_float2(__uint_as_float(a), __uint_as_float(b));
+// warp's 32 rows: chunk_load reads it from TMEM (two 16-lane loads), and
+// chunk_math adds w_y K(x, y) over its columns into the row sums acc[u] (rows
+// g4 + 8u of the quadrant, two columns per lane and 8-column block). Every
+// fourth block takes its exponentials on the FMA pipe.
+template <int NB>
+__device__ __forceinline__ void chunk_load(uint32_t taddr, float (&v0)[4 * NB], float (&v1)[4 * NB]) {
+  tmem_ld16x256<NB>(taddr, v0);                 // rows g4, g4 + 8
+  tmem_ld16x256<NB>(taddr + (16u << 16), v1);   // rows g4 + 16, g4 + 24
+  tmem_wait_ld();
 }
 
 template <int KIND, bool POLY, int NB>
-__device__ __forceinline__ void block_math(const uint32_t (&v0)[4 * NB], const uint32_t (&v1)[4 * NB], int j,
-                                           float2 w, float2 cc, int2 yi, const float (&rc)[4], const int (&xi)[4],
-                                           float negc, float coef0, int degree, float2 (&acc)[4]) {
-  acc[0] = __ffma2_rn(w, kernel_pair<KIND, POLY>(f2(v0[4 * j], v0[4 * j + 1]), rc[0], cc, xi[0], yi, negc, coef0,
-                                                 degree), acc[0]);
-  acc[1] = __ffma2_rn(w, kernel_pair<KIND, POLY>(f2(v0[4 * j + 2], v0[4 * j + 3]), rc[1], cc, xi[1], yi, negc,
-                                                 coef0, degree), acc[1]);
-  acc[2] = __ffma2_rn(w, kernel_pair<KIND, POLY>(f2(v1[4 * j], v1[4 * j + 1]), rc[2], cc, xi[2], yi, negc, coef0,
-                                                 degree), acc[2]);
-  acc[3] = __ffma2_rn(w, kernel_pair<KIND, POLY>(f2(v1[4 * j + 2], v1[4 * j + 3]), rc[3], cc, xi[3], yi, negc,
-                                                 coef0, degree), acc[3]);
+__device__ __forceinline__ void block_math(const float (&v0)[4 * NB], const float (&v1)[4 * NB], int j, float2 w,
+                                           float2 cc, int2 yi, const float (&rc)[4], const int (&xi)[4], float negc,
+                                           float coef0, int degree, float2 (&acc)[4]) {
+  acc[0] = __ffma2_rn(w, kernel_pair<KIND, POLY>(make_float2(v0[4 * j], v0[4 * j + 1]), rc[0], cc, xi[0], yi, negc,
+                                                 coef0, degree), acc[0]);
+  acc[1] = __ffma2_rn(w, kernel_pair<KIND, POLY>(make_float2(v0[4 * j + 2], v0[4 * j + 3]), rc[1], cc, xi[1], yi,
+                                                 negc, coef0, degree), acc[1]);
+  acc[2] = __ffma2_rn(w, kernel_pair<KIND, POLY>(make_float2(v1[4 * j], v1[4 * j + 1]), rc[2], cc, xi[2], yi, negc,
+                                                 coef0, degree), acc[2]);
+  acc[3] = __ffma2_rn(w, kernel_pair<KIND, POLY>(make_float2(v1[4 * j + 2], v1[4 * j + 3]), rc[3], cc, xi[3], yi,
+                                                 negc, coef0, degree), acc[3]);
 }
 
-template <int KIND, int NB, int POLYJ>
-__device__ __forceinline__ void chunk_math(const uint32_t (&v0)[4 * NB], const uint32_t (&v1)[4 * NB], const MetaSlot& m,
+template <int KIND, int NB>
+__device__ __forceinline__ void chunk_math(const float (&v0)[4 * NB], const float (&v1)[4 * NB], const MetaSlot& m,
                                            int c0, const float (&rc)[4], const int (&xi)[4], float negc, float coef0,
                                            int degree, float2 (&acc)[4]) {
 #pragma unroll
@@ -461,7 +424,7 @@ __device__ __forceinline__ void chunk_math(const uint32_t (&v0)[4 * NB], const u
     const float2 w = *reinterpret_cast<const float2*>(&m.col[1][c]);
     const int2 yi = *reinterpret_cast<const int2*>(&m.col[2][c]);
     const float2 cc = (KIND == K_GAUSS) ? __fmul2_rn(yn, make_float2(negc, negc)) : yn;
-    if (j == POLYJ) block_math<KIND, true, NB>(v0, v1, j, w, cc, yi, rc, xi, negc, coef0, degree, acc);
+    if ((j & 3) == 3) block_math<KIND, true, NB>(v0, v1, j, w, cc, yi, rc, xi, negc, coef0, degree, acc);
     else block_math<KIND, false, NB>(v0, v1, j, w, cc, yi, rc, xi, negc, coef0, degree, acc);
   }
 }
@@ -471,17 +434,15 @@ __device__ __forceinline__ void chunk_math(const uint32_t (&v0)[4 * NB], const u
 // (accumulator buffer g, and the metadata slots of those items), so one
 // group's TMEM loads, combine and stores overlap the other group's
 // arithmetic. Warp part h covers its quadrant's 32 rows and columns
-// [h TNV/2, (h+1) TNV/2) in chunks of CW = 16 columns, loading chunk c + 1
-// from TMEM while it computes chunk c (two register sets; the kernel's 576
-// threads leave 96 registers a thread); it frees the accumulator once the last
-// chunk is in registers. Block 1 of every odd chunk takes the FMA-pipe exp2.
+// [h TNV/2, (h+1) TNV/2) in chunks of CW (at most 32, to keep the values in
+// registers); it frees the accumulator once the last chunk is in registers.
 // A CTA with a single item runs it on both groups instead, each warp on a
 // quarter of the columns (part 2g + h). The parts of a row meet in shared
 // memory (by the group's item parity), and part 0 writes part[tile][row].
 template <int KIND, int TNV>
 __device__ __forceinline__ void dist_epilogue(const Dev& s, Shared& sh, uint32_t tmem, int total, int R, int rows,
                                               int warp, int lane) {
-  constexpr int CW = 16;                        // columns per chunk
+  constexpr int CW = TNV / 4 < 32 ? TNV / 4 : 32;   // columns per chunk
   constexpr int NB = CW / 8;                    // 8-column blocks per TMEM load
   const int e = warp - 2, g = e >> 3, h = (e >> 2) & 1, q = warp & 3;
   const int g4 = lane >> 2, c2 = 2 * (lane & 3);
@@ -520,38 +481,15 @@ __device__ __forceinline__ void dist_epilogue(const Dev& s, Shared& sh, uint32_t
       const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16) + buf * TNV;
       const int pc0 = solo ? (2 * g + h) * (TNV / 4) : h * (TNV / 2);   // first column of this part
       const int nch = (solo ? TNV / 4 : TNV / 2) / CW;
-      // two register sets: x for even chunks, y for odd ones
-      uint32_t x0[4 * NB], x1[4 * NB], y0[4 * NB], y1[4 * NB];
-      auto release = [&]() {
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&sh.tempty[buf]);       // the accumulator is free again
-      };
-      const uint32_t ta = tq + pc0;
-      tmem_issue16x256<NB>(ta, x0);
-      tmem_issue16x256<NB>(ta + (16u << 16), x1);
-      tmem_wait_regs(x0, x1);
-      if (!solo && nch == 1) release();
-      for (int ch = 0; ch < nch; ch += 2) {
-        const bool odd = ch + 1 < nch, next = ch + 2 < nch;
-        if (odd) {
-          tmem_issue16x256<NB>(ta + (ch + 1) * CW, y0);
-          tmem_issue16x256<NB>(ta + (ch + 1) * CW + (16u << 16), y1);
+      float v0[4 * NB], v1[4 * NB];
+      for (int ch = 0; ch < nch; ++ch) {
+        chunk_load<NB>(tq + pc0 + ch * CW, v0, v1);
+        if (!solo && ch == nch - 1) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sh.tempty[buf]);     // the accumulator is free again
         }
-        chunk_math<KIND, NB, -1>(x0, x1, m, pc0 + ch * CW + c2, rc, xi, negc, coef0, degree, acc);
-        if (odd) {
-          tmem_wait_regs(y0, y1);
-          if (!solo && ch + 1 == nch - 1) release();
-          if (next) {
-            tmem_issue16x256<NB>(ta + (ch + 2) * CW, x0);
-            tmem_issue16x256<NB>(ta + (ch + 2) * CW + (16u << 16), x1);
-          }
-          chunk_math<KIND, NB, 1>(y0, y1, m, pc0 + (ch + 1) * CW + c2, rc, xi, negc, coef0, degree, acc);
-          if (next) {
-            tmem_wait_regs(x0, x1);
-            if (!solo && ch + 2 == nch - 1) release();
-          }
-        }
+        chunk_math<KIND, NB>(v0, v1, m, pc0 + ch * CW + c2, rc, xi, negc, coef0, degree, acc);
       }
       if (!solo) {
         __syncwarp();
@@ -648,15 +586,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int R = (rows + TM - 1) / TM;
   const int nks = s.dp / KSE;
 
-  // Distance pass with s.pre_b: the producer stages the B tiles of its first
-  // item's first stages and that item's column metadata before the
-  // grid-dependency wait, while the batch gather still runs. They come from
-  // earlier steps; the batch rows and their metadata follow after the wait.
+  // Distance pass with s.pre_b: before the grid-dependency wait, while the
+  // batch gather still runs, the producer fetches the descriptors of its
+  // first 32 items (one per lane) and stages the B tiles of its first item's
+  // first stages and that item's column metadata. They come from earlier
+  // steps; the batch rows and their metadata follow after the wait.
   int npre = 0;                                  // first-item stages whose B tile is already on its way
+  int pyb_pre = 0;                               // this lane's first-round item: its B row
+  bool desc_pre = false;
   if constexpr (MODE == 0) {
     if (warp == 0 && s.pre_b) {
-      if (lane == 0 && (int)blockIdx.x < R * (*s.ntiles)) {
-        const int yb0 = s.tiles[blockIdx.x / R].row0;
+      const int tot0 = R * (*s.ntiles);
+      const int mine0 = (int)blockIdx.x + lane * (int)gridDim.x;
+      if (mine0 < tot0) pyb_pre = s.tiles[mine0 / R].row0;
+      desc_pre = true;
+      const int yb0 = __shfl_sync(0xffffffffu, pyb_pre, 0);
+      if (lane == 0 && (int)blockIdx.x < tot0) {
         MetaSlot& m = sh.meta.ring[0];
         mbar_expect_tx(&sh.mfull[0], META_BYTES);   // covers the row metadata issued after the wait
         bulk_load(m.col[0], s.yn + yb0, TNV * 4, &sh.mfull[0]);
@@ -693,7 +638,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (mine < total) {
           if constexpr (MODE == 0) {
             pya = (mine % R) * TM;
-            pyb = s.tiles[mine / R].row0;
+            pyb = (local == 0 && desc_pre) ? pyb_pre : s.tiles[mine / R].row0;
           } else {
             const PairTile pt = pair_tile<TNV>(s, mine);
             pya = (int)(pt.base + pt.rs);
