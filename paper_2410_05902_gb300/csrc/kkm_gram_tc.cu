@@ -247,36 +247,6 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   return y;
 }
 
-// 2^x on the FMA pipe, for two values at once (FP32, x >= -127 after the
-// clamp; the exponents here are <= 0 up to rounding). Cody-Waite range
-// reduction x = j + f, j = round(x) (adding 1.5 * 2^23 rounds to an integer
-// held in the low mantissa bits), f in [-1/2, 1/2]; 2^f is a degree-5
-// polynomial whose coefficients minimise the relative error on [-1/2, 1/2]
-// (minimax, from exp2_poly.py: 7.4e-8 exact, 2.1e-7 evaluated in FP32), and
-// 2^j is added to its exponent bits. Where x clamps to -127 the result is 0 or
-// a denormal of that size, as negligible as the 0 that ex2.approx.ftz gives.
-// The epilogue sends a quarter of its exponentials here and the rest to the
-// MUFU, whose 16 results per clock and SM otherwise bound it; the split of
-// exponentials between the two pipes follows FlashAttention-4 (Dao et al.).
-__device__ __forceinline__ float2 exp2_fma2(float2 x) {
-  constexpr float C0 = 1.0000001192092896f, C1 = 0.6931469440460205f, C2 = 0.24022120237350464f,
-                  C3 = 0.0555071160197258f, C4 = 0.009675559587776661f, C5 = 0.001327692880295217f;
-  constexpr float MAGIC = 12582912.0f;          // 1.5 * 2^23
-  x.x = fmaxf(x.x, -127.0f);
-  x.y = fmaxf(x.y, -127.0f);
-  const float2 t = __fadd2_rn(x, make_float2(MAGIC, MAGIC));
-  const float2 j = __fadd2_rn(t, make_float2(-MAGIC, -MAGIC));
-  const float2 f = __ffma2_rn(j, make_float2(-1.0f, -1.0f), x);
-  float2 p = __ffma2_rn(make_float2(C5, C5), f, make_float2(C4, C4));
-  p = __ffma2_rn(p, f, make_float2(C3, C3));
-  p = __ffma2_rn(p, f, make_float2(C2, C2));
-  p = __ffma2_rn(p, f, make_float2(C1, C1));
-  p = __ffma2_rn(p, f, make_float2(C0, C0));
-  // the low bits of t hold j + 2^22: shifted by 23 they leave j << 23 (mod 2^32)
-  return make_float2(__int_as_float(__float_as_int(p.x) + (__float_as_int(t.x) << 23)),
-                     __int_as_float(__float_as_int(p.y) + (__float_as_int(t.y) << 23)));
-}
-
 // Kernel values of one row against two columns from their Gram entries g.
 // Gaussian: rc = ||x||^2 * negc and cc = ||y||^2 * negc (negc = -log2(e)/kappa),
 //           K = 2^(rc + cc - 2 negc g). The exponent is -D^2 log2(e)/kappa with
@@ -285,32 +255,19 @@ __device__ __forceinline__ float2 exp2_fma2(float2 x) {
 // Laplacian: rc = ||x||^2, cc = ||y||^2, K = 2^(negc * sqrt(max(D^2, 0))).
 // Both give exactly 1 when the two rows are the same data point (K(x,x) = 1).
 // Linear and polynomial values of padding columns (yi = -2) are zeroed, as
-// those kernels are unbounded. POLY takes the exponential on the FMA pipe.
-template <int KIND, bool POLY = false>
+// those kernels are unbounded.
+template <int KIND>
 __device__ __forceinline__ float2 kernel_pair(float2 g, float rc, float2 cc, int xi, int2 yi, float negc,
                                               float coef0, int degree) {
   float2 k;
   if constexpr (KIND == K_GAUSS) {
     const float2 a = __ffma2_rn(g, make_float2(-2.0f * negc, -2.0f * negc), __fadd2_rn(make_float2(rc, rc), cc));
-    if constexpr (POLY) {
-      const float2 p = exp2_fma2(a);
-      k.x = xi == yi.x ? 1.0f : p.x;
-      k.y = xi == yi.y ? 1.0f : p.y;
-    } else {
-      k.x = xi == yi.x ? 1.0f : ex2_approx(a.x);
-      k.y = xi == yi.y ? 1.0f : ex2_approx(a.y);
-    }
+    k.x = xi == yi.x ? 1.0f : ex2_approx(a.x);
+    k.y = xi == yi.y ? 1.0f : ex2_approx(a.y);
   } else if constexpr (KIND == K_LAPLACE) {
     const float2 d2 = __ffma2_rn(g, make_float2(-2.0f, -2.0f), __fadd2_rn(make_float2(rc, rc), cc));
-    const float2 a = make_float2(sqrt_approx(fmaxf(d2.x, 0.0f)) * negc, sqrt_approx(fmaxf(d2.y, 0.0f)) * negc);
-    if constexpr (POLY) {
-      const float2 p = exp2_fma2(a);
-      k.x = xi == yi.x ? 1.0f : p.x;
-      k.y = xi == yi.y ? 1.0f : p.y;
-    } else {
-      k.x = xi == yi.x ? 1.0f : ex2_approx(a.x);
-      k.y = xi == yi.y ? 1.0f : ex2_approx(a.y);
-    }
+    k.x = xi == yi.x ? 1.0f : ex2_approx(sqrt_approx(fmaxf(d2.x, 0.0f)) * negc);
+    k.y = xi == yi.y ? 1.0f : ex2_approx(sqrt_approx(fmaxf(d2.y, 0.0f)) * negc);
   } else if constexpr (KIND == K_LINEAR) {
     k.x = yi.x == -2 ? 0.0f : g.x;
     k.y = yi.y == -2 ? 0.0f : g.y;
@@ -390,8 +347,7 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 // Distance-pass epilogue pieces. A chunk is CW accumulator columns of the
 // warp's 32 rows: chunk_load reads it from TMEM (two 16-lane loads), and
 // chunk_math adds w_y K(x, y) over its columns into the row sums acc[u] (rows
-// g4 + 8u of the quadrant, two columns per lane and 8-column block). Every
-// fourth block takes its exponentials on the FMA pipe.
+// g4 + 8u of the quadrant, two columns per lane and 8-column block).
 template <int NB>
 __device__ __forceinline__ void chunk_load(uint32_t taddr, float (&v0)[4 * NB], float (&v1)[4 * NB]) {
   tmem_ld16x256<NB>(taddr, v0);                 // rows g4, g4 + 8
@@ -399,17 +355,17 @@ __device__ __forceinline__ void chunk_load(uint32_t taddr, float (&v0)[4 * NB], 
   tmem_wait_ld();
 }
 
-template <int KIND, bool POLY, int NB>
+template <int KIND, int NB>
 __device__ __forceinline__ void block_math(const float (&v0)[4 * NB], const float (&v1)[4 * NB], int j, float2 w,
                                            float2 cc, int2 yi, const float (&rc)[4], const int (&xi)[4], float negc,
                                            float coef0, int degree, float2 (&acc)[4]) {
-  acc[0] = __ffma2_rn(w, kernel_pair<KIND, POLY>(make_float2(v0[4 * j], v0[4 * j + 1]), rc[0], cc, xi[0], yi, negc,
+  acc[0] = __ffma2_rn(w, kernel_pair<KIND>(make_float2(v0[4 * j], v0[4 * j + 1]), rc[0], cc, xi[0], yi, negc,
                                                  coef0, degree), acc[0]);
-  acc[1] = __ffma2_rn(w, kernel_pair<KIND, POLY>(make_float2(v0[4 * j + 2], v0[4 * j + 3]), rc[1], cc, xi[1], yi,
+  acc[1] = __ffma2_rn(w, kernel_pair<KIND>(make_float2(v0[4 * j + 2], v0[4 * j + 3]), rc[1], cc, xi[1], yi,
                                                  negc, coef0, degree), acc[1]);
-  acc[2] = __ffma2_rn(w, kernel_pair<KIND, POLY>(make_float2(v1[4 * j], v1[4 * j + 1]), rc[2], cc, xi[2], yi, negc,
+  acc[2] = __ffma2_rn(w, kernel_pair<KIND>(make_float2(v1[4 * j], v1[4 * j + 1]), rc[2], cc, xi[2], yi, negc,
                                                  coef0, degree), acc[2]);
-  acc[3] = __ffma2_rn(w, kernel_pair<KIND, POLY>(make_float2(v1[4 * j + 2], v1[4 * j + 3]), rc[3], cc, xi[3], yi,
+  acc[3] = __ffma2_rn(w, kernel_pair<KIND>(make_float2(v1[4 * j + 2], v1[4 * j + 3]), rc[3], cc, xi[3], yi,
                                                  negc, coef0, degree), acc[3]);
 }
 
@@ -424,8 +380,7 @@ __device__ __forceinline__ void chunk_math(const float (&v0)[4 * NB], const floa
     const float2 w = *reinterpret_cast<const float2*>(&m.col[1][c]);
     const int2 yi = *reinterpret_cast<const int2*>(&m.col[2][c]);
     const float2 cc = (KIND == K_GAUSS) ? __fmul2_rn(yn, make_float2(negc, negc)) : yn;
-    if ((j & 3) == 3) block_math<KIND, true, NB>(v0, v1, j, w, cc, yi, rc, xi, negc, coef0, degree, acc);
-    else block_math<KIND, false, NB>(v0, v1, j, w, cc, yi, rc, xi, negc, coef0, degree, acc);
+    block_math<KIND, NB>(v0, v1, j, w, cc, yi, rc, xi, negc, coef0, degree, acc);
   }
 }
 
