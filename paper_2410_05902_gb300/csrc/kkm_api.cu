@@ -334,6 +334,23 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
   s.wslots = c->use_tc ? 1 : 4;
   ALLOC(s.wpart, (size_t)s.max_pairs * s.wslots * 4);
   ALLOC(s.iter, 1); ALLOC(s.status, 1); ALLOC(s.stats, 3); ALLOC(s.obj, 1);
+  {
+    // the finalise step's rate sqrt(n/b) and 1/n, by the host's correctly rounded
+    // FP64 operations (the same values the device would compute)
+    double* rt = nullptr;
+    ALLOC(rt, 2 * ((int64_t)b + 1));
+    std::vector<double> h(2 * ((size_t)b + 1), 0.0);
+    for (int m = 1; m <= b; ++m) {
+      h[m] = 1.0 / (double)m;
+      h[b + 1 + m] = std::sqrt((double)m * s.inv_b);
+    }
+    e = cudaMemcpy(rt, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      c->err = std::string("rate table: ") + cudaGetErrorString(e);
+      return bail(KKM_ECUDA);
+    }
+    s.rtab = rt;
+  }
   ALLOC(c->d_init_idx, k);
   ALLOC(c->d_hbatch, b); ALLOC(c->d_hassign, b); ALLOC(c->d_hobj, 1);
   c->objpart_len = 1024;

@@ -143,6 +143,7 @@ struct Dev {
   int32_t* wpair_first; // [k]
   int32_t* wpair_cnt;   // [k]
   double* ncum;      // [k] points assigned to each center so far (N^j of the sklearn rate)
+  const double* rtab; // [2 (b + 1)]: 1/n at [n] and sqrt(n / b) at [b + 1 + n], n = 0..b (host-computed)
   double* wpart;     // [max_pairs][wslots][4 sums]: A, Bdd, E, M partials per tile
   int32_t wslots;    // partial slots per window-pass tile (4 SIMT, 1 tcgen05)
   int64_t* iter;     // [1] next iteration number

@@ -46,6 +46,54 @@ __device__ int block_exclusive_scan_1024(int v, int* total) {
   return excl;
 }
 
+// Exclusive scans of three ints per thread over a block of exactly 1024
+// threads, in one pass (two barriers plus one that frees the scratch).
+__device__ void block_exclusive_scan3_1024(const int (&v)[3], int (&excl)[3], int (&total)[3]) {
+  __shared__ int wsum3[32][3];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x[3] = {v[0], v[1], v[2]};
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int y = __shfl_up_sync(0xffffffffu, x[q], o);
+      if (lane >= o) x[q] += y;
+    }
+  if (lane == 31)
+    for (int q = 0; q < 3; ++q) wsum3[warp][q] = x[q];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      int t = wsum3[lane][q];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      wsum3[lane][q] = t;   // inclusive warp-total prefix
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    excl[q] = x[q] - v[q] + (warp > 0 ? wsum3[warp - 1][q] : 0);
+    total[q] = wsum3[31][q];
+  }
+  __syncthreads();
+}
+
+// Largest i in [0, n) with a[i] <= v, for a non-decreasing a with a[0] <= v.
+__device__ __forceinline__ int last_le(const int* a, int n, int v) {
+  int lo = 0, hi = n;                    // answer in [lo, hi)
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] <= v) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
 // Stores four consecutive source values at column c of a batch/support row in
 // the run's form and returns their contribution to ||row||^2 (the values the
 // Gram product will use: FP32, TF32, BF16 hi, or BF16 hi + lo). Per-element work
@@ -289,7 +337,8 @@ __global__ void __launch_bounds__(32 * AM_WARPS) k_argmin(Dev s, int rows, const
   }
 }
 
-__device__ void build_tiles_block(const Dev& s, int head, int size);
+__device__ int tile_count(const Dev& s, int& head, int& size);
+__device__ void tiles_write(const Dev& s, int first, int nt, int head, int size, int total);
 
 // Single CTA of 1024 threads. Stable counting sort of the batch by center,
 // alpha_i^j, <C_j, cm(B_j)>, and the per-center window plan: compaction,
@@ -308,6 +357,8 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out) {
   int16_t* sassign = (int16_t*)(sinner + b);// [b]   assignments (k <= 1024)
   int16_t* sperm = sassign + b;             // [b]   batch rows sorted by center (b <= 8192)
   uint16_t* wtab = (uint16_t*)(sperm + b);  // [32][k] per-warp counts / offsets of a chunk
+  __shared__ int s_rows;                    // support rows read by this step's distance pass
+  if (tid == 0) s_rows = 0;
   // per-center window state, loaded up front together with the assignments
   int c_head = 0, c_tail = 0, c_c1 = 0, c_wsum = 0, c_first = 0, c_nb = 0, c_oldest = 0;
   if (tid < k) {
@@ -391,13 +442,11 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out) {
       }
     }
   }
-  // support rows read by this step's distance pass
-  const int sz = tid < k ? c_tail - c_head : 0;
-  int s_total = 0;
-  block_exclusive_scan_1024(sz, &s_total);
+  if (tid < k) atomicAdd(&s_rows, c_tail - c_head);
 
   // window plan, one thread per center
   int npairs = 0, ncomp = 0;
+  int thead = 0, tsize = 0;                 // the window this update leaves (the next tile list)
   if (tid < k) {
     const int j = tid;
     const int n = cnt[j];
@@ -460,54 +509,46 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out) {
     }
     s.plan[j] = P;
     splan[j] = P;
+    thead = P.head_new;
+    tsize = P.tail_new - P.head_new;
   }
-  __syncthreads();
-  int ctotal = 0;
-  const int cfirst = block_exclusive_scan_1024(ncomp, &ctotal);
-  if (tid < k) s.comp_off[tid] = cfirst;
-  if (tid == 0) *s.comp_total = ctotal;
-  // the next step's tile list, from the windows this update leaves (the
-  // distance pass and argmin of this step have already consumed the current one)
-  {
-    int head = 0, size = 0;
-    if (tid < k) {
-      head = splan[tid].head_new;
-      size = splan[tid].tail_new - head;
-    }
-    build_tiles_block(s, head, size);
+  // one scan for the compaction offsets, the window-pass tiles and the next
+  // step's distance tiles (the distance pass and argmin of this step have
+  // already consumed the current tile list)
+  const int nt = tile_count(s, thead, tsize);
+  int v3[3] = {ncomp, npairs, nt}, ex3[3], tot3[3];
+  block_exclusive_scan3_1024(v3, ex3, tot3);
+  const int ptotal = tot3[1];
+  if (tid < k) {
+    s.comp_off[tid] = ex3[0];
+    s.wpair_first[tid] = ex3[1];
+    s.wpair_cnt[tid] = npairs;
+    base[tid] = ex3[1];
+    tot[tid] = npairs;
   }
   if (tid == 0) {
+    *s.comp_total = tot3[0];
+    *s.nwpairs = ptotal <= s.max_pairs ? ptotal : s.max_pairs;
+    if (ptotal > s.max_pairs) atomicOr(s.status, ST_CAPACITY);
     s.stats[0] += 1;
-    s.stats[1] += s_total;
+    s.stats[1] += s_rows;
     s.stats[2] += tiles_used;
     *s.iter += 1;
   }
-  int ptotal = 0;
-  const int pfirst = block_exclusive_scan_1024(npairs, &ptotal);
-  if (tid == 0) {
-    *s.nwpairs = ptotal <= s.max_pairs ? ptotal : s.max_pairs;
-    if (ptotal > s.max_pairs) atomicOr(s.status, ST_CAPACITY);
-  }
-  if (tid < k) {
-    s.wpair_first[tid] = pfirst;
-    s.wpair_cnt[tid] = npairs;
-    base[tid] = pfirst;
-    tot[tid] = npairs;
-  }
-  __syncthreads();
-  // the window-pass tile list: one warp per center, a lane per tile
-  for (int j = warp; j < k; j += 32) {
-    const int np = tot[j], pf = base[j];
-    if (np == 0 || pf + np > s.max_pairs) continue;
+  tiles_write(s, ex3[2], nt, thead, tsize, tot3[2]);   // its barrier also publishes base/tot
+  // the window-pass tile list: a thread per tile, its center by binary search
+  const int plim = ptotal <= s.max_pairs ? ptotal : s.max_pairs;
+  for (int e = tid; e < plim; e += 1024) {
+    const int j = last_le(base, k, e);
+    const int i = e - base[j];
+    if (i >= tot[j] || base[j] + tot[j] > s.max_pairs) continue;
     const Plan P = splan[j];
     const int TR = s.pair_rows, TC = s.pair_cols;
     const int nD = P.ndrop, nL = P.tail_new - P.head_c, n = P.cnt;
     const int cL = (nL + TC - 1) / TC, cB = (n + TC - 1) / TC;
     const int n0 = ((nD + TR - 1) / TR) * cL;
-    for (int e = lane; e < np; e += 32) {
-      const int f = e - n0;
-      s.wpairs[pf + e] = e < n0 ? WPair{j, 0, e / cL, e % cL} : WPair{j, 1, f / cB, f % cB};
-    }
+    const int f = i - n0;
+    s.wpairs[e] = i < n0 ? WPair{j, 0, i / cL, i % cL} : WPair{j, 1, f / cB, f % cB};
   }
 }
 
@@ -561,16 +602,23 @@ __global__ void k_move(Dev s) {
 // passes the window [head, head + size) of center j. Tiles start at head
 // rounded down to a multiple of 4 rows (16-byte aligned metadata); the rows
 // before head that this adds carry weight 0.
-__device__ void build_tiles_block(const Dev& s, int head, int size) {
-  __shared__ int t_first[1024], t_nt[1024], t_head[1024], t_size[1024];
-  const int tid = threadIdx.x, lane = tid & 31;
+// Tile counts of one center's window (thread j < k): the window [head,
+// head + size) is widened down to a multiple of 4 rows, so every tile starts
+// 4-aligned and its metadata copies are 16-byte aligned.
+__device__ int tile_count(const Dev& s, int& head, int& size) {
   if (size > 0) {
     size += head & 3;
     head &= ~3;
   }
-  const int nt = tid < s.k ? (size + s.tn - 1) / s.tn : 0;
-  int total = 0;
-  const int first = block_exclusive_scan_1024(nt, &total);
+  return (int)threadIdx.x < s.k ? (size + s.tn - 1) / s.tn : 0;
+}
+
+// Writes the tile list given each center's first tile and count (exclusive
+// scan over centers, total): tile_first/tile_cnt, ntiles, and one Tile per
+// thread, its center found by a binary search over the first tiles.
+__device__ void tiles_write(const Dev& s, int first, int nt, int head, int size, int total) {
+  __shared__ int t_first[1024], t_nt[1024], t_head[1024], t_size[1024];
+  const int tid = threadIdx.x;
   if (tid == 0) {
     *s.ntiles = total <= s.max_tiles ? total : s.max_tiles;
     if (total > s.max_tiles) atomicOr(s.status, ST_CAPACITY);
@@ -585,12 +633,22 @@ __device__ void build_tiles_block(const Dev& s, int head, int size) {
     t_size[tid] = size;
   }
   __syncthreads();
-  // one warp per center, a lane per tile
-  for (int j = tid >> 5; j < s.k; j += 32)
-    for (int t = lane; t < t_nt[j]; t += 32) {
-      const int c = t * s.tn;
-      s.tiles[t_first[j] + t] = Tile{j, (int32_t)((int64_t)j * s.cap + t_head[j] + c), min(s.tn, t_size[j] - c), 0};
+  const int lim = total <= s.max_tiles ? total : s.max_tiles;
+  for (int t = tid; t < lim; t += 1024) {
+    const int j = last_le(t_first, s.k, t);
+    const int i = t - t_first[j];
+    if (i < t_nt[j]) {
+      const int c = i * s.tn;
+      s.tiles[t] = Tile{j, (int32_t)((int64_t)j * s.cap + t_head[j] + c), min(s.tn, t_size[j] - c), 0};
     }
+  }
+}
+
+__device__ void build_tiles_block(const Dev& s, int head, int size) {
+  const int nt = tile_count(s, head, size);
+  int total = 0;
+  const int first = block_exclusive_scan_1024(nt, &total);
+  tiles_write(s, first, nt, head, size, total);
 }
 
 __device__ void build_tiles_block(const Dev& s) {
@@ -616,11 +674,21 @@ __global__ void __launch_bounds__(1024) k_build_tiles(Dev s) {
 //   [tail_c, tail_new) get alpha / b_j, rows that left the window get 0.
 // GB300 issues FP64 slowly, so the scalar FP64 work runs on one thread and the
 // per-row work is spread over the block, with independent loads in flight.
+// The scalar chain has no FP64 division or square root: 1/b_j and the beta
+// rate sqrt(b_j / b) come from a table the host fills at kkm_init, and the
+// thread's operands are loaded before the window sums so their latency overlaps.
 __global__ void __launch_bounds__(256) k_finalize(Dev s) {
   KKM_GRID_DEP_WAIT();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, j = blockIdx.x;
   const Plan P = s.plan[j];
   if (P.cnt == 0) return;
+  double ncum_j = 0.0, cn_old = 0.0, inv_n = 0.0, beta = 0.0;
+  if (tid == 0) {
+    ncum_j = s.ncum[j];
+    cn_old = s.cnorm[j];
+    inv_n = s.rtab[P.cnt];
+    beta = s.rtab[s.b + 1 + P.cnt];
+  }
   __shared__ double red[8][4];
   __shared__ double cm_s;
   __shared__ double keep_s, wnew_s;
@@ -642,35 +710,39 @@ __global__ void __launch_bounds__(256) k_finalize(Dev s) {
   }
   __syncthreads();
   const int n = P.cnt;
-  if (tid == 0) {
-    double q[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int w = 0; w < 8; ++w)
-      for (int t = 0; t < 4; ++t) q[t] += red[w][t];
-    const double A = q[0], Bdd = q[1], E = q[2], M = q[3];
-    const double dn = (double)n;
-    const double N = s.ncum[j] + dn;   // points assigned to j so far, this batch included
-    s.ncum[j] = N;
-    double a;
-    if (s.lr == 0) a = sqrt(dn * s.inv_b);
-    else if (s.lr == 2) a = dn / N;        // sklearn: the running-mean rate
-    else a = s.eta;
-    const double keep = 1.0 - a;
-    s.alpha[j] = a;
-    const double cmc = cm_s / dn;
-    s.cmc[j] = cmc;
-    // Sec. 4: ||C'||^2 = (1-a)^2 ||R||^2 + 2a(1-a) <R, m> + a^2 ||m||^2 with
-    // m = cm(B_j) and R = C - D, the part of the old center Eq. (1) keeps
-    const double m2 = M / (dn * dn);
-    const double R2 = s.cnorm[j] - 2.0 * A + Bdd;
-    const double Rm = cmc - E / dn;
-    const double cn = keep * keep * R2 + 2.0 * a * keep * Rm + a * a * m2;
-    s.cnorm[j] = cn;
-    s.cnorm32[j] = (float)cn;
-    s.head[j] = P.head_new;
-    s.tail[j] = P.tail_new;
-    s.c1[j] = P.c1_new;
-    keep_s = keep;
-    wnew_s = a / dn;
+  if (warp == 0) {
+    // lane t < 4 adds sum t over the eight warps, in warp order
+    double qt = 0.0;
+    if (lane < 4)
+      for (int w = 0; w < 8; ++w) qt += red[w][lane];
+    const double A = __shfl_sync(0xffffffffu, qt, 0), Bdd = __shfl_sync(0xffffffffu, qt, 1);
+    const double E = __shfl_sync(0xffffffffu, qt, 2), M = __shfl_sync(0xffffffffu, qt, 3);
+    if (lane == 0) {
+      const double dn = (double)n;
+      const double N = ncum_j + dn;      // points assigned to j so far, this batch included
+      s.ncum[j] = N;
+      double a;
+      if (s.lr == 0) a = beta;               // sqrt(b_j / b)
+      else if (s.lr == 2) a = dn / N;        // sklearn: the running-mean rate
+      else a = s.eta;
+      const double keep = 1.0 - a;
+      s.alpha[j] = a;
+      const double cmc = cm_s * inv_n;
+      s.cmc[j] = cmc;
+      // Sec. 4: ||C'||^2 = (1-a)^2 ||R||^2 + 2a(1-a) <R, m> + a^2 ||m||^2 with
+      // m = cm(B_j) and R = C - D, the part of the old center Eq. (1) keeps
+      const double m2 = M * inv_n * inv_n;
+      const double R2 = cn_old - 2.0 * A + Bdd;
+      const double Rm = cmc - E * inv_n;
+      const double cn = keep * keep * R2 + 2.0 * a * keep * Rm + a * a * m2;
+      s.cnorm[j] = cn;
+      s.cnorm32[j] = (float)cn;
+      s.head[j] = P.head_new;
+      s.tail[j] = P.tail_new;
+      s.c1[j] = P.c1_new;
+      keep_s = keep;
+      wnew_s = a * inv_n;
+    }
   }
   __syncthreads();
   const double keep = keep_s, wnew = wnew_s;
