@@ -98,6 +98,7 @@ __device__ __forceinline__ float sum16(float v) {
 template <int F>
 __global__ void __launch_bounds__(NT) k_dist_simt(Dev s, int rows) {
   KKM_GRID_DEP_WAIT();
+  KKM_LAUNCH_DEPENDENTS();
   __shared__ __align__(16) float As[BK][BM + 4];
   __shared__ __align__(16) float Bs[BK][BN + 4];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -142,6 +143,7 @@ __global__ void __launch_bounds__(NT) k_dist_simt(Dev s, int rows) {
 template <int F>
 __global__ void __launch_bounds__(NT) k_wgram_simt(Dev s) {
   KKM_GRID_DEP_WAIT();
+  KKM_LAUNCH_DEPENDENTS();
   __shared__ __align__(16) float As[BK][BM + 4];
   __shared__ __align__(16) float Bs[BK][BN + 4];
   __shared__ double red[4][NT / 32];

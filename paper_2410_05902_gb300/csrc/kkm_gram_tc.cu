@@ -578,6 +578,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   }
   KKM_GRID_DEP_WAIT();   // everything above reads only data of earlier steps
+  KKM_LAUNCH_DEPENDENTS();   // the next kernel may set itself up; it waits before reading our output
 
 
   const int total = (MODE == 0) ? R * (*s.ntiles) : *s.nwpairs;

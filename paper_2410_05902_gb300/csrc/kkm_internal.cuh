@@ -158,7 +158,10 @@ struct Dev {
 // anything the predecessor writes (a no-op when launched without the attribute).
 #define KKM_GRID_DEP_WAIT() asm volatile("griddepcontrol.wait;" ::: "memory")
 // Lets the next kernel in the stream start its pre-wait part. Issued only after
-// this kernel's own wait, so every kernel before it has completed by then.
+// this kernel's own wait, so every kernel before it has completed by then. The
+// step kernels all issue it; each of them waits at its first statement, except
+// the tcgen05 passes, whose pre-wait part sets up shared memory and TMEM and
+// (distance pass after the gather only) stages data of earlier steps.
 #define KKM_LAUNCH_DEPENDENTS() asm volatile("griddepcontrol.launch_dependents;" ::: "memory")
 
 // Launches `kern` with the programmatic-stream-serialization attribute.

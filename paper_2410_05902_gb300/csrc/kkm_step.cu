@@ -257,6 +257,7 @@ __global__ void __launch_bounds__(32 * AM_WARPS) k_argmin(Dev s, int rows, const
                                                           float* __restrict__ mind_out,
                                                           float* __restrict__ dist_out, int update) {
   KKM_GRID_DEP_WAIT();
+  KKM_LAUNCH_DEPENDENTS();   // the next kernel waits at its top (or only stages earlier steps' data)
   __shared__ float r_best[AM_WARPS][32], r_inner[AM_WARPS][32], r_f[AM_WARPS][32];
   __shared__ int r_j[AM_WARPS][32];
   __shared__ int c_first[1024], c_cnt[1024];
@@ -346,6 +347,7 @@ __device__ void tiles_write(const Dev& s, int first, int nt, int head, int size,
 // norm-recurrence Gram pass.
 __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out) {
   KKM_GRID_DEP_WAIT();
+  KKM_LAUNCH_DEPENDENTS();   // the next kernel waits at its top (or only stages earlier steps' data)
   extern __shared__ __align__(16) unsigned char smem[];
   const int k = s.k, b = s.b, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   Plan* splan = (Plan*)smem;                // [k]   this step's window plans
@@ -559,6 +561,7 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out) {
 // never overlap (see the capacity argument in kkm_internal.cuh).
 __global__ void k_move(Dev s) {
   KKM_GRID_DEP_WAIT();
+  KKM_LAUNCH_DEPENDENTS();   // the next kernel waits at its top (or only stages earlier steps' data)
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
   const int nwarps = gridDim.x * wpb;
@@ -679,6 +682,7 @@ __global__ void __launch_bounds__(1024) k_build_tiles(Dev s) {
 // thread's operands are loaded before the window sums so their latency overlaps.
 __global__ void __launch_bounds__(256) k_finalize(Dev s) {
   KKM_GRID_DEP_WAIT();
+  KKM_LAUNCH_DEPENDENTS();   // the next kernel waits at its top (or only stages earlier steps' data)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, j = blockIdx.x;
   const Plan P = s.plan[j];
   if (P.cnt == 0) return;
