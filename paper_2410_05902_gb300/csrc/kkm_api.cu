@@ -455,7 +455,7 @@ static kkm_status enqueue_step(kkm_ctx* c, cudaStream_t st, const int32_t* batch
   KKM_CU(kkm::launch_gather_batch(s, batch_idx, st), "batch gather");
   if (timed) KKM_CU(cudaEventRecord(c->ev[2 * c->ev_used], st), "timing event");
   for (int r = 0; r < (timed ? c->timing_reps : 1); ++r) {   // the pass is idempotent
-    if (c->use_tc) KKM_CU(kkm::launch_dist_tc(s, c->tmaps, s.b, st), "distance kernel (tcgen05)");
+    if (c->use_tc) KKM_CU(kkm::launch_dist_tc(s, c->tmaps, s.b, st, true), "distance kernel (tcgen05)");
     else KKM_CU(kkm::launch_dist_simt(s, s.b, st), "distance kernel");
   }
   if (timed) {

@@ -898,11 +898,15 @@ cudaError_t tc_prepare(Dev& s, void* maps_out) {
   return cudaSuccess;
 }
 
-cudaError_t launch_dist_tc(const Dev& s, const void* maps, int rows, cudaStream_t st) {
+cudaError_t launch_dist_tc(const Dev& s, const void* maps, int rows, cudaStream_t st, bool stage_early) {
   if (rows <= 0) return cudaSuccess;
-  if (s.tn == 64) return launch_mode<0, 64>(s, maps, rows, st);
-  if (s.tn == 256) return launch_mode<0, 256>(s, maps, rows, st);
-  return launch_mode<0, 128>(s, maps, rows, st);
+  // staging before the grid-dependency wait is only safe when the kernel just
+  // ahead writes none of what it stages (the gather, or this pass itself)
+  Dev d = s;
+  d.pre_b = (stage_early && s.pre_b) ? 1 : 0;
+  if (d.tn == 64) return launch_mode<0, 64>(d, maps, rows, st);
+  if (d.tn == 256) return launch_mode<0, 256>(d, maps, rows, st);
+  return launch_mode<0, 128>(d, maps, rows, st);
 }
 
 cudaError_t launch_wgram_tc(const Dev& s, const void* maps, cudaStream_t st) {

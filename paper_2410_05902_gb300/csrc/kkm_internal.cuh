@@ -91,8 +91,8 @@ struct Dev {
   int32_t num_sms;
   uint64_t seed;
   int32_t tn;        // support rows per distance tile
-  int32_t pre_b;     // distance pass: the support operand, its metadata and the tile list come from
-                     // kernels before the one just ahead, so they may be read before the grid-dependency wait
+  int32_t pre_b;     // distance pass: stage the support operand, its metadata and the tile list before
+                     // the grid-dependency wait (launch_dist_tc sets it per launch, only after the gather)
   int32_t pair_rows, pair_cols; // window-pass tile: row and column counts (64x64 SIMT, 128x64 tcgen05)
   int32_t bpad;      // rows of the batch buffers (>= b, multiple of 128)
   int32_t max_tiles, max_pairs;
@@ -279,7 +279,10 @@ cudaError_t launch_mind_sum(const Dev& s, int rows, double scale, double* out, c
 // maps: 256 bytes, 64-byte aligned, holding the two CUtensorMap of the pass
 bool tc_available();
 cudaError_t tc_prepare(Dev& s, void* maps);
-cudaError_t launch_dist_tc(const Dev& s, const void* maps, int rows, cudaStream_t st);
+// stage_early: the kernel just ahead on `st` (the batch gather, or this pass
+// itself) writes none of the support tiles, their metadata or the tile list,
+// so the pass may stage them before its grid-dependency wait.
+cudaError_t launch_dist_tc(const Dev& s, const void* maps, int rows, cudaStream_t st, bool stage_early = false);
 cudaError_t launch_wgram_tc(const Dev& s, const void* maps, cudaStream_t st);
 
 }  // namespace kkm

@@ -362,7 +362,10 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out) {
   __shared__ int s_rows;                    // support rows read by this step's distance pass
   if (tid == 0) s_rows = 0;
   // per-center window state, loaded up front together with the assignments
-  int c_head = 0, c_tail = 0, c_c1 = 0, c_wsum = 0, c_first = 0, c_nb = 0, c_oldest = 0;
+  // (and the two oldest entries of its block ring, so the usual step, which
+  // drops at most one block, needs no dependent load later)
+  int c_head = 0, c_tail = 0, c_c1 = 0, c_wsum = 0, c_first = 0, c_nb = 0;
+  int c_cnt0 = 0, c_cnt1 = 0, c_it0 = 0, c_it1 = 0, c_iter = 0;
   if (tid < k) {
     c_head = s.head[tid];
     c_tail = s.tail[tid];
@@ -370,7 +373,13 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out) {
     c_wsum = s.wsum[tid];
     c_first = s.blk_first[tid];
     c_nb = s.blk_num[tid];
-    c_oldest = s.blk_cnt[(int64_t)tid * s.nbcap + c_first];
+    c_iter = (int)(*s.iter);
+    const int64_t rb = (int64_t)tid * s.nbcap;
+    const int f1 = c_first + 1 == s.nbcap ? 0 : c_first + 1;
+    c_cnt0 = s.blk_cnt[rb + c_first];
+    c_cnt1 = s.blk_cnt[rb + f1];
+    c_it0 = s.blk_iter[rb + c_first];
+    c_it1 = s.blk_iter[rb + f1];
   }
   float macc = 0.0f;                        // this thread's share of sum_x min_j Delta
   for (int x = tid; x < b; x += 1024) {
@@ -380,6 +389,7 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out) {
   }
   const int tiles_used = *s.ntiles;         // tiles of this step's distance pass
   for (int j = tid; j < k; j += 1024) { cnt[j] = 0; base[j] = 0; }
+  for (int e = tid; e < 32 * k; e += 1024) wtab[e] = 0;
   __syncthreads();
   for (int x = tid; x < b; x += 1024) atomicAdd(&cnt[sassign[x]], 1);
   __syncthreads();
@@ -390,32 +400,35 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out) {
   if (tid < k) { coff[tid] = off; s.coff[tid] = off; s.counts[tid] = my; }
   if (tid == 0) s.coff[k] = total_rows;
   __syncthreads();
-  // stable ranks in chunks of 1024 rows
-  for (int c0 = 0; c0 < b; c0 += 1024) {
-    for (int e = tid; e < 32 * k; e += 1024) wtab[e] = 0;
-    __syncthreads();
+  // stable ranks in chunks of 1024 rows. wtab[w][j] holds warp w's count (then
+  // its exclusive prefix) for center j, tagged with the chunk (bits 11-14) so
+  // entries of earlier chunks read as 0 and the table is cleared only once.
+  // The running per-center base alternates between base and tot by chunk.
+  for (int c0 = 0, ci = 0; c0 < b; c0 += 1024, ++ci) {
+    const uint16_t tag = (uint16_t)((ci + 1) << 11);
+    int32_t* bcur = (ci & 1) ? tot : base;
+    int32_t* bnext = (ci & 1) ? base : tot;
     const int x = c0 + tid;
     const int j = x < b ? (int)sassign[x] : -1;
     const unsigned peers = __match_any_sync(0xffffffffu, j);
     const int rank = __popc(peers & ((1u << lane) - 1u));
-    if (j >= 0 && rank == 0) wtab[warp * k + j] = (uint16_t)__popc(peers);
+    if (j >= 0 && rank == 0) wtab[warp * k + j] = (uint16_t)(tag | __popc(peers));
     __syncthreads();
     // exclusive prefix of each center's per-warp counts over the 32 warps: one warp per center
     for (int jj = warp; jj < k; jj += 32) {
-      const int v = wtab[lane * k + jj];
-      int x = v;
+      const uint16_t e = wtab[lane * k + jj];
+      const int v = (e & 0x7800) == tag ? (int)(e & 0x7ff) : 0;
+      int xs = v;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
+        const int y = __shfl_up_sync(0xffffffffu, xs, o);
+        if (lane >= o) xs += y;
       }
-      wtab[lane * k + jj] = (uint16_t)(x - v);
-      if (lane == 31) tot[jj] = x;
+      wtab[lane * k + jj] = (uint16_t)(tag | (xs - v));
+      if (lane == 31) bnext[jj] = bcur[jj] + xs;
     }
     __syncthreads();
-    if (j >= 0) sperm[coff[j] + base[j] + wtab[warp * k + j] + rank] = (int16_t)x;
-    __syncthreads();
-    for (int jj = tid; jj < k; jj += 1024) base[jj] += tot[jj];
+    if (j >= 0) sperm[coff[j] + bcur[j] + (wtab[warp * k + j] & 0x7ff) + rank] = (int16_t)x;
     __syncthreads();
   }
   for (int r = tid; r < b; r += 1024) s.perm[r] = sperm[r];
@@ -473,12 +486,15 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out) {
       int first = c_first, nb = c_nb;
       int32_t* bi = s.blk_iter + (int64_t)j * s.nbcap;
       int32_t* bc = s.blk_cnt + (int64_t)j * s.nbcap;
+      const int f1 = c_first + 1 == s.nbcap ? 0 : c_first + 1;
       if (nb >= s.nbcap) {
         atomicOr(s.status, ST_CAPACITY);
       } else {
         const int slot = (first + nb) % s.nbcap;
-        bi[slot] = (int32_t)(*s.iter);
+        bi[slot] = c_iter;
         bc[slot] = n;
+        if (slot == first) { c_cnt0 = n; c_it0 = c_iter; }   // the ring was empty
+        else if (slot == f1) { c_cnt1 = n; c_it1 = c_iter; }
         ++nb;
       }
       int total = c_wsum + n;
@@ -486,16 +502,18 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out) {
       if (s.tau > 0) {
         // Q_i^j keeps the newest blocks whose counts reach tau: drop the
         // oldest block while the rest still sums to >= tau.
-        int oldest = (c_nb > 0) ? c_oldest : n;    // count of the oldest block in the ring
+        int oldest = c_cnt0, dropped = 0;          // count of the oldest block in the ring
         while (nb > 1 && total - oldest >= s.tau) {
           drop_rows += oldest;
           total -= oldest;
-          first = (first + 1) % s.nbcap;
+          first = first + 1 == s.nbcap ? 0 : first + 1;
           --nb;
-          oldest = bc[first];
+          ++dropped;
+          oldest = dropped == 1 ? c_cnt1 : bc[first];
         }
+        const int it_first = dropped == 0 ? c_it0 : (dropped == 1 ? c_it1 : bi[first]);
         // C_1 stays only while min Q_i^j = 1 (Eq. (1), Sec. 4.1).
-        if (P.c1_new && total >= s.tau && bi[first] != 1) {
+        if (P.c1_new && total >= s.tau && it_first != 1) {
           P.c1_new = 0;
           P.ndrop += 1;
         }
