@@ -246,14 +246,27 @@ def oracle_leg(X, kappa, init, forms, Xd, budget_s: float, prep: int = 4):
         times.append(time.perf_counter() - t0)
         i += 1
     t = statistics.median(times)
+    cores = oracle.kernels.num_threads()
+    # the same iterations on one core, a few of them (about a tenth of the budget)
+    t1 = []
+    oracle.kernels.set_threads(1)
+    t_start = time.perf_counter()
+    while (time.perf_counter() - t_start < max(0.1 * budget_s, t * cores) or not t1) and i < len(batches):
+        t0 = time.perf_counter()
+        ora.step(batches[i])
+        t1.append(time.perf_counter() - t0)
+        i += 1
+    oracle.kernels.set_threads(cores)
+    one_core = w.b * w.k / statistics.median(t1) if t1 else None
     desc = (f"FP64 oracle, full iterations {prep + 1}-{i} of the same workload from the same start "
-            f"(support S {min(S)}-{max(S)} rows), median over {len(times)} iterations")
+            f"(support S {min(S)}-{max(S)} rows), median over {len(times)} iterations on {cores} threads, "
+            f"then {len(t1)} on one thread")
     check = (f"teacher-forced iteration {prep + 1} (support S={S_check}): oracle state loaded into each "
              "GPU form, same batch, f_B and normwise distance error against the FP64 oracle")
     if ALGO == "table":
         check = (f"iteration {prep + 1} after {prep} iterations forced along the untruncated FP64 oracle's "
                  "trajectory (same batches and assignments): f_B and normwise distance error")
-    return w.b * w.k / t, oracle.kernels.num_threads(), desc, acc, check
+    return w.b * w.k / t, cores, desc, acc, check, one_core
 
 
 def run_reference(args):
@@ -402,6 +415,19 @@ def roofline(form, S, kernel_ms, n_rec, single_ms=None):
                 "kernel": f"k_dist_tc ({form}: tcgen05 Gram + kernel values + weighted sums)",
                 "peak_source": f"bf16_tflops burst, {peaks['source']}"}
     roof["traffic"] = measured_traffic(form)
+    if form != "fp32":
+        # the same against the sustained BF16 rate (a kernel timed inside a long step)
+        sus = peaks.get("bf16_tflops_sustained")
+        if sus:
+            sus = sus * (1.1 / 2.25 if form == "tf32" else 1.0)
+            roof["frac_sustained"] = achieved / sus
+    if KERNEL in ("gaussian", "laplacian") and ALGO != "table":
+        # exponentials: one per batch-point x support-row pair, against the MUFU's
+        # nominal 16 ex2 a clock per SM at the maximum SM clock
+        exp_rate = (w.b * S) / (kernel_ms / 1e3)
+        exp_peak = 152 * 16 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+        roof["exp_frac"] = exp_rate / exp_peak
+        roof["exp_peak_source"] = "152 SMs x 16 ex2/clk x max SM clock (nominal MUFU rate, derived)"
     roof["flops_per_launch"] = flops
     roof["avg_launch_ms"] = kernel_ms
     roof["launches_timed"] = n_rec
@@ -454,7 +480,7 @@ def run_ours(args):
     forms = ["fp32", "bf16x3", "tf32", "bf16"] if args.precision == "auto" else [args.precision]
     res = {f: time_form(f, args, X, Xd, kappa, init, rank, world, dev, barrier) for f in forms}
     if rank == 0:
-        cpu_v, cores, desc, acc, check = oracle_leg(X, kappa, init, forms, Xd, args.oracle_budget)
+        cpu_v, cores, desc, acc, check, one_core = oracle_leg(X, kappa, init, forms, Xd, args.oracle_budget)
         ok = [f for f in forms if acc[f]["obj_rel_err"] <= OBJ_BAR]
         chosen = max(ok, key=lambda f: res[f]["value"]) if ok else max(forms, key=lambda f: res[f]["value"])
         r = res[chosen]
@@ -475,7 +501,8 @@ def run_ours(args):
                       for f in forms},
             "accuracy_check": check,
             "roofline": roofline(chosen, r["S"], r["kernel_ms"], r["kernel_launches"], r["kernel_ms_single"]),
-            "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+                             "value_one_core": one_core},
             "e2e": {"value": r["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": 4 * w.b,
                     "d2h_bytes_per_step": 4 * w.b + 8, "steps": r["e2e_steps"],
                     "call": "kkm_step_host (pinned host batch indices in, assignments and f_B out, synchronised)"},
@@ -535,6 +562,8 @@ def run_batching(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     # the group orders its work on a stream of its own: bracket it with syncs
     torch.cuda.synchronize(dev)
+    for r in runs:
+        r.launches(reset=True)
     clocks.start()
     t0 = time.perf_counter()
     for _ in range(args.steps):
@@ -542,6 +571,7 @@ def run_batching(args):
     g.sync()
     wall = time.perf_counter() - t0
     clk = clocks.stop()
+    launches = sum(r.launches(reset=True) for r in runs)
     per_step = sum(sp.b * sp.k for sp in specs)
     value = per_step * args.steps / wall
     print(json.dumps({
@@ -557,7 +587,7 @@ def run_batching(args):
                    "distances_per_step": per_step, "state_prep_iters": PREP_ITERS,
                    "l2": "inputs larger than L2 (the 64 datasets hold about "
                          f"{sum(int(d[0].numel()) for d in data) * 4 / 1e9:.1f} GB)"},
-        "autotune": tune, "gpu_launches": 7 * len(runs) * args.steps, "clocks": clk,
+        "autotune": tune, "gpu_launches": launches, "clocks": clk,
     }))
     g.close()
     for r in runs:

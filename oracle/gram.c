@@ -74,3 +74,14 @@ int oracle_num_threads(void) {
   return 1;
 #endif
 }
+
+/* Sets the number of threads later calls use (a timing knob; the results do
+ * not depend on it, as no reduction crosses threads). */
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+  extern void omp_set_num_threads(int);
+  omp_set_num_threads(n > 0 ? n : 1);
+#else
+  (void)n;
+#endif
+}

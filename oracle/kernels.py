@@ -80,6 +80,7 @@ def _load():
                                                ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                                ctypes.c_double, ctypes.c_int, dp]
             lib.oracle_num_threads.restype = ctypes.c_int
+            lib.oracle_set_threads.argtypes = [ctypes.c_int]
             _lib = lib
     return _lib
 
@@ -87,6 +88,11 @@ def _load():
 def num_threads() -> int:
     """Threads the C helper uses (OpenMP's maximum, or 1 without OpenMP)."""
     return int(_load().oracle_num_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads later calls of the C helper use (timing only; results do not depend on it)."""
+    _load().oracle_set_threads(int(n))
 
 
 def _rows(a) -> np.ndarray:
