@@ -334,12 +334,6 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
   s.wslots = c->use_tc ? 1 : 4;
   ALLOC(s.wpart, (size_t)s.max_pairs * s.wslots * 4);
   ALLOC(s.iter, 1); ALLOC(s.status, 1); ALLOC(s.stats, 3); ALLOC(s.obj, 1);
-  ALLOC(s.rt_done, s.bpad / 128);
-  e = cudaMemset(s.rt_done, 0, (size_t)(s.bpad / 128) * sizeof(int32_t));
-  if (e != cudaSuccess) {
-    c->err = std::string("device memset: ") + cudaGetErrorString(e);
-    return bail(KKM_ECUDA);
-  }
   {
     // the finalise step's rate sqrt(n/b) and 1/n, by the host's correctly rounded
     // FP64 operations (the same values the device would compute)
@@ -431,10 +425,6 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
   return KKM_OK;
 }
 
-// The distance pass runs the step's argmin itself when the per-row work is
-// small: k <= 32 centers (each row then reads at most a few dozen partials).
-static bool fuse_argmin(const kkm_ctx* c) { return c->use_tc && !c->tab && c->s.k <= 32; }
-
 // The kernel sequence of one step, queued on `st`.
 static kkm_status enqueue_step(kkm_ctx* c, cudaStream_t st, const int32_t* batch_idx,
                                const int32_t* forced_assign, int32_t* assign_out, float* dist_out,
@@ -464,19 +454,15 @@ static kkm_status enqueue_step(kkm_ctx* c, cudaStream_t st, const int32_t* batch
   // with batch_idx NULL the gather draws the indices itself (SplitMix64)
   KKM_CU(kkm::launch_gather_batch(s, batch_idx, st), "batch gather");
   if (timed) KKM_CU(cudaEventRecord(c->ev[2 * c->ev_used], st), "timing event");
-  // with few centers the argmin runs in the distance pass's last CTA of each batch tile
-  const bool fuse = fuse_argmin(c);
-  const kkm::ArgFuse af{forced_assign, assign_out, dist_out, fuse ? 1 : 0};
   for (int r = 0; r < (timed ? c->timing_reps : 1); ++r) {   // the pass is idempotent
-    if (c->use_tc) KKM_CU(kkm::launch_dist_tc(s, c->tmaps, s.b, st, true, af), "distance kernel (tcgen05)");
+    if (c->use_tc) KKM_CU(kkm::launch_dist_tc(s, c->tmaps, s.b, st, true), "distance kernel (tcgen05)");
     else KKM_CU(kkm::launch_dist_simt(s, s.b, st), "distance kernel");
   }
   if (timed) {
     KKM_CU(cudaEventRecord(c->ev[2 * c->ev_used + 1], st), "timing event");
     c->ev_reps[c->ev_used++] = c->timing_reps;
   }
-  if (!fuse)
-    KKM_CU(kkm::launch_argmin(s, s.b, forced_assign, assign_out, nullptr, dist_out, true, st), "argmin");
+  KKM_CU(kkm::launch_argmin(s, s.b, forced_assign, assign_out, nullptr, dist_out, true, st), "argmin");
   KKM_CU(kkm::launch_sort_plan(s, batch_obj_out, st), "sort/plan");
   KKM_CU(kkm::launch_move(s, st), "row moves");
   if (c->use_tc) KKM_CU(kkm::launch_wgram_tc(s, c->tmaps, st), "window Gram (tcgen05)");
@@ -520,8 +506,8 @@ KKM_API kkm_status kkm_step(kkm_ctx* c, const int32_t* batch_idx, const int32_t*
     if (st != KKM_OK) return st;
     ++c->eager_steps;
   }
-  // gather, distance, argmin (unless fused), sort/plan, moves, window Gram, finalize (+ timing repeats)
-  c->launches += (fuse_argmin(c) ? 6 : 7) + (timed ? c->timing_reps - 1 : 0);
+  // gather, distance, argmin, sort/plan, moves, window Gram, finalize (+ timing repeats)
+  c->launches += 7 + (timed ? c->timing_reps - 1 : 0);
   ++c->iteration;
   return KKM_OK;
 }
@@ -1123,7 +1109,7 @@ KKM_API kkm_status kkm_group_step(kkm_group* g) {
     if (e != cudaSuccess) return gfail(g, KKM_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
   }
   for (kkm_ctx* c : g->runs) {
-    c->launches += fuse_argmin(c) ? 6 : 7;
+    c->launches += 7;
     ++c->iteration;
   }
   ++g->steps;

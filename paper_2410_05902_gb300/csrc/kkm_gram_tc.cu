@@ -87,11 +87,6 @@ struct Shared {
     float warp[NEPI][5][32];                    // window pass: per epilogue warp (load_pair_meta)
   } meta;
   float red[768];                                // distance pass: row sums of column parts (dist_epilogue)
-  // fused argmin (distance pass): per-warp candidates of a batch tile's rows,
-  // [warp][lane]; group g uses warps 8g..8g+7, a single-item CTA all sixteen
-  float am_best[NEPI][32], am_inner[NEPI][32], am_f[NEPI][32];
-  int am_j[NEPI][32];
-  int am_last[2];
   float wred[2][NEPI][4];                       // window pass: per-warp sums (item parity, warp, sum)
 };
 
@@ -389,69 +384,6 @@ __device__ __forceinline__ void chunk_math(const float (&v0)[4 * NB], const floa
   }
 }
 
-// Argmin of batch tile rt's rows by NW epilogue warps (warp index wi among
-// them): lane = row within a 32-row slice, slice = wi % 4, and the warp takes
-// centers wi / 4, wi / 4 + NW / 4, ... Per center the tile partials are summed
-// in four accumulators by tile index mod 4, combined as (i0 + i1) + (i2 + i3);
-// ties keep the lowest center. The partials come from other CTAs, so they are
-// read from L2 (ld.global.cg) after the acquiring fence.
-template <int NW>
-__device__ __forceinline__ void fused_argmin(const Dev& s, Shared& sh, const ArgFuse& af, int rt, int rows, int wi,
-                                             int wbase, int lane, uint32_t bar_id) {
-  const int slice = wi & 3, stripe = wi >> 2;
-  const int x = rt * TM + slice * 32 + lane;
-  const bool live = x < rows;
-  const int xr = live ? x : 0;
-  const float kxx = (float)kernel_self(s.kind, (double)__ldcg(s.xbn + xr), s.coef0, s.degree);
-  const int fa = af.forced ? af.forced[xr] : -1;
-  float best = 3.0e38f, best_inner = 0.0f, f_inner = 0.0f;
-  int bj = 0x7fffffff;
-  const int64_t ld = s.bpad;
-  for (int j = stripe; j < s.k; j += NW / 4) {
-    const int t0 = s.tile_first[j], nt = s.tile_cnt[j];
-    float i0 = 0.0f, i1 = 0.0f, i2 = 0.0f, i3 = 0.0f;
-    for (int t = 0; t < nt; t += 4) {
-      i0 += __ldcg(s.part + (int64_t)(t0 + t) * ld + xr);
-      if (t + 1 < nt) i1 += __ldcg(s.part + (int64_t)(t0 + t + 1) * ld + xr);
-      if (t + 2 < nt) i2 += __ldcg(s.part + (int64_t)(t0 + t + 2) * ld + xr);
-      if (t + 3 < nt) i3 += __ldcg(s.part + (int64_t)(t0 + t + 3) * ld + xr);
-    }
-    const float inner = (i0 + i1) + (i2 + i3);
-    const float dist = fmaf(-2.0f, inner, kxx + s.cnorm32[j]);
-    if (af.dist_out && live) af.dist_out[(int64_t)x * s.k + j] = dist;
-    if (dist < best) { best = dist; bj = j; best_inner = inner; }   // j increases: ties keep the lowest
-    if (j == fa) f_inner = inner;
-  }
-  const int wslot = wbase + wi;
-  sh.am_best[wslot][lane] = best;
-  sh.am_j[wslot][lane] = bj;
-  sh.am_inner[wslot][lane] = best_inner;
-  sh.am_f[wslot][lane] = f_inner;
-  asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "n"(32 * NW) : "memory");
-  if (stripe != 0 || !live) return;
-  for (int o = 1; o < NW / 4; ++o) {
-    const int os = wbase + slice + 4 * o;
-    const float ob = sh.am_best[os][lane];
-    const int oj = sh.am_j[os][lane];
-    if (ob < best || (ob == best && oj < bj)) { best = ob; bj = oj; best_inner = sh.am_inner[os][lane]; }
-    f_inner += sh.am_f[os][lane];   // only the warp owning fa is non-zero
-  }
-  int a = bj;
-  float a_inner = best_inner;
-  if (af.forced) {
-    if (fa < 0 || fa >= s.k) {
-      atomicOr(s.status, ST_BAD_ASSIGN);
-    } else {
-      a = fa;
-      a_inner = f_inner;
-    }
-  }
-  if (af.assign_out) af.assign_out[x] = bj;
-  s.assign[x] = a;
-  s.mind[x] = best;
-  s.inner_a[x] = a_inner;
-}
-
 // Distance-pass epilogue (warps 2-17): two groups of eight warps, two per TMEM
 // lane quadrant. Group g = (warp - 2) / 8 takes this CTA's items of parity g
 // (accumulator buffer g, and the metadata slots of those items), so one
@@ -464,7 +396,7 @@ __device__ __forceinline__ void fused_argmin(const Dev& s, Shared& sh, const Arg
 // memory (by the group's item parity), and part 0 writes part[tile][row].
 template <int KIND, int TNV>
 __device__ __forceinline__ void dist_epilogue(const Dev& s, Shared& sh, uint32_t tmem, int total, int R, int rows,
-                                              int warp, int lane, const ArgFuse& af) {
+                                              int warp, int lane) {
   constexpr int CW = TNV / 4 < 32 ? TNV / 4 : 32;   // columns per chunk
   constexpr int NB = CW / 8;                    // 8-column blocks per TMEM load
   const int e = warp - 2, g = e >> 3, h = (e >> 2) & 1, q = warp & 3;
@@ -546,30 +478,6 @@ __device__ __forceinline__ void dist_epilogue(const Dev& s, Shared& sh, uint32_t
       asm volatile("bar.sync %0, 64;" ::"r"(1 + g * 4 + q) : "memory");
       if (h == 0 && !dead && row < rows) s.part[(int64_t)(item / R) * s.bpad + row] = f + slot[rq];
     }
-    if (af.on) {
-      // count the item on its batch tile; the last of the tile's items runs its argmin
-      const int rt = item % R, T = total / R;
-      const uint32_t bid = solo ? 15u : 13u + (uint32_t)g;
-      const int nw = solo ? NEPI : NEPI / 2;
-      __threadfence();                                     // this warp's partials, before the count
-      asm volatile("bar.sync %0, %1;" ::"r"(bid), "r"(32 * nw) : "memory");
-      const bool leader = solo ? (e == 0) : ((e & 7) == 0);
-      if (leader && lane == 0) {
-        int last = 0;
-        if (!dead) {
-          const int prev = atomicAdd(&s.rt_done[rt], 1);
-          last = prev == T - 1;
-          if (last) s.rt_done[rt] = 0;                     // ready for the next launch
-        }
-        sh.am_last[solo ? 0 : g] = last;
-      }
-      asm volatile("bar.sync %0, %1;" ::"r"(bid), "r"(32 * nw) : "memory");
-      if (sh.am_last[solo ? 0 : g]) {
-        __threadfence();                                   // the other CTAs' partials, after the count
-        if (solo) fused_argmin<NEPI>(s, sh, af, rt, rows, e, 0, lane, bid);
-        else fused_argmin<NEPI / 2>(s, sh, af, rt, rows, e & 7, 8 * g, lane, bid);
-      }
-    }
   }
 }
 
@@ -590,7 +498,7 @@ __device__ __forceinline__ void dist_epilogue(const Dev& s, Shared& sh, uint32_t
 template <int KIND, int MODE, int OP, int TNV>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_dist_tc(Dev s, int rows, const __grid_constant__ CUtensorMap tmA,
-              const __grid_constant__ CUtensorMap tmB, ArgFuse af) {
+              const __grid_constant__ CUtensorMap tmB) {
   constexpr bool X3 = OP == OP_X3;
   constexpr int KSE = OP == OP_TF32 ? 32 : KS;   // operand elements per slice row
   extern __shared__ uint8_t smem_raw[];
@@ -787,7 +695,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   } else if constexpr (MODE == 0) {
     // ---------------------------------------------------------------- epilogue
-    dist_epilogue<KIND, TNV>(s, sh, tmem, total, R, rows, warp, lane, af);
+    dist_epilogue<KIND, TNV>(s, sh, tmem, total, R, rows, warp, lane);
   } else {
     // ---------------------------------------------------------------- epilogue
     // NEPI warps, NH per TMEM lane quadrant: warp e = warp - 2 reads lanes
@@ -912,8 +820,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 template <int KIND, int MODE, int OP, int TNV>
-cudaError_t launch_form(const Dev& s, const CUtensorMap& a, const CUtensorMap& b, int rows, cudaStream_t st,
-                        const ArgFuse& af) {
+cudaError_t launch_form(const Dev& s, const CUtensorMap& a, const CUtensorMap& b, int rows, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_dist_tc<KIND, MODE, OP, TNV>,
@@ -925,30 +832,29 @@ cudaError_t launch_form(const Dev& s, const CUtensorMap& a, const CUtensorMap& b
   // have: small runs then leave SMs free for the kernels of other runs
   const int64_t most = MODE == 0 ? (int64_t)((rows + TM - 1) / TM) * s.max_tiles : (int64_t)s.max_pairs;
   const int grid = (int)(most < s.num_sms ? (most > 0 ? most : 1) : s.num_sms);
-  return launch_pdl(k_dist_tc<KIND, MODE, OP, TNV>, dim3(grid), dim3(NTHREADS), SMEM_BYTES, st, s, rows, a, b, af);
+  return launch_pdl(k_dist_tc<KIND, MODE, OP, TNV>, dim3(grid), dim3(NTHREADS), SMEM_BYTES, st, s, rows, a, b);
 }
 
 template <int MODE, int OP, int TNV>
-cudaError_t launch_kind(const Dev& s, const CUtensorMap& a, const CUtensorMap& b, int rows, cudaStream_t st,
-                        const ArgFuse& af) {
+cudaError_t launch_kind(const Dev& s, const CUtensorMap& a, const CUtensorMap& b, int rows, cudaStream_t st) {
   switch (s.kind) {
-    case K_GAUSS: return launch_form<K_GAUSS, MODE, OP, TNV>(s, a, b, rows, st, af);
-    case K_LAPLACE: return launch_form<K_LAPLACE, MODE, OP, TNV>(s, a, b, rows, st, af);
-    case K_LINEAR: return launch_form<K_LINEAR, MODE, OP, TNV>(s, a, b, rows, st, af);
-    default: return launch_form<K_POLY, MODE, OP, TNV>(s, a, b, rows, st, af);
+    case K_GAUSS: return launch_form<K_GAUSS, MODE, OP, TNV>(s, a, b, rows, st);
+    case K_LAPLACE: return launch_form<K_LAPLACE, MODE, OP, TNV>(s, a, b, rows, st);
+    case K_LINEAR: return launch_form<K_LINEAR, MODE, OP, TNV>(s, a, b, rows, st);
+    default: return launch_form<K_POLY, MODE, OP, TNV>(s, a, b, rows, st);
   }
 }
 
 // maps: [0] batch rows, 128-row boxes; support rows with [1] 128-row, [2] 64-row, [3] 256-row boxes
 template <int MODE, int TNV>
-cudaError_t launch_mode(const Dev& s, const void* maps_in, int rows, cudaStream_t st, const ArgFuse& af) {
+cudaError_t launch_mode(const Dev& s, const void* maps_in, int rows, cudaStream_t st) {
   const CUtensorMap* m = static_cast<const CUtensorMap*>(maps_in);
   const CUtensorMap& a = (MODE == 0) ? m[0] : m[1];
   const CUtensorMap& b = (TNV == 256) ? m[3] : (TNV == 128) ? m[1] : m[2];
   switch (s.form) {
-    case FORM_BF16X3: return launch_kind<MODE, OP_X3, TNV>(s, a, b, rows, st, af);
-    case FORM_TF32: return launch_kind<MODE, OP_TF32, TNV>(s, a, b, rows, st, af);
-    default: return launch_kind<MODE, OP_BF16, TNV>(s, a, b, rows, st, af);
+    case FORM_BF16X3: return launch_kind<MODE, OP_X3, TNV>(s, a, b, rows, st);
+    case FORM_TF32: return launch_kind<MODE, OP_TF32, TNV>(s, a, b, rows, st);
+    default: return launch_kind<MODE, OP_BF16, TNV>(s, a, b, rows, st);
   }
 }
 
@@ -992,20 +898,19 @@ cudaError_t tc_prepare(Dev& s, void* maps_out) {
   return cudaSuccess;
 }
 
-cudaError_t launch_dist_tc(const Dev& s, const void* maps, int rows, cudaStream_t st, bool stage_early,
-                           const ArgFuse& af) {
+cudaError_t launch_dist_tc(const Dev& s, const void* maps, int rows, cudaStream_t st, bool stage_early) {
   if (rows <= 0) return cudaSuccess;
   // staging before the grid-dependency wait is only safe when the kernel just
   // ahead writes none of what it stages (the gather, or this pass itself)
   Dev d = s;
   d.pre_b = (stage_early && s.pre_b) ? 1 : 0;
-  if (d.tn == 64) return launch_mode<0, 64>(d, maps, rows, st, af);
-  if (d.tn == 256) return launch_mode<0, 256>(d, maps, rows, st, af);
-  return launch_mode<0, 128>(d, maps, rows, st, af);
+  if (d.tn == 64) return launch_mode<0, 64>(d, maps, rows, st);
+  if (d.tn == 256) return launch_mode<0, 256>(d, maps, rows, st);
+  return launch_mode<0, 128>(d, maps, rows, st);
 }
 
 cudaError_t launch_wgram_tc(const Dev& s, const void* maps, cudaStream_t st) {
-  return launch_mode<1, 64>(s, maps, 0, st, ArgFuse{});
+  return launch_mode<1, 64>(s, maps, 0, st);
 }
 
 }  // namespace kkm

@@ -144,7 +144,6 @@ struct Dev {
   int32_t* wpair_cnt;   // [k]
   double* ncum;      // [k] points assigned to each center so far (N^j of the sklearn rate)
   const double* rtab; // [2 (b + 1)]: 1/n at [n] and sqrt(n / b) at [b + 1 + n], n = 0..b (host-computed)
-  int32_t* rt_done;  // [bpad / 128] items of the distance pass finished per batch tile (fused argmin)
   double* wpart;     // [max_pairs][wslots][4 sums]: A, Bdd, E, M partials per tile
   int32_t wslots;    // partial slots per window-pass tile (4 SIMT, 1 tcgen05)
   int64_t* iter;     // [1] next iteration number
@@ -280,22 +279,10 @@ cudaError_t launch_mind_sum(const Dev& s, int rows, double scale, double* out, c
 // maps: 256 bytes, 64-byte aligned, holding the two CUtensorMap of the pass
 bool tc_available();
 cudaError_t tc_prepare(Dev& s, void* maps);
-// The argmin fused into the tcgen05 distance pass (on != 0): the last CTA to
-// finish a batch tile's items computes Delta(x, C_j), the argmin and the
-// step's per-row outputs (assign, mind, inner_a; update mode) for that tile's
-// rows, as k_argmin does. Batch-tile counters live in Dev::rt_done.
-struct ArgFuse {
-  const int32_t* forced;       // teacher-forced assignments or null
-  int32_t* assign_out;         // argmin per row or null
-  float* dist_out;             // [rows][k] distances or null
-  int on;
-};
-
 // stage_early: the kernel just ahead on `st` (the batch gather, or this pass
 // itself) writes none of the support tiles, their metadata or the tile list,
 // so the pass may stage them before its grid-dependency wait.
-cudaError_t launch_dist_tc(const Dev& s, const void* maps, int rows, cudaStream_t st, bool stage_early = false,
-                           const ArgFuse& af = ArgFuse{});
+cudaError_t launch_dist_tc(const Dev& s, const void* maps, int rows, cudaStream_t st, bool stage_early = false);
 cudaError_t launch_wgram_tc(const Dev& s, const void* maps, cudaStream_t st);
 
 }  // namespace kkm
