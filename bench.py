@@ -505,7 +505,7 @@ def run_ours(args):
                              "value_one_core": one_core},
             "e2e": {"value": r["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": 4 * w.b,
                     "d2h_bytes_per_step": 4 * w.b + 8, "steps": r["e2e_steps"],
-                    "call": "kkm_step_host (pinned host batch indices in, assignments and f_B out, synchronised)"},
+                    "call": "kkm_step_host (host batch indices in, assignments and f_B out, synchronised; they cross through the context's device-mapped page-locked staging area)"},
             "gpu_launches": r["launches"],
             "clocks": r["clocks"],
         }

@@ -221,10 +221,14 @@ kkm_status kkm_set_cum_counts(kkm_ctx* ctx, const int64_t* counts);
 kkm_status kkm_graph_enable(kkm_ctx* ctx, int32_t enable);
 
 /* kkm_step_host -- kkm_step with host buffers, for callers that keep the
- * batch on the CPU. It copies the b indices in (batch_idx may be NULL for the
- * built-in sampler), runs the step, copies the assignments and f_{B_i}(C_i)
- * back (either output may be NULL), and synchronises the stream. Page-locked
- * host buffers give the fastest copies. */
+ * batch on the CPU. batch_idx (b indices; NULL for the built-in sampler),
+ * assign_out (b) and batch_obj_out (f_{B_i}(C_i)) are ordinary host memory;
+ * either output may be NULL. The values pass through a staging area of the
+ * context in page-locked, device-mapped host memory: the call copies the
+ * indices into it, the step's kernels read them and write the results there
+ * across the CPU-GPU link (no copy-engine transfer), and after the stream
+ * synchronises the call copies the results out. It returns once the step is
+ * done. */
 kkm_status kkm_step_host(kkm_ctx* ctx, const int32_t* batch_idx, int32_t* assign_out,
                          double* batch_obj_out);
 

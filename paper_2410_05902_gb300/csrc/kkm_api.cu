@@ -23,6 +23,7 @@ using kkm::Dev;
 struct kkm_ctx {
   Dev s{};
   cudaStream_t stream = nullptr;
+  int32_t* h_status = nullptr;      // page-locked copy of the device status word (read after each sync)
   int device = 0;
   int64_t iteration = 1;
   int32_t max_iters = 0;
@@ -32,9 +33,17 @@ struct kkm_ctx {
   std::string err;
   std::vector<void*> allocs;
   int32_t* d_init_idx = nullptr;
+  // kkm_step_host's staging area: page-locked, device-mapped memory, so the
+  // step's kernels read the indices and write the results across the
+  // CPU-GPU link with no copy-engine transfer. h_* are the host views.
+  void* h_stage = nullptr;
+  int32_t* h_hbatch = nullptr;
+  int32_t* h_hassign = nullptr;
+  double* h_hobj = nullptr;
   int32_t* d_hbatch = nullptr;
   int32_t* d_hassign = nullptr;
   double* d_hobj = nullptr;
+  bool host_pending = false;         // a kkm_step_host call queued work it has not yet waited for
   double* d_objpart = nullptr;
   double* d_obj2 = nullptr;   // kkm_fit: f_B before and after the update
   int32_t objpart_len = 0;
@@ -101,6 +110,10 @@ void free_all(kkm_ctx* c) {
   c->gws_len = 0;
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   c->ev.clear();
+  if (c->h_status) cudaFreeHost(c->h_status);
+  c->h_status = nullptr;
+  if (c->h_stage) cudaFreeHost(c->h_stage);
+  c->h_stage = nullptr;
 }
 
 kkm_status check_usable(kkm_ctx* c) {
@@ -111,12 +124,14 @@ kkm_status check_usable(kkm_ctx* c) {
 }
 
 // Synchronises the stream and turns sticky device status bits into an error.
+// The status word comes back with the stream's own work (an async copy into
+// page-locked memory), so a call waits for the device once.
 kkm_status sync_and_check(kkm_ctx* c) {
-  cudaError_t e = cudaStreamSynchronize(c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
-  int32_t st = 0;
-  e = cudaMemcpy(&st, c->s.status, sizeof(st), cudaMemcpyDeviceToHost);
+  cudaError_t e = cudaMemcpyAsync(c->h_status, c->s.status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "status read");
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+  const int32_t st = *c->h_status;
   if (st != 0) {
     c->poisoned = true;
     std::string m = "device status:";
@@ -351,8 +366,33 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
     }
     s.rtab = rt;
   }
+  e = cudaHostAlloc(reinterpret_cast<void**>(&c->h_status), sizeof(int32_t), cudaHostAllocDefault);
+  if (e != cudaSuccess) {
+    c->h_status = nullptr;
+    c->err = std::string("host allocation: ") + cudaGetErrorString(e);
+    return bail(KKM_ENOMEM);
+  }
   ALLOC(c->d_init_idx, k);
-  ALLOC(c->d_hbatch, b); ALLOC(c->d_hassign, b); ALLOC(c->d_hobj, 1);
+  {
+    // kkm_step_host's staging area: [b indices][b assignments][f_B], mapped into the device
+    const size_t nb4 = ((size_t)b * sizeof(int32_t) + 15) & ~(size_t)15;
+    e = cudaHostAlloc(&c->h_stage, 2 * nb4 + 16, cudaHostAllocMapped);
+    void* dev = nullptr;
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&dev, c->h_stage, 0);
+    if (e != cudaSuccess) {
+      c->err = std::string("mapped host allocation: ") + cudaGetErrorString(e);
+      return bail(KKM_ENOMEM);
+    }
+    std::memset(c->h_stage, 0, 2 * nb4 + 16);
+    char* hb = static_cast<char*>(c->h_stage);
+    char* db = static_cast<char*>(dev);
+    c->h_hbatch = reinterpret_cast<int32_t*>(hb);
+    c->h_hassign = reinterpret_cast<int32_t*>(hb + nb4);
+    c->h_hobj = reinterpret_cast<double*>(hb + 2 * nb4);
+    c->d_hbatch = reinterpret_cast<int32_t*>(db);
+    c->d_hassign = reinterpret_cast<int32_t*>(db + nb4);
+    c->d_hobj = reinterpret_cast<double*>(db + 2 * nb4);
+  }
   c->objpart_len = 1024;
   ALLOC(c->d_objpart, c->objpart_len);
   if (tab) {
@@ -524,19 +564,23 @@ KKM_API kkm_status kkm_step_host(kkm_ctx* c, const int32_t* batch_idx, int32_t* 
   kkm_status st = check_usable(c);
   if (st != KKM_OK) return st;
   const int b = c->s.b;
-  if (batch_idx)
-    KKM_CU(cudaMemcpyAsync(c->d_hbatch, batch_idx, b * sizeof(int32_t), cudaMemcpyHostToDevice,
-                           c->stream), "batch upload");
+  if (c->host_pending) {            // an earlier call did not get to wait: its kernels may still read the area
+    st = sync_and_check(c);
+    if (st != KKM_OK) return st;
+    c->host_pending = false;
+  }
+  // the kernels read the indices and write the results in the mapped area
+  if (batch_idx) std::memcpy(c->h_hbatch, batch_idx, (size_t)b * sizeof(int32_t));
+  c->host_pending = true;
   st = kkm_step(c, batch_idx ? c->d_hbatch : nullptr, nullptr, assign_out ? c->d_hassign : nullptr,
                 nullptr, batch_obj_out ? c->d_hobj : nullptr);
   if (st != KKM_OK) return st;
-  if (assign_out)
-    KKM_CU(cudaMemcpyAsync(assign_out, c->d_hassign, b * sizeof(int32_t), cudaMemcpyDeviceToHost,
-                           c->stream), "assignment download");
-  if (batch_obj_out)
-    KKM_CU(cudaMemcpyAsync(batch_obj_out, c->d_hobj, sizeof(double), cudaMemcpyDeviceToHost,
-                           c->stream), "objective download");
-  return sync_and_check(c);
+  st = sync_and_check(c);
+  if (st != KKM_OK) return st;
+  c->host_pending = false;
+  if (assign_out) std::memcpy(assign_out, c->h_hassign, (size_t)b * sizeof(int32_t));
+  if (batch_obj_out) *batch_obj_out = *c->h_hobj;
+  return KKM_OK;
 }
 
 // Runs the distance pass and argmin over query rows in chunks of b rows.

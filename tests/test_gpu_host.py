@@ -1,0 +1,73 @@
+"""kkm_step_host (host buffers through the context's device-mapped staging area)
+against kkm_step with device buffers, and the back-to-back timing mode against
+plain steps: twin contexts on the same data, seed and initial centers must
+give bit-identical assignments, objectives and states."""
+import numpy as np
+import pytest
+
+from paper_2410_05902_gb300 import inputs
+
+from gpu_helpers import torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _twins(precision, graph, n=3000, d=24, k=8, b=256, tau=80):
+    torch = torch_cuda()
+    from paper_2410_05902_gb300.kkm import KKM
+    X, _ = inputs.isotropic_mixture(n, d, k, seed=31)
+    sigma = inputs.median_sigma(X, seed=1)
+    Xd = torch.from_numpy(X).cuda()
+    init = inputs.init_indices(n, k, seed=32)
+    runs = [KKM(Xd, k, b, kernel="gaussian", param=2 * sigma * sigma, tau=tau, precision=precision, seed=9,
+                init_idx=init) for _ in range(2)]
+    for r in runs:
+        r.graph(graph)
+    return torch, runs, n, b
+
+
+def _same_state(a, b):
+    sa, sb = a.get_state(), b.get_state()
+    for key in sa:
+        assert np.array_equal(np.asarray(sa[key]), np.asarray(sb[key])), key
+
+
+@pytest.mark.parametrize("precision,graph", [("bf16x3", True), ("fp32", False), ("bf16", True)])
+def test_step_host_matches_device_step(precision, graph):
+    torch, (h, dv), n, b = _twins(precision, graph)
+    a_dev = torch.empty(b, dtype=torch.int32, device="cuda")
+    o_dev = torch.empty(1, dtype=torch.float64, device="cuda")
+    batches = inputs.batch_stream(n, b, 6, seed=33)
+    for i in range(12):
+        # explicit batches first, then the built-in sampler
+        B = batches[i] if i < 6 else None
+        a_host, f_host = h.step_host(B)
+        dv.step(None if B is None else torch.from_numpy(B.astype(np.int32)).cuda(), None, a_dev, None, o_dev)
+        dv.sync()
+        assert np.array_equal(a_host, a_dev.cpu().numpy()), i
+        assert f_host == float(o_dev.cpu()[0]), i
+    _same_state(h, dv)
+    h.close()
+    dv.close()
+
+
+def test_back_to_back_timing_leaves_results_unchanged():
+    """Timing mode R > 1 launches the distance pass R times per step; the pass
+    is idempotent, so the run must match an untimed twin exactly."""
+    torch, (t, p), n, b = _twins("bf16", False)
+    t.timing(20)
+    a1 = torch.empty(b, dtype=torch.int32, device="cuda")
+    a2 = torch.empty(b, dtype=torch.int32, device="cuda")
+    for B in inputs.batch_stream(n, b, 8, seed=34):
+        bi = torch.from_numpy(B.astype(np.int32)).cuda()
+        t.step(bi, None, a1)
+        p.step(bi, None, a2)
+        t.sync()
+        p.sync()
+        assert torch.equal(a1, a2)
+    n_rec, ms = t.timing_read(reset=True)
+    t.timing(False)
+    assert n_rec == 8 and ms > 0.0
+    _same_state(t, p)
+    t.close()
+    p.close()
