@@ -414,18 +414,34 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out) {
     const int rank = __popc(peers & ((1u << lane) - 1u));
     if (j >= 0 && rank == 0) wtab[warp * k + j] = (uint16_t)(tag | __popc(peers));
     __syncthreads();
-    // exclusive prefix of each center's per-warp counts over the 32 warps: a
+    // exclusive prefix of each center's per-warp counts over the 32 warps. With
+    // few centers a warp scans one center (one or two rounds); with many, a
     // thread per center walks its column (consecutive centers, no bank conflicts)
-    for (int jj = tid; jj < k; jj += 1024) {
-      int run = 0;
-#pragma unroll 8
-      for (int w2 = 0; w2 < 32; ++w2) {
-        const uint16_t e = wtab[w2 * k + jj];
+    if (k <= 64) {
+      for (int jj = warp; jj < k; jj += 32) {
+        const uint16_t e = wtab[lane * k + jj];
         const int v = (e & 0x7800) == tag ? (int)(e & 0x7ff) : 0;
-        wtab[w2 * k + jj] = (uint16_t)(tag | run);
-        run += v;
+        int xs = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, xs, o);
+          if (lane >= o) xs += y;
+        }
+        wtab[lane * k + jj] = (uint16_t)(tag | (xs - v));
+        if (lane == 31) bnext[jj] = bcur[jj] + xs;
       }
-      bnext[jj] = bcur[jj] + run;
+    } else {
+      for (int jj = tid; jj < k; jj += 1024) {
+        int run = 0;
+#pragma unroll 8
+        for (int w2 = 0; w2 < 32; ++w2) {
+          const uint16_t e = wtab[w2 * k + jj];
+          const int v = (e & 0x7800) == tag ? (int)(e & 0x7ff) : 0;
+          wtab[w2 * k + jj] = (uint16_t)(tag | run);
+          run += v;
+        }
+        bnext[jj] = bcur[jj] + run;
+      }
     }
     __syncthreads();
     if (j >= 0) sperm[coff[j] + bcur[j] + (wtab[warp * k + j] & 0x7ff) + rank] = (int16_t)x;
