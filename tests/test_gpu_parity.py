@@ -109,6 +109,8 @@ def test_other_kernels_teacher_forced(kernel, extra):
     (300, 5, 7, 33, 1),       # tau = 1: only the newest block survives
     (300, 9, 4, 200, 500),    # tau larger than anything reached: no truncation
     (2500, 3, 12, 1000, 64),  # many centers, large batch, tiny d
+    (3000, 8, 80, 1024, 64),  # more than 64 centers: sort/plan scans a center per thread
+    (4000, 8, 80, 2048, 64),  # the same over two 1024-row chunks of the stable sort
 ])
 def test_edge_shapes_teacher_forced(n, d, k, b, tau):
     X = small_data(n=n, d=d, c=max(k, 2))
