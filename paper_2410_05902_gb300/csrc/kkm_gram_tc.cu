@@ -547,7 +547,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   // first stages and that item's column metadata. They come from earlier
   // steps; the batch rows and their metadata follow after the wait.
   int npre = 0;                                  // first-item stages whose B tile is already on its way
-  int pyb_pre = 0;                               // this lane's first-round item: its B row
+  int pya_pre = 0, pyb_pre = 0;                  // this lane's first-round item: its A and B rows
   bool desc_pre = false;
   if constexpr (MODE == 0) {
     if (warp == 0 && s.pre_b) {
@@ -576,6 +576,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       npre = __shfl_sync(0xffffffffu, npre, 0);
     }
+  } else {
+    // window pass: its pair list and plans come from the sort/plan kernel two
+    // launches back (the row moves just ahead write neither), so the producer
+    // fetches its first 32 pair descriptors before the wait
+    if (warp == 0) {
+      const int mine0 = (int)blockIdx.x + lane * (int)gridDim.x;
+      if (mine0 < *s.nwpairs) {
+        const PairTile pt = pair_tile<TNV>(s, mine0);
+        pya_pre = (int)(pt.base + pt.rs);
+        pyb_pre = (int)(pt.base + pt.cs);
+      }
+      desc_pre = true;
+    }
   }
   KKM_GRID_DEP_WAIT();   // everything above reads only data of earlier steps
   KKM_LAUNCH_DEPENDENTS();   // the next kernel may set itself up; it waits before reading our output
@@ -595,6 +608,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if constexpr (MODE == 0) {
             pya = (mine % R) * TM;
             pyb = (local == 0 && desc_pre) ? pyb_pre : s.tiles[mine / R].row0;
+          } else if (local == 0 && desc_pre) {
+            pya = pya_pre;
+            pyb = pyb_pre;
           } else {
             const PairTile pt = pair_tile<TNV>(s, mine);
             pya = (int)(pt.base + pt.rs);

@@ -283,6 +283,8 @@ cudaError_t tc_prepare(Dev& s, void* maps);
 // itself) writes none of the support tiles, their metadata or the tile list,
 // so the pass may stage them before its grid-dependency wait.
 cudaError_t launch_dist_tc(const Dev& s, const void* maps, int rows, cudaStream_t st, bool stage_early = false);
+// The window pass reads its pair list and plans before its grid-dependency
+// wait: launch it only right after k_move (which writes neither).
 cudaError_t launch_wgram_tc(const Dev& s, const void* maps, cudaStream_t st);
 
 }  // namespace kkm
