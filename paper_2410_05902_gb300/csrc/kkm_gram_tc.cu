@@ -541,11 +541,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int R = (rows + TM - 1) / TM;
   const int nks = s.dp / KSE;
 
-  // Distance pass with s.pre_b: before the grid-dependency wait, while the
-  // batch gather still runs, the producer fetches the descriptors of its
-  // first 32 items (one per lane) and stages the B tiles of its first item's
-  // first stages and that item's column metadata. They come from earlier
-  // steps; the batch rows and their metadata follow after the wait.
+  // Distance pass with s.pre_b (set per launch when the kernel just ahead, the
+  // batch gather or this pass itself, writes none of it): before the
+  // grid-dependency wait the producer fetches the descriptors of its first 32
+  // items (one per lane) and stages the B tiles of its first item's first
+  // stages and that item's column metadata. They come from earlier steps;
+  // the batch rows and their metadata follow after the wait.
   int npre = 0;                                  // first-item stages whose B tile is already on its way
   int pya_pre = 0, pyb_pre = 0;                  // this lane's first-round item: its A and B rows
   bool desc_pre = false;
