@@ -676,10 +676,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (lane == 0) {
       bool ok = true;
       uint32_t it = 0, local = 0;
-      // K steps of the last slice that reach a real column (the padding past d
-      // is zero in both operands, so the MMAs over padding alone add nothing)
-      constexpr int KSTEP = OP == OP_TF32 ? 8 : 16;          // elements per MMA K step
-      const int klast = (s.d - (nks - 1) * KSE + KSTEP - 1) / KSTEP;
       for (int item = blockIdx.x; ok && item < total; item += gridDim.x, ++local) {
         const uint32_t buf = local & 1u, bph = (local >> 1) & 1u;
         if (!mbar_wait(&sh.tempty[buf], bph ^ 1u)) { ok = false; break; }
@@ -691,12 +687,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (!mbar_wait(&sh.full[st], ph)) { ok = false; break; }
           tc_fence_after();
           const uint32_t a0 = smem_u32(smem + st * SB);
-          const int kn = sl == nks - 1 ? klast : 4;
           if constexpr (X3) {
             const uint32_t alo = a0 + A_BYTES, bhi = a0 + 2 * A_BYTES, blo = bhi + BB;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-              if (k >= kn) break;
               mma_op<OP>(d, sw128_desc(a0 + 32u * k), sw128_desc(bhi + 32u * k), IDESC, (sl | k) != 0 ? 1u : 0u);
               mma_op<OP>(d, sw128_desc(a0 + 32u * k), sw128_desc(blo + 32u * k), IDESC, 1u);
               mma_op<OP>(d, sw128_desc(alo + 32u * k), sw128_desc(bhi + 32u * k), IDESC, 1u);
@@ -704,10 +698,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           } else {
             const uint32_t b0 = a0 + A_BYTES;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {   // four 32-byte K steps per 128-byte slice row
-              if (k >= kn) break;
+            for (int k = 0; k < 4; ++k)   // four 32-byte K steps per 128-byte slice row
               mma_op<OP>(d, sw128_desc(a0 + 32u * k), sw128_desc(b0 + 32u * k), IDESC, (sl | k) != 0 ? 1u : 0u);
-            }
           }
           mma_commit(&sh.empty[st]);
         }
