@@ -149,18 +149,23 @@ __global__ void k_center_sum(Dev s, int nch, const double* part, double* cn) {
 // One warp per query row x against the window of its assigned center, lane =
 // window row. Forward: Delta(x). Adjoint (BWD): dL/dx, and the row's share of
 // dL/ds. Per-block FP64 partials of sum Delta and of the ds terms. NK = feature
-// registers per lane for the query gradient (32 * NK >= d).
+// registers per lane for the query gradient (32 * NK >= d). The warp stages
+// each block of 32 window rows in shared memory, RC features at a time, with
+// coalesced loads (a lane per feature); each lane then reads its own row there
+// (rows padded to RC + 1 floats, no bank conflicts).
+constexpr int RC = 64;                           // features per staged chunk
 template <bool BWD, int NK>
 __global__ void __launch_bounds__(32 * GW) k_rows(Dev s, BandParams bp, const float* __restrict__ Q, int64_t m,
                                                   int64_t ldq, const int32_t* __restrict__ assign,
                                                   const double* __restrict__ cn, float* __restrict__ delta,
                                                   const double* __restrict__ grad_loss, float* __restrict__ grad_q,
                                                   int64_t ldg, double* __restrict__ blk) {
-  extern __shared__ float xs[];                 // [GW][d]
+  extern __shared__ float xs[];                 // [GW][d] query rows, then [GW][32][RC + 1] staged window rows
   __shared__ double red[GW][2];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t x = (int64_t)blockIdx.x * GW + w;
   float* xr = xs + (int64_t)w * s.d;
+  float (*ys)[RC + 1] = reinterpret_cast<float (*)[RC + 1]>(xs + (int64_t)GW * s.d + (int64_t)w * 32 * (RC + 1));
   double my_delta = 0.0, my_ds = 0.0;
   if (x < m) {
     int j = assign[x];
@@ -180,11 +185,22 @@ __global__ void __launch_bounds__(32 * GW) k_rows(Dev s, BandParams bp, const fl
       const int t = t0 + lane;
       const bool live = t < size;
       const int64_t row = base + (live ? t : 0);
-      const float* yr = support_row(s, row);
+      const int nrow = min(32, size - t0);
+      const int64_t my_yi = s.yi[row];
       float d2 = 0.0f;
-      for (int k = 0; k < s.d; ++k) {
-        const float df = xr[k] - yr[k];
-        d2 = fmaf(df, df, d2);
+      for (int k0 = 0; k0 < s.d; k0 += RC) {
+        const int kn = min(RC, s.d - k0);
+        __syncwarp();
+        for (int r = 0; r < nrow; ++r) {         // row r of the block, a lane per feature
+          const float* src = s.X + __shfl_sync(0xffffffffu, my_yi, r) * s.ldx + k0;
+          for (int kk = lane; kk < kn; kk += 32) ys[r][kk] = src[kk];
+        }
+        __syncwarp();
+        if (live)
+          for (int kk = 0; kk < kn; ++kk) {
+            const float df = xr[k0 + kk] - ys[lane][kk];
+            d2 = fmaf(df, df, d2);
+          }
       }
       float K, dks, g;
       pair_terms(bp, d2, K, dks, g);
@@ -195,10 +211,11 @@ __global__ void __launch_bounds__(32 * GW) k_rows(Dev s, BandParams bp, const fl
         const float c = wt * g * K;
         csum += c;
         // u = sum_t c_t y_t: broadcast each lane's c, lanes over the features
+        // (rows from the staged block when it holds all the features)
         const int nt = min(32, size - t0);
         for (int tt = 0; tt < nt; ++tt) {
           const float ct = __shfl_sync(0xffffffffu, c, tt);
-          const float* yt = support_row(s, base + t0 + tt);
+          const float* yt = s.d <= RC ? ys[tt] : support_row(s, base + t0 + tt);
 #pragma unroll
           for (int i = 0; i < NK; ++i) {
             const int k = lane + 32 * i;
@@ -263,7 +280,7 @@ cudaError_t launch_rows(const Dev& s, const BandParams& bp, const float* Q, int6
   static bool attr = false;
   if (!attr) {
     const cudaError_t e = cudaFuncSetAttribute(k_rows<BWD, NK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               GW * 1024 * 4);
+                                               GW * (1024 + 32 * (RC + 1)) * 4);
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -307,7 +324,7 @@ cudaError_t launch_objective(const Dev& s, double log_sigma, const float* Q, int
   k_center_sum<<<(s.k + 127) / 128, 128, 0, st>>>(s, nch, part, cn);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t smem = (size_t)GW * s.d * sizeof(float);
+  const size_t smem = (size_t)GW * (s.d + 32 * (RC + 1)) * sizeof(float);   // query rows + staged window rows
   if (grad_q) {
     if (s.d <= 64) e = launch_rows<true, 2>(s, bp, Q, m, ldq, assign, cn, nullptr, grad_loss, grad_q, ldg, blk, nblk, smem, st);
     else if (s.d <= 128) e = launch_rows<true, 4>(s, bp, Q, m, ldq, assign, cn, nullptr, grad_loss, grad_q, ldg, blk, nblk, smem, st);
