@@ -80,9 +80,10 @@ __global__ void __launch_bounds__(32 * GW) k_center_pairs(Dev s, BandParams bp, 
   const int j = blockIdx.x, c = blockIdx.y;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int head = s.head[j], size = s.tail[j] - head;
+  const int r0 = c * 32;
+  if (r0 >= size) return;   // the grid covers the window capacity; k_center_sum reads only chunks < size
   const int64_t base = (int64_t)j * s.cap + head;
   float acc = 0.0f, accs = 0.0f;
-  const int r0 = c * 32;
   if (r0 < size) {
     float wa[4];
 #pragma unroll
@@ -133,12 +134,13 @@ __global__ void __launch_bounds__(32 * GW) k_center_pairs(Dev s, BandParams bp, 
   }
 }
 
-// N_j, N'_j from the chunk partials (fixed order).
+// N_j, N'_j from the partials of the chunks that cover the window (fixed order).
 __global__ void k_center_sum(Dev s, int nch, const double* part, double* cn) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= s.k) return;
+  const int used = min(nch, (s.tail[j] - s.head[j] + 31) / 32);
   double a = 0.0, b = 0.0;
-  for (int c = 0; c < nch; ++c) {
+  for (int c = 0; c < used; ++c) {
     a += part[((int64_t)j * nch + c) * 2];
     b += part[((int64_t)j * nch + c) * 2 + 1];
   }
