@@ -76,6 +76,7 @@ __device__ __forceinline__ void pair_terms(const BandParams& bp, float d2, float
 __global__ void __launch_bounds__(32 * GW) k_center_pairs(Dev s, BandParams bp, int nch, double* part) {
   __shared__ float A[32][DCH + 1];
   __shared__ float B[32][DCH + 1];
+  __shared__ int64_t ia[32], ib[32];            // data rows of the chunk's and the staged block's support rows
   __shared__ double red[GW][2];
   const int j = blockIdx.x, c = blockIdx.y;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -84,23 +85,42 @@ __global__ void __launch_bounds__(32 * GW) k_center_pairs(Dev s, BandParams bp, 
   if (r0 >= size) return;   // the grid covers the window capacity; k_center_sum reads only chunks < size
   const int64_t base = (int64_t)j * s.cap + head;
   float acc = 0.0f, accs = 0.0f;
-  if (r0 < size) {
+  // stages rows idx[0..32) (features k0..k0+kn) into T: every load issued before the stores
+  auto stage = [&](float (*T)[DCH + 1], const int64_t* idx, int k0, int kn) {
+    float v[(32 * DCH) / (32 * GW)];
+#pragma unroll
+    for (int q = 0; q < (32 * DCH) / (32 * GW); ++q) {
+      const int e = threadIdx.x + q * 32 * GW;
+      const int r = e / kn, k = e - r * kn;
+      v[q] = e < 32 * kn && idx[r] >= 0 ? __ldg(s.X + idx[r] * s.ldx + k0 + k) : 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < (32 * DCH) / (32 * GW); ++q) {
+      const int e = threadIdx.x + q * 32 * GW;
+      const int r = e / kn, k = e - r * kn;
+      if (e < 32 * kn) T[r][k] = v[q];
+    }
+  };
+  if (threadIdx.x < 32) ia[threadIdx.x] = r0 + (int)threadIdx.x < size ? (int64_t)s.yi[base + r0 + threadIdx.x] : -1;
+  const bool a_once = s.d <= DCH;               // one feature chunk: the chunk's rows are staged once
+  {
     float wa[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int r = r0 + w + GW * u;
       wa[u] = r < size ? s.w32[base + r] : 0.0f;
     }
+    __syncthreads();
+    if (a_once) stage(A, ia, 0, s.d);
     for (int t0 = 0; t0 < size; t0 += 32) {
       float d2[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      __syncthreads();
+      if (threadIdx.x < 32) ib[threadIdx.x] = t0 + (int)threadIdx.x < size ? (int64_t)s.yi[base + t0 + threadIdx.x] : -1;
       for (int k0 = 0; k0 < s.d; k0 += DCH) {
         const int kn = min(DCH, s.d - k0);
         __syncthreads();
-        for (int e = threadIdx.x; e < 32 * kn; e += 32 * GW) {
-          const int r = e / kn, k = e - r * kn;
-          A[r][k] = r0 + r < size ? support_row(s, base + r0 + r)[k0 + k] : 0.0f;
-          B[r][k] = t0 + r < size ? support_row(s, base + t0 + r)[k0 + k] : 0.0f;
-        }
+        if (!a_once) stage(A, ia, k0, kn);
+        stage(B, ib, k0, kn);
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -193,9 +213,25 @@ __global__ void __launch_bounds__(32 * GW) k_rows(Dev s, BandParams bp, const fl
       for (int k0 = 0; k0 < s.d; k0 += RC) {
         const int kn = min(RC, s.d - k0);
         __syncwarp();
-        for (int r = 0; r < nrow; ++r) {         // row r of the block, a lane per feature
-          const float* src = s.X + __shfl_sync(0xffffffffu, my_yi, r) * s.ldx + k0;
-          for (int kk = lane; kk < kn; kk += 32) ys[r][kk] = src[kk];
+        // rows r of the block, a lane per feature: eight rows' loads in flight
+        // before their stores (read-only loads, so they need not wait for them)
+        for (int rb = 0; rb < nrow; rb += 8) {
+          float v[8][2];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int r = rb + q;
+            const float* src = s.X + __shfl_sync(0xffffffffu, my_yi, r & 31) * s.ldx + k0;
+            v[q][0] = (r < nrow && lane < kn) ? __ldg(src + lane) : 0.0f;
+            v[q][1] = (r < nrow && lane + 32 < kn) ? __ldg(src + lane + 32) : 0.0f;
+          }
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int r = rb + q;
+            if (r < nrow) {
+              if (lane < kn) ys[r][lane] = v[q][0];
+              if (lane + 32 < kn) ys[r][lane + 32] = v[q][1];
+            }
+          }
         }
         __syncwarp();
         if (live)
