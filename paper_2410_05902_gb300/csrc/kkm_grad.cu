@@ -74,8 +74,8 @@ __device__ __forceinline__ void pair_terms(const BandParams& bp, float d2, float
 // feature columns per pass. Warp w takes rows w, w+8, w+16, w+24 of the
 // chunk; lane l the l-th row of the staged window slice.
 __global__ void __launch_bounds__(32 * GW) k_center_pairs(Dev s, BandParams bp, int nch, double* part) {
-  __shared__ float A[32][DCH + 1];
-  __shared__ float B[32][DCH + 1];
+  __shared__ __align__(16) float A[32][DCH + 4];   // rows padded to 16 bytes: float4 reads,
+  __shared__ __align__(16) float B[32][DCH + 4];   // no bank conflicts within a quarter-warp
   __shared__ int64_t ia[32], ib[32];            // data rows of the chunk's and the staged block's support rows
   __shared__ double red[GW][2];
   const int j = blockIdx.x, c = blockIdx.y;
@@ -86,19 +86,21 @@ __global__ void __launch_bounds__(32 * GW) k_center_pairs(Dev s, BandParams bp, 
   const int64_t base = (int64_t)j * s.cap + head;
   float acc = 0.0f, accs = 0.0f;
   // stages rows idx[0..32) (features k0..k0+kn) into T: every load issued before the stores
-  auto stage = [&](float (*T)[DCH + 1], const int64_t* idx, int k0, int kn) {
+  // (features past kn up to the next multiple of 4 are zero: they add nothing)
+  auto stage = [&](float (*T)[DCH + 4], const int64_t* idx, int k0, int kn) {
+    const int kp = (kn + 3) & ~3;
     float v[(32 * DCH) / (32 * GW)];
 #pragma unroll
     for (int q = 0; q < (32 * DCH) / (32 * GW); ++q) {
       const int e = threadIdx.x + q * 32 * GW;
-      const int r = e / kn, k = e - r * kn;
-      v[q] = e < 32 * kn && idx[r] >= 0 ? __ldg(s.X + idx[r] * s.ldx + k0 + k) : 0.0f;
+      const int r = e / kp, k = e - r * kp;
+      v[q] = e < 32 * kp && k < kn && idx[r] >= 0 ? __ldg(s.X + idx[r] * s.ldx + k0 + k) : 0.0f;
     }
 #pragma unroll
     for (int q = 0; q < (32 * DCH) / (32 * GW); ++q) {
       const int e = threadIdx.x + q * 32 * GW;
-      const int r = e / kn, k = e - r * kn;
-      if (e < 32 * kn) T[r][k] = v[q];
+      const int r = e / kp, k = e - r * kp;
+      if (e < 32 * kp) T[r][k] = v[q];
     }
   };
   if (threadIdx.x < 32) ia[threadIdx.x] = r0 + (int)threadIdx.x < size ? (int64_t)s.yi[base + r0 + threadIdx.x] : -1;
@@ -122,15 +124,22 @@ __global__ void __launch_bounds__(32 * GW) k_center_pairs(Dev s, BandParams bp, 
         if (!a_once) stage(A, ia, k0, kn);
         stage(B, ib, k0, kn);
         __syncthreads();
+        const int kp = (kn + 3) & ~3;
+        for (int k = 0; k < kp; k += 4) {
+          const float4 b4 = *reinterpret_cast<const float4*>(&B[lane][k]);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int ra = w + GW * u;
-          float sum = d2[u];
-          for (int k = 0; k < kn; ++k) {
-            const float df = A[ra][k] - B[lane][k];
+          for (int u = 0; u < 4; ++u) {
+            const float4 a4 = *reinterpret_cast<const float4*>(&A[w + GW * u][k]);
+            float sum = d2[u];
+            float df = a4.x - b4.x;
             sum = fmaf(df, df, sum);
+            df = a4.y - b4.y;
+            sum = fmaf(df, df, sum);
+            df = a4.z - b4.z;
+            sum = fmaf(df, df, sum);
+            df = a4.w - b4.w;
+            d2[u] = fmaf(df, df, sum);
           }
-          d2[u] = sum;
         }
       }
       const float wb = t0 + lane < size ? s.w32[base + t0 + lane] : 0.0f;
@@ -213,19 +222,19 @@ __global__ void __launch_bounds__(32 * GW) k_rows(Dev s, BandParams bp, const fl
       for (int k0 = 0; k0 < s.d; k0 += RC) {
         const int kn = min(RC, s.d - k0);
         __syncwarp();
-        // rows r of the block, a lane per feature: eight rows' loads in flight
+        // rows r of the block, a lane per feature: sixteen rows' loads in flight
         // before their stores (read-only loads, so they need not wait for them)
-        for (int rb = 0; rb < nrow; rb += 8) {
-          float v[8][2];
+        for (int rb = 0; rb < nrow; rb += 16) {
+          float v[16][2];
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
+          for (int q = 0; q < 16; ++q) {
             const int r = rb + q;
             const float* src = s.X + __shfl_sync(0xffffffffu, my_yi, r & 31) * s.ldx + k0;
             v[q][0] = (r < nrow && lane < kn) ? __ldg(src + lane) : 0.0f;
             v[q][1] = (r < nrow && lane + 32 < kn) ? __ldg(src + lane + 32) : 0.0f;
           }
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
+          for (int q = 0; q < 16; ++q) {
             const int r = rb + q;
             if (r < nrow) {
               if (lane < kn) ys[r][lane] = v[q][0];
