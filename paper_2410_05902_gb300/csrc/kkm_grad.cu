@@ -47,13 +47,6 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
-// The FP32 data row of support row `row`, read from X through its data index
-// (exact in every precision form; the BF16 copies of the distance pass are
-// not used here).
-__device__ __forceinline__ const float* support_row(const Dev& s, int64_t row) {
-  return s.X + (int64_t)s.yi[row] * s.ldx;
-}
-
 // K, dK/ds and g of one pair from its squared distance.
 __device__ __forceinline__ void pair_terms(const BandParams& bp, float d2, float& K, float& dks, float& g) {
   d2 = fmaxf(d2, 0.0f);
@@ -69,20 +62,32 @@ __device__ __forceinline__ void pair_terms(const BandParams& bp, float d2, float
   }
 }
 
-// N_j and N'_j partials: block (chunk c of 32 window rows of center j) x the
-// whole window of j, 32 window rows at a time staged in shared memory, DCH
-// feature columns per pass. Warp w takes rows w, w+8, w+16, w+24 of the
-// chunk; lane l the l-th row of the staged window slice.
-__global__ void __launch_bounds__(32 * GW) k_center_pairs(Dev s, BandParams bp, int nch, double* part) {
+// 4-byte asynchronous global -> shared copies (staging with every load in flight,
+// no registers held).
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// N_j and N'_j partials. Block (j, y) takes the 32-row chunks c = y, y + py, ...
+// of center j's window; chunk c meets chunks c + dl (mod nc) for dl = 0..nc/2,
+// so each unordered pair of chunks is summed once (twice its weight off the
+// diagonal; with nc even, the pair at distance nc/2 belongs to the lower
+// chunk). 32 rows and DCH feature columns of each side are staged in shared
+// memory; warp w takes rows w, w+8, w+16, w+24 of chunk c, lane l row l of the
+// other chunk. Every block writes its partial (zero when it has no chunk).
+__global__ void __launch_bounds__(32 * GW) k_center_pairs(Dev s, BandParams bp, int py, double* part) {
   __shared__ __align__(16) float A[32][DCH + 4];   // rows padded to 16 bytes: float4 reads,
   __shared__ __align__(16) float B[32][DCH + 4];   // no bank conflicts within a quarter-warp
   __shared__ int64_t ia[32], ib[32];            // data rows of the chunk's and the staged block's support rows
   __shared__ double red[GW][2];
-  const int j = blockIdx.x, c = blockIdx.y;
+  const int j = blockIdx.x, y = blockIdx.y;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int head = s.head[j], size = s.tail[j] - head;
-  const int r0 = c * 32;
-  if (r0 >= size) return;   // the grid covers the window capacity; k_center_sum reads only chunks < size
+  const int nc = (size + 31) / 32, h = nc / 2;
   const int64_t base = (int64_t)j * s.cap + head;
   float acc = 0.0f, accs = 0.0f;
   // stages rows idx[0..32) (features k0..k0+kn) into T: every load issued before the stores
@@ -103,18 +108,24 @@ __global__ void __launch_bounds__(32 * GW) k_center_pairs(Dev s, BandParams bp, 
       if (e < 32 * kp) T[r][k] = v[q];
     }
   };
-  if (threadIdx.x < 32) ia[threadIdx.x] = r0 + (int)threadIdx.x < size ? (int64_t)s.yi[base + r0 + threadIdx.x] : -1;
   const bool a_once = s.d <= DCH;               // one feature chunk: the chunk's rows are staged once
-  {
+  for (int c = y; c < nc; c += py) {
+    const int r0 = c * 32;
     float wa[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int r = r0 + w + GW * u;
       wa[u] = r < size ? s.w32[base + r] : 0.0f;
     }
+    __syncthreads();                            // the previous chunk's readers of ia and A are done
+    if (threadIdx.x < 32) ia[threadIdx.x] = r0 + (int)threadIdx.x < size ? (int64_t)s.yi[base + r0 + threadIdx.x] : -1;
     __syncthreads();
     if (a_once) stage(A, ia, 0, s.d);
-    for (int t0 = 0; t0 < size; t0 += 32) {
+    for (int dl = 0; dl <= h; ++dl) {
+      if ((nc & 1) == 0 && dl == h && c >= h) break;   // the pair {c - h, c} is the lower chunk's
+      const int cb = c + dl < nc ? c + dl : c + dl - nc;
+      const int t0 = cb * 32;
+      const float fac = dl == 0 ? 1.0f : 2.0f;
       float d2[4] = {0.0f, 0.0f, 0.0f, 0.0f};
       __syncthreads();
       if (threadIdx.x < 32) ib[threadIdx.x] = t0 + (int)threadIdx.x < size ? (int64_t)s.yi[base + t0 + threadIdx.x] : -1;
@@ -142,7 +153,7 @@ __global__ void __launch_bounds__(32 * GW) k_center_pairs(Dev s, BandParams bp, 
           }
         }
       }
-      const float wb = t0 + lane < size ? s.w32[base + t0 + lane] : 0.0f;
+      const float wb = t0 + lane < size ? fac * s.w32[base + t0 + lane] : 0.0f;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         float K, dks, g;
@@ -159,150 +170,255 @@ __global__ void __launch_bounds__(32 * GW) k_center_pairs(Dev s, BandParams bp, 
   if (threadIdx.x < 2) {
     double v = 0.0;
     for (int q = 0; q < GW; ++q) v += red[q][threadIdx.x];
-    part[((int64_t)j * nch + c) * 2 + threadIdx.x] = v;
+    part[((int64_t)j * py + y) * 2 + threadIdx.x] = v;
   }
 }
 
-// N_j, N'_j from the partials of the chunks that cover the window (fixed order).
-__global__ void k_center_sum(Dev s, int nch, const double* part, double* cn) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= s.k) return;
-  const int used = min(nch, (s.tail[j] - s.head[j] + 31) / 32);
-  double a = 0.0, b = 0.0;
-  for (int c = 0; c < used; ++c) {
-    a += part[((int64_t)j * nch + c) * 2];
-    b += part[((int64_t)j * nch + c) * 2 + 1];
+// One block of 1024 threads. (1) N_j, N'_j from the py partials of each center
+// (fixed order). (2) The query rows grouped by assigned center: counts,
+// offsets, the row list (rows of a center in any order: every per-row result
+// is independent of it), and the row items (center, first list position,
+// rows <= GW) the row kernel deals one per block. Out-of-range assignments
+// raise ST_BAD_ASSIGN and count as center 0.
+__global__ void __launch_bounds__(1024) k_prepare(Dev s, int py, const double* __restrict__ part,
+                                                  double* __restrict__ cn, const int32_t* __restrict__ assign,
+                                                  int64_t m, int* __restrict__ list, int4* __restrict__ items,
+                                                  int* __restrict__ nitems) {
+  __shared__ int cnt[1024], cur[1024], off[1025], ist[1025];
+  const int t = threadIdx.x;
+  if (t < s.k) {
+    double a = 0.0, b = 0.0;
+    for (int q = 0; q < py; ++q) {
+      a += part[((int64_t)t * py + q) * 2];
+      b += part[((int64_t)t * py + q) * 2 + 1];
+    }
+    cn[2 * t] = a;
+    cn[2 * t + 1] = b;
+    cnt[t] = 0;
+    cur[t] = 0;
   }
-  cn[2 * j] = a;
-  cn[2 * j + 1] = b;
-}
-
-// One warp per query row x against the window of its assigned center, lane =
-// window row. Forward: Delta(x). Adjoint (BWD): dL/dx, and the row's share of
-// dL/ds. Per-block FP64 partials of sum Delta and of the ds terms. NK = feature
-// registers per lane for the query gradient (32 * NK >= d). The warp stages
-// each block of 32 window rows in shared memory, RC features at a time, with
-// coalesced loads (a lane per feature); each lane then reads its own row there
-// (rows padded to RC + 1 floats, no bank conflicts).
-constexpr int RC = 64;                           // features per staged chunk
-template <bool BWD, int NK>
-__global__ void __launch_bounds__(32 * GW) k_rows(Dev s, BandParams bp, const float* __restrict__ Q, int64_t m,
-                                                  int64_t ldq, const int32_t* __restrict__ assign,
-                                                  const double* __restrict__ cn, float* __restrict__ delta,
-                                                  const double* __restrict__ grad_loss, float* __restrict__ grad_q,
-                                                  int64_t ldg, double* __restrict__ blk) {
-  extern __shared__ float xs[];                 // [GW][d] query rows, then [GW][32][RC + 1] staged window rows
-  __shared__ double red[GW][2];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t x = (int64_t)blockIdx.x * GW + w;
-  float* xr = xs + (int64_t)w * s.d;
-  float (*ys)[RC + 1] = reinterpret_cast<float (*)[RC + 1]>(xs + (int64_t)GW * s.d + (int64_t)w * 32 * (RC + 1));
-  double my_delta = 0.0, my_ds = 0.0;
-  if (x < m) {
+  __syncthreads();
+  bool bad = false;
+  for (int64_t x = t; x < m; x += 1024) {
     int j = assign[x];
     if (j < 0 || j >= s.k) {
-      if (lane == 0) atomicOr(s.status, ST_BAD_ASSIGN);
+      bad = true;
       j = 0;
     }
-    for (int k = lane; k < s.d; k += 32) xr[k] = Q[x * ldq + k];
-    __syncwarp();
-    const int head = s.head[j], size = s.tail[j] - head;
-    const int64_t base = (int64_t)j * s.cap + head;
-    float inner = 0.0f, dsum = 0.0f, csum = 0.0f;
-    float u[NK];
+    atomicAdd(&cnt[j], 1);
+  }
+  if (bad) atomicOr(s.status, ST_BAD_ASSIGN);
+  __syncthreads();
+  if (t < 32) {
+    // exclusive scans of the row counts and of the row items per center: a lane
+    // per run of consecutive centers, then a warp scan of the run totals
+    const int per = (s.k + 31) / 32, j0 = t * per, j1 = min(s.k, j0 + per);
+    int sc = 0, si = 0;
+    for (int j = j0; j < j1; ++j) {
+      sc += cnt[j];
+      si += (cnt[j] + GW - 1) / GW;
+    }
+    int ic = sc, ii = si;
 #pragma unroll
-    for (int i = 0; i < NK; ++i) u[i] = 0.0f;
-    for (int t0 = 0; t0 < size; t0 += 32) {
-      const int t = t0 + lane;
-      const bool live = t < size;
-      const int64_t row = base + (live ? t : 0);
-      const int nrow = min(32, size - t0);
-      const int64_t my_yi = s.yi[row];
-      float d2 = 0.0f;
-      for (int k0 = 0; k0 < s.d; k0 += RC) {
-        const int kn = min(RC, s.d - k0);
-        __syncwarp();
-        // rows r of the block, a lane per feature: sixteen rows' loads in flight
-        // before their stores (read-only loads, so they need not wait for them)
-        for (int rb = 0; rb < nrow; rb += 16) {
-          float v[16][2];
+    for (int o = 1; o < 32; o <<= 1) {
+      const int vc = __shfl_up_sync(0xffffffffu, ic, o), vi = __shfl_up_sync(0xffffffffu, ii, o);
+      if (t >= o) {
+        ic += vc;
+        ii += vi;
+      }
+    }
+    int ec = ic - sc, ei = ii - si;
+    for (int j = j0; j < j1; ++j) {
+      off[j] = ec;
+      ist[j] = ei;
+      ec += cnt[j];
+      ei += (cnt[j] + GW - 1) / GW;
+    }
+    if (t == 31) {
+      off[s.k] = ic;
+      ist[s.k] = ii;
+      *nitems = ii;
+    }
+  }
+  __syncthreads();
+  for (int64_t x = t; x < m; x += 1024) {
+    int j = assign[x];
+    if (j < 0 || j >= s.k) j = 0;
+    list[off[j] + atomicAdd(&cur[j], 1)] = (int)x;
+  }
+  const int ni = ist[s.k];
+  for (int it = t; it < ni; it += 1024) {
+    int lo = 0, hi = s.k - 1;                   // the largest center whose items start at or before it
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (ist[mid] <= it) lo = mid;
+      else hi = mid - 1;
+    }
+    const int p = off[lo] + (it - ist[lo]) * GW;
+    items[it] = make_int4(lo, p, min(GW, off[lo + 1] - p), 0);
+  }
+}
+
+// One row item per block: up to GW query rows x assigned to the same center j,
+// a warp each, against j's window. Forward: Delta(x). Adjoint (BWD): dL/dx and
+// the row's share of dL/ds. The window goes through shared memory in slabs of
+// SR rows and RC features, copied once per block for all of its rows (4-byte
+// asynchronous copies, all in flight at once); lane l takes row l of each
+// 32-row tile of the slab. Per-row results go to rowv[2x], rowv[2x+1] (the
+// Delta and ds terms), summed in row order afterwards. NK = feature registers
+// per lane for the query gradient (32 * NK >= d).
+constexpr int RC = 64;                           // features per staged chunk
+constexpr int RP = RC + 4;                       // staged row pitch: float4 reads without bank conflicts
+constexpr int NT = 8;                            // 32-row tiles per slab
+constexpr int SR = 32 * NT;                      // window rows per slab
+template <bool BWD, int NK>
+__global__ void __launch_bounds__(32 * GW) k_rows(Dev s, BandParams bp, const float* __restrict__ Q, int64_t m,
+                                                  int64_t ldq, const int* __restrict__ list,
+                                                  const int4* __restrict__ items, const int* __restrict__ nitems,
+                                                  const double* __restrict__ cn, float* __restrict__ delta,
+                                                  const double* __restrict__ grad_loss, float* __restrict__ grad_q,
+                                                  int64_t ldg, double* __restrict__ rowv) {
+  extern __shared__ __align__(16) float sm[];   // [GW][dq] query rows | [SR][RP] slab | [SR] weights | [SR] row offsets
+  const int dq = (s.d + 3) & ~3;
+  float* xq = sm;
+  float* ys = xq + GW * dq;
+  float* yw = ys + SR * RP;
+  int64_t* yx = reinterpret_cast<int64_t*>(yw + SR);
+  if ((int)blockIdx.x >= *nitems) return;
+  const int4 item = items[blockIdx.x];
+  const int j = item.x, n = item.z;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const bool mine = w < n;
+  const int64_t x = mine ? list[item.y + w] : 0;
+  const int head = s.head[j], size = s.tail[j] - head;
+  const int64_t base = (int64_t)j * s.cap + head;
+  float* xr = xq + w * dq;
+  if (mine) {
+    for (int k = lane; k < dq; k += 32) {
+      if (k < s.d) cp_async4(xr + k, Q + x * ldq + k);
+      else xr[k] = 0.0f;
+    }
+  }
+  float inner = 0.0f, dsum = 0.0f, csum = 0.0f;
+  float u[NK];
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const int r = rb + q;
-            const float* src = s.X + __shfl_sync(0xffffffffu, my_yi, r & 31) * s.ldx + k0;
-            v[q][0] = (r < nrow && lane < kn) ? __ldg(src + lane) : 0.0f;
-            v[q][1] = (r < nrow && lane + 32 < kn) ? __ldg(src + lane + 32) : 0.0f;
-          }
+  for (int i = 0; i < NK; ++i) u[i] = 0.0f;
+  for (int s0 = 0; s0 < size; s0 += SR) {
+    const int nr = min(SR, size - s0);
+    const int ntile = (nr + 31) / 32;
+    __syncthreads();                            // the previous slab's readers are done
+    for (int r = threadIdx.x; r < nr; r += 32 * GW) {
+      yx[r] = (int64_t)s.yi[base + s0 + r] * s.ldx;
+      yw[r] = s.w32[base + s0 + r];
+    }
+    __syncthreads();
+    float d2[NT];
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const int r = rb + q;
-            if (r < nrow) {
-              if (lane < kn) ys[r][lane] = v[q][0];
-              if (lane + 32 < kn) ys[r][lane + 32] = v[q][1];
+    for (int t8 = 0; t8 < NT; ++t8) d2[t8] = 0.0f;
+    for (int k0 = 0; k0 < s.d; k0 += RC) {
+      const int kn = min(RC, s.d - k0), kp = (kn + 3) & ~3;
+      if (k0 > 0) __syncthreads();              // the previous feature chunk's readers are done
+      for (int r = w; r < nr; r += GW) {
+        const float* src = s.X + yx[r] + k0;
+        float* dst = ys + r * RP;
+        for (int c = lane; c < kp; c += 32) {
+          if (c < kn) cp_async4(dst + c, src + c);
+          else dst[c] = 0.0f;
+        }
+      }
+      cp_async_wait_all();
+      __syncthreads();
+      if (mine) {
+        const float* q = xr + k0;
+        for (int kk = 0; kk < kp; kk += 4) {
+          const float4 q4 = *reinterpret_cast<const float4*>(q + kk);
+#pragma unroll
+          for (int t8 = 0; t8 < NT; ++t8) {
+            if (t8 < ntile) {
+              const float4 y4 = *reinterpret_cast<const float4*>(ys + (t8 * 32 + lane) * RP + kk);
+              float sum = d2[t8];
+              float df = q4.x - y4.x;
+              sum = fmaf(df, df, sum);
+              df = q4.y - y4.y;
+              sum = fmaf(df, df, sum);
+              df = q4.z - y4.z;
+              sum = fmaf(df, df, sum);
+              df = q4.w - y4.w;
+              d2[t8] = fmaf(df, df, sum);
             }
           }
         }
-        __syncwarp();
-        if (live)
-          for (int kk = 0; kk < kn; ++kk) {
-            const float df = xr[k0 + kk] - ys[lane][kk];
-            d2 = fmaf(df, df, d2);
-          }
       }
-      float K, dks, g;
-      pair_terms(bp, d2, K, dks, g);
-      const float wt = live ? s.w32[row] : 0.0f;
-      inner = fmaf(wt, K, inner);
-      if constexpr (BWD) {
-        dsum = fmaf(wt, dks, dsum);
-        const float c = wt * g * K;
-        csum += c;
-        // u = sum_t c_t y_t: broadcast each lane's c, lanes over the features
-        // (rows from the staged block when it holds all the features)
-        const int nt = min(32, size - t0);
-        for (int tt = 0; tt < nt; ++tt) {
-          const float ct = __shfl_sync(0xffffffffu, c, tt);
-          const float* yt = s.d <= RC ? ys[tt] : support_row(s, base + t0 + tt);
+    }
+    if (mine) {
+      float cv[NT];
 #pragma unroll
-          for (int i = 0; i < NK; ++i) {
-            const int k = lane + 32 * i;
-            if (k < s.d) u[i] = fmaf(ct, yt[k], u[i]);
+      for (int t8 = 0; t8 < NT; ++t8) {
+        cv[t8] = 0.0f;
+        if (t8 < ntile) {
+          const int r = t8 * 32 + lane;
+          const bool live = r < nr;
+          float K, dks, g;
+          pair_terms(bp, live ? d2[t8] : 0.0f, K, dks, g);
+          const float wt = live ? yw[r] : 0.0f;
+          inner = fmaf(wt, K, inner);
+          if constexpr (BWD) {
+            dsum = fmaf(wt, dks, dsum);
+            cv[t8] = wt * g * K;
+            csum += cv[t8];
+          }
+        }
+      }
+      if constexpr (BWD) {
+        // u = sum_t c_t y_t: broadcast each lane's c, lanes over the features
+        // (rows from the slab when it holds all the features, else from X)
+#pragma unroll
+        for (int t8 = 0; t8 < NT; ++t8) {
+          const int nt = min(32, nr - t8 * 32);
+          for (int tt = 0; tt < nt; ++tt) {
+            const float ct = __shfl_sync(0xffffffffu, cv[t8], tt);
+            const float* yt = s.d <= RC ? ys + (t8 * 32 + tt) * RP : s.X + yx[t8 * 32 + tt];
+#pragma unroll
+            for (int i = 0; i < NK; ++i) {
+              const int k = lane + 32 * i;
+              if (k < s.d) u[i] = fmaf(ct, yt[k], u[i]);
+            }
           }
         }
       }
     }
-    const double in = warp_sum_d((double)inner);
-    my_delta = 1.0 - 2.0 * in + cn[2 * j];
-    if (!BWD && lane == 0 && delta) delta[x] = (float)my_delta;
-    if constexpr (BWD) {
-      const double ds = warp_sum_d((double)dsum);
-      my_ds = -2.0 * ds + cn[2 * j + 1];
-      const float cs = warp_sum_f(csum);
-      const float scale = (float)(2.0 * grad_loss[0] / (double)m);
+  }
+  cp_async_wait_all();                          // an empty window staged nothing: the query row's copies
+  __syncwarp();
+  if (!mine) return;
+  const double in = warp_sum_d((double)inner);
+  const double my_delta = 1.0 - 2.0 * in + cn[2 * j];
+  double my_ds = 0.0;
+  if (!BWD && lane == 0 && delta) delta[x] = (float)my_delta;
+  if constexpr (BWD) {
+    const double ds = warp_sum_d((double)dsum);
+    my_ds = -2.0 * ds + cn[2 * j + 1];
+    const float cs = warp_sum_f(csum);
+    const float scale = (float)(2.0 * grad_loss[0] / (double)m);
 #pragma unroll
-      for (int i = 0; i < NK; ++i) {
-        const int k = lane + 32 * i;
-        if (k < s.d) grad_q[x * ldg + k] = scale * fmaf(xr[k], cs, -u[i]);
-      }
+    for (int i = 0; i < NK; ++i) {
+      const int k = lane + 32 * i;
+      if (k < s.d) grad_q[x * ldg + k] = scale * fmaf(xr[k], cs, -u[i]);
     }
   }
-  if (lane == 0) { red[w][0] = my_delta; red[w][1] = my_ds; }
-  __syncthreads();
-  if (threadIdx.x < 2) {
-    double v = 0.0;
-    for (int q = 0; q < GW; ++q) v += red[q][threadIdx.x];
-    blk[(int64_t)blockIdx.x * 2 + threadIdx.x] = v;
+  if (lane == 0) {
+    rowv[2 * x] = my_delta;
+    rowv[2 * x + 1] = my_ds;
   }
 }
 
 // loss = (1/m) sum Delta; ds = grad_loss * (1/m) sum (ds terms). One block, fixed order.
-__global__ void k_rows_sum(int nblk, int64_t m, const double* blk, double* loss, const double* grad_loss,
-                           double* ds) {
+__global__ void k_rows_sum(int64_t m, const double* rowv, double* loss, const double* grad_loss, double* ds) {
   __shared__ double r0[256], r1[256];
   double a = 0.0, b = 0.0;
-  for (int i = threadIdx.x; i < nblk; i += 256) {
-    a += blk[2 * i];
-    b += blk[2 * i + 1];
+  for (int64_t i = threadIdx.x; i < m; i += 256) {
+    a += rowv[2 * i];
+    b += rowv[2 * i + 1];
   }
   r0[threadIdx.x] = a;
   r1[threadIdx.x] = b;
@@ -320,20 +436,48 @@ __global__ void k_rows_sum(int nblk, int64_t m, const double* blk, double* loss,
   }
 }
 
+constexpr size_t ROWS_SMEM_MAX = (size_t)(GW * 1024 + SR * RP + SR) * sizeof(float) + SR * sizeof(int64_t);
+
 template <bool BWD, int NK>
-cudaError_t launch_rows(const Dev& s, const BandParams& bp, const float* Q, int64_t m, int64_t ldq,
-                        const int32_t* assign, const double* cn, float* delta, const double* grad_loss, float* grad_q,
-                        int64_t ldg, double* blk, int64_t nblk, size_t smem, cudaStream_t st) {
+cudaError_t launch_rows(const Dev& s, const BandParams& bp, const float* Q, int64_t m, int64_t ldq, const int* list,
+                        const int4* items, const int* nitems, int64_t nblk, const double* cn, float* delta,
+                        const double* grad_loss, float* grad_q, int64_t ldg, double* rowv, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(k_rows<BWD, NK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               GW * (1024 + 32 * (RC + 1)) * 4);
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_rows<BWD, NK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ROWS_SMEM_MAX);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_rows<BWD, NK><<<(unsigned)nblk, 32 * GW, smem, st>>>(s, bp, Q, m, ldq, assign, cn, delta, grad_loss, grad_q, ldg,
-                                                         blk);
+  const size_t smem = (size_t)(GW * ((s.d + 3) & ~3) + SR * RP + SR) * sizeof(float) + SR * sizeof(int64_t);
+  k_rows<BWD, NK><<<(unsigned)nblk, 32 * GW, smem, st>>>(s, bp, Q, m, ldq, list, items, nitems, cn, delta, grad_loss,
+                                                         grad_q, ldg, rowv);
   return cudaGetLastError();
+}
+
+// Objective workspace, carved from ws (doubles; cudaMalloc'd, so 16-byte aligned):
+// row items | pair partials | N_j, N'_j | per-row terms | item count | row list.
+struct GradWs {
+  int4* items;
+  double* part;
+  double* cn;
+  double* rowv;
+  int* nitems;
+  int* list;
+};
+
+int pair_blocks(const Dev& s) { return (s.cap + 31) / 32 < 8 ? (s.cap + 31) / 32 : 8; }
+int64_t row_items_max(const Dev& s, int64_t m) { return (m + GW - 1) / GW + s.k; }
+
+GradWs carve(const Dev& s, int64_t m, double* ws) {
+  GradWs g;
+  g.items = reinterpret_cast<int4*>(ws);
+  g.part = ws + 2 * row_items_max(s, m);
+  g.cn = g.part + (size_t)s.k * pair_blocks(s) * 2;
+  g.rowv = g.cn + (size_t)s.k * 2;
+  g.nitems = reinterpret_cast<int*>(g.rowv + 2 * m);
+  g.list = g.nitems + 2;
+  return g;
 }
 
 BandParams band_params(const Dev& s, double log_sigma) {
@@ -348,41 +492,36 @@ BandParams band_params(const Dev& s, double log_sigma) {
 
 }  // namespace
 
-int grad_center_chunks(const Dev& s) { return (s.cap + 31) / 32; }
-
 size_t grad_workspace_doubles(const Dev& s, int64_t m) {
-  const int64_t nblk = (m + GW - 1) / GW;
-  return (size_t)s.k * grad_center_chunks(s) * 2 + (size_t)s.k * 2 + (size_t)nblk * 2;
+  return (size_t)(2 * row_items_max(s, m)) + (size_t)s.k * pair_blocks(s) * 2 + (size_t)s.k * 2 + (size_t)m * 2 + 1 +
+         (size_t)(m + 1) / 2;
 }
 
 cudaError_t launch_objective(const Dev& s, double log_sigma, const float* Q, int64_t m, int64_t ldq,
                              const int32_t* assign, double* loss, float* delta, const double* grad_loss,
                              float* grad_q, int64_t ldg, double* grad_s, double* ws, cudaStream_t st) {
+  if (m > (int64_t)0x3fffffff || s.k > 1024) return cudaErrorInvalidValue;
   const BandParams bp = band_params(s, log_sigma);
-  const int nch = grad_center_chunks(s);
-  double* part = ws;
-  double* cn = part + (size_t)s.k * nch * 2;
-  double* blk = cn + (size_t)s.k * 2;
-  const int64_t nblk = (m + GW - 1) / GW;
-  if (nblk > (int64_t)0x7fffffff) return cudaErrorInvalidValue;
-  k_center_pairs<<<dim3(s.k, nch), 32 * GW, 0, st>>>(s, bp, nch, part);
+  const int py = pair_blocks(s);
+  const GradWs g = carve(s, m, ws);
+  const int64_t nblk = row_items_max(s, m);
+  k_center_pairs<<<dim3(s.k, py), 32 * GW, 0, st>>>(s, bp, py, g.part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_center_sum<<<(s.k + 127) / 128, 128, 0, st>>>(s, nch, part, cn);
+  k_prepare<<<1, 1024, 0, st>>>(s, py, g.part, g.cn, assign, m, g.list, g.items, g.nitems);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t smem = (size_t)GW * (s.d + 32 * (RC + 1)) * sizeof(float);   // query rows + staged window rows
   if (grad_q) {
-    if (s.d <= 64) e = launch_rows<true, 2>(s, bp, Q, m, ldq, assign, cn, nullptr, grad_loss, grad_q, ldg, blk, nblk, smem, st);
-    else if (s.d <= 128) e = launch_rows<true, 4>(s, bp, Q, m, ldq, assign, cn, nullptr, grad_loss, grad_q, ldg, blk, nblk, smem, st);
-    else if (s.d <= 256) e = launch_rows<true, 8>(s, bp, Q, m, ldq, assign, cn, nullptr, grad_loss, grad_q, ldg, blk, nblk, smem, st);
-    else if (s.d <= 512) e = launch_rows<true, 16>(s, bp, Q, m, ldq, assign, cn, nullptr, grad_loss, grad_q, ldg, blk, nblk, smem, st);
-    else e = launch_rows<true, 32>(s, bp, Q, m, ldq, assign, cn, nullptr, grad_loss, grad_q, ldg, blk, nblk, smem, st);
+    if (s.d <= 64) e = launch_rows<true, 2>(s, bp, Q, m, ldq, g.list, g.items, g.nitems, nblk, g.cn, nullptr, grad_loss, grad_q, ldg, g.rowv, st);
+    else if (s.d <= 128) e = launch_rows<true, 4>(s, bp, Q, m, ldq, g.list, g.items, g.nitems, nblk, g.cn, nullptr, grad_loss, grad_q, ldg, g.rowv, st);
+    else if (s.d <= 256) e = launch_rows<true, 8>(s, bp, Q, m, ldq, g.list, g.items, g.nitems, nblk, g.cn, nullptr, grad_loss, grad_q, ldg, g.rowv, st);
+    else if (s.d <= 512) e = launch_rows<true, 16>(s, bp, Q, m, ldq, g.list, g.items, g.nitems, nblk, g.cn, nullptr, grad_loss, grad_q, ldg, g.rowv, st);
+    else e = launch_rows<true, 32>(s, bp, Q, m, ldq, g.list, g.items, g.nitems, nblk, g.cn, nullptr, grad_loss, grad_q, ldg, g.rowv, st);
   } else {
-    e = launch_rows<false, 1>(s, bp, Q, m, ldq, assign, cn, delta, nullptr, nullptr, 0, blk, nblk, smem, st);
+    e = launch_rows<false, 1>(s, bp, Q, m, ldq, g.list, g.items, g.nitems, nblk, g.cn, delta, nullptr, nullptr, 0, g.rowv, st);
   }
   if (e != cudaSuccess) return e;
-  k_rows_sum<<<1, 256, 0, st>>>((int)nblk, m, blk, loss, grad_loss, grad_s);
+  k_rows_sum<<<1, 256, 0, st>>>(m, g.rowv, loss, grad_loss, grad_s);
   return cudaGetLastError();
 }
 

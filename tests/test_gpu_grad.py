@@ -94,6 +94,22 @@ def test_objective_and_adjoint_small(kernel, precision):
     run.close()
 
 
+def test_objective_wide_rows_and_long_windows():
+    """d = 150 (several feature chunks in the pair and row kernels, ragged last
+    chunk), windows of more than 256 rows (several slabs of the row kernel), a
+    ragged batch of 333 rows, and arbitrary assignments that leave a center
+    without rows."""
+    X, _ = inputs.isotropic_mixture(3000, 150, 3, seed=6)
+    run, Xd, s = _run(X, 3, 300, 400, "gaussian", "fp32", 6)
+    assert max(run.get_state()["rows_per_center"]) > 256
+    batch = inputs.batch_stream(len(X), 333, 1, seed=9)[0]
+    rng = np.random.default_rng(5)
+    for assign in (rng.integers(0, 2, size=333),
+                   run.assign(Xd[batch.astype(np.int64)])[0].cpu().numpy()):
+        _check(run, Xd, X, "gaussian", s, batch, np.asarray(assign))
+    run.close()
+
+
 def test_autograd_matches_the_adjoint():
     torch = torch_cuda()
     from paper_2410_05902_gb300.autograd import objective
