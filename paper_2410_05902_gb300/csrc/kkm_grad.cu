@@ -26,7 +26,6 @@ namespace kkm {
 namespace {
 
 constexpr int GW = 8;          // warps per block
-constexpr int DCH = 128;       // feature columns staged per pass (pair kernel)
 
 struct BandParams {
   int kind;         // K_GAUSS or K_LAPLACE
@@ -72,95 +71,111 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+// Window slabs in shared memory: SR rows of RC features (pitch RP: float4
+// reads without bank conflicts), with each row's weight and data-row offset.
+constexpr int RC = 64;                           // features per staged chunk
+constexpr int RP = RC + 4;                       // staged row pitch
+constexpr int NT = 8;                            // 32-row tiles per slab
+constexpr int SR = 32 * NT;                      // rows per slab
+constexpr size_t SLAB_SMEM = (size_t)(SR * RP + SR) * sizeof(float) + SR * sizeof(int64_t);
+
 // N_j and N'_j partials. Block (j, y) takes the 32-row chunks c = y, y + py, ...
-// of center j's window; chunk c meets chunks c + dl (mod nc) for dl = 0..nc/2,
-// so each unordered pair of chunks is summed once (twice its weight off the
-// diagonal; with nc even, the pair at distance nc/2 belongs to the lower
-// chunk). 32 rows and DCH feature columns of each side are staged in shared
-// memory; warp w takes rows w, w+8, w+16, w+24 of chunk c, lane l row l of the
-// other chunk. Every block writes its partial (zero when it has no chunk).
+// of center j's window; chunk c meets its partners c + dl (mod nc) for
+// dl = 0..nc/2, so each unordered pair of chunks is summed once (weight 2 off
+// the diagonal; with nc even, the pair at distance nc/2 belongs to the lower
+// chunk). A slab holds chunk c in its first tile and up to NT - 1 partners in
+// the others, copied with 4-byte asynchronous copies, all in flight at once
+// (rows past the window are zero with zero weight). Warp w takes rows w, w+8,
+// w+16, w+24 of chunk c, lane l row l of each partner. Every block writes its
+// partial (zero when it has no chunk).
 __global__ void __launch_bounds__(32 * GW) k_center_pairs(Dev s, BandParams bp, int py, double* part) {
-  __shared__ __align__(16) float A[32][DCH + 4];   // rows padded to 16 bytes: float4 reads,
-  __shared__ __align__(16) float B[32][DCH + 4];   // no bank conflicts within a quarter-warp
-  __shared__ int64_t ia[32], ib[32];            // data rows of the chunk's and the staged block's support rows
+  extern __shared__ __align__(16) float sm[];
+  float* ys = sm;                               // [SR][RP]
+  float* yw = ys + SR * RP;                     // [SR] weights, partners' doubled off the diagonal
+  int64_t* yx = reinterpret_cast<int64_t*>(yw + SR);   // [SR] data-row offsets, -1 past the window
   __shared__ double red[GW][2];
+  KKM_GRID_DEP_WAIT();
+  KKM_LAUNCH_DEPENDENTS();
   const int j = blockIdx.x, y = blockIdx.y;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int head = s.head[j], size = s.tail[j] - head;
   const int nc = (size + 31) / 32, h = nc / 2;
   const int64_t base = (int64_t)j * s.cap + head;
   float acc = 0.0f, accs = 0.0f;
-  // stages rows idx[0..32) (features k0..k0+kn) into T: every load issued before the stores
-  // (features past kn up to the next multiple of 4 are zero: they add nothing)
-  auto stage = [&](float (*T)[DCH + 4], const int64_t* idx, int k0, int kn) {
-    const int kp = (kn + 3) & ~3;
-    float v[(32 * DCH) / (32 * GW)];
-#pragma unroll
-    for (int q = 0; q < (32 * DCH) / (32 * GW); ++q) {
-      const int e = threadIdx.x + q * 32 * GW;
-      const int r = e / kp, k = e - r * kp;
-      v[q] = e < 32 * kp && k < kn && idx[r] >= 0 ? __ldg(s.X + idx[r] * s.ldx + k0 + k) : 0.0f;
-    }
-#pragma unroll
-    for (int q = 0; q < (32 * DCH) / (32 * GW); ++q) {
-      const int e = threadIdx.x + q * 32 * GW;
-      const int r = e / kp, k = e - r * kp;
-      if (e < 32 * kp) T[r][k] = v[q];
-    }
-  };
-  const bool a_once = s.d <= DCH;               // one feature chunk: the chunk's rows are staged once
   for (int c = y; c < nc; c += py) {
-    const int r0 = c * 32;
-    float wa[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int r = r0 + w + GW * u;
-      wa[u] = r < size ? s.w32[base + r] : 0.0f;
-    }
-    __syncthreads();                            // the previous chunk's readers of ia and A are done
-    if (threadIdx.x < 32) ia[threadIdx.x] = r0 + (int)threadIdx.x < size ? (int64_t)s.yi[base + r0 + threadIdx.x] : -1;
-    __syncthreads();
-    if (a_once) stage(A, ia, 0, s.d);
-    for (int dl = 0; dl <= h; ++dl) {
-      if ((nc & 1) == 0 && dl == h && c >= h) break;   // the pair {c - h, c} is the lower chunk's
-      const int cb = c + dl < nc ? c + dl : c + dl - nc;
-      const int t0 = cb * 32;
-      const float fac = dl == 0 ? 1.0f : 2.0f;
-      float d2[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    const int nb = ((nc & 1) == 0 && c >= h) ? h : h + 1;   // partners of c
+    for (int q0 = 0; q0 < nb; q0 += NT - 1) {
+      const int nq = min(NT - 1, nb - q0);
+      const int nr = 32 * (1 + nq);
+      __syncthreads();                          // the previous slab's readers are done
+      for (int r = threadIdx.x; r < nr; r += 32 * GW) {
+        int t = c * 32 + r;
+        float f = 1.0f;
+        if (r >= 32) {
+          const int dl = q0 + (r >> 5) - 1;
+          t = (c + dl < nc ? c + dl : c + dl - nc) * 32 + (r & 31);
+          f = dl == 0 ? 1.0f : 2.0f;
+        }
+        const bool live = t < size;
+        yx[r] = live ? (int64_t)s.yi[base + t] * s.ldx : -1;
+        yw[r] = live ? f * s.w32[base + t] : 0.0f;
+      }
       __syncthreads();
-      if (threadIdx.x < 32) ib[threadIdx.x] = t0 + (int)threadIdx.x < size ? (int64_t)s.yi[base + t0 + threadIdx.x] : -1;
-      for (int k0 = 0; k0 < s.d; k0 += DCH) {
-        const int kn = min(DCH, s.d - k0);
-        __syncthreads();
-        if (!a_once) stage(A, ia, k0, kn);
-        stage(B, ib, k0, kn);
-        __syncthreads();
-        const int kp = (kn + 3) & ~3;
-        for (int k = 0; k < kp; k += 4) {
-          const float4 b4 = *reinterpret_cast<const float4*>(&B[lane][k]);
+      float d2[NT - 1][4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float4 a4 = *reinterpret_cast<const float4*>(&A[w + GW * u][k]);
-            float sum = d2[u];
-            float df = a4.x - b4.x;
-            sum = fmaf(df, df, sum);
-            df = a4.y - b4.y;
-            sum = fmaf(df, df, sum);
-            df = a4.z - b4.z;
-            sum = fmaf(df, df, sum);
-            df = a4.w - b4.w;
-            d2[u] = fmaf(df, df, sum);
+      for (int q = 0; q < NT - 1; ++q)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) d2[q][u] = 0.0f;
+      for (int k0 = 0; k0 < s.d; k0 += RC) {
+        const int kn = min(RC, s.d - k0), kp = (kn + 3) & ~3;
+        if (k0 > 0) __syncthreads();            // the previous feature chunk's readers are done
+        for (int r = w; r < nr; r += GW) {
+          const int64_t o = yx[r];
+          float* dst = ys + r * RP;
+          for (int cc = lane; cc < kp; cc += 32) {
+            if (o >= 0 && cc < kn) cp_async4(dst + cc, s.X + o + k0 + cc);
+            else dst[cc] = 0.0f;
+          }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        for (int kk = 0; kk < kp; kk += 4) {
+          float4 a4[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) a4[u] = *reinterpret_cast<const float4*>(ys + (w + GW * u) * RP + kk);
+#pragma unroll
+          for (int q = 0; q < NT - 1; ++q) {
+            if (q < nq) {
+              const float4 b4 = *reinterpret_cast<const float4*>(ys + (32 + 32 * q + lane) * RP + kk);
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                float sum = d2[q][u];
+                float df = a4[u].x - b4.x;
+                sum = fmaf(df, df, sum);
+                df = a4[u].y - b4.y;
+                sum = fmaf(df, df, sum);
+                df = a4[u].z - b4.z;
+                sum = fmaf(df, df, sum);
+                df = a4[u].w - b4.w;
+                d2[q][u] = fmaf(df, df, sum);
+              }
+            }
           }
         }
       }
-      const float wb = t0 + lane < size ? fac * s.w32[base + t0 + lane] : 0.0f;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        float K, dks, g;
-        pair_terms(bp, d2[u], K, dks, g);
-        const float ww = wa[u] * wb;
-        acc = fmaf(ww, K, acc);
-        accs = fmaf(ww, dks, accs);
+      for (int q = 0; q < NT - 1; ++q) {
+        if (q < nq) {
+          const float wb = yw[32 + 32 * q + lane];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            float K, dks, g;
+            pair_terms(bp, d2[q][u], K, dks, g);
+            const float ww = yw[w + GW * u] * wb;
+            acc = fmaf(ww, K, acc);
+            accs = fmaf(ww, dks, accs);
+          }
+        }
       }
     }
   }
@@ -185,6 +200,8 @@ __global__ void __launch_bounds__(1024) k_prepare(Dev s, int py, const double* _
                                                   int64_t m, int* __restrict__ list, int4* __restrict__ items,
                                                   int* __restrict__ nitems) {
   __shared__ int cnt[1024], cur[1024], off[1025], ist[1025];
+  KKM_GRID_DEP_WAIT();
+  KKM_LAUNCH_DEPENDENTS();
   const int t = threadIdx.x;
   if (t < s.k) {
     double a = 0.0, b = 0.0;
@@ -267,10 +284,6 @@ __global__ void __launch_bounds__(1024) k_prepare(Dev s, int py, const double* _
 // 32-row tile of the slab. Per-row results go to rowv[2x], rowv[2x+1] (the
 // Delta and ds terms), summed in row order afterwards. NK = feature registers
 // per lane for the query gradient (32 * NK >= d).
-constexpr int RC = 64;                           // features per staged chunk
-constexpr int RP = RC + 4;                       // staged row pitch: float4 reads without bank conflicts
-constexpr int NT = 8;                            // 32-row tiles per slab
-constexpr int SR = 32 * NT;                      // window rows per slab
 template <bool BWD, int NK>
 __global__ void __launch_bounds__(32 * GW) k_rows(Dev s, BandParams bp, const float* __restrict__ Q, int64_t m,
                                                   int64_t ldq, const int* __restrict__ list,
@@ -284,6 +297,8 @@ __global__ void __launch_bounds__(32 * GW) k_rows(Dev s, BandParams bp, const fl
   float* ys = xq + GW * dq;
   float* yw = ys + SR * RP;
   int64_t* yx = reinterpret_cast<int64_t*>(yw + SR);
+  KKM_GRID_DEP_WAIT();
+  KKM_LAUNCH_DEPENDENTS();
   if ((int)blockIdx.x >= *nitems) return;
   const int4 item = items[blockIdx.x];
   const int j = item.x, n = item.z;
@@ -415,6 +430,8 @@ __global__ void __launch_bounds__(32 * GW) k_rows(Dev s, BandParams bp, const fl
 // loss = (1/m) sum Delta; ds = grad_loss * (1/m) sum (ds terms). One block, fixed order.
 __global__ void k_rows_sum(int64_t m, const double* rowv, double* loss, const double* grad_loss, double* ds) {
   __shared__ double r0[256], r1[256];
+  KKM_GRID_DEP_WAIT();
+  KKM_LAUNCH_DEPENDENTS();
   double a = 0.0, b = 0.0;
   for (int64_t i = threadIdx.x; i < m; i += 256) {
     a += rowv[2 * i];
@@ -450,9 +467,8 @@ cudaError_t launch_rows(const Dev& s, const BandParams& bp, const float* Q, int6
     attr = true;
   }
   const size_t smem = (size_t)(GW * ((s.d + 3) & ~3) + SR * RP + SR) * sizeof(float) + SR * sizeof(int64_t);
-  k_rows<BWD, NK><<<(unsigned)nblk, 32 * GW, smem, st>>>(s, bp, Q, m, ldq, list, items, nitems, cn, delta, grad_loss,
-                                                         grad_q, ldg, rowv);
-  return cudaGetLastError();
+  return launch_pdl(k_rows<BWD, NK>, dim3((unsigned)nblk), dim3(32 * GW), smem, st, s, bp, Q, m, ldq, list, items,
+                    nitems, cn, delta, grad_loss, grad_q, ldg, rowv);
 }
 
 // Objective workspace, carved from ws (doubles; cudaMalloc'd, so 16-byte aligned):
@@ -505,11 +521,16 @@ cudaError_t launch_objective(const Dev& s, double log_sigma, const float* Q, int
   const int py = pair_blocks(s);
   const GradWs g = carve(s, m, ws);
   const int64_t nblk = row_items_max(s, m);
-  k_center_pairs<<<dim3(s.k, py), 32 * GW, 0, st>>>(s, bp, py, g.part);
-  cudaError_t e = cudaGetLastError();
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(k_center_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SLAB_SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  cudaError_t e = launch_pdl(k_center_pairs, dim3(s.k, py), dim3(32 * GW), SLAB_SMEM, st, s, bp, py, g.part);
   if (e != cudaSuccess) return e;
-  k_prepare<<<1, 1024, 0, st>>>(s, py, g.part, g.cn, assign, m, g.list, g.items, g.nitems);
-  e = cudaGetLastError();
+  e = launch_pdl(k_prepare, dim3(1), dim3(1024), 0, st, s, py, (const double*)g.part, g.cn, assign, m, g.list, g.items,
+                 g.nitems);
   if (e != cudaSuccess) return e;
   if (grad_q) {
     if (s.d <= 64) e = launch_rows<true, 2>(s, bp, Q, m, ldq, g.list, g.items, g.nitems, nblk, g.cn, nullptr, grad_loss, grad_q, ldg, g.rowv, st);
@@ -521,8 +542,7 @@ cudaError_t launch_objective(const Dev& s, double log_sigma, const float* Q, int
     e = launch_rows<false, 1>(s, bp, Q, m, ldq, g.list, g.items, g.nitems, nblk, g.cn, delta, nullptr, nullptr, 0, g.rowv, st);
   }
   if (e != cudaSuccess) return e;
-  k_rows_sum<<<1, 256, 0, st>>>(m, g.rowv, loss, grad_loss, grad_s);
-  return cudaGetLastError();
+  return launch_pdl(k_rows_sum, dim3(1), dim3(256), 0, st, m, (const double*)g.rowv, loss, grad_loss, grad_s);
 }
 
 }  // namespace kkm
