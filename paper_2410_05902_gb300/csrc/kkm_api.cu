@@ -687,10 +687,11 @@ kkm_status objective_call(kkm_ctx* c, const float* Q, int64_t m, int64_t ldq, co
     if (e != cudaSuccess) return fail(c, KKM_ENOMEM, std::string("workspace: ") + cudaGetErrorString(e));
     c->gws = static_cast<double*>(p);
     c->gws_len = need;
+    KKM_CU(cudaMemsetAsync(p, 0, need * sizeof(double), c->stream), "workspace clear");   // the kernels' counter starts at 0
   }
   KKM_CU(kkm::launch_objective(s, log_sigma, Q, m, ldq, assign, loss, delta, grad_loss, grad_q, ldg, grad_s,
                                c->gws, c->stream), "objective kernels");
-  c->launches += 4;
+  c->launches += 2;
   return KKM_OK;
 }
 
