@@ -257,7 +257,7 @@ kkm_status kkm_objective(kkm_ctx* ctx, const float* Q, int64_t m, int64_t ldq, d
  * Laplacian sigma = e^s (the context's own kernel parameter is not used or
  * changed). Only the Gaussian and Laplacian kernels qualify (KKM_ENOTSUP
  * otherwise), with d <= 1024.
- *   Q        : device, m x d FP32, leading dimension ldq >= d; m >= 1.
+ *   Q        : device, m x d FP32, leading dimension ldq >= d; 1 <= m < 2^30.
  *   assign   : device, m int32 centers in [0, k) (an index outside sets the
  *              device status; the next synchronising call returns KKM_EINVAL).
  *   loss_out : device, 1 double: the objective.
@@ -267,8 +267,10 @@ kkm_status kkm_objective(kkm_ctx* ctx, const float* Q, int64_t m, int64_t ldq, d
  *   grad_q         : device, m x d FP32 (leading dimension ldg >= d):
  *                    grad_loss * d objective / d Q. Support rows are constants.
  *   grad_log_sigma : device, 1 double: grad_loss * d objective / d s.
- * Both calls are asynchronous on the context's stream and allocate a
- * workspace that grows with m and lives until kkm_destroy. */
+ * Both calls are asynchronous on the context's stream (two kernel launches
+ * each) and allocate a workspace that grows with m and lives until
+ * kkm_destroy. Results are deterministic: every sum across rows and blocks
+ * runs in a fixed order. */
 kkm_status kkm_objective_fwd(kkm_ctx* ctx, const float* Q, int64_t m, int64_t ldq, const int32_t* assign,
                              double log_sigma, double* loss_out, float* delta_out);
 kkm_status kkm_objective_bwd(kkm_ctx* ctx, const float* Q, int64_t m, int64_t ldq, const int32_t* assign,

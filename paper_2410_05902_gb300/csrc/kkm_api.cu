@@ -675,7 +675,8 @@ kkm_status objective_call(kkm_ctx* c, const float* Q, int64_t m, int64_t ldq, co
   if (s.kind != kkm::K_GAUSS && s.kind != kkm::K_LAPLACE)
     return fail(c, KKM_ENOTSUP, "the bandwidth objective needs the Gaussian or Laplacian kernel");
   if (s.d > 1024) return fail(c, KKM_ENOTSUP, "the bandwidth objective supports d <= 1024");
-  if (m < 1 || !Q || ldq < s.d || !assign) return fail(c, KKM_EINVAL, "bad query rows or assignments");
+  if (m < 1 || m >= ((int64_t)1 << 30) || !Q || ldq < s.d || !assign)
+    return fail(c, KKM_EINVAL, "bad query rows or assignments (1 <= m < 2^30)");
   if (!std::isfinite(log_sigma)) return fail(c, KKM_EINVAL, "log_sigma must be finite");
   const size_t need = kkm::grad_workspace_doubles(s, m);
   if (need > c->gws_len) {
