@@ -341,6 +341,7 @@ def time_form(form, args, X, Xd, kappa, init, rank, world, dev, barrier):
     ev0.record(stream)
     for _ in range(args.steps):
         run.step()
+    run.flush()                           # the last step's weight update (each step queues the previous one's)
     ev1.record(stream)
     barrier()
     ms = ev0.elapsed_time(ev1)
@@ -376,10 +377,12 @@ def time_form(form, args, X, Xd, kappa, init, rank, world, dev, barrier):
     o_out = torch.empty(1, dtype=torch.float64, pin_memory=True).numpy()
     for s_ in range(3):
         kb.kkm_step_host(run.ctx, idx_np[s_], a_out, o_out)
+    run.sync()                            # applies the warm-up's last weight update
     barrier()
     t0 = time.perf_counter()
     for s_ in range(e2e_steps):
         kb.kkm_step_host(run.ctx, idx_np[s_], a_out, o_out)
+    run.sync()                            # and the last timed step's
     t_e2e = reduce_max(time.perf_counter() - t0, world, dev)
     run.close()
     return {"ms": ms, "value": whole_job_value(w.b, w.k, args.steps, world, ms / 1e3), "clocks": clk,

@@ -188,9 +188,18 @@ kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d, int64_t
  *   dist_out      : device, b x k FP32 row-major, or NULL. Receives Delta(x, C_i^j).
  *   batch_obj_out : device, one double, or NULL. Receives
  *                   f_{B_i}(C_i) = (1/b) sum_x min_j Delta(x, C_i^j) (Sec. 3).
- * An index out of range is found on the device, and it poisons the context. */
+ * An index out of range is found on the device, and it poisons the context.
+ * The last kernel of the weight update (k_finalize) is queued at the start of
+ * the next kkm_step, where it runs beside the next batch's gather, or by the
+ * next call that reads or replaces the centers (every call below but
+ * kkm_stats and the timing and launch counters), or by kkm_flush. The
+ * outputs above do not depend on it. */
 kkm_status kkm_step(kkm_ctx* ctx, const int32_t* batch_idx, const int32_t* forced_assign,
                     int32_t* assign_out, float* dist_out, double* batch_obj_out);
+
+/* kkm_flush -- queues the weight update the last kkm_step left pending, if
+ * any, on the context's stream (asynchronous; nothing to do otherwise). */
+kkm_status kkm_flush(kkm_ctx* ctx);
 
 /* kkm_step_eval -- kkm_step (device sampler when batch_idx is NULL) that
  * also evaluates the updated centers on the same batch: obj_before_dev

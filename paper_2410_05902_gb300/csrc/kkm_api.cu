@@ -44,6 +44,7 @@ struct kkm_ctx {
   int32_t* d_hassign = nullptr;
   double* d_hobj = nullptr;
   bool host_pending = false;         // a kkm_step_host call queued work it has not yet waited for
+  bool fin_pending = false;          // the last step's k_finalize is still to run (see flush)
   double* d_objpart = nullptr;
   double* d_obj2 = nullptr;   // kkm_fit: f_B before and after the update
   int32_t objpart_len = 0;
@@ -121,6 +122,26 @@ kkm_status check_usable(kkm_ctx* c) {
   if (c->poisoned) return fail(c, KKM_ESTATE, "context poisoned by an earlier device-side fault");
   if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, KKM_ECUDA, "cudaSetDevice failed");
   return KKM_OK;
+}
+
+// A step (windows form, kkm_step) ends with its window pass and leaves its
+// weight update, k_finalize, to the start of the next step, where it runs
+// beside the next batch's gather. Every call that reads or replaces the
+// centers first runs it here (on the context's stream).
+kkm_status flush(kkm_ctx* c) {
+  if (!c->fin_pending) return KKM_OK;
+  cudaError_t e = kkm::launch_finalize(c->s, c->stream, true);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->s.fin_pending, 0, sizeof(int32_t), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "pending weight update");
+  c->fin_pending = false;
+  c->launches += 1;
+  return KKM_OK;
+}
+
+// check_usable, then the pending weight update.
+kkm_status check_ready(kkm_ctx* c) {
+  const kkm_status st = check_usable(c);
+  return st != KKM_OK ? st : flush(c);
 }
 
 // Synchronises the stream and turns sticky device status bits into an error.
@@ -348,7 +369,7 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
   ALLOC(s.wpairs, s.max_pairs); ALLOC(s.nwpairs, 1); ALLOC(s.wpair_first, k); ALLOC(s.wpair_cnt, k);
   s.wslots = c->use_tc ? 1 : 4;
   ALLOC(s.wpart, (size_t)s.max_pairs * s.wslots * 4);
-  ALLOC(s.iter, 1); ALLOC(s.status, 1); ALLOC(s.stats, 3); ALLOC(s.obj, 1);
+  ALLOC(s.iter, 1); ALLOC(s.fin_pending, 1); ALLOC(s.status, 1); ALLOC(s.stats, 3); ALLOC(s.obj, 1);
   {
     // the finalise step's rate sqrt(n/b) and 1/n, by the host's correctly rounded
     // FP64 operations (the same values the device would compute)
@@ -466,9 +487,12 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
 }
 
 // The kernel sequence of one step, queued on `st`.
+// rotated (kkm_step, windows form): the previous step's k_finalize first (a
+// no-op unless one is pending), the gather beside it, and this step's
+// k_finalize left pending. Otherwise (run groups) finalize ends the step.
 static kkm_status enqueue_step(kkm_ctx* c, cudaStream_t st, const int32_t* batch_idx,
                                const int32_t* forced_assign, int32_t* assign_out, float* dist_out,
-                               double* batch_obj_out, bool timed) {
+                               double* batch_obj_out, bool timed, bool rotated) {
   const Dev& s = c->s;
   if (c->tab) {
     // table form (Appendix A): distances off the table, sort, lay out the batch,
@@ -492,7 +516,8 @@ static kkm_status enqueue_step(kkm_ctx* c, cudaStream_t st, const int32_t* batch
     return KKM_OK;
   }
   // with batch_idx NULL the gather draws the indices itself (SplitMix64)
-  KKM_CU(kkm::launch_gather_batch(s, batch_idx, st), "batch gather");
+  if (rotated) KKM_CU(kkm::launch_finalize(s, st, true), "pending weight update");
+  KKM_CU(kkm::launch_gather_batch(s, batch_idx, st, rotated), "batch gather");
   if (timed) KKM_CU(cudaEventRecord(c->ev[2 * c->ev_used], st), "timing event");
   for (int r = 0; r < (timed ? c->timing_reps : 1); ++r) {   // the pass is idempotent
     if (c->use_tc) KKM_CU(kkm::launch_dist_tc(s, c->tmaps, s.b, st, true), "distance kernel (tcgen05)");
@@ -503,11 +528,11 @@ static kkm_status enqueue_step(kkm_ctx* c, cudaStream_t st, const int32_t* batch
     c->ev_reps[c->ev_used++] = c->timing_reps;
   }
   KKM_CU(kkm::launch_argmin(s, s.b, forced_assign, assign_out, nullptr, dist_out, true, st), "argmin");
-  KKM_CU(kkm::launch_sort_plan(s, batch_obj_out, st), "sort/plan");
+  KKM_CU(kkm::launch_sort_plan(s, batch_obj_out, st, rotated), "sort/plan");
   KKM_CU(kkm::launch_move(s, st), "row moves");
   if (c->use_tc) KKM_CU(kkm::launch_wgram_tc(s, c->tmaps, st), "window Gram (tcgen05)");
   else KKM_CU(kkm::launch_wgram(s, st), "window Gram");
-  KKM_CU(kkm::launch_finalize(s, st), "finalize");
+  if (!rotated) KKM_CU(kkm::launch_finalize(s, st), "finalize");
   return KKM_OK;
 }
 
@@ -524,7 +549,7 @@ KKM_API kkm_status kkm_step(kkm_ctx* c, const int32_t* batch_idx, const int32_t*
       if (!c->cap_stream)
         KKM_CU(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "capture stream");
       KKM_CU(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-      st = enqueue_step(c, c->cap_stream, batch_idx, forced_assign, assign_out, dist_out, batch_obj_out, false);
+      st = enqueue_step(c, c->cap_stream, batch_idx, forced_assign, assign_out, dist_out, batch_obj_out, false, true);
       cudaGraph_t g = nullptr;
       const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
       if (st != KKM_OK) {
@@ -542,15 +567,19 @@ KKM_API kkm_status kkm_step(kkm_ctx* c, const int32_t* batch_idx, const int32_t*
     }
     KKM_CU(cudaGraphLaunch(c->gexec, c->stream), "graph launch");
   } else {
-    st = enqueue_step(c, c->stream, batch_idx, forced_assign, assign_out, dist_out, batch_obj_out, timed);
+    st = enqueue_step(c, c->stream, batch_idx, forced_assign, assign_out, dist_out, batch_obj_out, timed, true);
     if (st != KKM_OK) return st;
     ++c->eager_steps;
   }
-  // gather, distance, argmin, sort/plan, moves, window Gram, finalize (+ timing repeats)
+  // (the previous step's finalize), gather, distance, argmin, sort/plan, moves,
+  // window Gram (+ timing repeats)
   c->launches += 7 + (timed ? c->timing_reps - 1 : 0);
+  c->fin_pending = !c->tab;
   ++c->iteration;
   return KKM_OK;
 }
+
+KKM_API kkm_status kkm_flush(kkm_ctx* c) { return check_ready(c); }
 
 KKM_API kkm_status kkm_graph_enable(kkm_ctx* c, int32_t enable) {
   kkm_status st = check_usable(c);
@@ -631,7 +660,7 @@ static kkm_status assign_chunks(kkm_ctx* c, const float* Q, int64_t m, int64_t l
 
 KKM_API kkm_status kkm_assign(kkm_ctx* c, const float* Q, int64_t m, int64_t ldq, int32_t* assign_out,
                               float* mind_out, float* dist_out) {
-  kkm_status st = check_usable(c);
+  kkm_status st = check_ready(c);
   if (st != KKM_OK) return st;
   if (c->tab) return fail(c, KKM_ENOTSUP, "the table form scores only the rows of X (kkm_objective)");
   if (m < 0 || (m > 0 && (!Q || ldq < c->s.d))) return fail(c, KKM_EINVAL, "bad query matrix");
@@ -639,7 +668,7 @@ KKM_API kkm_status kkm_assign(kkm_ctx* c, const float* Q, int64_t m, int64_t ldq
 }
 
 KKM_API kkm_status kkm_objective(kkm_ctx* c, const float* Q, int64_t m, int64_t ldq, double* out) {
-  kkm_status st = check_usable(c);
+  kkm_status st = check_ready(c);
   if (st != KKM_OK) return st;
   if (!out) return fail(c, KKM_EINVAL, "out is NULL");
   if (c->tab) {
@@ -700,7 +729,7 @@ kkm_status objective_call(kkm_ctx* c, const float* Q, int64_t m, int64_t ldq, co
 
 KKM_API kkm_status kkm_objective_fwd(kkm_ctx* c, const float* Q, int64_t m, int64_t ldq, const int32_t* assign,
                                      double log_sigma, double* loss_out, float* delta_out) {
-  kkm_status st = check_usable(c);
+  kkm_status st = check_ready(c);
   if (st != KKM_OK) return st;
   if (!loss_out) return fail(c, KKM_EINVAL, "loss_out is NULL");
   return objective_call(c, Q, m, ldq, assign, log_sigma, loss_out, delta_out, nullptr, nullptr, 0, nullptr);
@@ -709,7 +738,7 @@ KKM_API kkm_status kkm_objective_fwd(kkm_ctx* c, const float* Q, int64_t m, int6
 KKM_API kkm_status kkm_objective_bwd(kkm_ctx* c, const float* Q, int64_t m, int64_t ldq, const int32_t* assign,
                                      double log_sigma, const double* grad_loss, float* grad_q, int64_t ldg,
                                      double* grad_log_sigma) {
-  kkm_status st = check_usable(c);
+  kkm_status st = check_ready(c);
   if (st != KKM_OK) return st;
   if (!grad_loss || !grad_q || !grad_log_sigma || ldg < c->s.d)
     return fail(c, KKM_EINVAL, "grad_loss, grad_q (ldg >= d) and grad_log_sigma are required");
@@ -722,6 +751,8 @@ KKM_API kkm_status kkm_step_eval(kkm_ctx* c, const int32_t* batch_idx, double* o
   if (st != KKM_OK) return st;
   if (!obj_before_dev || !obj_after_dev) return fail(c, KKM_EINVAL, "obj_before_dev and obj_after_dev are required");
   st = kkm_step(c, batch_idx, nullptr, nullptr, nullptr, obj_before_dev);
+  if (st != KKM_OK) return st;
+  st = flush(c);                     // the step's weight update
   if (st != KKM_OK) return st;
   // f_{B_i}(C_{i+1}): the distance pass and argmin again on the same batch
   // rows, against the windows, weights and norms the step just wrote
@@ -741,7 +772,7 @@ KKM_API kkm_status kkm_step_eval(kkm_ctx* c, const int32_t* batch_idx, double* o
 
 KKM_API kkm_status kkm_fit(kkm_ctx* c, int64_t max_iters, double eps, int64_t* iters_done,
                            double* last_improvement) {
-  kkm_status st = check_usable(c);
+  kkm_status st = check_ready(c);
   if (st != KKM_OK) return st;
   if (max_iters < 0 || std::isnan(eps)) return fail(c, KKM_EINVAL, "max_iters >= 0 and a non-NaN eps required");
   int64_t done = 0;
@@ -763,7 +794,7 @@ KKM_API kkm_status kkm_fit(kkm_ctx* c, int64_t max_iters, double eps, int64_t* i
 }
 
 KKM_API kkm_status kkm_get_cum_counts(kkm_ctx* c, int64_t* counts) {
-  kkm_status st = check_usable(c);
+  kkm_status st = check_ready(c);
   if (st != KKM_OK) return st;
   if (!counts) return fail(c, KKM_EINVAL, "counts is NULL");
   st = sync_and_check(c);
@@ -775,7 +806,7 @@ KKM_API kkm_status kkm_get_cum_counts(kkm_ctx* c, int64_t* counts) {
 }
 
 KKM_API kkm_status kkm_set_cum_counts(kkm_ctx* c, const int64_t* counts) {
-  kkm_status st = check_usable(c);
+  kkm_status st = check_ready(c);
   if (st != KKM_OK) return st;
   if (!counts) return fail(c, KKM_EINVAL, "counts is NULL");
   std::vector<double> h(c->s.k);
@@ -790,13 +821,13 @@ KKM_API kkm_status kkm_set_cum_counts(kkm_ctx* c, const int64_t* counts) {
 }
 
 KKM_API kkm_status kkm_sync(kkm_ctx* c) {
-  kkm_status st = check_usable(c);
+  kkm_status st = check_ready(c);
   if (st != KKM_OK) return st;
   return sync_and_check(c);
 }
 
 KKM_API kkm_status kkm_get_state_sizes(kkm_ctx* c, int64_t* total_rows, int64_t* total_blocks) {
-  kkm_status st = check_usable(c);
+  kkm_status st = check_ready(c);
   if (st != KKM_OK) return st;
   if (c->tab) return fail(c, KKM_ENOTSUP, "the table form keeps no support rows");
   st = sync_and_check(c);
@@ -818,7 +849,7 @@ KKM_API kkm_status kkm_get_state(kkm_ctx* c, int64_t* iteration, int32_t* rows_p
                                  int64_t* row_idx, double* row_w, int32_t* blocks_per_center,
                                  int64_t* block_iter, int32_t* block_count, uint8_t* c1_kept,
                                  double* cnorm) {
-  kkm_status st = check_usable(c);
+  kkm_status st = check_ready(c);
   if (st != KKM_OK) return st;
   if (c->tab) return fail(c, KKM_ENOTSUP, "the table form keeps no support rows");
   st = sync_and_check(c);
@@ -880,7 +911,7 @@ KKM_API kkm_status kkm_set_state(kkm_ctx* c, int64_t iteration, const int32_t* r
                                  const int32_t* blocks_per_center, const int64_t* block_iter,
                                  const int32_t* block_count, const uint8_t* c1_kept,
                                  const double* cnorm) {
-  kkm_status st = check_usable(c);
+  kkm_status st = check_ready(c);
   if (st != KKM_OK) return st;
   if (c->tab) return fail(c, KKM_ENOTSUP, "the table form keeps no support rows");
   const Dev& s = c->s;
@@ -1064,7 +1095,7 @@ kkm_status group_enqueue(kkm_group* g, cudaStream_t from) {
   for (size_t i = 0; i < g->runs.size(); ++i) {
     kkm_ctx* c = g->runs[i];
     if (cudaStreamWaitEvent(g->branch[i], g->ev[0], 0) != cudaSuccess) return gfail(g, KKM_ECUDA, "fork wait");
-    const kkm_status st = enqueue_step(c, g->branch[i], nullptr, nullptr, nullptr, nullptr, nullptr, false);
+    const kkm_status st = enqueue_step(c, g->branch[i], nullptr, nullptr, nullptr, nullptr, nullptr, false, false);
     if (st != KKM_OK) return gfail(g, st, "run " + std::to_string(i) + ": " + c->err);
     if (cudaEventRecord(g->ev[1 + i], g->branch[i]) != cudaSuccess) return gfail(g, KKM_ECUDA, "join event");
     if (cudaStreamWaitEvent(from, g->ev[1 + i], 0) != cudaSuccess) return gfail(g, KKM_ECUDA, "join wait");
@@ -1131,6 +1162,10 @@ KKM_API kkm_status kkm_group_step(kkm_group* g) {
     if (c->poisoned) return gfail(g, KKM_ESTATE, "a run is poisoned");
     if (c->s.tau == 0 && !c->tab && c->iteration > c->max_iters)
       return gfail(g, KKM_ESTATE, "an untruncated run has done max_iters iterations");
+    if (c->fin_pending) {               // a kkm_step on the run since the last group step
+      if (flush(c) != KKM_OK || cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return gfail(g, KKM_ECUDA, "pending weight update of a run");
+    }
   }
   if (g->steps == 0) {
     const kkm_status st = group_enqueue(g, g->stream);

@@ -148,6 +148,7 @@ struct Dev {
   int32_t wslots;    // partial slots per window-pass tile (4 SIMT, 1 tcgen05)
   int64_t* iter;     // [1] next iteration number
   int32_t* status;   // [1] sticky device status bits
+  int32_t* fin_pending;   // [1] 1 while a step's weight update (k_finalize) is still to run
   int64_t* stats;    // [3] steps, support rows, tiles
   double* obj;       // [1] last batch objective
   float* cmpart;     // [k][32] FP32 lane partials of sum_{x in B_j} <phi(x), C_j>
@@ -240,15 +241,20 @@ struct TabBuf {
 // ------------------------------------------------------------ launchers
 // All return cudaGetLastError() of their launches.
 cudaError_t launch_sample(const Dev& s, cudaStream_t st);
-cudaError_t launch_gather_batch(const Dev& s, const int32_t* idx, cudaStream_t st);
+// rotated: the gather follows the previous step's k_finalize, does its work
+// before its grid-dependency wait (it neither reads nor writes what finalize
+// touches), then clears fin_pending and releases the distance pass
+cudaError_t launch_gather_batch(const Dev& s, const int32_t* idx, cudaStream_t st, bool rotated = false);
 cudaError_t launch_gather_query(const Dev& s, const float* Q, int64_t ldq, int rows, cudaStream_t st);
 cudaError_t launch_dist_simt(const Dev& s, int rows, cudaStream_t st);
 cudaError_t launch_argmin(const Dev& s, int rows, const int32_t* forced, int32_t* assign_out,
                           float* mind_out, float* dist_out, bool update, cudaStream_t st);
-cudaError_t launch_sort_plan(const Dev& s, double* obj_out, cudaStream_t st);
+// set_pending: the step's k_finalize runs at the start of the next step (or a flush)
+cudaError_t launch_sort_plan(const Dev& s, double* obj_out, cudaStream_t st, bool set_pending = false);
 cudaError_t launch_move(const Dev& s, cudaStream_t st);
 cudaError_t launch_wgram(const Dev& s, cudaStream_t st);
-cudaError_t launch_finalize(const Dev& s, cudaStream_t st);
+// if_pending: a no-op unless fin_pending is set
+cudaError_t launch_finalize(const Dev& s, cudaStream_t st, bool if_pending = false);
 // batch objective at fixed assignments and its adjoint (kkm_grad.cu); ws holds
 // grad_workspace_doubles(s, m) doubles. With grad_q == NULL only the forward
 // runs (loss, delta); otherwise the adjoint (grad_q, grad_s).

@@ -204,13 +204,7 @@ __global__ void k_sample(Dev s) {
 
 // One warp per batch slot: X[idx] -> batch row, norm, data index. With idx
 // NULL the slot's index is drawn here: SplitMix64 output (i-1)*b + slot.
-__global__ void k_gather_batch(Dev s, const int32_t* __restrict__ idx) {
-  KKM_GRID_DEP_WAIT();
-  // the distance pass may now stage what it reads from earlier steps (the
-  // support tiles, their metadata, the tile list); this kernel writes none of it
-  KKM_LAUNCH_DEPENDENTS();
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (warp >= s.b) return;
+__device__ __forceinline__ void gather_one(const Dev& s, const int32_t* __restrict__ idx, int warp) {
   int64_t i;
   if (idx) {
     i = idx[warp];
@@ -230,7 +224,27 @@ __global__ void k_gather_batch(Dev s, const int32_t* __restrict__ idx) {
   }
 }
 
-// One warp per query row: Q[r] -> batch row (no data index: K(x,x) is never forced).
+// Not rotated: waits first, then lets the distance pass stage what it reads
+// from earlier steps (the support tiles, their metadata, the tile list; this
+// kernel writes none of it). Rotated (launched right after the previous step's
+// k_finalize): the rows are gathered first, while finalize runs (finalize
+// touches none of the batch buffers, the indices or the iteration counter);
+// then the wait, the clear of fin_pending, and only then the distance pass's
+// release, since its early staging reads the weights finalize writes.
+__global__ void k_gather_batch(Dev s, const int32_t* __restrict__ idx, int rotated) {
+  if (!rotated) {
+    KKM_GRID_DEP_WAIT();
+    KKM_LAUNCH_DEPENDENTS();
+  }
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (warp < s.b) gather_one(s, idx, warp);
+  if (rotated) {
+    KKM_GRID_DEP_WAIT();
+    if (blockIdx.x == 0 && threadIdx.x == 0) *s.fin_pending = 0;
+    KKM_LAUNCH_DEPENDENTS();
+  }
+}
+
 __global__ void k_gather_query(Dev s, const float* __restrict__ Q, int64_t ldq, int rows) {
   KKM_GRID_DEP_WAIT();
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -345,7 +359,7 @@ __device__ void tiles_write(const Dev& s, int first, int nt, int head, int size,
 // alpha_i^j, <C_j, cm(B_j)>, and the per-center window plan: compaction,
 // block push, the drops of Eq. (1), C_1 retirement, and the tile pairs of the
 // norm-recurrence Gram pass.
-__global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out) {
+__global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out, int set_pending) {
   KKM_GRID_DEP_WAIT();
   KKM_LAUNCH_DEPENDENTS();   // the next kernel waits at its top (or only stages earlier steps' data)
   extern __shared__ __align__(16) unsigned char smem[];
@@ -570,6 +584,7 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out) {
     s.stats[1] += s_rows;
     s.stats[2] += tiles_used;
     *s.iter += 1;
+    if (set_pending) *s.fin_pending = 1;
   }
   tiles_write(s, ex3[2], nt, thead, tsize, tot3[2]);   // its barrier also publishes base/tot
   // the window-pass tile list: a thread per tile, its center by binary search
@@ -714,9 +729,10 @@ __global__ void __launch_bounds__(1024) k_build_tiles(Dev s) {
 // The scalar chain has no FP64 division or square root: 1/b_j and the beta
 // rate sqrt(b_j / b) come from a table the host fills at kkm_init, and the
 // thread's operands are loaded before the window sums so their latency overlaps.
-__global__ void __launch_bounds__(256) k_finalize(Dev s) {
+__global__ void __launch_bounds__(256) k_finalize(Dev s, int if_pending) {
   KKM_GRID_DEP_WAIT();
-  KKM_LAUNCH_DEPENDENTS();   // the next kernel waits at its top (or only stages earlier steps' data)
+  KKM_LAUNCH_DEPENDENTS();   // the next kernel waits at its top (or, the rotated gather, touches none of this)
+  if (if_pending && *s.fin_pending == 0) return;   // nothing to apply (the first step, or after a flush)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, j = blockIdx.x;
   const Plan P = s.plan[j];
   if (P.cnt == 0) return;
@@ -1166,8 +1182,8 @@ cudaError_t launch_sample(const Dev& s, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather_batch(const Dev& s, const int32_t* idx, cudaStream_t st) {
-  cudaError_t e = launch_pdl(k_gather_batch, dim3((s.b * 32 + 255) / 256), dim3(256), 0, st, s, idx);
+cudaError_t launch_gather_batch(const Dev& s, const int32_t* idx, cudaStream_t st, bool rotated) {
+  cudaError_t e = launch_pdl(k_gather_batch, dim3((s.b * 32 + 255) / 256), dim3(256), 0, st, s, idx, rotated ? 1 : 0);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
@@ -1190,7 +1206,7 @@ cudaError_t launch_argmin(const Dev& s, int rows, const int32_t* forced, int32_t
 
 int sort_plan_smem(int k, int b) { return k * (int)sizeof(Plan) + 4 * k * 4 + b * (4 + 2 + 2) + 32 * k * 2; }
 
-cudaError_t launch_sort_plan(const Dev& s, double* obj_out, cudaStream_t st) {
+cudaError_t launch_sort_plan(const Dev& s, double* obj_out, cudaStream_t st, bool set_pending) {
   const int smem = sort_plan_smem(s.k, s.b);
   static bool attr_set = false;
   if (!attr_set) {
@@ -1198,7 +1214,7 @@ cudaError_t launch_sort_plan(const Dev& s, double* obj_out, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  cudaError_t e = launch_pdl(k_sort_plan, dim3(1), dim3(1024), smem, st, s, obj_out);
+  cudaError_t e = launch_pdl(k_sort_plan, dim3(1), dim3(1024), smem, st, s, obj_out, set_pending ? 1 : 0);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
@@ -1211,8 +1227,8 @@ cudaError_t launch_move(const Dev& s, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const Dev& s, cudaStream_t st) {
-  cudaError_t e = launch_pdl(k_finalize, dim3(s.k), dim3(256), 0, st, s);
+cudaError_t launch_finalize(const Dev& s, cudaStream_t st, bool if_pending) {
+  cudaError_t e = launch_pdl(k_finalize, dim3(s.k), dim3(256), 0, st, s, if_pending ? 1 : 0);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

@@ -72,6 +72,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "kkm_objective_fwd": ([_P, _P, c_int64, c_int64, _P, c_double, _P, _P], c_int32),
         "kkm_objective_bwd": ([_P, _P, c_int64, c_int64, _P, c_double, _P, _P, c_int64, _P], c_int32),
         "kkm_sync": ([_P], c_int32),
+        "kkm_flush": ([_P], c_int32),
         "kkm_get_state_sizes": ([_P, POINTER(c_int64), POINTER(c_int64)], c_int32),
         "kkm_get_state": ([_P, POINTER(c_int64), _P, _P, _P, _P, _P, _P, _P, _P], c_int32),
         "kkm_set_state": ([_P, c_int64, _P, _P, _P, _P, _P, _P, _P, _P], c_int32),
@@ -185,6 +186,10 @@ def kmeanspp(X, k: int, kernel: str = "gaussian", param: float = 1.0, coef0: flo
 
 def kkm_sync(ctx) -> None:
     _check(load().kkm_sync(ctx), ctx)
+
+
+def kkm_flush(ctx) -> None:
+    _check(load().kkm_flush(ctx), ctx)
 
 
 def kkm_stats(ctx, reset: bool = False) -> tuple[int, int, int]:
@@ -368,6 +373,10 @@ class KKM:
 
     def sync(self):
         kkm_sync(self.ctx)
+
+    def flush(self):
+        """Queue the weight update the last step left pending (asynchronous)."""
+        kkm_flush(self.ctx)
 
     def get_state(self) -> dict:
         return kkm_get_state(self.ctx, self.k)
