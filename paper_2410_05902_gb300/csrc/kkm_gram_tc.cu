@@ -545,8 +545,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   // batch gather or this pass itself, writes none of it): before the
   // grid-dependency wait the producer fetches the descriptors of its first 32
   // items (one per lane) and stages the B tiles of its first item's first
-  // stages and that item's column metadata. They come from earlier steps;
-  // the batch rows and their metadata follow after the wait.
+  // stages and that item's column norms and indices. They come from the sort,
+  // plan and row moves of earlier steps. The column weights (written by the
+  // previous step's weight update, which may still be running beside the
+  // gather), the batch rows and their metadata follow after the wait.
   int npre = 0;                                  // first-item stages whose B tile is already on its way
   int pya_pre = 0, pyb_pre = 0;                  // this lane's first-round item: its A and B rows
   bool desc_pre = false;
@@ -561,7 +563,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         MetaSlot& m = sh.meta.ring[0];
         mbar_expect_tx(&sh.mfull[0], META_BYTES);   // covers the row metadata issued after the wait
         bulk_load(m.col[0], s.yn + yb0, TNV * 4, &sh.mfull[0]);
-        bulk_load(m.col[1], s.w32 + yb0, TNV * 4, &sh.mfull[0]);
         bulk_load(m.col[2], s.yi + yb0, TNV * 4, &sh.mfull[0]);
         npre = nks < NST ? nks : NST;
         for (int sl = 0; sl < npre; ++sl) {
@@ -627,12 +628,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (!mbar_wait(&sh.mempty[ms], ((local / MS) & 1u) ^ 1u)) ok = false;
           if (ok) {
             MetaSlot& m = sh.meta.ring[ms];
-            if (local != 0 || npre == 0) {             // else staged before the wait
+            if (local != 0 || npre == 0) {             // else norms and indices staged before the wait
               mbar_expect_tx(&sh.mfull[ms], META_BYTES);
               bulk_load(m.col[0], s.yn + yb, TNV * 4, &sh.mfull[ms]);
-              bulk_load(m.col[1], s.w32 + yb, TNV * 4, &sh.mfull[ms]);
               bulk_load(m.col[2], s.yi + yb, TNV * 4, &sh.mfull[ms]);
             }
+            bulk_load(m.col[1], s.w32 + yb, TNV * 4, &sh.mfull[ms]);
             bulk_load(m.row[0], s.xbn + ya, TM * 4, &sh.mfull[ms]);
             bulk_load(m.row[1], s.xbi + ya, TM * 4, &sh.mfull[ms]);
             ++mi;

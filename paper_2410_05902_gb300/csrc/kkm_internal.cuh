@@ -159,10 +159,15 @@ struct Dev {
 // anything the predecessor writes (a no-op when launched without the attribute).
 #define KKM_GRID_DEP_WAIT() asm volatile("griddepcontrol.wait;" ::: "memory")
 // Lets the next kernel in the stream start its pre-wait part. Issued only after
-// this kernel's own wait, so every kernel before it has completed by then. The
-// step kernels all issue it; each of them waits at its first statement, except
-// the tcgen05 passes, whose pre-wait part sets up shared memory and TMEM and
-// (distance pass after the gather only) stages data of earlier steps.
+// this kernel's own wait, so every kernel before it has completed by then,
+// with one exception: the rotated gather (which follows the previous step's
+// k_finalize) issues it before its wait. The distance pass it releases reads
+// before its own wait only what the previous step's sort, plan and row moves
+// wrote, and those completed before the gather was launched. The step kernels
+// all issue it; each of them waits at its first statement, except the
+// tcgen05 passes, whose pre-wait part sets up shared memory and TMEM and
+// (distance pass after the gather only) stages data of earlier steps, and
+// the rotated gather.
 #define KKM_LAUNCH_DEPENDENTS() asm volatile("griddepcontrol.launch_dependents;" ::: "memory")
 
 // Launches `kern` with the programmatic-stream-serialization attribute.
@@ -242,8 +247,8 @@ struct TabBuf {
 // All return cudaGetLastError() of their launches.
 cudaError_t launch_sample(const Dev& s, cudaStream_t st);
 // rotated: the gather follows the previous step's k_finalize, does its work
-// before its grid-dependency wait (it neither reads nor writes what finalize
-// touches), then clears fin_pending and releases the distance pass
+// and releases the distance pass before its grid-dependency wait (neither
+// touches before its wait what finalize writes), then clears fin_pending
 cudaError_t launch_gather_batch(const Dev& s, const int32_t* idx, cudaStream_t st, bool rotated = false);
 cudaError_t launch_gather_query(const Dev& s, const float* Q, int64_t ldq, int rows, cudaStream_t st);
 cudaError_t launch_dist_simt(const Dev& s, int rows, cudaStream_t st);

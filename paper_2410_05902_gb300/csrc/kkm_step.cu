@@ -225,12 +225,14 @@ __device__ __forceinline__ void gather_one(const Dev& s, const int32_t* __restri
 }
 
 // Not rotated: waits first, then lets the distance pass stage what it reads
-// from earlier steps (the support tiles, their metadata, the tile list; this
-// kernel writes none of it). Rotated (launched right after the previous step's
-// k_finalize): the rows are gathered first, while finalize runs (finalize
-// touches none of the batch buffers, the indices or the iteration counter);
-// then the wait, the clear of fin_pending, and only then the distance pass's
-// release, since its early staging reads the weights finalize writes.
+// from earlier steps (the support tiles, their norms and indices, the tile
+// list; this kernel writes none of it). Rotated (launched right after the
+// previous step's k_finalize): the rows are gathered first, while finalize
+// runs (finalize touches none of the batch buffers, the indices or the
+// iteration counter), and the distance pass is released at once: its early
+// staging reads nothing finalize writes (it loads the weights after its own
+// wait, which returns once this kernel, and so finalize, has completed).
+// Then the wait and the clear of fin_pending.
 __global__ void k_gather_batch(Dev s, const int32_t* __restrict__ idx, int rotated) {
   if (!rotated) {
     KKM_GRID_DEP_WAIT();
@@ -239,9 +241,9 @@ __global__ void k_gather_batch(Dev s, const int32_t* __restrict__ idx, int rotat
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (warp < s.b) gather_one(s, idx, warp);
   if (rotated) {
+    KKM_LAUNCH_DEPENDENTS();
     KKM_GRID_DEP_WAIT();
     if (blockIdx.x == 0 && threadIdx.x == 0) *s.fin_pending = 0;
-    KKM_LAUNCH_DEPENDENTS();
   }
 }
 
