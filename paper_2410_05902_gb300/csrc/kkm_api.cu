@@ -362,7 +362,7 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
   ALLOC(s.blk_iter, (size_t)k * s.nbcap); ALLOC(s.blk_cnt, (size_t)k * s.nbcap);
   ALLOC(s.blk_first, k); ALLOC(s.blk_num, k);
   ALLOC(s.assign, s.bpad); ALLOC(s.mind, s.bpad); ALLOC(s.inner_a, s.bpad);
-  ALLOC(s.counts, k); ALLOC(s.alpha, k); ALLOC(s.coff, k + 1); ALLOC(s.perm, s.bpad);
+  ALLOC(s.counts, k); ALLOC(s.alpha, k); ALLOC(s.coff, k + 1); ALLOC(s.perm, s.bpad); ALLOC(s.mvdst, s.bpad);
   ALLOC(s.cmc, k); ALLOC(s.ncum, k); ALLOC(c->d_obj2, 2); ALLOC(s.plan, k); ALLOC(s.comp_off, k); ALLOC(s.comp_total, 1);
   ALLOC(s.tiles, s.max_tiles); ALLOC(s.ntiles, 1); ALLOC(s.tile_first, k); ALLOC(s.tile_cnt, k);
   ALLOC(s.part, (size_t)s.max_tiles * s.bpad);

@@ -129,6 +129,7 @@ struct Dev {
   double* alpha;     // [k]
   int32_t* coff;     // [k + 1] exclusive offsets of the center-sorted batch
   int32_t* perm;     // [b] batch rows sorted by center (stable)
+  int64_t* mvdst;    // [b] support row that sorted batch row w moves to (k_sort_plan), -1 past capacity
   double* cmc;       // [k] <C_j, cm(B_j)>
   Plan* plan;        // [k]
   int32_t* comp_off; // [k] first flat row of each center's compaction copy

@@ -589,6 +589,13 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out, int 
     if (set_pending) *s.fin_pending = 1;
   }
   tiles_write(s, ex3[2], nt, thead, tsize, tot3[2]);   // its barrier also publishes base/tot
+  // where k_move puts each sorted batch row: after the window's tail (after
+  // the compaction, when there is one), in sorted order
+  for (int r = tid; r < b; r += 1024) {
+    const int x = sperm[r], j = sassign[x];
+    const int pos = splan[j].tail_c + (r - coff[j]);
+    s.mvdst[r] = pos < s.cap - REGION_PAD ? (int64_t)j * s.cap + pos : -1;   // else flagged ST_CAPACITY
+  }
   // the window-pass tile list: a thread per tile, its center by binary search
   const int plim = ptotal <= s.max_pairs ? ptotal : s.max_pairs;
   for (int e = tid; e < plim; e += 1024) {
@@ -620,11 +627,8 @@ __global__ void k_move(Dev s) {
   for (int w = blockIdx.x * wpb + (threadIdx.x >> 5); w < items; w += nwarps) {
     if (w < s.b) {
       const int x = s.perm[w];
-      const int j = s.assign[x];
-      const Plan P = s.plan[j];
-      const int pos = P.tail_c + (w - s.coff[j]);
-      if (pos >= s.cap - REGION_PAD) continue;      // flagged ST_CAPACITY in the plan
-      const int64_t dst = (int64_t)j * s.cap + pos;
+      const int64_t dst = s.mvdst[w];              // the sort/plan's destination
+      if (dst < 0) continue;                        // flagged ST_CAPACITY in the plan
       warp_copy_row(s, false, x, dst);
       if (lane == 0) {
         s.yn[dst] = s.xbn[x];

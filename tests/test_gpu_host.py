@@ -71,3 +71,39 @@ def test_back_to_back_timing_leaves_results_unchanged():
     _same_state(t, p)
     t.close()
     p.close()
+
+
+@pytest.mark.parametrize("precision,graph", [("bf16", True), ("fp32", False)])
+def test_deferred_weight_update_applied_once(precision, graph):
+    """A step leaves its weight update pending until the next step or the next
+    call that reads the centers. Twin runs: one steps straight through, the
+    other flushes, synchronises, reads the state and scores queries between
+    its steps (each of which queues the pending update once). Assignments,
+    batch objectives and final states must agree bit for bit."""
+    torch, (a, b_), n, b = _twins(precision, graph)
+    Xq = a.X[:300].contiguous()
+    outs = []
+    for r, busy in ((a, False), (b_, True)):
+        res = []
+        o = torch.empty(1, dtype=torch.float64, device="cuda")     # fixed outputs: the graph replays
+        asg = torch.empty(b, dtype=torch.int32, device="cuda")
+        for i in range(10):
+            r.step(None, None, asg, None, o)
+            if busy:
+                if i % 3 == 0:
+                    r.flush()
+                    r.flush()                    # nothing left to apply
+                elif i % 3 == 1:
+                    r.get_state()
+                else:
+                    r.assign(Xq)
+                r.sync()
+            res.append((asg.cpu().numpy(), float(o.cpu()[0])))
+        r.sync()
+        outs.append(res)
+    for i, ((aa, fa), (ab, fb)) in enumerate(zip(*outs)):
+        assert np.array_equal(aa, ab), i
+        assert fa == fb, i
+    _same_state(a, b_)
+    a.close()
+    b_.close()
