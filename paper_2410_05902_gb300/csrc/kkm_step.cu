@@ -272,8 +272,10 @@ __global__ void __launch_bounds__(32 * AM_WARPS) k_argmin(Dev s, int rows, const
                                                           int32_t* __restrict__ assign_out,
                                                           float* __restrict__ mind_out,
                                                           float* __restrict__ dist_out, int update) {
-  KKM_GRID_DEP_WAIT();
-  KKM_LAUNCH_DEPENDENTS();   // the next kernel waits at its top (or only stages earlier steps' data)
+  // Before the wait: the tile tables, the center norms, the batch rows' norms
+  // and the forced assignments. They come from kernels that completed before
+  // this one was launched (it is launched once the distance pass has passed
+  // its own wait): the sort/plan, the weight update and the gather.
   __shared__ float r_best[AM_WARPS][32], r_inner[AM_WARPS][32], r_f[AM_WARPS][32];
   __shared__ int r_j[AM_WARPS][32];
   __shared__ int c_first[1024], c_cnt[1024];
@@ -289,6 +291,8 @@ __global__ void __launch_bounds__(32 * AM_WARPS) k_argmin(Dev s, int rows, const
   const int xr = live ? x : 0;
   const float kxx = (float)kernel_self(s.kind, (double)s.xbn[xr], s.coef0, s.degree);
   const int fa = forced ? forced[xr] : -1;
+  KKM_GRID_DEP_WAIT();       // the distance pass's partial sums
+  KKM_LAUNCH_DEPENDENTS();   // the next kernel waits at its top
   __syncthreads();
   float best = 3.0e38f, best_inner = 0.0f, f_inner = 0.0f;
   int bj = 0x7fffffff;
