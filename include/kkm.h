@@ -201,6 +201,15 @@ kkm_status kkm_step(kkm_ctx* ctx, const int32_t* batch_idx, const int32_t* force
  * any, on the context's stream (asynchronous; nothing to do otherwise). */
 kkm_status kkm_flush(kkm_ctx* ctx);
 
+/* kkm_steps -- n iterations of kkm_step with the built-in sampler and no
+ * outputs: the fixed-iteration loop of the experiments (Sec. 6). With graphs
+ * enabled (kkm_graph_enable) it replays a captured graph of 16 iterations,
+ * inside which consecutive iterations meet through programmatic dependent
+ * launch, and runs the remainder one step at a time. The result is the same,
+ * bit for bit, as n calls of kkm_step(ctx, NULL, NULL, NULL, NULL, NULL).
+ * Asynchronous; n >= 0. */
+kkm_status kkm_steps(kkm_ctx* ctx, int64_t n);
+
 /* kkm_step_eval -- kkm_step (device sampler when batch_idx is NULL) that
  * also evaluates the updated centers on the same batch: obj_before_dev
  * receives f_{B_i}(C_i) and obj_after_dev f_{B_i}(C_{i+1}) (device doubles,

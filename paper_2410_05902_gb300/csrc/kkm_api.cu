@@ -62,6 +62,7 @@ struct kkm_ctx {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
   const void* gkey[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaGraphExec_t gexec_multi = nullptr;     // kkm_steps: STEPS_PER_GRAPH sampler steps per replay
   // table form of Algorithm 1 (kkm_config.algo = KKM_ALGO_TABLE)
   bool tab = false;
   kkm::TabBuf tb{};
@@ -102,6 +103,8 @@ cudaError_t dalloc(kkm_ctx* c, T** p, size_t count) {
 void free_all(kkm_ctx* c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   c->gexec = nullptr;
+  if (c->gexec_multi) cudaGraphExecDestroy(c->gexec_multi);
+  c->gexec_multi = nullptr;
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   c->cap_stream = nullptr;
   for (void* p : c->allocs) cudaFree(p);
@@ -580,6 +583,59 @@ KKM_API kkm_status kkm_step(kkm_ctx* c, const int32_t* batch_idx, const int32_t*
 }
 
 KKM_API kkm_status kkm_flush(kkm_ctx* c) { return check_ready(c); }
+
+// Iterations the kkm_steps graph holds. Within it consecutive steps meet
+// through programmatic dependent launch, as the kernels of one step do;
+// between two graph launches they do not.
+constexpr int STEPS_PER_GRAPH = 16;
+
+KKM_API kkm_status kkm_steps(kkm_ctx* c, int64_t n) {
+  kkm_status st = check_usable(c);
+  if (st != KKM_OK) return st;
+  if (n < 0) return fail(c, KKM_EINVAL, "n must be >= 0");
+  if (c->s.tau == 0 && !c->tab && c->iteration - 1 + n > c->max_iters)
+    return fail(c, KKM_ESTATE, "untruncated run: n steps would pass max_iters");
+  const bool timed = c->timing && c->ev_used < (int64_t)c->ev.size() / 2;
+  int64_t left = n;
+  if (c->graph_on && !timed) {
+    if (c->eager_steps == 0 && left > 0) {   // the first step runs eagerly, as kkm_step's does
+      st = kkm_step(c, nullptr, nullptr, nullptr, nullptr, nullptr);
+      if (st != KKM_OK) return st;
+      --left;
+    }
+    if (left >= STEPS_PER_GRAPH && !c->gexec_multi) {
+      if (!c->cap_stream)
+        KKM_CU(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "capture stream");
+      KKM_CU(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+      for (int i = 0; i < STEPS_PER_GRAPH && st == KKM_OK; ++i)
+        st = enqueue_step(c, c->cap_stream, nullptr, nullptr, nullptr, nullptr, nullptr, false, !c->tab);
+      cudaGraph_t g = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+      if (st != KKM_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+      }
+      if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+      const cudaError_t ei = cudaGraphInstantiate(&c->gexec_multi, g, 0);
+      cudaGraphDestroy(g);
+      if (ei != cudaSuccess) {
+        c->gexec_multi = nullptr;
+        return cuda_fail(c, ei, "graph instantiate");
+      }
+    }
+    for (; left >= STEPS_PER_GRAPH; left -= STEPS_PER_GRAPH) {
+      KKM_CU(cudaGraphLaunch(c->gexec_multi, c->stream), "graph launch");
+      c->launches += 7 * STEPS_PER_GRAPH;
+      c->iteration += STEPS_PER_GRAPH;
+      c->fin_pending = !c->tab;
+    }
+  }
+  for (; left > 0; --left) {
+    st = kkm_step(c, nullptr, nullptr, nullptr, nullptr, nullptr);
+    if (st != KKM_OK) return st;
+  }
+  return KKM_OK;
+}
 
 KKM_API kkm_status kkm_graph_enable(kkm_ctx* c, int32_t enable) {
   kkm_status st = check_usable(c);

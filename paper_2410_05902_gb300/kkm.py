@@ -73,6 +73,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "kkm_objective_bwd": ([_P, _P, c_int64, c_int64, _P, c_double, _P, _P, c_int64, _P], c_int32),
         "kkm_sync": ([_P], c_int32),
         "kkm_flush": ([_P], c_int32),
+        "kkm_steps": ([_P, c_int64], c_int32),
         "kkm_get_state_sizes": ([_P, POINTER(c_int64), POINTER(c_int64)], c_int32),
         "kkm_get_state": ([_P, POINTER(c_int64), _P, _P, _P, _P, _P, _P, _P, _P], c_int32),
         "kkm_set_state": ([_P, c_int64, _P, _P, _P, _P, _P, _P, _P, _P], c_int32),
@@ -190,6 +191,10 @@ def kkm_sync(ctx) -> None:
 
 def kkm_flush(ctx) -> None:
     _check(load().kkm_flush(ctx), ctx)
+
+
+def kkm_steps(ctx, n: int) -> None:
+    _check(load().kkm_steps(ctx, int(n)), ctx)
 
 
 def kkm_stats(ctx, reset: bool = False) -> tuple[int, int, int]:
@@ -318,6 +323,10 @@ class KKM:
         """One iteration. Optional outputs are CUDA tensors the caller allocated."""
         kkm_step(self.ctx, self._ptr(batch_idx), self._ptr(forced_assign), self._ptr(assign_out),
                  self._ptr(dist_out), self._ptr(obj_out))
+
+    def steps(self, n: int):
+        """n iterations with the built-in sampler, no outputs (16 per graph replay when graphs are on)."""
+        kkm_steps(self.ctx, n)
 
     def step_host(self, batch_idx: np.ndarray | None = None):
         """One iteration with host buffers; returns (assignments, f_B) as numpy / float."""

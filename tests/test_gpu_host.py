@@ -107,3 +107,23 @@ def test_deferred_weight_update_applied_once(precision, graph):
     _same_state(a, b_)
     a.close()
     b_.close()
+
+
+@pytest.mark.parametrize("precision,graph", [("bf16", True), ("fp32", False)])
+def test_steps_match_single_steps(precision, graph):
+    """kkm_steps(n) (16 iterations per graph replay, the rest one by one) gives
+    the same centers, bit for bit, as n calls of kkm_step with the sampler."""
+    torch, (a, b_), n, b = _twins(precision, graph)
+    a.steps(37)
+    for _ in range(37):
+        b_.step()
+    a.sync()
+    b_.sync()
+    _same_state(a, b_)
+    a.steps(16)
+    for _ in range(16):
+        b_.step()
+    assert a.stats()[0] == b_.stats()[0] == 53
+    _same_state(a, b_)
+    a.close()
+    b_.close()
