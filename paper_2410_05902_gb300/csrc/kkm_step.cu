@@ -740,14 +740,18 @@ __global__ void __launch_bounds__(1024) k_build_tiles(Dev s) {
 // rate sqrt(b_j / b) come from a table the host fills at kkm_init, and the
 // thread's operands are loaded before the window sums so their latency overlaps.
 __global__ void __launch_bounds__(256) k_finalize(Dev s, int if_pending) {
-  KKM_GRID_DEP_WAIT();
-  KKM_LAUNCH_DEPENDENTS();   // the next kernel waits at its top (or, the rotated gather, touches none of this)
-  if (if_pending && *s.fin_pending == 0) return;   // nothing to apply (the first step, or after a flush)
+  // Before the wait: the pending flag, the plan, the running count, the old
+  // norm, the rate table, the pair range and the sort/plan's partials of
+  // <phi(x), C_j>. Their writers (the sort/plan, the gather, earlier weight
+  // updates) completed before this kernel was launched: it is launched once
+  // the kernel ahead (the window pass, or a full dependency) has passed its
+  // own wait. Only the window-pass sums need the wait, and no block returns
+  // before it, so this kernel never completes ahead of the one it follows.
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, j = blockIdx.x;
+  const bool skip = if_pending && *s.fin_pending == 0;   // nothing to apply (the first step, or after a flush)
   const Plan P = s.plan[j];
-  if (P.cnt == 0) return;
   double ncum_j = 0.0, cn_old = 0.0, inv_n = 0.0, beta = 0.0;
-  if (tid == 0) {
+  if (tid == 0 && !skip && P.cnt > 0) {
     ncum_j = s.ncum[j];
     cn_old = s.cnorm[j];
     inv_n = s.rtab[P.cnt];
@@ -756,11 +760,18 @@ __global__ void __launch_bounds__(256) k_finalize(Dev s, int if_pending) {
   __shared__ double red[8][4];
   __shared__ double cm_s;
   __shared__ double keep_s, wnew_s;
-  // window-pass sums: element e of a tile's partials is sum e & 3 (A, Bdd, E, M);
-  // with a stride of 256 every thread stays on sum tid & 3
   const int per = s.wslots * 4;
   const int p0 = s.wpair_first[j];
   const int np = (p0 + s.wpair_cnt[j] <= s.max_pairs) ? s.wpair_cnt[j] : 0;
+  if (warp == 0 && !skip && P.cnt > 0) {
+    const double v = warp_sum((double)s.cmpart[(int64_t)j * 32 + lane]);
+    if (lane == 0) cm_s = v;
+  }
+  KKM_GRID_DEP_WAIT();
+  KKM_LAUNCH_DEPENDENTS();   // the next kernel waits at its top (or, the rotated gather, touches none of this)
+  if (skip || P.cnt == 0) return;
+  // window-pass sums: element e of a tile's partials is sum e & 3 (A, Bdd, E, M);
+  // with a stride of 256 every thread stays on sum tid & 3
   const double* wp = s.wpart + (int64_t)p0 * per;
   double acc = 0.0;
 #pragma unroll 4
@@ -768,10 +779,6 @@ __global__ void __launch_bounds__(256) k_finalize(Dev s, int if_pending) {
 #pragma unroll
   for (int o = 4; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane < 4) red[warp][lane] = acc;
-  if (warp == 0) {
-    const double v = warp_sum((double)s.cmpart[(int64_t)j * 32 + lane]);
-    if (lane == 0) cm_s = v;
-  }
   __syncthreads();
   const int n = P.cnt;
   if (warp == 0) {
