@@ -261,9 +261,11 @@ cudaError_t launch_move(const Dev& s, cudaStream_t st);
 cudaError_t launch_wgram(const Dev& s, cudaStream_t st);
 // if_pending: a no-op unless fin_pending is set
 cudaError_t launch_finalize(const Dev& s, cudaStream_t st, bool if_pending = false);
-// batch objective at fixed assignments and its adjoint (kkm_grad.cu); ws holds
-// grad_workspace_doubles(s, m) doubles. With grad_q == NULL only the forward
-// runs (loss, delta); otherwise the adjoint (grad_q, grad_s).
+// batch objective at fixed assignments and its adjoint (kkm_grad.cu): two
+// launches. ws holds grad_workspace_doubles(s, m) doubles, zeroed when it is
+// allocated (its first int is the row kernel's finished-block counter, which
+// every call leaves at zero). With grad_q == NULL only the forward runs
+// (loss, delta); otherwise the adjoint (grad_q, grad_s).
 // kernel k-means++ seeding (kkm_seed.cu): chosen[0..k) on the device;
 // d2 holds n doubles, part ceil(n/8) doubles
 cudaError_t launch_kmeanspp(const float* X, int64_t n, int d, int64_t ldx, int k, int kind, double param,
