@@ -92,6 +92,8 @@ def test_null_context_calls(lib):
     assert lib.kkm_destroy(None) == kkm.KKM_OK
     assert lib.kkm_step(None, None, None, None, None, None) == kkm.KKM_EINVAL
     assert lib.kkm_sync(None) == kkm.KKM_EINVAL
+    assert lib.kkm_flush(None) == kkm.KKM_EINVAL
+    assert lib.kkm_steps(None, 5) == kkm.KKM_EINVAL
     out = ctypes.c_double()
     assert lib.kkm_objective(None, None, 0, 0, ctypes.byref(out)) == kkm.KKM_EINVAL
 
