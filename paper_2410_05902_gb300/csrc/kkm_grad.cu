@@ -571,13 +571,9 @@ cudaError_t launch_rows(const Dev& s, const BandParams& bp, const float* Q, int6
                         const int4* items, const int* nitems, int64_t nblk, const double* part, int py, float* delta,
                         const double* grad_loss, float* grad_q, int64_t ldg, double* rowv, int* done, double* loss,
                         double* grad_s, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(k_rows<BWD, NK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ROWS_SMEM_MAX);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  const cudaError_t e = smem_limit_once(k_rows<BWD, NK>, (int)ROWS_SMEM_MAX, attr);
+  if (e != cudaSuccess) return e;
   const size_t smem = (size_t)(GW * ((s.d + 3) & ~3) + SR * RP + SR + SR * GW) * sizeof(float) + SR * sizeof(int64_t);
   return launch_pdl(k_rows<BWD, NK>, dim3((unsigned)nblk), dim3(32 * GW), smem, st, s, bp, Q, m, ldq, list, items,
                     nitems, part, py, delta, grad_loss, grad_q, ldg, rowv, done, loss, grad_s);
@@ -634,15 +630,11 @@ cudaError_t launch_objective(const Dev& s, double log_sigma, const float* Q, int
   const int py = pair_blocks(s);
   const GradWs g = carve(s, m, ws);
   const int64_t nblk = row_items_max(s, m);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_center_pairs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SLAB_SMEM);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_center_pairs<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SLAB_SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  cudaError_t e = launch_pdl(s.kind == K_GAUSS ? k_center_pairs<true> : k_center_pairs<false>, dim3(s.k * py + 1),
+  static std::atomic<uint64_t> attr_g{0}, attr_l{0};
+  cudaError_t e = s.kind == K_GAUSS ? smem_limit_once(k_center_pairs<true>, (int)SLAB_SMEM, attr_g)
+                                    : smem_limit_once(k_center_pairs<false>, (int)SLAB_SMEM, attr_l);
+  if (e != cudaSuccess) return e;
+  e = launch_pdl(s.kind == K_GAUSS ? k_center_pairs<true> : k_center_pairs<false>, dim3(s.k * py + 1),
                              dim3(32 * GW), SLAB_SMEM, st, s, bp, py, g.part, assign, m, g.list, g.items, g.nitems);
   if (e != cudaSuccess) return e;
   const double* part = g.part;

@@ -839,12 +839,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
 template <int KIND, int MODE, int OP, int TNV>
 cudaError_t launch_form(const Dev& s, const CUtensorMap& a, const CUtensorMap& b, int rows, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_dist_tc<KIND, MODE, OP, TNV>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  static std::atomic<uint64_t> attr{0};
+  {
+    const cudaError_t e = smem_limit_once(k_dist_tc<KIND, MODE, OP, TNV>, SMEM_BYTES, attr);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   // one CTA per SM, but never more CTAs than the most items this launch can
   // have: small runs then leave SMs free for the kernels of other runs

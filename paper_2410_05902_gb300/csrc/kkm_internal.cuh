@@ -32,6 +32,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
+#include <atomic>
 
 namespace kkm {
 
@@ -170,6 +171,21 @@ struct Dev {
 // (distance pass after the gather only) stages data of earlier steps, and
 // the rotated gather.
 #define KKM_LAUNCH_DEPENDENTS() asm volatile("griddepcontrol.launch_dependents;" ::: "memory")
+
+// Raises `kern`'s dynamic shared-memory limit to `bytes` on the current device,
+// once per device: the attribute belongs to the function on that device.
+// `done` is the caller's per-kernel mask of devices already set.
+template <typename Kern>
+inline cudaError_t smem_limit_once(Kern kern, int bytes, std::atomic<uint64_t>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = dev < 64 ? (uint64_t)1 << dev : 0;
+  if (bit && (done.load(std::memory_order_relaxed) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_relaxed);
+  return e;
+}
 
 // Launches `kern` with the programmatic-stream-serialization attribute.
 template <typename... Params, typename... Args>

@@ -1225,13 +1225,10 @@ int sort_plan_smem(int k, int b) { return k * (int)sizeof(Plan) + 4 * k * 4 + b 
 
 cudaError_t launch_sort_plan(const Dev& s, double* obj_out, cudaStream_t st, bool set_pending) {
   const int smem = sort_plan_smem(s.k, s.b);
-  static bool attr_set = false;
-  if (!attr_set) {
-    const cudaError_t e = cudaFuncSetAttribute(k_sort_plan, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  cudaError_t e = launch_pdl(k_sort_plan, dim3(1), dim3(1024), smem, st, s, obj_out, set_pending ? 1 : 0);
+  static std::atomic<uint64_t> attr{0};
+  cudaError_t e = smem_limit_once(k_sort_plan, 200 * 1024, attr);
+  if (e != cudaSuccess) return e;
+  e = launch_pdl(k_sort_plan, dim3(1), dim3(1024), smem, st, s, obj_out, set_pending ? 1 : 0);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
