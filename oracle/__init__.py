@@ -21,13 +21,13 @@ textbook algorithms, invariants the paper proves, or brute force.
 """
 from .kernels import GAUSSIAN, LAPLACIAN, LINEAR, POLY, Kernel, kernel_diag, kernel_matrix, kernel_wsum
 from .kkm import (CenterRep, MiniBatchKernelKMeans, StepRecord, combination_norm2,
-                  distance_to_combination)
+                  distance_to_combination, state_distances)
 from .rng import batch_indices, index_below, splitmix64
 from .init import kmeanspp
 from . import grad
 
 __all__ = [
     "GAUSSIAN", "LAPLACIAN", "LINEAR", "POLY", "Kernel", "kernel_diag", "kernel_matrix",
-    "kernel_wsum", "CenterRep", "combination_norm2", "distance_to_combination", "MiniBatchKernelKMeans", "StepRecord", "batch_indices",
+    "kernel_wsum", "CenterRep", "combination_norm2", "distance_to_combination", "state_distances", "MiniBatchKernelKMeans", "StepRecord", "batch_indices",
     "index_below", "splitmix64", "kmeanspp", "grad",
 ]

@@ -85,6 +85,37 @@ def distance_to_combination(X, q, idx, w, kernel: Kernel) -> float:
     return float(kernel_diag(q, kernel)[0] - 2.0 * cross + combination_norm2(X, idx, w, kernel))
 
 
+def state_distances(X, Q, state: dict, kernel: Kernel):
+    """Delta(q, C^j) for every row q of Q against centers given explicitly by a
+    window state (the layout of ``MiniBatchKernelKMeans.state``: support rows
+    center by center with their weights), plus ||C^j||^2 of each center.
+
+    Every term is computed directly from Eq. (1)'s weighted sum of feature
+    vectors, as in ``MiniBatchKernelKMeans.distances``: the center norms are
+    sum_{s,t} w_s w_t K(y_s, y_t), not a carried value. The state's own
+    ``cnorm`` entry is not read. Returns (dist (m, k), cnorm (k,)).
+    """
+    X = np.asarray(X, dtype=np.float64)
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    if Q.ndim == 1:
+        Q = Q[None, :]
+    rows = np.asarray(state["rows_per_center"], dtype=np.int64)
+    idx = np.asarray(state["row_idx"], dtype=np.int64)
+    w = np.asarray(state["row_w"], dtype=np.float64)
+    k = len(rows)
+    off = np.concatenate([[0], np.cumsum(rows)])
+    kqq = kernel_diag(Q, kernel)
+    out = np.empty((Q.shape[0], k), dtype=np.float64)
+    cn = np.empty(k, dtype=np.float64)
+    for j in range(k):
+        ij, wj = idx[off[j]:off[j + 1]], w[off[j]:off[j + 1]]
+        Y = X[ij]
+        cn[j] = float(wj @ kernel_matrix(Y, Y, kernel) @ wj) if len(ij) else 0.0
+        cross = kernel_wsum(Q, Y, wj, kernel) if len(ij) else np.zeros(Q.shape[0])
+        out[:, j] = kqq - 2.0 * cross + cn[j]
+    return out, cn
+
+
 class MiniBatchKernelKMeans:
     """Algorithm 2 (``tau`` an int) or Algorithm 1 (``tau=None``), FP64."""
 

@@ -204,6 +204,32 @@ def test_truncated_distances_equal_explicit_vectors():
     assert any(not m.center(j).c1_kept for j in range(3))   # truncation did happen
 
 
+def test_state_distances_equal_explicit_vectors():
+    """Distances against an explicit window state: with the linear kernel they are
+    squared distances to the explicit centroids sum_s w_s y_s, and the returned
+    norms are ||sum_s w_s y_s||^2. With the Gaussian kernel they equal the
+    oracle's own distances for the state it holds."""
+    X, _ = inputs.isotropic_mixture(300, 5, 3, seed=16)
+    X = X.astype(np.float64)
+    m = MiniBatchKernelKMeans(X, 3, Kernel(LINEAR), 32, [4, 5, 6], tau=24)
+    for B in inputs.batch_stream(len(X), 32, 8, seed=5):
+        m.step(B)
+    st = m.state()
+    off = np.concatenate([[0], np.cumsum(st["rows_per_center"])])
+    C = np.stack([st["row_w"][off[j]:off[j + 1]] @ X[st["row_idx"][off[j]:off[j + 1]]] for j in range(3)])
+    Q = X[:40]
+    d, cn = oracle.state_distances(X, Q, st, Kernel(LINEAR))
+    np.testing.assert_allclose(d, ((Q[:, None, :] - C[None]) ** 2).sum(-1), rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(cn, (C * C).sum(1), rtol=1e-10)
+    kg = Kernel(GAUSSIAN, 20.0)
+    g = MiniBatchKernelKMeans(X, 3, kg, 32, [4, 5, 6], tau=24)
+    for B in inputs.batch_stream(len(X), 32, 6, seed=8):
+        g.step(B)
+    d2, cn2 = oracle.state_distances(X, Q, g.state(), kg)
+    np.testing.assert_allclose(d2, g.distances(Q), rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(cn2, g.center_norms(), rtol=1e-12)
+
+
 # ------------------------------------------- degree-2 polynomial, brute force
 def _poly2_features(X, c):
     n, d = X.shape
