@@ -1,14 +1,22 @@
 """Benchmark: batch-point x center distances per second, one mini-batch kernel
-k-means iteration per step, on the MNIST-shaped synthetic workload
-(n=70000, d=784, k=10, b=1024, tau=200, Gaussian kernel with the median
-heuristic, beta learning rate).
+k-means iteration per step. The default workload is the largest single-GPU
+one: n=1e6 points in d=128 from a 100-component anisotropic Gaussian mixture,
+k=100, b=4096, tau=200, Gaussian kernel with the median heuristic, beta
+learning rate.
 
 A step is one full iteration of the method: sample the batch on the device,
 gather it, run the distance pass, assign by argmin, do the counting sort and
 window plan, move the rows, run the window Gram pass and the FP64 norm
 recurrence. The reported value is b*k / t_step, summed over ranks.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16|bf16x3]
+Timing: the state is first brought to its steady-state size, then the timed
+call (kkm_steps of K iterations) is warmed up so that its CUDA graphs are
+captured before the timed region. The timed region is a run of blocks, each
+exactly K steps bracketed by a barrier and a device synchronisation on both
+sides and timed with CUDA events; blocks repeat for about a second so that the
+clock sampler sees the region, and the median block gives ms_per_step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision auto|fp32|bf16|bf16x3|tf32]
   python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
 
 Under torchrun each rank runs an independent replica on its own GPU. The
@@ -33,7 +41,7 @@ if ROOT not in sys.path:
 
 from paper_2410_05902_gb300 import inputs  # noqa: E402
 
-WORKLOAD = inputs.WORKLOADS["image"]
+WORKLOAD = inputs.WORKLOADS["precision"]
 METRIC = "batch-point×center distances/s per iteration on 1 GB300 (BF16 vs FP32) at ≤1e-4 obj err"
 UNIT = "distances/s"
 PREP_ITERS = 20         # iterations that bring the windows to their steady-state size
@@ -188,35 +196,60 @@ def make_workload(seed_offset: int = 0):
     return X, kappa, init
 
 
+def shared_config(world: int) -> dict:
+    """The workload description both arms print (the driver compares them)."""
+    w = WORKLOAD
+    xbytes = 4 * w.n * w.d
+    return {"workload": workload_desc(w),
+            "l2": f"inputs larger than L2: X is {xbytes / 1e6:.0f} MB (L2 129 MB); the method's support "
+                  "state stays resident between iterations, as the method keeps it",
+            "parallelism": f"replicas x{world} (independent runs, no collective)"}
+
+
+PREP_ORACLE = 6         # oracle iterations before the teacher-forced check (steady-state support)
+CHECK_ITERS = 2         # teacher-forced iterations checked per form
+
+
 # ------------------------------------------------------------------ oracle leg
-def oracle_leg(X, kappa, init, forms, Xd, budget_s: float, prep: int = 4):
+def oracle_leg(X, kappa, init, forms, Xd, budget_s: float, end_states: dict, prep: int = PREP_ORACLE):
     """The FP64 oracle on the host cores, rank 0 only. It is the CPU baseline
     and also the accuracy check of every GPU form.
 
-    The oracle runs the workload from the same start on a seeded batch stream.
-    After `prep` iterations its state is loaded into a fresh GPU context of each
-    form (kkm_set_state), and both sides take the next iteration on the same
-    batch. The GPU's f_B and distances are compared with the oracle's
-    (teacher-forced step). The oracle then keeps iterating until `budget_s` of
-    timed iterations is spent; its median b*k per second is the CPU baseline.
+    Teacher-forced check: the oracle runs the workload from the same start on
+    a seeded batch stream. After `prep` iterations (the support has reached
+    its steady-state size) its state is loaded into a fresh GPU context of each
+    form (kkm_set_state) and both sides take the next CHECK_ITERS iterations on
+    the same batches, the GPU forced to the oracle's assignments, reloading
+    the oracle's state before each. f_B and the distances are compared.
+
+    End-of-trajectory check: `end_states[form]` holds the GPU's own windows
+    and weights after its timed region and the f_B and distances the GPU
+    computed on one more batch from them. The oracle evaluates that batch
+    against the same windows and weights in FP64 with every center norm
+    computed directly (no recurrence), so the check covers the norm
+    recurrence after thousands of GPU iterations as well as the distances.
+
+    The oracle then keeps iterating until `budget_s` of timed iterations is
+    spent; its median b*k per second is the CPU baseline.
     """
     import torch
     import oracle
     from paper_2410_05902_gb300.kkm import KKM
     w = WORKLOAD
     X64 = X.astype(np.float64)
-    ora = oracle.MiniBatchKernelKMeans(X64, w.k, oracle_kernel(kappa), w.b, init,
-                                       tau=None if ALGO == "table" else w.tau)
+    kern = oracle_kernel(kappa)
+    ora = oracle.MiniBatchKernelKMeans(X64, w.k, kern, w.b, init, tau=None if ALGO == "table" else w.tau)
     batches = inputs.batch_stream(w.n, w.b, 400, seed=77)
     recs = [ora.step(batches[i]) for i in range(prep)]
-    state = ora.state()
-    S_check = int(state["rows_per_center"].sum())
-    t0 = time.perf_counter()
-    rec = ora.step(batches[prep])
-    times = [time.perf_counter() - t0]
+    states, checks = [], []
+    times = []
+    for c in range(CHECK_ITERS):
+        states.append(ora.state())
+        t0 = time.perf_counter()
+        checks.append(ora.step(batches[prep + c]))
+        times.append(time.perf_counter() - t0)
+    S_check = int(states[0]["rows_per_center"].sum())
     acc = {}
-    bi = torch.from_numpy(batches[prep].astype(np.int32)).to(Xd.device)
-    fa = torch.from_numpy(rec.assign.astype(np.int32)).to(Xd.device)
     for form in forms:
         run = KKM(Xd, w.k, w.b, kernel=KERNEL, param=kappa, tau=0 if ALGO == "table" else w.tau,
                   precision=form, init_idx=init, algo=ALGO)
@@ -225,18 +258,38 @@ def oracle_leg(X, kappa, init, forms, Xd, budget_s: float, prep: int = 4):
             for r in recs:
                 run.step(torch.from_numpy(r.batch.astype(np.int32)).to(Xd.device),
                          torch.from_numpy(r.assign.astype(np.int32)).to(Xd.device))
-        else:
-            run.set_state(state)
-        dist_out = torch.empty((w.b, w.k), dtype=torch.float32, device=Xd.device)
-        obj = torch.empty(1, dtype=torch.float64, device=Xd.device)
-        run.step(bi, fa, None, dist_out, obj)
-        run.sync()
-        d = dist_out.cpu().numpy().astype(np.float64)
-        f = float(obj.cpu()[0])
-        acc[form] = {"obj_rel_err": abs(f - rec.batch_objective) / abs(rec.batch_objective),
-                     "dist_rel_err": float(np.max(np.abs(d - rec.dist)) / np.max(np.abs(rec.dist)))}
+        o_err, d_err = [], []
+        for st, rec in zip(states, checks):
+            if ALGO != "table":
+                run.set_state(st)
+            bi = torch.from_numpy(rec.batch.astype(np.int32)).to(Xd.device)
+            fa = torch.from_numpy(rec.assign.astype(np.int32)).to(Xd.device)
+            dist_out = torch.empty((w.b, w.k), dtype=torch.float32, device=Xd.device)
+            obj = torch.empty(1, dtype=torch.float64, device=Xd.device)
+            run.step(bi, fa, None, dist_out, obj)
+            run.sync()
+            d = dist_out.cpu().numpy().astype(np.float64)
+            o_err.append(abs(float(obj.cpu()[0]) - rec.batch_objective) / abs(rec.batch_objective))
+            d_err.append(float(np.max(np.abs(d - rec.dist)) / np.max(np.abs(rec.dist))))
         run.close()
-    i = prep + 1
+        acc[form] = {"obj_rel_err_forced": max(o_err), "dist_rel_err": max(d_err)}
+        es = end_states.get(form)
+        if es is not None:
+            ref, cn_ref = oracle.state_distances(X64, X64[es["batch"]], es["state"], kern)
+            f_ref = float(np.mean(ref.min(axis=1)))
+            acc[form]["obj_rel_err_end"] = abs(es["obj"] - f_ref) / abs(f_ref)
+            acc[form]["dist_rel_err_end"] = float(np.max(np.abs(es["dist"] - ref)) / np.max(np.abs(ref)))
+            acc[form]["cnorm_rel_err_end"] = float(np.max(np.abs(es["state"]["cnorm"] - cn_ref)) /
+                                                   np.max(np.abs(cn_ref)))
+            acc[form]["end_iteration"] = int(es["state"]["iteration"])
+            gap = np.sort(ref, axis=1)
+            gap = gap[:, 1] - gap[:, 0]
+            bad = np.nonzero(es["assign"] != ref.argmin(axis=1))[0]
+            acc[form]["assign_mismatch_end"] = int(len(bad))
+            acc[form]["assign_mismatch_outside_ties_end"] = int(np.sum(
+                gap[bad] > 2e-3 * float(np.max(np.abs(ref)))))
+        acc[form]["obj_rel_err"] = max(acc[form]["obj_rel_err_forced"], acc[form].get("obj_rel_err_end", 0.0))
+    i = prep + CHECK_ITERS
     t_start = time.perf_counter()
     S = [S_check]
     while time.perf_counter() - t_start < budget_s and i < len(batches):
@@ -261,16 +314,26 @@ def oracle_leg(X, kappa, init, forms, Xd, budget_s: float, prep: int = 4):
     desc = (f"FP64 oracle, full iterations {prep + 1}-{i} of the same workload from the same start "
             f"(support S {min(S)}-{max(S)} rows), median over {len(times)} iterations on {cores} threads, "
             f"then {len(t1)} on one thread")
-    check = (f"teacher-forced iteration {prep + 1} (support S={S_check}): oracle state loaded into each "
-             "GPU form, same batch, f_B and normwise distance error against the FP64 oracle")
+    check = (f"teacher-forced iterations {prep + 1}-{prep + CHECK_ITERS} (support S={S_check}): oracle state "
+             "loaded into each GPU form, same batches and assignments, f_B and normwise distance error "
+             "against the FP64 oracle (obj_rel_err_forced); end of the timed trajectory: the GPU's own "
+             "windows and weights after its timed steps, one more batch scored by the GPU and by the "
+             "oracle with directly computed center norms (obj_rel_err_end, cnorm_rel_err_end); "
+             "obj_rel_err is the larger of the two")
     if ALGO == "table":
-        check = (f"iteration {prep + 1} after {prep} iterations forced along the untruncated FP64 oracle's "
-                 "trajectory (same batches and assignments): f_B and normwise distance error")
+        check = (f"iterations {prep + 1}-{prep + CHECK_ITERS} after {prep} iterations forced along the "
+                 "untruncated FP64 oracle's trajectory (same batches and assignments): f_B and normwise "
+                 "distance error")
     return w.b * w.k / t, cores, desc, acc, check, one_core
 
 
 def run_reference(args):
-    """The oracle as the reference arm: rank 0 only, on the host cores."""
+    """The oracle as the reference arm: rank 0 only, on the host cores.
+
+    A step is one full FP64 oracle iteration of the workload (b batch points
+    against k centers, the window update and the directly computed center
+    norms), the same unit of work as the GPU arm's step, from a state brought
+    to its steady-state support size first."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
@@ -278,36 +341,30 @@ def run_reference(args):
     w = WORKLOAD
     X, kappa, init = make_workload()
     ora = oracle.MiniBatchKernelKMeans(X, w.k, oracle_kernel(kappa), w.b, init, tau=w.tau)
-    batches = inputs.batch_stream(w.n, w.b, 200, seed=77)
-    for i in range(4):
+    batches = inputs.batch_stream(w.n, w.b, PREP_ORACLE + args.warmup + args.steps, seed=77)
+    for i in range(PREP_ORACLE):
         ora.step(batches[i])
-    S = sum(len(ora.center(j).idx) for j in range(w.k))
-    # one step = distances of m batch rows to all k centers at this support size;
-    # m is sized so the whole run stays within about two minutes
-    Xb = X[batches[4]].astype(np.float64)
-    t0 = time.perf_counter()
-    ora.distances(Xb[:8])
-    per_row = max((time.perf_counter() - t0) / 8, 1e-6)
-    m = int(max(1, min(w.b, 100.0 / max(args.steps + args.warmup, 1) / per_row)))
+    S0 = sum(len(ora.center(j).idx) for j in range(w.k))
     for s in range(args.warmup):
-        r0 = (s * m) % (w.b - m + 1)
-        ora.distances(Xb[r0:r0 + m])
+        ora.step(batches[PREP_ORACLE + s])
     times = []
     for s in range(args.steps):
-        r0 = ((args.warmup + s) * m) % (w.b - m + 1)
         t0 = time.perf_counter()
-        ora.distances(Xb[r0:r0 + m])
+        ora.step(batches[PREP_ORACLE + args.warmup + s])
         times.append(time.perf_counter() - t0)
+    S1 = sum(len(ora.center(j).idx) for j in range(w.k))
     total = sum(times)
-    value = m * w.k * args.steps / total
+    value = w.b * w.k * args.steps / total
     cores = oracle.kernels.num_threads()
-    sample = (f"per step: FP64 oracle distances of {m} batch rows to all {w.k} centers at steady-state "
-              f"support S={S} rows (iteration 5 of the same workload)")
+    sample = (f"per step: one full FP64 oracle iteration of the workload (b={w.b} batch points x k={w.k} "
+              f"centers, window update, direct center norms), iterations "
+              f"{PREP_ORACLE + args.warmup + 1}-{PREP_ORACLE + args.warmup + args.steps} after "
+              f"{PREP_ORACLE} preparation and {args.warmup} warm-up iterations (support S {S0}-{S1} rows)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": workload_desc(w)},
+        "data": "synthetic", "config": shared_config(world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -315,38 +372,65 @@ def run_reference(args):
 
 # ------------------------------------------------------------------- GPU leg
 def time_form(form, args, X, Xd, kappa, init, rank, world, dev, barrier):
-    """Timed region, distance-kernel timing and end-to-end pass of one precision form."""
+    """Timed region, end-of-trajectory state, distance-kernel timing and
+    end-to-end pass of one precision form."""
     import torch
-    import torch.distributed as dist
     from paper_2410_05902_gb300 import kkm as kb
     from paper_2410_05902_gb300.kkm import KKM
     w = WORKLOAD
+    K = args.steps
     stream = torch.cuda.current_stream(dev)
     run = KKM(Xd, w.k, w.b, kernel=KERNEL, param=kappa, tau=0 if ALGO == "table" else w.tau, precision=form,
               seed=1000 + rank, init_idx=init, dist_tile=args.dist_tile, algo=ALGO)
     for _ in range(PREP_ITERS):
         run.step()
     run.graph(not args.no_graph)          # steps replay captured CUDA graphs
-    for _ in range(args.warmup):
-        run.step()
+    # warm-up through the timed call itself: its graphs (16 iterations per
+    # replay, and the single-step one for a remainder) are captured here
+    for _ in range(max(2, -(-args.warmup // K))):
+        run.steps(K)
+    run.flush()
     run.sync()
     run.stats(reset=True)
     run.launches(reset=True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+
+    def block() -> float:
+        barrier()
+        ev0.record(stream)
+        run.steps(K)                          # the fixed-iteration loop with the built-in sampler
+        run.flush()                           # the last step's weight update (each step queues the previous one's)
+        ev1.record(stream)
+        barrier()
+        return ev0.elapsed_time(ev1)
+
+    # blocks of exactly K steps for about args.min_time seconds, the same count on every rank
+    first = block()
+    nblk = max(1, int(args.min_time * 1e3 / max(first, 1e-3)))
+    nblk = int(reduce_max(float(min(nblk, args.max_blocks)), world, dev))
     clocks = Clocks(dev.index).ready() if rank == 0 else None
     barrier()
     if clocks:
         clocks.start()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    run.steps(args.steps)                 # the fixed-iteration loop: 16 iterations per graph replay
-    run.flush()                           # the last step's weight update (each step queues the previous one's)
-    ev1.record(stream)
-    barrier()
-    ms = ev0.elapsed_time(ev1)
+    blocks = [block() for _ in range(nblk)]
     clk = clocks.stop() if clocks else None
     launches = run.launches(reset=True)
     steps_done, srows, _ = run.stats(reset=True)
+    ms = reduce_max(statistics.median(blocks), world, dev)
+    # end of the timed trajectory: the windows and weights the GPU holds, and
+    # its distances and f_B on one more batch (checked against the oracle on rank 0)
+    end = None
+    if rank == 0:
+        state = run.get_state()
+        B = inputs.batch_stream(w.n, w.b, 1, seed=4242)[0]
+        dist_out = torch.empty((w.b, w.k), dtype=torch.float32, device=dev)
+        a_out = torch.empty(w.b, dtype=torch.int32, device=dev)
+        obj = torch.empty(1, dtype=torch.float64, device=dev)
+        run.step(torch.from_numpy(B.astype(np.int32)).to(dev), None, a_out, dist_out, obj)
+        run.sync()
+        end = {"state": state, "batch": B, "dist": dist_out.cpu().numpy().astype(np.float64),
+               "assign": a_out.cpu().numpy(), "obj": float(obj.cpu()[0])}
     # per-launch time of the distance kernel: CUDA events on the context's
     # stream, over eager steps of the same workload right after the timed
     # region (events inside a replayed graph keep only the last replay). The
@@ -356,55 +440,72 @@ def time_form(form, args, X, Xd, kappa, init, rank, world, dev, barrier):
     # read every step); one launch between two events also counts the launch gap.
     run.timing(True)
     run.timing_read(reset=True)
-    for _ in range(min(args.steps, 500)):
+    for _ in range(min(max(K, 50), 500)):
         run.step()
     n_single, k_single = run.timing_read(reset=True)
     run.timing(KERNEL_REPS)
-    for _ in range(min(args.steps, 100)):
+    for _ in range(min(max(K, 50), 100)):
         run.step()
     n_rec, k_ms = run.timing_read(reset=True)
     run.timing(False)
     run.sync()
-    ms = reduce_max(ms, world, dev)
     # end to end through the public host-buffer call: index upload, step,
     # assignment and objective download, synchronise, every step
-    e2e_steps = max(50, min(args.steps, 2000))
+    e2e_steps = max(50, min(K * 10, 2000))
     pinned_idx = torch.empty((e2e_steps, w.b), dtype=torch.int32, pin_memory=True)
     pinned_idx.copy_(torch.from_numpy(inputs.batch_stream(w.n, w.b, e2e_steps, seed=500 + rank).astype(np.int32)))
     idx_np = pinned_idx.numpy()
-    a_out = torch.empty(w.b, dtype=torch.int32, pin_memory=True).numpy()
-    o_out = torch.empty(1, dtype=torch.float64, pin_memory=True).numpy()
+    a_host = torch.empty(w.b, dtype=torch.int32, pin_memory=True).numpy()
+    o_host = torch.empty(1, dtype=torch.float64, pin_memory=True).numpy()
     for s_ in range(3):
-        kb.kkm_step_host(run.ctx, idx_np[s_], a_out, o_out)
+        kb.kkm_step_host(run.ctx, idx_np[s_], a_host, o_host)
     run.sync()                            # applies the warm-up's last weight update
     barrier()
     t0 = time.perf_counter()
     for s_ in range(e2e_steps):
-        kb.kkm_step_host(run.ctx, idx_np[s_], a_out, o_out)
+        kb.kkm_step_host(run.ctx, idx_np[s_], a_host, o_host)
     run.sync()                            # and the last timed step's
     t_e2e = reduce_max(time.perf_counter() - t0, world, dev)
     run.close()
-    return {"ms": ms, "value": whole_job_value(w.b, w.k, args.steps, world, ms / 1e3), "clocks": clk,
-            "launches": launches, "S": srows / max(steps_done, 1), "kernel_ms": k_ms / max(n_rec, 1),
-            "kernel_launches": n_rec * KERNEL_REPS, "kernel_ms_single": k_single / max(n_single, 1), "e2e_value": whole_job_value(w.b, w.k, e2e_steps, world, t_e2e),
-            "e2e_steps": e2e_steps}
+    q = sorted(blocks)
+    return {"ms": ms, "value": whole_job_value(w.b, w.k, K, world, ms / 1e3), "clocks": clk,
+            "launches": launches // max(nblk, 1), "S": srows / max(steps_done, 1),
+            "kernel_ms": k_ms / max(n_rec, 1), "kernel_launches": n_rec * KERNEL_REPS,
+            "kernel_ms_single": k_single / max(n_single, 1),
+            "e2e_value": whole_job_value(w.b, w.k, e2e_steps, world, t_e2e), "e2e_steps": e2e_steps,
+            "blocks": nblk, "block_ms_p10": q[len(q) // 10], "block_ms_p90": q[(9 * len(q)) // 10],
+            "block_ms_first": first, "end": end}
 
 
 KERNEL_REPS = 20      # back-to-back distance-pass launches per timing record
 
 
-def roofline(form, S, kernel_ms, n_rec, single_ms=None):
+def device_sms(dev=None) -> int:
+    import torch
+    return int(torch.cuda.get_device_properties(dev if dev is not None else 0).multi_processor_count)
+
+
+def roofline(form, S, kernel_ms, n_rec, single_ms=None, sms=None, probe=None):
     w = WORKLOAD
     peaks = load_peaks()
+    sms = sms or device_sms()
     # algorithmic Gram flops of one distance-pass launch: 2 b S d (windows) or
     # 2 n b d (table form: every row of X against the batch)
     flops = 2.0 * w.n * w.b * w.d if ALGO == "table" else 2.0 * w.b * S * w.d
     achieved = flops / (kernel_ms / 1e3) / 1e12
     if form == "fp32":
-        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        if probe and probe.get("ffma_per_clk_sm"):
+            # the faster of the scalar and the packed f32x2 FMA rates
+            fma = max(probe["ffma_per_clk_sm"], probe.get("ffma2_fp32_per_clk_sm") or 0.0)
+            peak = sms * fma * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            src = (f"{sms} SMs x measured {fma:.1f} FP32 FMA/clk/SM (the faster of scalar and f32x2; "
+                   f"{probe['source']}) x 2 flop x max SM clock")
+        else:
+            peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            src = f"{sms} SMs x 128 FP32 FMA/clk x 2 flop x max SM clock (derived)"
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "kernel": "k_dist_simt<FP32> (FP32 FFMA Gram + kernel values + weighted sums)",
-                "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 flop x max SM clock (derived)"}
+                "peak_source": src}
     elif form == "tf32":
         # TF32 dense: the measured BF16 burst times the nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s)
         peak = peaks["bf16_tflops"] * 1.1 / 2.25
@@ -424,12 +525,16 @@ def roofline(form, S, kernel_ms, n_rec, single_ms=None):
             sus = sus * (1.1 / 2.25 if form == "tf32" else 1.0)
             roof["frac_sustained"] = achieved / sus
     if KERNEL in ("gaussian", "laplacian") and ALGO != "table":
-        # exponentials: one per batch-point x support-row pair, against the MUFU's
-        # nominal 16 ex2 a clock per SM at the maximum SM clock
+        # exponentials: one per batch-point x support-row pair
         exp_rate = (w.b * S) / (kernel_ms / 1e3)
-        exp_peak = 152 * 16 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+        if probe and probe.get("ex2_per_clk_sm"):
+            exp_peak = sms * probe["ex2_per_clk_sm"] * peaks.get("sm_max_mhz", 2070.0) * 1e6
+            roof["exp_peak_source"] = (f"{sms} SMs x measured {probe['ex2_per_clk_sm']:.2f} ex2.approx/clk/SM "
+                                       f"({probe['source']}) x max SM clock")
+        else:
+            exp_peak = sms * 16 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+            roof["exp_peak_source"] = f"{sms} SMs x 16 ex2/clk x max SM clock (nominal MUFU rate, derived)"
         roof["exp_frac"] = exp_rate / exp_peak
-        roof["exp_peak_source"] = "152 SMs x 16 ex2/clk x max SM clock (nominal MUFU rate, derived)"
     roof["flops_per_launch"] = flops
     roof["avg_launch_ms"] = kernel_ms
     roof["launches_timed"] = n_rec
@@ -441,11 +546,21 @@ def roofline(form, S, kernel_ms, n_rec, single_ms=None):
     return roof
 
 
+def measure_unit_rates():
+    """Per-SM rates of the MUFU ex2.approx and the FP32 FMA pipe, measured
+    now on this device by the library's probe (kkm_probe_unit_rate)."""
+    from paper_2410_05902_gb300 import kkm as kb
+    d = kb.unit_rates()
+    d["source"] = "kkm_probe_unit_rate, measured in this run"
+    return d
+
+
 def measured_traffic(form):
     """DRAM bytes per launch of the distance kernel from the committed ncu
-    summary, when it was taken on the current kernel source (else None)."""
+    summary of this workload, when it was taken on the current kernel source
+    (else None)."""
     import hashlib
-    p = os.path.join(ROOT, "profiles", "traffic_image_distance_pass.json")
+    p = os.path.join(ROOT, "profiles", f"traffic_{WORKLOAD.name}_distance_pass.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
@@ -479,10 +594,12 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    probe = measure_unit_rates() if rank == 0 else None
     forms = ["fp32", "bf16x3", "tf32", "bf16"] if args.precision == "auto" else [args.precision]
     res = {f: time_form(f, args, X, Xd, kappa, init, rank, world, dev, barrier) for f in forms}
     if rank == 0:
-        cpu_v, cores, desc, acc, check, one_core = oracle_leg(X, kappa, init, forms, Xd, args.oracle_budget)
+        ends = {f: res[f].pop("end") for f in forms}
+        cpu_v, cores, desc, acc, check, one_core = oracle_leg(X, kappa, init, forms, Xd, args.oracle_budget, ends)
         ok = [f for f in forms if acc[f]["obj_rel_err"] <= OBJ_BAR]
         chosen = max(ok, key=lambda f: res[f]["value"]) if ok else max(forms, key=lambda f: res[f]["value"])
         r = res[chosen]
@@ -490,20 +607,26 @@ def run_ours(args):
             "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[chosen], "data": "synthetic",
-            "config": {"workload": workload_desc(w), "precision": chosen,
-                       "form_rule": f"fastest form with objective error <= {OBJ_BAR} against the FP64 oracle",
-                       "meets_obj_bar": chosen in ok, "support_rows_S": r["S"],
-                       "state_prep_iters": PREP_ITERS,
-                       "l2": f"inputs larger than L2: X is {X.nbytes / 1e6:.0f} MB (L2 129 MB); the "
-                             "method's support state stays resident between iterations",
-                       "parallelism": f"replicas x{world} (independent runs, no collective)",
+            "config": shared_config(world),
+            "form": {"chosen": chosen,
+                     "rule": f"fastest form with objective error <= {OBJ_BAR} against the FP64 oracle",
+                     "meets_obj_bar": chosen in ok},
+            "timing": {"support_rows_S": r["S"], "state_prep_iters": PREP_ITERS,
+                       "blocks": r["blocks"], "block_ms_median": r["ms"], "block_ms_p10": r["block_ms_p10"],
+                       "block_ms_p90": r["block_ms_p90"], "block_ms_first": r["block_ms_first"],
+                       "region": f"{r['blocks']} blocks of exactly {args.steps} steps (kkm_steps + flush), "
+                                 "each bracketed by barrier + synchronize and CUDA events; ms_per_step from "
+                                 "the median block; graphs captured during the warm-up",
                        "step_launch": "eager kernel launches" if args.no_graph else
-                       "kkm_steps: CUDA graph of 16 iterations replayed (programmatic dependent launch between iterations)"},
+                       "kkm_steps: CUDA graph of 16 iterations replayed (programmatic dependent launch between "
+                       "iterations); a remainder below 16 replays the single-step graph"},
             "forms": {f: {"value": res[f]["value"], "ms_per_step": res[f]["ms"] / args.steps,
                           "dist_kernel_ms": res[f]["kernel_ms"], "e2e": res[f]["e2e_value"], **acc[f]}
                       for f in forms},
             "accuracy_check": check,
-            "roofline": roofline(chosen, r["S"], r["kernel_ms"], r["kernel_launches"], r["kernel_ms_single"]),
+            "roofline": roofline(chosen, r["S"], r["kernel_ms"], r["kernel_launches"], r["kernel_ms_single"],
+                                 device_sms(dev), probe),
+            "unit_rates": probe,
             "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
                              "value_one_core": one_core},
             "e2e": {"value": r["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": 4 * w.b,
@@ -690,15 +813,19 @@ def run_compare_fullbatch(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["auto", "fp32", "bf16", "bf16x3", "tf32"], default="auto",
                     help="auto: time every form, report the fastest that meets the objective bar")
     ap.add_argument("--oracle-budget", type=float, default=20.0)
     ap.add_argument("--no-graph", action="store_true", help="launch every kernel instead of replaying a graph")
-    ap.add_argument("--workload", choices=sorted(inputs.WORKLOADS) + ["batching"], default="image",
-                    help="image (default) is the headline workload; the others are secondary measurements")
+    ap.add_argument("--workload", choices=sorted(inputs.WORKLOADS) + ["batching"], default="precision",
+                    help="precision (default: 1e6 x 128, k=100, b=4096) is the headline workload; the others "
+                         "are secondary measurements")
+    ap.add_argument("--min-time", type=float, default=1.0,
+                    help="seconds of timed blocks (each exactly --steps steps); the median block is reported")
+    ap.add_argument("--max-blocks", type=int, default=5000)
     ap.add_argument("--compare-fullbatch", action="store_true",
                     help="truncated mini-batch against full-batch kernel k-means (time, f_X, ARI, NMI)")
     ap.add_argument("--objective-grad", action="store_true",

@@ -146,6 +146,15 @@ int32_t kkm_version(void);
 kkm_status kkm_kmeanspp(const float* X, int64_t n, int32_t d, int64_t ldx, int32_t k, const kkm_kernel* kernel,
                         uint64_t seed, int64_t* out_idx, void* stream);
 
+/* kkm_form_supported -- whether a precision form (kkm_precision) runs on a
+ * device of compute capability cc_major.cc_minor: KKM_OK, or KKM_ENOTSUP for
+ * the tensor-core forms (BF16, split-BF16, TF32) on anything but 10.3, where
+ * the library has only its tcgen05 passes built for sm_103a and no CUDA-core
+ * stand-in. KKM_EINVAL for an unknown form. Host only, no CUDA call; kkm_init
+ * applies the same rule to the current device. The paper has no counterpart
+ * (its precision is not stated). */
+kkm_status kkm_form_supported(int32_t precision, int32_t cc_major, int32_t cc_minor);
+
 /* kkm_init -- creates a run (the inputs of Algorithms 1/2).
  *   out        : host; receives the new context, or NULL on failure.
  *   X          : device, n x d FP32 dataset, leading dimension ldx >= d.
@@ -162,6 +171,8 @@ kkm_status kkm_kmeanspp(const float* X, int64_t n, int32_t d, int64_t ldx, int32
  *                k distinct indices with the library's own seeded sampler.
  *   stream     : cudaStream_t on which every later call of this context
  *                queues its work. NULL means the legacy default stream.
+ * KKM_ENOTSUP when cfg->precision is not FP32 and the device is not compute
+ * capability 10.3 (see kkm_form_supported).
  * Allocates all device state up front: the support store of k*(2*tau + 4*b + 8)
  * rows (k*(1 + b*max_iters) when untruncated) and the step workspaces. No
  * later call allocates. Sets ||C_1^j||^2 = K(x, x). */
@@ -404,6 +415,22 @@ kkm_status kkm_distances_noalloc(const float* Q, int64_t m, int64_t ldq, int32_t
                                  const double* cnorm, int32_t k, const kkm_kernel* kernel,
                                  float* dist_out, int32_t* assign_out, void* stream);
 const char* kkm_noalloc_last_error(void);
+
+/* kkm_probe_unit_rate -- measured issue rate of one arithmetic unit on the
+ * current device. The paper has no counterpart: it supplies the denominators
+ * of the distance pass's roofline (the pass's epilogue spends one MUFU
+ * exponential and a few FP32 FMAs per kernel value).
+ *   op         : 0 ex2.approx.ftz.f32 (MUFU), 1 scalar FP32 fma, 2 packed
+ *                f32x2 fma (counted as two FP32 FMAs)
+ *   iters      : loop trips per thread, 1 .. 2^24 (eight operations each)
+ *   per_clk_sm : host out, operations per SM per SM clock (median over the
+ *                SMs' own cycle counters, so independent of the clock rate)
+ *   per_second : host out, operations per second over the whole device
+ *   stream     : cudaStream_t, NULL for the legacy default stream
+ * One block of 1024 threads runs on every SM. The call allocates and frees
+ * two small device buffers, and it synchronises. KKM_EINVAL for a bad op or
+ * iters, KKM_ECUDA when a CUDA call fails. */
+kkm_status kkm_probe_unit_rate(int32_t op, int64_t iters, double* per_clk_sm, double* per_second, void* stream);
 
 /* Frees everything the context allocated. NULL is accepted. It synchronises first. */
 kkm_status kkm_destroy(kkm_ctx* ctx);

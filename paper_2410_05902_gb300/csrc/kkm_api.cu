@@ -188,6 +188,12 @@ KKM_API const char* kkm_last_error(const kkm_ctx* ctx) {
   return ctx ? ctx->err.c_str() : g_init_error.c_str();
 }
 
+KKM_API kkm_status kkm_form_supported(int32_t precision, int32_t cc_major, int32_t cc_minor) {
+  if (precision < KKM_PREC_FP32 || precision > KKM_PREC_TF32) return KKM_EINVAL;
+  if (precision == KKM_PREC_FP32) return KKM_OK;       // CUDA-core kernels, any device the build runs on
+  return (cc_major == 10 && cc_minor == 3) ? KKM_OK : KKM_ENOTSUP;   // tcgen05 passes built for sm_103a
+}
+
 KKM_API kkm_status kkm_kmeanspp(const float* X, int64_t n, int32_t d, int64_t ldx, int32_t k,
                                 const kkm_kernel* kernel, uint64_t seed, int64_t* out_idx, void* stream) {
   if (!X || !kernel || !out_idx) return fail(nullptr, KKM_EINVAL, "X, kernel and out_idx are required");
@@ -312,17 +318,18 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
   else { s.dp = (int32_t)kkm::round_up(d, 64); s.ld = 2 * s.dp; }
   s.bpad = (int32_t)kkm::round_up(b, 128);
 
-  // tensor-core distance pass for the BF16 forms when the device supports it
+  // the tensor-core forms run only on the tcgen05 passes built for sm_103a:
+  // there is no CUDA-core stand-in for them
   c->use_tc = false;
   if (s.form != kkm::FORM_FP32) {
     int maj = 0, min = 0;
     cudaDeviceGetAttribute(&maj, cudaDevAttrComputeCapabilityMajor, c->device);
     cudaDeviceGetAttribute(&min, cudaDevAttrComputeCapabilityMinor, c->device);
-    c->use_tc = (maj == 10 && min == 3) && kkm::tc_available();
-  }
-  if (s.form == kkm::FORM_TF32 && !c->use_tc) {
-    c->err = "the TF32 form needs a compute capability 10.3 device";
-    return bail(KKM_ENOTSUP);
+    if (kkm_form_supported(s.form, maj, min) != KKM_OK) {
+      c->err = "the BF16, split-BF16 and TF32 forms need a compute capability 10.3 device (tcgen05)";
+      return bail(KKM_ENOTSUP);
+    }
+    c->use_tc = true;
   }
   s.tn = c->use_tc ? (cfg->dist_tile == 0 ? (tab ? 64 : 256) : cfg->dist_tile) : 64;
   s.pair_rows = c->use_tc ? 128 : 64;

@@ -876,8 +876,6 @@ cudaError_t launch_mode(const Dev& s, const void* maps_in, int rows, cudaStream_
 
 }  // namespace
 
-bool tc_available() { return true; }
-
 // Tensor maps of the batch rows and the support store: 2-D tensors of ld
 // columns (BF16, or FP32 for the TF32 form), boxes of one 128-byte row of
 // columns (64 BF16 or 32 FP32) x 128 (64, 256) rows, 128-byte swizzle.

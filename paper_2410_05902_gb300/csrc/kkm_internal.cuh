@@ -305,9 +305,8 @@ cudaError_t launch_tab_objective(const Dev& s, const TabBuf& q, const float* xn,
                                  cudaStream_t st);
 cudaError_t launch_mind_sum(const Dev& s, int rows, double scale, double* out, cudaStream_t st);  // scale * sum of mind
 
-// tensor-core distance pass (BF16 forms); returns cudaErrorNotSupported when unavailable
-// maps: 256 bytes, 64-byte aligned, holding the two CUtensorMap of the pass
-bool tc_available();
+// tensor-core passes (BF16, split-BF16 and TF32 forms)
+// maps: 512 bytes, 64-byte aligned, holding the four CUtensorMap of the passes
 cudaError_t tc_prepare(Dev& s, void* maps);
 // stage_early: the kernel just ahead on `st` (the batch gather, or this pass
 // itself) writes none of the support tiles, their metadata or the tile list,

@@ -85,6 +85,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "kkm_distances_noalloc": ([_P, c_int64, c_int64, c_int32, _P, c_int64, c_int64, _P, _P, _P,
                                    c_int32, POINTER(kkm_kernel), _P, _P, _P], c_int32),
         "kkm_noalloc_last_error": ([], ctypes.c_char_p),
+        "kkm_form_supported": ([c_int32, c_int32, c_int32], c_int32),
+        "kkm_probe_unit_rate": ([c_int32, c_int64, POINTER(c_double), POINTER(c_double), _P], c_int32),
         "kkm_destroy": ([_P], c_int32),
         "kkm_step_eval": ([_P, _P, _P, _P], c_int32),
         "kkm_kmeanspp": ([_P, c_int64, c_int32, c_int64, c_int32, POINTER(kkm_kernel), c_uint64, _P, _P], c_int32),
@@ -233,6 +235,24 @@ def kkm_distances_noalloc(Q: int, m: int, ldq: int, d: int, Y: int, S: int, ldy:
                                    dist_out, assign_out, stream)
     if st != KKM_OK:
         raise KKMError(st, lib.kkm_noalloc_last_error().decode())
+
+
+def kkm_probe_unit_rate(op: int, iters: int, stream: int | None = None) -> tuple[float, float]:
+    """(operations per SM per clock, operations per second) of one unit (see kkm.h)."""
+    a, b_ = c_double(), c_double()
+    st = load().kkm_probe_unit_rate(int(op), int(iters), ctypes.byref(a), ctypes.byref(b_), stream)
+    if st != KKM_OK:
+        raise KKMError(st, "kkm_probe_unit_rate failed")
+    return a.value, b_.value
+
+
+def unit_rates() -> dict:
+    """MUFU ex2.approx, scalar FP32 FMA and packed f32x2 FMA rates of the current device."""
+    ex2, ex2_s = kkm_probe_unit_rate(0, 65536)
+    fma, fma_s = kkm_probe_unit_rate(1, 262144)
+    fma2, fma2_s = kkm_probe_unit_rate(2, 131072)
+    return {"ex2_per_clk_sm": ex2, "ex2_per_s": ex2_s, "ffma_per_clk_sm": fma, "ffma_per_s": fma_s,
+            "ffma2_fp32_per_clk_sm": fma2, "ffma2_fp32_per_s": fma2_s}
 
 
 def kkm_get_state(ctx, k: int) -> dict:

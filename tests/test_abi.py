@@ -124,3 +124,25 @@ def test_kmeanspp_validates_on_host(lib):
 def test_binding_fails_loudly_without_library(tmp_path):
     with pytest.raises(RuntimeError, match="not built"):
         kkm.load(str(tmp_path / "missing.so"))
+
+
+def test_tensor_core_forms_refuse_other_devices(lib):
+    """The BF16, split-BF16 and TF32 forms run only on the tcgen05 passes built
+    for sm_103a: any other device gets KKM_ENOTSUP, never a CUDA-core stand-in."""
+    for prec in (kkm.KKM_PREC_BF16, kkm.KKM_PREC_BF16X3, kkm.KKM_PREC_TF32):
+        assert lib.kkm_form_supported(prec, 10, 3) == kkm.KKM_OK
+        for cc in ((10, 0), (9, 0), (12, 0), (8, 9), (10, 1)):
+            assert lib.kkm_form_supported(prec, *cc) == kkm.KKM_ENOTSUP
+    for cc in ((10, 3), (9, 0), (8, 0)):
+        assert lib.kkm_form_supported(kkm.KKM_PREC_FP32, *cc) == kkm.KKM_OK
+    assert lib.kkm_form_supported(7, 10, 3) == kkm.KKM_EINVAL
+    assert lib.kkm_form_supported(-1, 10, 3) == kkm.KKM_EINVAL
+
+
+def test_probe_rejects_bad_arguments(lib):
+    a, b = ctypes.c_double(), ctypes.c_double()
+    assert lib.kkm_probe_unit_rate(3, 10, ctypes.byref(a), ctypes.byref(b), None) == kkm.KKM_EINVAL
+    assert lib.kkm_probe_unit_rate(-1, 10, ctypes.byref(a), ctypes.byref(b), None) == kkm.KKM_EINVAL
+    assert lib.kkm_probe_unit_rate(0, 0, ctypes.byref(a), ctypes.byref(b), None) == kkm.KKM_EINVAL
+    assert lib.kkm_probe_unit_rate(0, 1 << 25, ctypes.byref(a), ctypes.byref(b), None) == kkm.KKM_EINVAL
+    assert lib.kkm_probe_unit_rate(0, 10, None, ctypes.byref(b), None) == kkm.KKM_EINVAL
