@@ -1,0 +1,111 @@
+"""Parity at the shape of the 1e6 x 128 workload, and over a long trajectory.
+
+Headline shape: d=128, k=100, b=4096 from a 100-component anisotropic
+mixture (random covariances, condition <= 100), tau=200. The oracle runs six
+iterations first, which brings the support to S ~ 19-20k rows (about 24
+distance-pass items per SM), then each form takes teacher-forced steps from
+the oracle's state: distances, argmin outside certified near-ties, f_B,
+windows, weights and center norms. n is 1e5 instead of 1e6 to keep the FP64
+oracle's data small; the kernels' work depends on b, S, d and k, not n.
+
+Long trajectory: 200 iterations of the small workload (n=2000, d=16, k=10,
+b=256) with the GPU's state never reloaded. Each iteration both sides take
+the same batch; the GPU's update follows the oracle's assignment (its own
+argmin is checked against the oracle's outside certified near-ties), so the
+two trajectories stay the same while the GPU carries ||C||^2 by its FP64
+recurrence for all 200 iterations. f_B is held to 1e-4 every iteration and
+the final ||C||^2 to 1e-6 of the oracle's direct w^T K w.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_05902_gb300 import inputs
+from gpu_helpers import (CN_RTOL, DIST_TOL, OBJ_TOL, Pair, compare_states, dist_rel_err,
+                         near_tie_ok)
+
+pytestmark = pytest.mark.gpu
+
+N_HEAD, D_HEAD, K_HEAD, B_HEAD, TAU = 100_000, 128, 100, 4096, 200
+PREP = 6
+
+
+@pytest.fixture(scope="module")
+def headline_data():
+    X, _ = inputs.anisotropic_mixture(N_HEAD, D_HEAD, 100, seed=12345)
+    sigma = inputs.median_sigma(X, seed=1)
+    init = inputs.init_indices(N_HEAD, K_HEAD, seed=3)
+    batches = inputs.batch_stream(N_HEAD, B_HEAD, PREP + 2, seed=77)
+    return X, sigma, init, batches
+
+
+_prepped = {}
+
+
+def _oracle_after_prep(kernel, headline_data):
+    """The oracle after PREP iterations, with its state and the next two records (cached per kernel)."""
+    if kernel not in _prepped:
+        X, sigma, init, batches = headline_data
+        param = 2 * sigma * sigma if kernel == "gaussian" else sigma
+        kern = oracle.Kernel(oracle.GAUSSIAN if kernel == "gaussian" else oracle.LAPLACIAN, param)
+        ora = oracle.MiniBatchKernelKMeans(X.astype(np.float64), K_HEAD, kern, B_HEAD, init, tau=TAU)
+        for B in batches[:PREP]:
+            ora.step(B)
+        states, recs = [], []
+        for B in batches[PREP:PREP + 2]:
+            states.append(ora.state())
+            recs.append(ora.step(B))
+        states.append(ora.state())
+        # (state before, record, state after) of each of the two steps
+        _prepped[kernel] = (param, [(states[c], recs[c], states[c + 1]) for c in range(2)])
+    return _prepped[kernel]
+
+
+@pytest.mark.parametrize("kernel", ["gaussian", "laplacian"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3", "tf32", "bf16"])
+def test_teacher_forced_headline_shape(precision, kernel, headline_data):
+    X, sigma, init, batches = headline_data
+    param, steps = _oracle_after_prep(kernel, headline_data)
+    p = Pair(X, k=K_HEAD, b=B_HEAD, kernel=kernel, param=param, tau=TAU, precision=precision, init=init)
+    torch = p.torch
+    p.gpu.stats(reset=True)
+    for st, rec, after in steps:
+        p.gpu.set_state(st)
+        d, a, f = p.gpu_step(rec.batch, forced=rec.assign)
+        err = dist_rel_err(d, rec.dist)
+        assert err <= DIST_TOL[precision], f"distance rel err {err:.3e}"
+        ok, nbad = near_tie_ok(a, rec, p.abs_tol(rec))
+        assert ok, f"{nbad} assignments differ outside certified near-ties"
+        # every form, BF16 included, is held to the 1e-4 objective bar at this shape
+        assert abs(f - rec.batch_objective) <= OBJ_TOL * abs(rec.batch_objective)
+        # windows exact, weights to FP64 rounding, norms to the form's accuracy
+        compare_states(p.gpu.get_state(), after, cn_rtol=CN_RTOL[precision])
+    steps_done, srows, tiles = p.gpu.stats(reset=True)
+    S = srows / steps_done
+    assert S > 18000, f"support only {S:.0f} rows"
+    items = (B_HEAD // 128) * tiles / steps_done
+    assert items > 10 * torch.cuda.get_device_properties(0).multi_processor_count
+    p.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_long_trajectory_recurrence(precision):
+    """200 iterations with the GPU state never reloaded (see the module docstring)."""
+    X, _ = inputs.isotropic_mixture(2000, 16, 10, seed=12345)
+    p = Pair(X, k=10, b=256, tau=200, precision=precision)
+    worst_f = 0.0
+    for B in inputs.batch_stream(len(X), 256, 200, seed=2024):
+        rec = p.ora.step(B)
+        d, a, f = p.gpu_step(B, forced=rec.assign)
+        assert dist_rel_err(d, rec.dist) <= DIST_TOL[precision]
+        ok, nbad = near_tie_ok(a, rec, p.abs_tol(rec))
+        assert ok, f"iteration {rec.iteration}: {nbad} assignments differ outside near-ties"
+        rel = abs(f - rec.batch_objective) / abs(rec.batch_objective)
+        worst_f = max(worst_f, rel)
+        assert rel <= OBJ_TOL, f"iteration {rec.iteration}: f_B rel err {rel:.2e}"
+    gs, os_ = p.gpu.get_state(), p.ora.state()
+    cn_err = float(np.max(np.abs(gs["cnorm"] - os_["cnorm"]) / np.abs(os_["cnorm"])))
+    assert cn_err <= 1e-6, f"||C||^2 after 200 iterations: rel err {cn_err:.2e}"
+    compare_states(gs, os_, cn_rtol=1e-6)
+    assert gs["iteration"] == 201
+    p.close()
