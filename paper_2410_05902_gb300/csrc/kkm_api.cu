@@ -332,14 +332,20 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
     c->use_tc = true;
   }
   s.tn = c->use_tc ? (cfg->dist_tile == 0 ? (tab ? 64 : 256) : cfg->dist_tile) : 64;
+  if (tab && s.tn == 256) s.tn = 128;   // the table form's layout kernels take one partial per tile
+  s.ppt = (c->use_tc && s.tn == 256) ? 2 : 1;
   s.pair_rows = c->use_tc ? 128 : 64;
-  s.pair_cols = 64;
+  s.pair_cols = c->use_tc ? kkm::WPASS_TNV : 64;
+  s.walign = c->use_tc ? 4 : 1;
   const int64_t TR = s.pair_rows, TC = s.pair_cols;   // window-pass tile
   s.max_tiles = tab ? (int32_t)(k + (b + s.tn - 1) / s.tn + 1)
                     : (int32_t)((int64_t)k * ((wmax + s.tn - 1) / s.tn + 1));
-  const int64_t smax = (int64_t)k * wmax;
-  const int64_t p1 = ((smax + TR - 1) / TR + k) * ((wmax + b + TC - 1) / TC);
-  const int64_t p2 = ((b + TR - 1) / TR + k) * ((b + TC - 1) / TC + k);
+  // window-pass tiles per step: per center, ceil((rows + a) / TR) x ceil((cols + a) / TC)
+  // for the dropped rows against the window and the new block, and for the new
+  // block against itself, with a < walign rows of alignment slack
+  const int64_t smax = (int64_t)k * wmax, al = s.walign;
+  const int64_t p1 = ((smax + al * k + TR - 1) / TR + k) * ((wmax + b + al + TC - 1) / TC + 1);
+  const int64_t p2 = ((b + al * k + TR - 1) / TR + k) * ((b + al + TC - 1) / TC + 1);
   if (p1 + p2 >= (int64_t(1) << 31)) {
     c->err = "window pass would need too many tiles";
     return bail(KKM_EINVAL);
@@ -375,9 +381,9 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
   ALLOC(s.counts, k); ALLOC(s.alpha, k); ALLOC(s.coff, k + 1); ALLOC(s.perm, s.bpad); ALLOC(s.mvdst, s.bpad);
   ALLOC(s.cmc, k); ALLOC(s.ncum, k); ALLOC(c->d_obj2, 2); ALLOC(s.plan, k); ALLOC(s.comp_off, k); ALLOC(s.comp_total, 1);
   ALLOC(s.tiles, s.max_tiles); ALLOC(s.ntiles, 1); ALLOC(s.tile_first, k); ALLOC(s.tile_cnt, k);
-  ALLOC(s.part, (size_t)s.max_tiles * s.bpad);
+  ALLOC(s.part, (size_t)s.max_tiles * s.ppt * s.bpad);
   ALLOC(s.wpairs, s.max_pairs); ALLOC(s.nwpairs, 1); ALLOC(s.wpair_first, k); ALLOC(s.wpair_cnt, k);
-  s.wslots = c->use_tc ? 1 : 4;
+  s.wslots = 4;
   ALLOC(s.wpart, (size_t)s.max_pairs * s.wslots * 4);
   ALLOC(s.iter, 1); ALLOC(s.fin_pending, 1); ALLOC(s.status, 1); ALLOC(s.stats, 3); ALLOC(s.obj, 1);
   {

@@ -33,6 +33,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 #include <atomic>
+#include <type_traits>
 
 namespace kkm {
 
@@ -49,6 +50,7 @@ constexpr int ST_CAPACITY = 4;
 constexpr int ST_TIMEOUT = 8;
 
 constexpr int REGION_PAD = 256;   // unused rows at the end of each support region (the widest tile)
+constexpr int WPASS_TNV = 128;    // tcgen05 window pass: support rows per column tile
 
 // Column tile of the distance pass: support rows [row0, row0 + ncols) of center j.
 struct Tile {
@@ -92,9 +94,11 @@ struct Dev {
   int32_t num_sms;
   uint64_t seed;
   int32_t tn;        // support rows per distance tile
+  int32_t ppt;       // partials per distance tile in part[] (2 for 256-row tcgen05 tiles: one per column half)
   int32_t pre_b;     // distance pass: stage the support operand, its metadata and the tile list before
                      // the grid-dependency wait (launch_dist_tc sets it per launch, only after the gather)
-  int32_t pair_rows, pair_cols; // window-pass tile: row and column counts (64x64 SIMT, 128x64 tcgen05)
+  int32_t pair_rows, pair_cols; // window-pass tile: row and column counts (64x64 SIMT, 128x128 tcgen05)
+  int32_t walign;    // window-pass tiles start at range starts rounded down to this many rows (1 SIMT, 4 tcgen05)
   int32_t bpad;      // rows of the batch buffers (>= b, multiple of 128)
   int32_t max_tiles, max_pairs;
   const float* X;
@@ -139,7 +143,7 @@ struct Dev {
   int32_t* ntiles;   // [1]
   int32_t* tile_first; // [k]
   int32_t* tile_cnt;   // [k]
-  float* part;       // [max_tiles * bpad] per-tile weighted kernel sums
+  float* part;       // [max_tiles * ppt * bpad] per-tile weighted kernel sums (ppt partials per tile)
   WPair* wpairs;     // [max_pairs]
   int32_t* nwpairs;  // [1]
   int32_t* wpair_first; // [k]
@@ -147,7 +151,7 @@ struct Dev {
   double* ncum;      // [k] points assigned to each center so far (N^j of the sklearn rate)
   const double* rtab; // [2 (b + 1)]: 1/n at [n] and sqrt(n / b) at [b + 1 + n], n = 0..b (host-computed)
   double* wpart;     // [max_pairs][wslots][4 sums]: A, Bdd, E, M partials per tile
-  int32_t wslots;    // partial slots per window-pass tile (4 SIMT, 1 tcgen05)
+  int32_t wslots;    // partial slots per window-pass tile (4: SIMT slot 0 only, tcgen05 one per TMEM lane quadrant)
   int64_t* iter;     // [1] next iteration number
   int32_t* status;   // [1] sticky device status bits
   int32_t* fin_pending;   // [1] 1 while a step's weight update (k_finalize) is still to run

@@ -280,9 +280,9 @@ __global__ void __launch_bounds__(32 * AM_WARPS) k_argmin(Dev s, int rows, const
   __shared__ int r_j[AM_WARPS][32];
   __shared__ int c_first[1024], c_cnt[1024];
   __shared__ float c_norm[1024];
-  for (int j = threadIdx.x; j < s.k; j += 32 * AM_WARPS) {
-    c_first[j] = s.tile_first[j];
-    c_cnt[j] = s.tile_cnt[j];
+  for (int j = threadIdx.x; j < s.k; j += 32 * AM_WARPS) {   // a tile holds ppt consecutive partials
+    c_first[j] = s.tile_first[j] * s.ppt;
+    c_cnt[j] = s.tile_cnt[j] * s.ppt;
     c_norm[j] = s.cnorm32[j];
   }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -559,9 +559,14 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out, int 
       s.blk_first[j] = first;
       s.blk_num[j] = nb;
       s.wsum[j] = total;
+      // window-pass tiles: the dropped rows D against the old window and the new
+      // block, and the new block against itself; tiles start at the range starts
+      // rounded down to walign rows
       const int TR = s.pair_rows, TC = s.pair_cols;
+      const int hoff = P.head_c & (s.walign - 1), toff = P.tail_c & (s.walign - 1);
       const int nD = P.ndrop, nL = P.tail_new - P.head_c;
-      npairs = ((nD + TR - 1) / TR) * ((nL + TC - 1) / TC) + ((n + TR - 1) / TR) * ((n + TC - 1) / TC);
+      const int rD = nD > 0 ? (nD + hoff + TR - 1) / TR : 0;
+      npairs = rD * ((nL + hoff + TC - 1) / TC) + ((n + toff + TR - 1) / TR) * ((n + toff + TC - 1) / TC);
     }
     s.plan[j] = P;
     splan[j] = P;
@@ -608,9 +613,10 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out, int 
     if (i >= tot[j] || base[j] + tot[j] > s.max_pairs) continue;
     const Plan P = splan[j];
     const int TR = s.pair_rows, TC = s.pair_cols;
+    const int hoff = P.head_c & (s.walign - 1), toff = P.tail_c & (s.walign - 1);
     const int nD = P.ndrop, nL = P.tail_new - P.head_c, n = P.cnt;
-    const int cL = (nL + TC - 1) / TC, cB = (n + TC - 1) / TC;
-    const int n0 = ((nD + TR - 1) / TR) * cL;
+    const int cL = (nL + hoff + TC - 1) / TC, cB = (n + toff + TC - 1) / TC;
+    const int n0 = (nD > 0 ? (nD + hoff + TR - 1) / TR : 0) * cL;
     const int f = i - n0;
     s.wpairs[e] = i < n0 ? WPair{j, 0, i / cL, i % cL} : WPair{j, 1, f / cB, f % cB};
   }
