@@ -120,8 +120,7 @@ typedef struct kkm_config {
   int32_t precision; /* kkm_precision */
   int32_t max_iters; /* untruncated runs only: iterations the support store must hold (>= 1) */
   uint64_t seed;     /* SplitMix64 seed of the built-in batch sampler */
-  int32_t dist_tile; /* tensor-core forms: support rows per distance-pass tile, 64, 128 or 256; 0 = 256
-                        (the table form uses at most 128) */
+  int32_t dist_tile; /* tensor-core forms: support rows per distance-pass tile, 64, 128 or 256; 0 = 256 */
   int32_t algo;      /* kkm_algo */
 } kkm_config;
 

@@ -332,8 +332,7 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
     c->use_tc = true;
   }
   s.tn = c->use_tc ? (cfg->dist_tile == 0 ? (tab ? 64 : 256) : cfg->dist_tile) : 64;
-  if (tab && s.tn == 256) s.tn = 128;   // the table form's layout kernels take one partial per tile
-  s.ppt = (c->use_tc && s.tn == 256) ? 2 : 1;
+  s.ppt = c->use_tc ? kkm::tc_parts_per_tile(s.tn) : 1;
   s.pair_rows = c->use_tc ? 128 : 64;
   s.pair_cols = c->use_tc ? kkm::WPASS_TNV : 64;
   s.walign = c->use_tc ? 4 : 1;
@@ -383,7 +382,8 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
   ALLOC(s.tiles, s.max_tiles); ALLOC(s.ntiles, 1); ALLOC(s.tile_first, k); ALLOC(s.tile_cnt, k);
   ALLOC(s.part, (size_t)s.max_tiles * s.ppt * s.bpad);
   ALLOC(s.wpairs, s.max_pairs); ALLOC(s.nwpairs, 1); ALLOC(s.wpair_first, k); ALLOC(s.wpair_cnt, k);
-  s.wslots = 4;
+  // window-pass partial slots per item: one per TMEM lane quadrant and per group of a team
+  s.wslots = c->use_tc ? 4 * kkm::tc_parts_per_tile(kkm::WPASS_TNV) : 4;
   ALLOC(s.wpart, (size_t)s.max_pairs * s.wslots * 4);
   ALLOC(s.iter, 1); ALLOC(s.fin_pending, 1); ALLOC(s.status, 1); ALLOC(s.stats, 3); ALLOC(s.obj, 1);
   {
@@ -445,7 +445,7 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
     ALLOC(g.xbn, npad);
     ALLOC(g.xbi, npad);
     g.bpad = (int32_t)npad;
-    ALLOC(g.part, (size_t)s.max_tiles * npad);
+    ALLOC(g.part, (size_t)s.max_tiles * s.ppt * npad);
     ALLOC(c->tb.T, (size_t)k * n);
     ALLOC(c->tb.bs_off, k + 1);
     c->tb.part = g.part;

@@ -74,19 +74,22 @@ constexpr int A_RES_MAX = 96 * 1024;            // largest batch tile kept resid
 //               holds one slice of the B tile. A is reloaded only when the
 //               row tile changes.
 //   streaming:  (A too large to keep) a stage holds one slice of A and B.
-constexpr int NEPI = 16;                         // epilogue warps (2 .. 17)
+constexpr int NEPI = 16;                         // epilogue warps (2 .. 17): four on each scheduler
 constexpr int NGRP = 4;                          // epilogue groups, one warp per TMEM lane quadrant each
 constexpr int MWARP = 2 + NEPI;                  // the metadata warp
 constexpr int NTHREADS = 32 * (MWARP + 1);      // TMA warp, MMA warp, epilogue, metadata warp
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;   // 2 s per wait
 constexpr float ROW_EXP_FLOOR = -100.0f;        // Gaussian: rc at or above it keeps 2^t finite
+#ifndef DIST_NB
+#define DIST_NB 2                                // distance-pass epilogue: 8-column blocks per TMEM chunk
+#endif
 
 // TMEM accumulators (TNV columns each, at most 512 columns), teams of
 // groups (one per accumulator), groups per team (= partials per tile), and
 // metadata slots
 template <int TNV> struct Geo {
   static constexpr int NACC = 512 / TNV < 4 ? 512 / TNV : 4;
-  static constexpr int NTEAM = NACC;
+  static constexpr int NTEAM = NACC < NGRP ? NACC : NGRP;
   static constexpr int GPT = NGRP / NTEAM;
   static constexpr int MS = TNV == 256 ? 4 : 8;
   static constexpr uint32_t TMEM_COLS = (uint32_t)(NACC * TNV);
@@ -497,7 +500,9 @@ __device__ __forceinline__ void dist_epilogue(const Dev& s, Shared<TNV>& sh, uin
   constexpr int QPP = NGRP / GPT;                // all-mode quarters per partial
   const int ph = all ? g / QPP : h;             // this group's partial
   const bool lead = !all || g % QPP == 0;        // writes the partial and frees the slot and accumulator
-  bool dead = false;                            // a wait ran out: skip the work, keep the barriers
+  // part[] must hold GPT partials per tile, as the host sized it (Dev::ppt)
+  bool dead = s.ppt != GPT;                     // a wait ran out (or bad layout): skip the work, keep the barriers
+  if (dead && lane == 0 && warp == 2) atomicOr(s.status, ST_CAPACITY);
   uint32_t local = 0;
   for (int item = rg.lo; item < rg.hi; ++item, ++local) {
     if (!all && (int)(local % NTEAM) != team) continue;
@@ -527,19 +532,10 @@ __device__ __forceinline__ void dist_epilogue(const Dev& s, Shared<TNV>& sh, uin
       bool fast = false;
       if constexpr (KIND == K_GAUSS)
         fast = __all_sync(0xffffffffu, fminf(fminf(rc[0], rc[1]), fminf(rc[2], rc[3])) >= ROW_EXP_FLOOR);
-      // 16-column chunks, two in flight: the next chunk's TMEM loads are issued
-      // before the current chunk's arithmetic and waited for after it
-      constexpr int NB = 2, CW = 16;
-      const int nch = ncols / CW;
-      auto math = [&](const float (&w0)[4 * NB], const float (&w1)[4 * NB], int ch) {
-        const int c = cbeg + ch * CW + c2;
-        if constexpr (KIND == K_GAUSS) {
-          if (fast) gauss_chunk<NB, true>(w0, w1, m.col[0], m.col[1], c, negc, C2, rc, acc);
-          else gauss_chunk<NB, false>(w0, w1, m.col[0], m.col[1], c, negc, C2, rc, acc);
-        } else {
-          generic_chunk<KIND, NB>(w0, w1, m.col[0], m.col[1], m.col[2], c, negc, coef0, degree, rc, xi, acc);
-        }
-      };
+      // chunks of CW columns, two in flight: the next chunk's TMEM loads are
+      // issued before the current chunk's arithmetic and waited for after it
+      // (tcgen05.wait::ld waits for every load in flight, so a chunk's
+      // arithmetic is what hides the next chunk's load latency)
       auto release = [&]() {                    // the accumulator is free again
         if (!all) {
           tc_fence_before();
@@ -547,21 +543,37 @@ __device__ __forceinline__ void dist_epilogue(const Dev& s, Shared<TNV>& sh, uin
           if (lane == 0) mbar_arrive(&sh.tempty[buf]);
         }
       };
-      float a0[4 * NB], a1[4 * NB], b0[4 * NB], b1[4 * NB];
-      chunk_issue<NB>(tq, a0, a1);
-      tmem_wait_ld();
-      for (int ch = 0; ch < nch; ch += 2) {
-        if (ch + 1 < nch) chunk_issue<NB>(tq + (ch + 1) * CW, b0, b1);
-        else release();
-        math(a0, a1, ch);
-        if (ch + 1 < nch) {
-          tmem_wait_ld();
-          if (ch + 2 < nch) chunk_issue<NB>(tq + (ch + 2) * CW, a0, a1);
+      auto run = [&](auto nbt) {
+        constexpr int NB = decltype(nbt)::value, CW = 8 * NB;
+        const int nch = ncols / CW;
+        auto math = [&](const float (&w0)[4 * NB], const float (&w1)[4 * NB], int ch) {
+          const int c = cbeg + ch * CW + c2;
+          if constexpr (KIND == K_GAUSS) {
+            if (fast) gauss_chunk<NB, true>(w0, w1, m.col[0], m.col[1], c, negc, C2, rc, acc);
+            else gauss_chunk<NB, false>(w0, w1, m.col[0], m.col[1], c, negc, C2, rc, acc);
+          } else {
+            generic_chunk<KIND, NB>(w0, w1, m.col[0], m.col[1], m.col[2], c, negc, coef0, degree, rc, xi, acc);
+          }
+        };
+        float a0[4 * NB], a1[4 * NB], b0[4 * NB], b1[4 * NB];
+        chunk_issue<NB>(tq, a0, a1);
+        tmem_wait_ld();
+        for (int ch = 0; ch < nch; ch += 2) {
+          if (ch + 1 < nch) chunk_issue<NB>(tq + (ch + 1) * CW, b0, b1);
           else release();
-          math(b0, b1, ch + 1);
-          if (ch + 2 < nch) tmem_wait_ld();
+          math(a0, a1, ch);
+          if (ch + 1 < nch) {
+            tmem_wait_ld();
+            if (ch + 2 < nch) chunk_issue<NB>(tq + (ch + 2) * CW, a0, a1);
+            else release();
+            math(b0, b1, ch + 1);
+            if (ch + 2 < nch) tmem_wait_ld();
+          }
         }
-      }
+      };
+      if (ncols % (8 * DIST_NB) == 0) run(std::integral_constant<int, DIST_NB>{});
+      else if (ncols % 32 == 0) run(std::integral_constant<int, 4>{});
+      else run(std::integral_constant<int, 2>{});
       float fr[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) fr[u] = quad_sum(acc[u].x + acc[u].y);
@@ -620,7 +632,9 @@ __device__ __forceinline__ void pair_epilogue(const Dev& s, Shared<TNV>& sh, uin
   constexpr int QPP = NGRP / GPT;
   const int ph = all ? g / QPP : h;
   const bool lead = !all || g % QPP == 0;
-  bool dead = false;
+  // wpart[] must hold 4 GPT slots per item, as the host sized it (Dev::wslots)
+  bool dead = s.wslots != 4 * GPT;
+  if (dead && lane == 0 && warp == 2) atomicOr(s.status, ST_CAPACITY);
   uint32_t local = 0;
   for (int item = rg.lo; item < rg.hi; ++item, ++local) {
     if (!all && (int)(local % NTEAM) != team) continue;
@@ -1232,6 +1246,10 @@ cudaError_t tc_prepare(Dev& s, void* maps_out) {
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   }
   return cudaSuccess;
+}
+
+int tc_parts_per_tile(int tn) {
+  return tn == 256 ? Geo<256>::GPT : tn == 64 ? Geo<64>::GPT : Geo<128>::GPT;
 }
 
 cudaError_t launch_dist_tc(const Dev& s, const void* maps, int rows, cudaStream_t st, bool stage_early) {

@@ -151,7 +151,8 @@ struct Dev {
   double* ncum;      // [k] points assigned to each center so far (N^j of the sklearn rate)
   const double* rtab; // [2 (b + 1)]: 1/n at [n] and sqrt(n / b) at [b + 1 + n], n = 0..b (host-computed)
   double* wpart;     // [max_pairs][wslots][4 sums]: A, Bdd, E, M partials per tile
-  int32_t wslots;    // partial slots per window-pass tile (4: SIMT slot 0 only, tcgen05 one per TMEM lane quadrant)
+  int32_t wslots;    // partial slots per window-pass tile (SIMT: 4, slot 0 used; tcgen05: one per TMEM lane
+                     // quadrant and team group)
   int64_t* iter;     // [1] next iteration number
   int32_t* status;   // [1] sticky device status bits
   int32_t* fin_pending;   // [1] 1 while a step's weight update (k_finalize) is still to run
@@ -312,6 +313,8 @@ cudaError_t launch_mind_sum(const Dev& s, int rows, double scale, double* out, c
 // tensor-core passes (BF16, split-BF16 and TF32 forms)
 // maps: 512 bytes, 64-byte aligned, holding the four CUtensorMap of the passes
 cudaError_t tc_prepare(Dev& s, void* maps);
+// partials the distance pass writes per tile of tn support rows (Dev::ppt)
+int tc_parts_per_tile(int tn);
 // stage_early: the kernel just ahead on `st` (the batch gather, or this pass
 // itself) writes none of the support tiles, their metadata or the tile list,
 // so the pass may stage them before its grid-dependency wait.

@@ -1083,7 +1083,7 @@ __global__ void __launch_bounds__(256) k_tab_center(Dev s, TabBuf q) {
     if (tid == 0) s.alpha[j] = 0.0;
     return;
   }
-  const int t0 = s.tile_first[j], nt = s.tile_cnt[j];
+  const int t0 = s.tile_first[j] * s.ppt, nt = s.tile_cnt[j] * s.ppt;   // ppt partials per tile
   float acc = 0.0f;
   for (int p = s.coff[j] + tid; p < s.coff[j] + n; p += 256) {
     const int64_t i = s.xbi[s.perm[p]];
@@ -1121,7 +1121,7 @@ __global__ void __launch_bounds__(256) k_tab_update(Dev s, TabBuf q, int init) {
   if (!init && s.counts[j] == 0) return;
   const double a = init ? 1.0 : s.alpha[j];
   const float af = (float)a, kf = (float)(1.0 - a);
-  const int t0 = s.tile_first[j], nt = s.tile_cnt[j];
+  const int t0 = s.tile_first[j] * s.ppt, nt = s.tile_cnt[j] * s.ppt;   // ppt partials per tile
   float* T = q.T + (int64_t)j * s.n;
 #pragma unroll 4
   for (int64_t x = (int64_t)blockIdx.x * 1024 + threadIdx.x; x < min((int64_t)(blockIdx.x + 1) * 1024, s.n);
