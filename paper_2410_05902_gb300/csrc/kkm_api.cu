@@ -382,8 +382,8 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
   ALLOC(s.tiles, s.max_tiles); ALLOC(s.ntiles, 1); ALLOC(s.tile_first, k); ALLOC(s.tile_cnt, k);
   ALLOC(s.part, (size_t)s.max_tiles * s.ppt * s.bpad);
   ALLOC(s.wpairs, s.max_pairs); ALLOC(s.nwpairs, 1); ALLOC(s.wpair_first, k); ALLOC(s.wpair_cnt, k);
-  // window-pass partial slots per item: one per TMEM lane quadrant and per group of a team
-  s.wslots = c->use_tc ? 4 * kkm::tc_parts_per_tile(kkm::WPASS_TNV) : 4;
+  // window-pass partial slots (of four sums) per item: one per group of a team
+  s.wslots = c->use_tc ? kkm::tc_parts_per_tile(kkm::WPASS_TNV) : 4;
   ALLOC(s.wpart, (size_t)s.max_pairs * s.wslots * 4);
   ALLOC(s.iter, 1); ALLOC(s.fin_pending, 1); ALLOC(s.status, 1); ALLOC(s.stats, 3); ALLOC(s.obj, 1);
   {

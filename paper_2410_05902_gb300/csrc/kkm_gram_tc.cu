@@ -181,6 +181,7 @@ template <int TNV> struct Shared {
   union {
     float red[2][NGRP][4][32];     // distance pass, all groups on one item: row sums (item parity, group, quadrant, row)
     double wred[2][NGRP][4][4];    // window pass, the same: the four sums
+    double wq[NGRP][2][4][4];      // window pass, a group per item: (group, buffer, quadrant, sum)
   } x;
 };
 
@@ -632,8 +633,9 @@ __device__ __forceinline__ void pair_epilogue(const Dev& s, Shared<TNV>& sh, uin
   constexpr int QPP = NGRP / GPT;
   const int ph = all ? g / QPP : h;
   const bool lead = !all || g % QPP == 0;
-  // wpart[] must hold 4 GPT slots per item, as the host sized it (Dev::wslots)
-  bool dead = s.wslots != 4 * GPT;
+  // wpart[] must hold GPT slots of four sums per item, as the host sized it (Dev::wslots)
+  bool dead = s.wslots != GPT;
+  uint32_t gi = 0;                               // items this group has taken (shared-memory buffer parity)
   if (dead && lane == 0 && warp == 2) atomicOr(s.status, ST_CAPACITY);
   uint32_t local = 0;
   for (int item = rg.lo; item < rg.hi; ++item, ++local) {
@@ -730,18 +732,28 @@ __device__ __forceinline__ void pair_epilogue(const Dev& s, Shared<TNV>& sh, uin
       tB = warp_sum64(wr * (double)pick4(fb, us));
       tE = warp_sum64(wr * (double)pick4(fe, us));
     }
-    double* out = s.wpart + (((int64_t)item * GPT + ph) * 4 + q) * 4;
+    // The item's four sums (A, Bdd, E for kind 0; M for kind 1) over its 128
+    // rows: the quadrant warps' FP64 sums meet in shared memory and one warp
+    // adds them in quadrant order (group by group in the all-groups mode).
+    double* out = s.wpart + ((int64_t)item * GPT + ph) * 4;
+    const bool first = ((warp - 2) & 3) == 0;   // the group's first warp
     if (!all) {
-      if (!dead) {
-        __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(&sh.mempty[ms]);
-          out[0] = kind == 0 ? tA : 0.0;
-          out[1] = kind == 0 ? tB : 0.0;
-          out[2] = kind == 0 ? tE : 0.0;
-          out[3] = kind == 0 ? 0.0 : tE;
-        }
+      double (*wq)[4] = sh.x.wq[g][gi & 1u];
+      if (lane == 0) {
+        wq[q][0] = tA;
+        wq[q][1] = tB;
+        wq[q][2] = tE;
       }
+      __syncwarp();
+      if (lane == 0 && !dead) mbar_arrive(&sh.mempty[ms]);
+      asm volatile("bar.sync %0, 128;" ::"r"(2 + g) : "memory");   // every warp of the group, dead or not
+      if (first && !dead && lane < 4) {
+        const int src = lane == 3 ? 2 : lane;   // M is the E sum of a kind-1 item
+        const bool keep = (lane < 3) == (kind == 0);
+        const double v = ((wq[0][src] + wq[1][src]) + wq[2][src]) + wq[3][src];
+        out[lane] = keep ? v : 0.0;
+      }
+      ++gi;
     } else {
       double (*wr)[4][4] = sh.x.wred[local & 1u];
       if (lane == 0) {
@@ -753,12 +765,13 @@ __device__ __forceinline__ void pair_epilogue(const Dev& s, Shared<TNV>& sh, uin
       tc_fence_before();
       asm volatile("bar.sync 1, %0;" ::"n"(32 * NEPI) : "memory");
       if (lead) {
-        if (!dead && lane < 4) {
-          const int k0 = (int)wr[g][q][3];
-          const int src = lane == 3 ? 2 : lane;   // sums A, Bdd, E; M is the E sum of a kind-1 item
+        if (first && !dead && lane < 4) {
+          const int k0 = (int)wr[g][0][3];
+          const int src = lane == 3 ? 2 : lane;
           const bool keep = (lane < 3) == (k0 == 0);
-          double v = wr[g][q][src];
-          for (int o = 1; o < QPP; ++o) v += wr[g + o][q][src];
+          double v = 0.0;
+          for (int o = 0; o < QPP; ++o)
+            v += ((wr[g + o][0][src] + wr[g + o][1][src]) + wr[g + o][2][src]) + wr[g + o][3][src];
           out[lane] = keep ? v : 0.0;
         }
         __syncwarp();

@@ -151,8 +151,7 @@ struct Dev {
   double* ncum;      // [k] points assigned to each center so far (N^j of the sklearn rate)
   const double* rtab; // [2 (b + 1)]: 1/n at [n] and sqrt(n / b) at [b + 1 + n], n = 0..b (host-computed)
   double* wpart;     // [max_pairs][wslots][4 sums]: A, Bdd, E, M partials per tile
-  int32_t wslots;    // partial slots per window-pass tile (SIMT: 4, slot 0 used; tcgen05: one per TMEM lane
-                     // quadrant and team group)
+  int32_t wslots;    // partial slots per window-pass tile (SIMT: 4, slot 0 used; tcgen05: one per team group)
   int64_t* iter;     // [1] next iteration number
   int32_t* status;   // [1] sticky device status bits
   int32_t* fin_pending;   // [1] 1 while a step's weight update (k_finalize) is still to run

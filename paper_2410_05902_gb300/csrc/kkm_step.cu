@@ -378,7 +378,8 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out, int 
   float* sinner = (float*)(coff + k);       // [b]   <phi(x), C_a> at the used assignment
   int16_t* sassign = (int16_t*)(sinner + b);// [b]   assignments (k <= 1024)
   int16_t* sperm = sassign + b;             // [b]   batch rows sorted by center (b <= 8192)
-  uint16_t* wtab = (uint16_t*)(sperm + b);  // [32][k] per-warp counts / offsets of a chunk
+  uint16_t* wtab = (uint16_t*)(sperm + b);  // [32][k] per-warp counts, then their exclusive prefixes
+  uint16_t* srank = wtab + 32 * k;          // [b]   rank of a row among its warp's rows of its center
   __shared__ int s_rows;                    // support rows read by this step's distance pass
   if (tid == 0) s_rows = 0;
   // per-center window state, loaded up front together with the assignments
@@ -408,10 +409,43 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out, int 
     macc += s.mind[x];
   }
   const int tiles_used = *s.ntiles;         // tiles of this step's distance pass
-  for (int j = tid; j < k; j += 1024) { cnt[j] = 0; base[j] = 0; }
   for (int e = tid; e < 32 * k; e += 1024) wtab[e] = 0;
   __syncthreads();
-  for (int x = tid; x < b; x += 1024) atomicAdd(&cnt[sassign[x]], 1);
+  // Stable counting sort of the batch by center in one pass. Warp w ranks the
+  // contiguous rows [w seg, (w+1) seg), seg = ceil(b / 32), 32 at a time:
+  // match.any gives each row its rank among the step's rows of the same
+  // center, and wtab[w][j] (the rows of center j this warp has seen so far)
+  // is added to it. No block barrier is needed until every warp is done.
+  const int seg = (b + 31) / 32;
+  {
+    const int r0 = warp * seg, r1 = min(b, r0 + seg);
+    uint16_t* wc = wtab + warp * k;
+    for (int x0 = r0; x0 < r1; x0 += 32) {
+      const int x = x0 + lane;
+      const int j = x < r1 ? (int)sassign[x] : -1;
+      const unsigned peers = __match_any_sync(0xffffffffu, j);
+      const int rank = __popc(peers & ((1u << lane) - 1u));
+      const int before = j >= 0 ? (int)wc[j] : 0;
+      __syncwarp();
+      if (j >= 0 && rank == 0) wc[j] = (uint16_t)(before + __popc(peers));
+      if (x < r1) srank[x] = (uint16_t)(before + rank);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // per center: the exclusive prefix of the 32 warps' counts (a warp per
+  // center, a lane per warp) and the center's count
+  for (int j = warp; j < k; j += 32) {
+    const int v = wtab[lane * k + j];
+    int xs = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, xs, o);
+      if (lane >= o) xs += y;
+    }
+    wtab[lane * k + j] = (uint16_t)(xs - v);
+    if (lane == 31) cnt[j] = xs;
+  }
   __syncthreads();
   // exclusive offsets over centers (k <= 1024: one center per thread)
   const int my = tid < k ? cnt[tid] : 0;
@@ -420,53 +454,11 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out, int 
   if (tid < k) { coff[tid] = off; s.coff[tid] = off; s.counts[tid] = my; }
   if (tid == 0) s.coff[k] = total_rows;
   __syncthreads();
-  // stable ranks in chunks of 1024 rows. wtab[w][j] holds warp w's count (then
-  // its exclusive prefix) for center j, tagged with the chunk (bits 11-14) so
-  // entries of earlier chunks read as 0 and the table is cleared only once.
-  // The running per-center base alternates between base and tot by chunk.
-  for (int c0 = 0, ci = 0; c0 < b; c0 += 1024, ++ci) {
-    const uint16_t tag = (uint16_t)((ci + 1) << 11);
-    int32_t* bcur = (ci & 1) ? tot : base;
-    int32_t* bnext = (ci & 1) ? base : tot;
-    const int x = c0 + tid;
-    const int j = x < b ? (int)sassign[x] : -1;
-    const unsigned peers = __match_any_sync(0xffffffffu, j);
-    const int rank = __popc(peers & ((1u << lane) - 1u));
-    if (j >= 0 && rank == 0) wtab[warp * k + j] = (uint16_t)(tag | __popc(peers));
-    __syncthreads();
-    // exclusive prefix of each center's per-warp counts over the 32 warps. With
-    // few centers a warp scans one center (one or two rounds); with many, a
-    // thread per center walks its column (consecutive centers, no bank conflicts)
-    if (k <= 64) {
-      for (int jj = warp; jj < k; jj += 32) {
-        const uint16_t e = wtab[lane * k + jj];
-        const int v = (e & 0x7800) == tag ? (int)(e & 0x7ff) : 0;
-        int xs = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(0xffffffffu, xs, o);
-          if (lane >= o) xs += y;
-        }
-        wtab[lane * k + jj] = (uint16_t)(tag | (xs - v));
-        if (lane == 31) bnext[jj] = bcur[jj] + xs;
-      }
-    } else {
-      for (int jj = tid; jj < k; jj += 1024) {
-        int run = 0;
-#pragma unroll 8
-        for (int w2 = 0; w2 < 32; ++w2) {
-          const uint16_t e = wtab[w2 * k + jj];
-          const int v = (e & 0x7800) == tag ? (int)(e & 0x7ff) : 0;
-          wtab[w2 * k + jj] = (uint16_t)(tag | run);
-          run += v;
-        }
-        bnext[jj] = bcur[jj] + run;
-      }
-    }
-    __syncthreads();
-    if (j >= 0) sperm[coff[j] + bcur[j] + (wtab[warp * k + j] & 0x7ff) + rank] = (int16_t)x;
-    __syncthreads();
+  for (int x = tid; x < b; x += 1024) {
+    const int j = sassign[x];
+    sperm[coff[j] + wtab[(x / seg) * k + j] + srank[x]] = (int16_t)x;
   }
+  __syncthreads();
   for (int r = tid; r < b; r += 1024) s.perm[r] = sperm[r];
   // per center, the 32 lane partials (FP32) of sum_{x in B_j} <phi(x), C_j>;
   // k_finalize adds them in FP64
@@ -780,7 +772,7 @@ __global__ void __launch_bounds__(256) k_finalize(Dev s, int if_pending) {
   // with a stride of 256 every thread stays on sum tid & 3
   const double* wp = s.wpart + (int64_t)p0 * per;
   double acc = 0.0;
-#pragma unroll 4
+#pragma unroll 8
   for (int e = tid; e < np * per; e += 256) acc += wp[e];
 #pragma unroll
   for (int o = 4; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -1227,7 +1219,7 @@ cudaError_t launch_argmin(const Dev& s, int rows, const int32_t* forced, int32_t
   return cudaGetLastError();
 }
 
-int sort_plan_smem(int k, int b) { return k * (int)sizeof(Plan) + 4 * k * 4 + b * (4 + 2 + 2) + 32 * k * 2; }
+int sort_plan_smem(int k, int b) { return k * (int)sizeof(Plan) + 4 * k * 4 + b * (4 + 2 + 2 + 2) + 32 * k * 2; }
 
 cudaError_t launch_sort_plan(const Dev& s, double* obj_out, cudaStream_t st, bool set_pending) {
   const int smem = sort_plan_smem(s.k, s.b);
