@@ -384,8 +384,11 @@ kkm_status kkm_launches(kkm_ctx* ctx, int64_t* launches, int32_t reset);
  *   Y        : device, S x d FP32 support rows, leading dimension ldy >= d
  *   w        : device, S FP32 weights
  *   seg_off  : device, k + 1 int32 offsets. Center j owns the rows
- *              [seg_off[j], seg_off[j+1]) of Y. The offsets must be
- *              non-decreasing from 0 to S; values outside [0, S] are clamped.
+ *              [seg_off[j], seg_off[j+1]) of Y; an empty range is a center
+ *              with no support row (its inner products are 0). The offsets
+ *              must be non-decreasing within [0, S]. Offsets that are not are
+ *              found on the device: every distance of the call is then NaN
+ *              and every assignment -1.
  *   cnorm    : device, k doubles, ||C_j||^2
  *   kernel   : host, as in kkm_init
  *   dist_out : device, m x k FP32 row-major, or NULL
@@ -397,15 +400,22 @@ kkm_status kkm_launches(kkm_ctx* ctx, int64_t* launches, int32_t reset);
  * KKM_NOALLOC_MAX_ROWS_PER_PASS.
  *
  * Memory: the only scratch is one fixed array of KKM_NOALLOC_SCRATCH_BYTES
- * inside the library. It is device memory that every GPU loading the library
- * holds until the process exits. The call never allocates or frees, neither
- * directly nor through a library. The first call on each device, with that
- * device current, looks up the array's address (cudaGetSymbolAddress). Make
- * that first call before any stream capture. Every call shares the array:
+ * inside the library. CUDA loads modules lazily by default, so the array and
+ * the call's kernels come onto a device at the first call made with that
+ * device current: that call looks up the array's address
+ * (cudaGetSymbolAddress) and launches the kernels, and so reserves the
+ * scratch and the code. A call with m = 0 does only that (launching each
+ * kernel once on empty work) and reads no other argument. Make the first
+ * call on each device, for example with m = 0, before reserving the rest of
+ * the device memory and before any stream capture. After it the call never
+ * allocates or frees, neither directly nor through a library, and the device
+ * keeps the array until the process exits. Every call shares the array:
  * calls whose work overlaps on the GPU (two streams with no ordering between
  * them) race on it, while calls queued one after another on one stream are
- * safe. The call only queues work on `stream`. Errors are reported through
- * kkm_noalloc_last_error(), a per-thread message. */
+ * safe. The call only queues work on `stream`; a failed launch is reported
+ * from that launch's own status, not from an error left by earlier work.
+ * Errors are reported through kkm_noalloc_last_error(), a per-thread
+ * message. */
 #define KKM_NOALLOC_MAX_ROWS_PER_PASS 1024
 #define KKM_NOALLOC_MAX_TILES 1024
 #define KKM_NOALLOC_MAX_SUPPORT 65536

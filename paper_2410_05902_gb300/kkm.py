@@ -227,11 +227,14 @@ def kkm_launches(ctx, reset: bool = False) -> int:
 
 
 def kkm_distances_noalloc(Q: int, m: int, ldq: int, d: int, Y: int, S: int, ldy: int, w: int,
-                          seg_off: int, cnorm: int, k: int, kernel: kkm_kernel, dist_out: int | None,
+                          seg_off: int, cnorm: int, k: int, kernel: kkm_kernel | None, dist_out: int | None,
                           assign_out: int | None, stream: int | None) -> None:
-    """Distances and argmin against caller-held centers, with no allocation (see kkm.h)."""
+    """Distances and argmin against caller-held centers, with no allocation
+    (kkm.h). m = 0 only loads the call's scratch and kernels on the current
+    device; kernel may then be None."""
     lib = load()
-    st = lib.kkm_distances_noalloc(Q, m, ldq, d, Y, S, ldy, w, seg_off, cnorm, k, ctypes.byref(kernel),
+    kp = ctypes.byref(kernel) if kernel is not None else None
+    st = lib.kkm_distances_noalloc(Q, m, ldq, d, Y, S, ldy, w, seg_off, cnorm, k, kp,
                                    dist_out, assign_out, stream)
     if st != KKM_OK:
         raise KKMError(st, lib.kkm_noalloc_last_error().decode())
@@ -438,3 +441,4 @@ class KKM:
             self.close()
         except Exception:
             pass
+
