@@ -366,6 +366,67 @@ kkm_status kkm_timing_read(kkm_ctx* ctx, int64_t* launches, double* total_ms, in
  * the host at each launch) since kkm_init or the last reset. Host output. */
 kkm_status kkm_launches(kkm_ctx* ctx, int64_t* launches, int32_t reset);
 
+/* ------------------------------------------------------------------------
+ * Full-batch kernel k-means (kernel Lloyd) -- the baseline the paper
+ * compares its mini-batch algorithm with (Sec. 6; its O(n^2) cost per
+ * iteration is the motivation of Sec. 1).
+ *
+ * Every iteration assigns all n points to their nearest center and moves
+ * every center that got points to the mean of its points in feature space,
+ * C_j = (1/n_j) sum_{x in X_j} phi(x). This equals Algorithm 1 with the whole
+ * data set as the batch and learning rate 1; a center with no points keeps
+ * its value. The run keeps T[j][x] = <phi(x), C_j> (k x n FP32) and
+ * ||C_j||^2 = (1/n_j) sum_{x in X_j} T[j][x]; T comes from the n x n Gram
+ * pass of X against X sorted by center, in the chosen precision form.
+ * Distances and the argmin use Delta(x, C_j) = K(x,x) - 2 T[j][x] + ||C_j||^2
+ * in FP32 (ties go to the lowest j); f_X sums the minima in FP64.
+ * ------------------------------------------------------------------------ */
+typedef struct kkm_lloyd kkm_lloyd;
+
+/* kkm_lloyd_init -- a run on X and k initial points; assigns every point to
+ * its nearest initial point before it returns (f_X at the initial centers).
+ *   X         : device, n x d FP32, leading dimension ldx >= d. Read only
+ *               during this call (the run keeps its own operand copy).
+ *   k         : 1 <= k <= min(n, 1024)
+ *   kernel    : host, as in kkm_init
+ *   precision : kkm_precision; the BF16, split-BF16 and TF32 forms need a
+ *               compute capability 10.3 device (else KKM_ENOTSUP)
+ *   init_idx  : host, k indices into X (the initial centers phi(x_i))
+ *   chunk_rows: rows of X per Gram-pass launch, a multiple of 128, or 0 for
+ *               the largest chunk whose partial sums fit in 1 GiB
+ *   stream    : cudaStream_t the run queues its work on
+ * Device memory: about (2 n + k tn) ld operand elements, k n floats for T and
+ * the chunk's partial sums. Synchronises the stream before returning. */
+kkm_status kkm_lloyd_init(kkm_lloyd** out, const float* X, int64_t n, int32_t d, int64_t ldx, int32_t k,
+                          const kkm_kernel* kernel, int32_t precision, const int64_t* init_idx,
+                          int64_t chunk_rows, void* stream);
+/* kkm_lloyd_iterate -- queues `iters` iterations (center update from the
+ * current assignment, then the new assignment). Does not synchronise. */
+kkm_status kkm_lloyd_iterate(kkm_lloyd* run, int32_t iters);
+/* kkm_lloyd_read -- synchronises; host outputs (each may be NULL): f_X at the
+ * current centers, the number of points whose assignment the last
+ * assignment changed (all n after kkm_lloyd_init; 0 at Lloyd's fixed point),
+ * and the iterations run. Reports device-side errors (KKM_ETIMEOUT for a
+ * bounded wait in the Gram pass that gave up). */
+kkm_status kkm_lloyd_read(kkm_lloyd* run, double* obj, int64_t* changed, int64_t* iters_done);
+/* kkm_lloyd_assignments -- device outputs (each may be NULL): the n
+ * assignments at the current centers, and min_j Delta(x, C_j). Queued on the
+ * run's stream. */
+kkm_status kkm_lloyd_assignments(kkm_lloyd* run, int32_t* assign_out, float* mind_out);
+/* kkm_lloyd_distances -- device output: Delta(x, C_j), n x k FP32 row-major,
+ * the values the assignment compares. Queued on the run's stream. */
+kkm_status kkm_lloyd_distances(kkm_lloyd* run, float* dist_out);
+/* kkm_lloyd_center_norms -- host output: ||C_j||^2 (k doubles). Synchronises. */
+kkm_status kkm_lloyd_center_norms(kkm_lloyd* run, double* out);
+/* kkm_lloyd_info -- host outputs (each may be NULL): kernels launched so far
+ * (host count), Gram-pass chunks per iteration and rows per chunk. */
+kkm_status kkm_lloyd_info(const kkm_lloyd* run, int64_t* launches, int32_t* chunks, int64_t* chunk_rows);
+/* kkm_lloyd_destroy -- synchronises the stream and frees the run (NULL is a no-op). */
+kkm_status kkm_lloyd_destroy(kkm_lloyd* run);
+/* kkm_lloyd_last_error -- the message of the run's last failure, or, for
+ * NULL, of this thread's last failed kkm_lloyd_init. */
+const char* kkm_lloyd_last_error(const kkm_lloyd* run);
+
 /* kkm_distances_noalloc -- distances and nearest centers with no allocation.
  *
  * The paper has no counterpart to this call. It exists for callers that

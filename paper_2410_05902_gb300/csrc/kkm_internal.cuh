@@ -309,6 +309,39 @@ cudaError_t launch_tab_objective(const Dev& s, const TabBuf& q, const float* xn,
                                  cudaStream_t st);
 cudaError_t launch_mind_sum(const Dev& s, int rows, double scale, double* out, cudaStream_t st);  // scale * sum of mind
 
+// ------------------------------------------------ full-batch kernel Lloyd
+// The Gram view's Dev (xb*: every row of X in the operand form, y*: the
+// support buffer of X sorted by center) plus these buffers (kkm_lloyd.cu).
+constexpr int LLOYD_RANK_ROWS = 1024;   // rows per chunk of the counting sort's ranking
+struct LloydBuf {
+  float* T;               // [k][n] <phi(x), C_j>, center-major
+  int32_t* assign;        // [n] assignment at the current centers
+  float* mind;            // [n] min_j Delta(x, C_j) at the current centers
+  int32_t* rank;          // [n] rank of x among the rows of its center within its ranking chunk
+  int32_t* ccnt;          // [nrk][k] rows of center j in ranking chunk c (chunk-major)
+  int32_t* cbase;         // [nrk][k] position of chunk c's first row of center j within center j
+  int32_t* bs_off;        // [k + 1] first support-buffer row of each center (blocks of whole tiles)
+  double* blk;            // [nblk] objective partials of the assignment pass
+  int32_t* blk_changed;   // [nblk] changed-assignment partials
+  double* obj;            // [1] f_X at the current centers
+  int64_t* changed;       // [1] rows whose assignment the last assignment pass changed
+  int32_t nrk;            // ranking chunks, ceil(n / LLOYD_RANK_ROWS)
+  int32_t nblk;           // blocks of the assignment pass
+};
+// counting sort of X by assignment: ranks, then offsets, tiles and weights 1/n_j
+cudaError_t launch_lloyd_sort(const Dev& g, const LloydBuf& L, cudaStream_t st);
+// the center-sorted rows into the support buffer
+cudaError_t launch_lloyd_scatter(const Dev& g, const LloydBuf& L, cudaStream_t st);
+// T[j][row0 + r] from the Gram pass partials of one chunk of rows (gc: the chunk's view);
+// all: every center (initial centers), else only centers with rows
+cudaError_t launch_lloyd_reduce(const Dev& gc, const LloydBuf& L, int64_t row0, int rows, bool all, cudaStream_t st);
+// ||C_j||^2 = (1/n_j) sum_{x in X_j} T[j][x] for the centers with rows
+cudaError_t launch_lloyd_cnorm(const Dev& g, const LloydBuf& L, cudaStream_t st);
+// argmin over the centers for every row, f_X and the changed count; first: every row counts as changed
+cudaError_t launch_lloyd_assign(const Dev& g, const LloydBuf& L, bool first, cudaStream_t st);
+// Delta(x, C_j) for every row and center, FP32 (n x k row-major)
+cudaError_t launch_lloyd_dist(const Dev& g, const LloydBuf& L, float* out, cudaStream_t st);
+
 // tensor-core passes (BF16, split-BF16 and TF32 forms)
 // maps: 512 bytes, 64-byte aligned, holding the four CUtensorMap of the passes
 cudaError_t tc_prepare(Dev& s, void* maps);

@@ -1189,6 +1189,216 @@ __global__ void __launch_bounds__(256) k_tab_objective(Dev s, TabBuf q, const fl
   }
 }
 
+// ------------------------------------------------------------------------
+// Full-batch kernel k-means (kernel Lloyd), the baseline of Sec. 6. Every
+// iteration assigns all n points to their nearest center, then every center
+// with points becomes the mean of its points in feature space,
+// C_j = (1/n_j) sum_{x in X_j} phi(x). With T[j][x] = <phi(x), C_j>,
+//   Delta(x, C_j) = K(x, x) - 2 T[j][x] + ||C_j||^2,
+//   ||C_j||^2 = (1/n_j) sum_{x in X_j} T[j][x],
+// and T is the n x n Gram pass of X against X sorted by center, weights
+// 1/n_j. A center that gets no points keeps its row of T and its norm.
+
+// Ranking of the counting sort: one warp per chunk of LLOYD_RANK_ROWS rows,
+// 32 rows at a time in row order, so a row's rank among its chunk's rows of
+// the same center follows row order (the sort is stable).
+__global__ void __launch_bounds__(32) k_lloyd_rank(Dev g, LloydBuf L) {
+  __shared__ int cnt[1024];
+  const int lane = threadIdx.x, c = blockIdx.x;
+  for (int j = lane; j < g.k; j += 32) cnt[j] = 0;
+  __syncwarp();
+  const int64_t base = (int64_t)c * LLOYD_RANK_ROWS;
+  for (int p = 0; p < LLOYD_RANK_ROWS; p += 32) {
+    const int64_t x = base + p + lane;
+    const int a = x < g.n ? (int)min((unsigned)L.assign[x], (unsigned)(g.k - 1)) : -1;
+    const unsigned grp = __match_any_sync(0xffffffffu, a);
+    const int start = a >= 0 ? cnt[a] : 0;
+    __syncwarp();
+    if (a >= 0) {
+      L.rank[x] = start + __popc(grp & ((1u << lane) - 1u));
+      if (lane == __ffs(grp) - 1) cnt[a] = start + __popc(grp);
+    }
+    __syncwarp();
+  }
+  for (int j = lane; j < g.k; j += 32) L.ccnt[(int64_t)c * g.k + j] = cnt[j];
+}
+
+// Single CTA: per center, the position of every ranking chunk's first row
+// (cbase) and n_j; the center offsets of the sorted order; the support-buffer
+// layout (center j in whole tiles from its first tile's row) and its tile
+// list; weight 0 on the rows that pad a center's last tile.
+__global__ void __launch_bounds__(1024) k_lloyd_plan(Dev g, LloydBuf L) {
+  const int k = g.k, tid = threadIdx.x;
+  int my = 0;
+  if (tid < k) {
+    for (int c = 0; c < L.nrk; ++c) {
+      const int64_t e = (int64_t)c * k + tid;
+      const int v = L.ccnt[e];
+      L.cbase[e] = my;
+      my += v;
+    }
+  }
+  int total = 0;
+  const int off = block_exclusive_scan_1024(my, &total);
+  const int nt = tid < k ? (my + g.tn - 1) / g.tn : 0;
+  int ntot = 0;
+  const int tf = block_exclusive_scan_1024(nt, &ntot);
+  const int bo = tf * g.tn;
+  if (tid < k) {
+    g.counts[tid] = my;
+    g.coff[tid] = off;
+    L.bs_off[tid] = bo;
+    g.tile_first[tid] = tf;
+    g.tile_cnt[tid] = nt;
+    for (int t = 0; t < nt; ++t) g.tiles[tf + t] = Tile{tid, bo + t * g.tn, min(g.tn, my - t * g.tn), 0};
+    for (int r = bo + my; r < bo + nt * g.tn; ++r) {
+      g.w64[r] = 0.0;
+      g.w32[r] = 0.0f;
+    }
+  }
+  if (tid == 0) {
+    g.coff[k] = total;
+    L.bs_off[k] = ntot * g.tn;
+    *g.ntiles = ntot;
+  }
+}
+
+// Every row of X (the Gram view's operand row) into its place in the support
+// buffer, with weight 1/n_j, and its index into the center-sorted order (a
+// warp per row).
+__global__ void k_lloyd_scatter(Dev g, LloydBuf L) {
+  const int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (x >= g.n) return;
+  const int a = L.assign[x];
+  const int pos = L.cbase[(x / LLOYD_RANK_ROWS) * g.k + a] + L.rank[x];
+  const int64_t dst = (int64_t)L.bs_off[a] + pos;
+  warp_copy_row(g, false, x, dst);
+  if ((threadIdx.x & 31) == 0) {
+    const double w = 1.0 / (double)g.counts[a];
+    g.yn[dst] = g.xbn[x];
+    g.yi[dst] = (int32_t)x;
+    g.w64[dst] = w;
+    g.w32[dst] = (float)w;
+    g.perm[g.coff[a] + pos] = (int32_t)x;
+  }
+}
+
+// T[j][row0 + x] = the sum of center j's tile partials of the chunk's row x
+// (grid: x in blocks of 1024, y = center).
+__global__ void __launch_bounds__(256) k_lloyd_reduce(Dev gc, LloydBuf L, int64_t row0, int rows, int all) {
+  const int j = blockIdx.y;
+  if (!all && gc.counts[j] == 0) return;
+  const int t0 = gc.tile_first[j] * gc.ppt, nt = gc.tile_cnt[j] * gc.ppt;   // ppt partials per tile
+  float* T = L.T + (int64_t)j * gc.n + row0;
+  const int end = min((int)(blockIdx.x + 1) * 1024, rows);
+  for (int x = blockIdx.x * 1024 + threadIdx.x; x < end; x += 256) {
+    float sv = 0.0f;
+    for (int t = 0; t < nt; ++t) sv += gc.part[(int64_t)(t0 + t) * gc.bpad + x];
+    T[x] = sv;
+  }
+}
+
+// ||C_j||^2 = (1/n_j) sum_{x in X_j} T[j][x]: FP32 thread sums, FP64 combine
+// (a block of 256 per center with points).
+__global__ void __launch_bounds__(256) k_lloyd_cnorm(Dev g, LloydBuf L) {
+  __shared__ double red[8];
+  const int j = blockIdx.x, tid = threadIdx.x;
+  const int nj = g.counts[j];
+  if (nj == 0) return;
+  const float* T = L.T + (int64_t)j * g.n;
+  float acc = 0.0f;
+  for (int p = g.coff[j] + tid; p < g.coff[j] + nj; p += 256) acc += T[g.perm[p]];
+  const double w = warp_sum((double)acc);
+  if ((tid & 31) == 0) red[tid >> 5] = w;
+  __syncthreads();
+  if (tid == 0) {
+    double m2 = 0.0;
+    for (int v = 0; v < 8; ++v) m2 += red[v];
+    m2 /= (double)nj;
+    g.cnorm[j] = m2;
+    g.cnorm32[j] = (float)m2;
+  }
+}
+
+// The nearest center of every row (ties to the lowest j), FP32 distances as
+// in the table form, and per block the FP64 sum of the minima and the count
+// of rows whose assignment changed.
+__global__ void __launch_bounds__(256) k_lloyd_assign(Dev g, LloydBuf L, int first) {
+  __shared__ double red[8];
+  __shared__ int redc[8];
+  double acc = 0.0;
+  int ch = 0;
+  for (int64_t x = (int64_t)blockIdx.x * 256 + threadIdx.x; x < g.n; x += (int64_t)gridDim.x * 256) {
+    const float kxx = (float)kernel_self(g.kind, (double)g.xbn[x], g.coef0, g.degree);
+    float best = 3.0e38f;
+    int bj = 0;
+    for (int j = 0; j < g.k; ++j) {
+      const float dist = fmaf(-2.0f, L.T[(int64_t)j * g.n + x], kxx + g.cnorm32[j]);
+      if (dist < best) {
+        best = dist;
+        bj = j;
+      }
+    }
+    if (first || L.assign[x] != bj) ++ch;
+    L.assign[x] = bj;
+    L.mind[x] = best;
+    acc += (double)best;
+  }
+  acc = warp_sum(acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ch += __shfl_xor_sync(0xffffffffu, ch, o);
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = acc;
+    redc[threadIdx.x >> 5] = ch;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    int c = 0;
+    for (int v = 0; v < 8; ++v) {
+      t += red[v];
+      c += redc[v];
+    }
+    L.blk[blockIdx.x] = t;
+    L.blk_changed[blockIdx.x] = c;
+  }
+}
+
+// f_X and the changed count from the block partials, in a fixed order.
+__global__ void __launch_bounds__(256) k_lloyd_total(LloydBuf L, double inv_n) {
+  __shared__ double red[256];
+  __shared__ long long redc[256];
+  const int tid = threadIdx.x;
+  double t = 0.0;
+  long long c = 0;
+  for (int i = tid; i < L.nblk; i += 256) {
+    t += L.blk[i];
+    c += L.blk_changed[i];
+  }
+  red[tid] = t;
+  redc[tid] = c;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (tid < w) {
+      red[tid] += red[tid + w];
+      redc[tid] += redc[tid + w];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    *L.obj = red[0] * inv_n;
+    *L.changed = redc[0];
+  }
+}
+
+// Delta(x, C_j) for every row and center, the assignment pass's arithmetic.
+__global__ void __launch_bounds__(256) k_lloyd_dist(Dev g, LloydBuf L, float* __restrict__ out) {
+  const int64_t x = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (x >= g.n) return;
+  const float kxx = (float)kernel_self(g.kind, (double)g.xbn[x], g.coef0, g.degree);
+  for (int j = 0; j < g.k; ++j) out[x * g.k + j] = fmaf(-2.0f, L.T[(int64_t)j * g.n + x], kxx + g.cnorm32[j]);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
@@ -1314,6 +1524,46 @@ cudaError_t launch_tab_init(const Dev& s, const Dev& g, const TabBuf& q, const i
 cudaError_t launch_tab_objective(const Dev& s, const TabBuf& q, const float* xn, double* blk, int nblk,
                                  cudaStream_t st) {
   k_tab_objective<<<nblk, 256, 0, st>>>(s, q, xn, blk);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------- kernel Lloyd
+cudaError_t launch_lloyd_sort(const Dev& g, const LloydBuf& L, cudaStream_t st) {
+  k_lloyd_rank<<<L.nrk, 32, 0, st>>>(g, L);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_lloyd_plan<<<1, 1024, 0, st>>>(g, L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lloyd_scatter(const Dev& g, const LloydBuf& L, cudaStream_t st) {
+  k_lloyd_scatter<<<(unsigned)((g.n * 32 + 255) / 256), 256, 0, st>>>(g, L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lloyd_reduce(const Dev& gc, const LloydBuf& L, int64_t row0, int rows, bool all,
+                                cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+  k_lloyd_reduce<<<dim3((unsigned)((rows + 1023) / 1024), (unsigned)gc.k), 256, 0, st>>>(gc, L, row0, rows,
+                                                                                        all ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lloyd_cnorm(const Dev& g, const LloydBuf& L, cudaStream_t st) {
+  k_lloyd_cnorm<<<g.k, 256, 0, st>>>(g, L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lloyd_assign(const Dev& g, const LloydBuf& L, bool first, cudaStream_t st) {
+  k_lloyd_assign<<<L.nblk, 256, 0, st>>>(g, L, first ? 1 : 0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_lloyd_total<<<1, 256, 0, st>>>(L, 1.0 / (double)g.n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lloyd_dist(const Dev& g, const LloydBuf& L, float* out, cudaStream_t st) {
+  k_lloyd_dist<<<(unsigned)((g.n + 255) / 256), 256, 0, st>>>(g, L, out);
   return cudaGetLastError();
 }
 

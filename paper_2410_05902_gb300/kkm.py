@@ -98,6 +98,16 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "kkm_group_sync": ([_P], c_int32),
         "kkm_group_last_error": ([_P], ctypes.c_char_p),
         "kkm_group_destroy": ([_P], c_int32),
+        "kkm_lloyd_init": ([POINTER(_P), _P, c_int64, c_int32, c_int64, c_int32, POINTER(kkm_kernel), c_int32,
+                            POINTER(c_int64), c_int64, _P], c_int32),
+        "kkm_lloyd_iterate": ([_P, c_int32], c_int32),
+        "kkm_lloyd_read": ([_P, POINTER(c_double), POINTER(c_int64), POINTER(c_int64)], c_int32),
+        "kkm_lloyd_assignments": ([_P, _P, _P], c_int32),
+        "kkm_lloyd_distances": ([_P, _P], c_int32),
+        "kkm_lloyd_center_norms": ([_P, _P], c_int32),
+        "kkm_lloyd_info": ([_P, POINTER(c_int64), POINTER(c_int32), POINTER(c_int64)], c_int32),
+        "kkm_lloyd_destroy": ([_P], c_int32),
+        "kkm_lloyd_last_error": ([_P], ctypes.c_char_p),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -238,6 +248,58 @@ def kkm_distances_noalloc(Q: int, m: int, ldq: int, d: int, Y: int, S: int, ldy:
                                    dist_out, assign_out, stream)
     if st != KKM_OK:
         raise KKMError(st, lib.kkm_noalloc_last_error().decode())
+
+
+def _lcheck(status: int, run) -> None:
+    if status != KKM_OK:
+        msg = load().kkm_lloyd_last_error(run)
+        raise KKMError(status, msg.decode() if msg else "")
+
+
+def kkm_lloyd_init(X_ptr: int, n: int, d: int, ldx: int, k: int, kernel: kkm_kernel, precision: int,
+                   init_idx, chunk_rows: int, stream: int | None):
+    run = c_void_p()
+    ii = np.ascontiguousarray(init_idx, dtype=np.int64)
+    if ii.shape != (k,):
+        raise ValueError("init_idx must hold k indices")
+    st = load().kkm_lloyd_init(ctypes.byref(run), X_ptr, n, d, ldx, k, ctypes.byref(kernel), precision,
+                               ii.ctypes.data_as(POINTER(c_int64)), chunk_rows, stream)
+    _lcheck(st, None)
+    return run
+
+
+def kkm_lloyd_iterate(run, iters: int) -> None:
+    _lcheck(load().kkm_lloyd_iterate(run, iters), run)
+
+
+def kkm_lloyd_read(run) -> tuple[float, int, int]:
+    o, ch, it = c_double(), c_int64(), c_int64()
+    _lcheck(load().kkm_lloyd_read(run, ctypes.byref(o), ctypes.byref(ch), ctypes.byref(it)), run)
+    return o.value, ch.value, it.value
+
+
+def kkm_lloyd_assignments(run, assign_out: int | None, mind_out: int | None) -> None:
+    _lcheck(load().kkm_lloyd_assignments(run, assign_out, mind_out), run)
+
+
+def kkm_lloyd_distances(run, dist_out: int) -> None:
+    _lcheck(load().kkm_lloyd_distances(run, dist_out), run)
+
+
+def kkm_lloyd_center_norms(run, k: int) -> np.ndarray:
+    out = np.zeros(k, np.float64)
+    _lcheck(load().kkm_lloyd_center_norms(run, _np_ptr(out)), run)
+    return out
+
+
+def kkm_lloyd_info(run) -> tuple[int, int, int]:
+    la, ch, rows = c_int64(), c_int32(), c_int64()
+    _lcheck(load().kkm_lloyd_info(run, ctypes.byref(la), ctypes.byref(ch), ctypes.byref(rows)), run)
+    return la.value, ch.value, rows.value
+
+
+def kkm_lloyd_destroy(run) -> None:
+    load().kkm_lloyd_destroy(run)
 
 
 def kkm_probe_unit_rate(op: int, iters: int, stream: int | None = None) -> tuple[float, float]:
@@ -442,3 +504,65 @@ class KKM:
         except Exception:
             pass
 
+
+class Lloyd:
+    """Full-batch kernel k-means (kernel Lloyd) through kkm_lloyd_*: every
+    iteration assigns all points, then moves every center with points to the
+    mean of its points in feature space (the baseline of Sec. 6)."""
+
+    def __init__(self, X, k: int, init_idx, kernel: str = "gaussian", param: float = 1.0, coef0: float = 0.0,
+                 degree: int = 2, precision: str = "fp32", chunk_rows: int = 0, stream=None):
+        import torch
+        if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float32 and X.dim() == 2):
+            raise TypeError("X must be a 2-D float32 CUDA tensor")
+        if X.stride(1) != 1:
+            raise ValueError("X rows must be contiguous")
+        self._torch = torch
+        self.n, self.d = X.shape
+        self.k = int(k)
+        self.device = X.device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(X.device)
+        kern = kkm_kernel(KERNELS[kernel], float(param), float(coef0), int(degree))
+        with torch.cuda.device(X.device):
+            self.run = kkm_lloyd_init(X.data_ptr(), self.n, self.d, X.stride(0), self.k, kern,
+                                      PRECISIONS[precision], init_idx, int(chunk_rows), self.stream.cuda_stream)
+
+    def iterate(self, iters: int = 1) -> None:
+        """Queue `iters` iterations (asynchronous)."""
+        kkm_lloyd_iterate(self.run, iters)
+
+    def read(self) -> tuple[float, int, int]:
+        """(f_X at the current centers, assignments changed by the last assignment, iterations run)."""
+        return kkm_lloyd_read(self.run)
+
+    def assignments(self):
+        """(assignments int32 (n,), min_j Delta float32 (n,)) as CUDA tensors."""
+        torch = self._torch
+        a = torch.empty(self.n, dtype=torch.int32, device=self.device)
+        md = torch.empty(self.n, dtype=torch.float32, device=self.device)
+        kkm_lloyd_assignments(self.run, a.data_ptr(), md.data_ptr())
+        return a, md
+
+    def distances(self):
+        """Delta(x, C_j) as an (n, k) float32 CUDA tensor."""
+        out = self._torch.empty((self.n, self.k), dtype=self._torch.float32, device=self.device)
+        kkm_lloyd_distances(self.run, out.data_ptr())
+        return out
+
+    def center_norms(self) -> np.ndarray:
+        return kkm_lloyd_center_norms(self.run, self.k)
+
+    def info(self) -> tuple[int, int, int]:
+        """(kernels launched, Gram-pass chunks per iteration, rows per chunk)."""
+        return kkm_lloyd_info(self.run)
+
+    def close(self) -> None:
+        if self.run:
+            kkm_lloyd_destroy(self.run)
+            self.run = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -2,11 +2,9 @@
 
 ``full_batch`` runs full-batch kernel k-means (kernel Lloyd: every iteration
 assigns all n points, then every center becomes the mean of its points in
-feature space) on the library's own kernels. It is the windowed run with the
-batch equal to X in order (b = n), the constant rate eta = 1 and tau = 1:
-with alpha = 1 a center's older blocks carry weight 0, and tau = 1 keeps
-only the newest block, the cluster mean. A cluster that gets no points keeps
-its center (alpha = 0). Limited to n <= 8192, the library's batch bound.
+feature space) through the library's kkm_lloyd_* entry points: the n x n
+Gram pass of X against X sorted by center, on the same distance kernels as
+the mini-batch run. A cluster that gets no points keeps its center.
 
 ``adjusted_rand`` and ``normalized_mutual_info`` are the usual external
 indices against the latent labels of the synthetic generators (ARI of Hubert
@@ -61,37 +59,34 @@ def normalized_mutual_info(labels_true, labels_pred) -> float:
 
 
 def full_batch(X, k: int, kernel: str, param: float, init_idx, iters: int, precision: str = "fp32",
-               coef0: float = 0.0, degree: int = 2, stop_when_stable: bool = True):
+               coef0: float = 0.0, degree: int = 2, stop_when_stable: bool = True, chunk_rows: int = 0,
+               trace: list | None = None):
     """Full-batch kernel k-means on the GPU (see the module docstring).
 
-    Returns (assignments of the last iteration, f_X after it, iterations run,
-    seconds on the device). With stop_when_stable the loop ends once an
-    iteration leaves every assignment unchanged (Lloyd's fixed point).
+    Returns (assignments at the final centers, f_X at them, iterations run,
+    seconds of the loop on the host clock). With stop_when_stable the loop
+    ends after the first iteration that changes no assignment (Lloyd's fixed
+    point). With a list as ``trace``, appends (iterations, seconds since the
+    loop started, f_X) after the initial assignment and after every iteration.
     """
     import torch
-    from .kkm import KKM
-    n = X.shape[0]
-    if n > 8192:
-        raise ValueError("full_batch needs n <= 8192 (one batch holds all of X)")
-    run = KKM(X, k, n, kernel=kernel, param=param, coef0=coef0, degree=degree, tau=1, lr="const", eta=1.0,
-              precision=precision, init_idx=init_idx)
-    idx = torch.arange(n, dtype=torch.int32, device=X.device)
-    a = torch.empty(n, dtype=torch.int32, device=X.device)
-    prev = None
+    from .kkm import Lloyd
+    run = Lloyd(X, k, np.asarray(init_idx, np.int64), kernel=kernel, param=param, coef0=coef0, degree=degree,
+                precision=precision, chunk_rows=chunk_rows)
     done = 0
-    run.sync()
     t0 = time.perf_counter()
+    fx, _, _ = run.read()
+    if trace is not None:
+        trace.append((0, 0.0, fx))
     for _ in range(iters):
-        run.step(idx, None, a)
-        done += 1
-        if stop_when_stable:
-            cur = a.clone()
-            if prev is not None and torch.equal(cur, prev):
-                break
-            prev = cur
-    run.sync()
+        run.iterate(1)
+        fx, changed, done = run.read()
+        if trace is not None:
+            trace.append((done, time.perf_counter() - t0, fx))
+        if stop_when_stable and changed == 0:
+            break
     seconds = time.perf_counter() - t0
-    assign = run.assign(X)[0].cpu().numpy()
-    fx = run.objective()
+    assign = run.assignments()[0].cpu().numpy()
+    torch.cuda.synchronize()
     run.close()
     return assign, fx, done, seconds

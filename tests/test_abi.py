@@ -146,3 +146,45 @@ def test_probe_rejects_bad_arguments(lib):
     assert lib.kkm_probe_unit_rate(0, 0, ctypes.byref(a), ctypes.byref(b), None) == kkm.KKM_EINVAL
     assert lib.kkm_probe_unit_rate(0, 1 << 25, ctypes.byref(a), ctypes.byref(b), None) == kkm.KKM_EINVAL
     assert lib.kkm_probe_unit_rate(0, 10, None, ctypes.byref(b), None) == kkm.KKM_EINVAL
+
+
+def _lloyd_init(lib, **over):
+    args = dict(X=ctypes.c_void_p(0x1000), n=100, d=8, ldx=8, k=4, precision=kkm.KKM_PREC_FP32, chunk_rows=0,
+                kernel=kkm.kkm_kernel(kkm.KKM_GAUSSIAN, 2.0, 0.0, 2), init=np.arange(4, dtype=np.int64))
+    args.update(over)
+    run = ctypes.c_void_p()
+    init = args["init"]
+    ip = None if init is None else init.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    st = lib.kkm_lloyd_init(ctypes.byref(run), args["X"], args["n"], args["d"], args["ldx"], args["k"],
+                            ctypes.byref(args["kernel"]), args["precision"], ip, args["chunk_rows"], None)
+    return st, run
+
+
+@pytest.mark.parametrize("over,needle", [
+    (dict(n=0), "n must be"),
+    (dict(d=0), "d must be"),
+    (dict(ldx=4), "ldx"),
+    (dict(k=0), "k must be"),
+    (dict(k=200), "k must be"),
+    (dict(X=None), "required"),
+    (dict(init=None), "required"),
+    (dict(init=np.array([0, 1, 2, 100], np.int64)), "init_idx"),
+    (dict(init=np.array([0, 1, -1, 3], np.int64)), "init_idx"),
+    (dict(chunk_rows=100), "chunk_rows"),
+    (dict(chunk_rows=-128), "chunk_rows"),
+    (dict(precision=9), "precision"),
+    (dict(kernel=kkm.kkm_kernel(kkm.KKM_LAPLACIAN, 0.0, 0.0, 2)), "kernel param"),
+    (dict(kernel=kkm.kkm_kernel(kkm.KKM_POLY, 1.0, 0.0, 9)), "degree"),
+])
+def test_lloyd_init_rejects_bad_arguments(lib, over, needle):
+    st, run = _lloyd_init(lib, **over)
+    assert st == kkm.KKM_EINVAL
+    assert not run.value
+    assert needle in lib.kkm_lloyd_last_error(None).decode()
+
+
+def test_lloyd_calls_reject_a_null_handle(lib):
+    assert lib.kkm_lloyd_iterate(None, 1) == kkm.KKM_EINVAL
+    assert lib.kkm_lloyd_read(None, None, None, None) == kkm.KKM_EINVAL
+    assert lib.kkm_lloyd_distances(None, None) == kkm.KKM_EINVAL
+    assert lib.kkm_lloyd_destroy(None) == kkm.KKM_OK
