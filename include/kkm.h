@@ -91,8 +91,8 @@ typedef enum kkm_lr { KKM_LR_BETA = 0, KKM_LR_CONST = 1, KKM_LR_SKLEARN = 2 } kk
  *   TF32   : tcgen05 kind::tf32, operands rounded to TF32 (10 explicit
  *            mantissa bits, round to nearest with ties away), FP32
  *            accumulation.
- * The tensor-core forms need a compute capability 10.3 device (KKM_ENOTSUP
- * for TF32 elsewhere; BF16 and BF16X3 fall back to CUDA-core products). */
+ * The tensor-core forms need a compute capability 10.3 device: kkm_init
+ * returns KKM_ENOTSUP for them on any other device (no CUDA-core stand-in). */
 typedef enum kkm_precision {
   KKM_PREC_FP32 = 0,
   KKM_PREC_BF16 = 1,
@@ -513,14 +513,33 @@ kkm_status kkm_destroy(kkm_ctx* ctx);
  *   group's work. The runs' own streams are synchronised once here; while
  *   grouped, a run must not be stepped on its own, and kkm_group_sync must
  *   precede any other call on a run. The group does not own the runs.
+ *   The runs' device buffers and settings are captured here: a group of
+ *   windows-form runs steps them with one launch per step phase over all
+ *   runs (gather, argmin, sort/plan, row moves, weight update) and one launch
+ *   per Gram pass and class of runs sharing form, kernel kind and distance
+ *   tile; each block of such a launch does what one block of one run's own
+ *   launch would, so every run's results equal its single-run steps. A group
+ *   with table-form runs steps each run on a branch of its own.
  * kkm_group_step -- one iteration of every run (each with its built-in
- *   sampler), asynchronous. From the second call on, the whole iteration of
- *   all runs is one CUDA graph launch whose per-run branches run concurrently.
+ *   sampler), asynchronous. From the second call on, the iteration of all
+ *   runs is one CUDA graph launch.
  * kkm_group_sync -- synchronises and reports each run's device status.
+ * kkm_group_set_chains -- before the first group step: deal the runs to
+ *   `chains` chains (1 <= chains <= n), each stepped by its own per-phase
+ *   launches on a graph branch of its own with a share of the SMs by
+ *   estimated work, so one chain's short phases overlap another's Gram
+ *   passes. chains = 0 steps every run on a graph branch of its own with its
+ *   own kernels (the launch structure of a group with table-form runs, which
+ *   accept no other value: KKM_ENOTSUP). The default is 2 for 16 runs or
+ *   more, else 1. Which is fastest depends on the mix of runs; measure.
+ * kkm_group_launches -- host outputs (each may be NULL): kernels the group's
+ *   steps have launched and kernels per step; reset != 0 clears the count.
  * kkm_group_last_error(NULL) gives the calling thread's last create failure. */
 typedef struct kkm_group kkm_group;
 kkm_status kkm_group_create(kkm_group** out, kkm_ctx* const* runs, int32_t n, void* stream);
 kkm_status kkm_group_step(kkm_group* group);
+kkm_status kkm_group_set_chains(kkm_group* group, int32_t chains);
+kkm_status kkm_group_launches(kkm_group* group, int64_t* launches, int32_t* per_step, int32_t reset);
 kkm_status kkm_group_sync(kkm_group* group);
 const char* kkm_group_last_error(kkm_group* group);
 kkm_status kkm_group_destroy(kkm_group* group);

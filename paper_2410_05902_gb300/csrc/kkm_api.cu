@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <tuple>
 #include <unordered_set>
 #include <vector>
 
@@ -1123,11 +1124,18 @@ KKM_API kkm_status kkm_launches(kkm_ctx* c, int64_t* launches, int32_t reset) {
 }
 
 // ------------------------------------------------------------ run groups
-// Many independent runs stepped together: one step of every run is one CUDA
-// graph launch. The graph forks from a root stream into one branch per run,
-// each branch holding that run's kernel sequence, and joins back, so the
-// runs' kernels run concurrently on the GPU. The first group step runs
-// eagerly through the same branches; the graph is captured on the second.
+// Many independent runs stepped together. For runs of the windows form (the
+// usual case) a group step is one launch per step phase over every run: the
+// gather, the argmin, the sort/plan, the row moves and the weight update each
+// cover all runs in one grid, and the two Gram passes take one launch per
+// class of runs that share their kernel template (tensor-core or FP32 form,
+// kernel kind, distance tile). Each block of such a launch plays one block of
+// one run's own launch (kkm::GroupPhase), so every run computes what it
+// would alone. The runs' Dev structs and TMA descriptors sit in device memory,
+// written at creation. A group that holds table-form runs keeps the general
+// path: a graph that forks into one branch per run, each branch that run's
+// kernel sequence, and joins back. Either way the first group step runs
+// eagerly and the second captures the step as a CUDA graph.
 struct kkm_group {
   int device = 0;
   std::vector<kkm_ctx*> runs;
@@ -1138,7 +1146,32 @@ struct kkm_group {
   std::vector<cudaEvent_t> ev;     // [0] fork, [1 + i] join of run i
   cudaGraphExec_t gexec = nullptr;
   int64_t steps = 0;
+  int64_t launches = 0;            // kernels launched by the group's steps (host count)
   std::string err;
+  // the per-phase path
+  bool batched = false;
+  int32_t chains_req = 0;                // chains asked for (0: automatic)
+  kkm::GroupRun* d_runs = nullptr;       // the runs, ordered by chain, then class
+  int32_t* d_first = nullptr;            // every phase's first-block table
+  struct Phase {
+    kkm::GroupPhase g{};
+    int blocks = 0;
+  };
+  struct Pass {                           // one class of runs: a Gram pass over all of them
+    Phase ph;
+    bool tc = false;
+    int form = 0, kind = 0, tn = 0;
+  };
+  // A chain: a share of the runs stepped by one launch per phase, on a graph
+  // branch of its own, so that one chain's short phases overlap another's
+  // Gram passes; each chain's tensor-core passes take its share of the SMs.
+  struct Chain {
+    Phase gather, argmin, sort_plan, move, finalize;
+    int sort_smem = 0;
+    std::vector<Pass> dist, window;
+  };
+  std::vector<Chain> chains;
+  int launches_per_step = 0;
 };
 
 namespace {
@@ -1151,6 +1184,8 @@ kkm_status gfail(kkm_group* g, kkm_status st, const std::string& msg) {
 }
 
 void group_free(kkm_group* g) {
+  if (g->d_runs) cudaFree(g->d_runs);
+  if (g->d_first) cudaFree(g->d_first);
   if (g->gexec) cudaGraphExecDestroy(g->gexec);
   for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
   for (cudaStream_t b : g->branch) cudaStreamDestroy(b);
@@ -1158,8 +1193,48 @@ void group_free(kkm_group* g) {
   if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
 }
 
+// One step of the runs of one chain, one launch per phase (and per class for the Gram passes).
+kkm_status chain_enqueue(kkm_group* g, const kkm_group::Chain& c, cudaStream_t st) {
+  auto ok = [&](cudaError_t e, const char* what) {
+    return e == cudaSuccess ? KKM_OK : gfail(g, KKM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  };
+  kkm_status r = ok(kkm::launch_group_gather(c.gather.g, c.gather.blocks, st), "group gather");
+  for (const auto& p : c.dist) {
+    if (r != KKM_OK) return r;
+    r = ok(p.tc ? kkm::launch_group_tc(p.ph.g, 0, p.form, p.kind, p.tn, p.ph.blocks, st)
+                : kkm::launch_group_simt(p.ph.g, 0, p.form, p.ph.blocks, st),
+           "group distance pass");
+  }
+  if (r == KKM_OK) r = ok(kkm::launch_group_argmin(c.argmin.g, c.argmin.blocks, st), "group argmin");
+  if (r == KKM_OK) r = ok(kkm::launch_group_sort_plan(c.sort_plan.g, c.sort_smem, st), "group sort/plan");
+  if (r == KKM_OK) r = ok(kkm::launch_group_move(c.move.g, c.move.blocks, st), "group row moves");
+  for (const auto& p : c.window) {
+    if (r != KKM_OK) return r;
+    r = ok(p.tc ? kkm::launch_group_tc(p.ph.g, 1, p.form, p.kind, p.tn, p.ph.blocks, st)
+                : kkm::launch_group_simt(p.ph.g, 1, p.form, p.ph.blocks, st),
+           "group window pass");
+  }
+  if (r == KKM_OK) r = ok(kkm::launch_group_finalize(c.finalize.g, c.finalize.blocks, st), "group finalize");
+  return r;
+}
+
+// One step of every run: the chains on branches forked from `st` and joined back.
+kkm_status group_enqueue_batched(kkm_group* g, cudaStream_t st) {
+  if (g->chains.size() == 1) return chain_enqueue(g, g->chains[0], st);
+  if (cudaEventRecord(g->ev[0], st) != cudaSuccess) return gfail(g, KKM_ECUDA, "fork event");
+  for (size_t c = 0; c < g->chains.size(); ++c) {
+    if (cudaStreamWaitEvent(g->branch[c], g->ev[0], 0) != cudaSuccess) return gfail(g, KKM_ECUDA, "fork wait");
+    const kkm_status r = chain_enqueue(g, g->chains[c], g->branch[c]);
+    if (r != KKM_OK) return r;
+    if (cudaEventRecord(g->ev[1 + c], g->branch[c]) != cudaSuccess) return gfail(g, KKM_ECUDA, "join event");
+    if (cudaStreamWaitEvent(st, g->ev[1 + c], 0) != cudaSuccess) return gfail(g, KKM_ECUDA, "join wait");
+  }
+  return KKM_OK;
+}
+
 // Fork from `from`, queue one step of every run on its branch, join back.
 kkm_status group_enqueue(kkm_group* g, cudaStream_t from) {
+  if (g->batched) return group_enqueue_batched(g, from);
   if (cudaEventRecord(g->ev[0], from) != cudaSuccess) return gfail(g, KKM_ECUDA, "fork event");
   for (size_t i = 0; i < g->runs.size(); ++i) {
     kkm_ctx* c = g->runs[i];
@@ -1172,12 +1247,170 @@ kkm_status group_enqueue(kkm_group* g, cudaStream_t from) {
   return KKM_OK;
 }
 
+// Estimated Gram-pass work of one run per step (support rows once the
+// windows are full, times the batch, times the operand width): the weight by
+// which runs are dealt to chains and chains get their share of the SMs.
+double run_work(const kkm::Dev& s) {
+  const double width = (double)std::max(s.d, 1) * (s.form == kkm::FORM_BF16X3 ? 3.0 : 1.0);
+  const double tau = s.tau > 0 ? s.tau : (double)s.b;
+  return (double)s.b * (s.k * tau + s.b) * (width + 64.0);   // + 64: the kernel values, whatever d is
+}
+
+// The per-phase layout of a group of windows-form runs: the runs dealt to
+// `nchains` chains (longest work first, each to the least loaded chain),
+// ordered by chain and class, every phase's first-block table, and the runs'
+// Dev structs and descriptors copied to the device.
+cudaError_t group_build_batched(kkm_group* g, int nchains) {
+  const int n = (int)g->runs.size();
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+  if (sms < 1) sms = 148;
+  if (g->d_runs) cudaFree(g->d_runs);
+  if (g->d_first) cudaFree(g->d_first);
+  g->d_runs = nullptr;
+  g->d_first = nullptr;
+  nchains = std::max(1, std::min(nchains, n));
+  // distance-pass class (form, kind, tile); the window pass ignores the tile
+  auto key = [](const kkm_ctx* c) {
+    return std::make_tuple(c->use_tc ? 1 : 0, (int)c->s.form, (int)c->s.kind, (int)c->s.tn);
+  };
+  auto wkey = [](const kkm_ctx* c) { return std::make_tuple(c->use_tc ? 1 : 0, (int)c->s.form, (int)c->s.kind); };
+  std::vector<double> work(n);
+  for (int i = 0; i < n; ++i) work[i] = run_work(g->runs[i]->s);
+  std::vector<int> by_work(n), chain_of(n);
+  for (int i = 0; i < n; ++i) by_work[i] = i;
+  std::stable_sort(by_work.begin(), by_work.end(), [&](int a, int b) { return work[a] > work[b]; });
+  std::vector<double> load(nchains, 0.0);
+  for (int i : by_work) {
+    const int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    chain_of[i] = c;
+    load[c] += work[i];
+  }
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    if (chain_of[a] != chain_of[b]) return chain_of[a] < chain_of[b];
+    return key(g->runs[a]) < key(g->runs[b]);
+  });
+  std::vector<kkm::GroupRun> hr(n);
+  for (int i = 0; i < n; ++i) {
+    const kkm_ctx* c = g->runs[order[i]];
+    std::memcpy(hr[i].maps, c->tmaps, sizeof(hr[i].maps));
+    hr[i].s = c->s;
+    hr[i].s.pre_b = 0;   // the group passes read item counts after their grid-dependency wait
+  }
+  cudaError_t e = cudaMalloc(&g->d_runs, sizeof(kkm::GroupRun) * (size_t)n);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(g->d_runs, hr.data(), sizeof(kkm::GroupRun) * (size_t)n, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+
+  std::vector<int32_t> first;
+  struct Pending { int chain, which; size_t off; int lo; int cnt; };
+  std::vector<Pending> pend;
+  // appends the first-block table of runs [lo, lo + blocks.size())
+  auto table = [&](int chain, int which, int lo, const std::vector<int>& blocks) {
+    const size_t off = first.size();
+    int64_t acc = 0;
+    for (int b : blocks) {
+      first.push_back((int32_t)acc);
+      acc += b;
+    }
+    first.push_back((int32_t)acc);
+    pend.push_back({chain, which, off, lo, (int)blocks.size()});
+    return (int)acc;
+  };
+  double total_load = 0.0;
+  for (double l : load) total_load += l;
+  g->chains.assign(nchains, kkm_group::Chain{});
+  std::vector<std::vector<int>> dist_lo(nchains), win_lo(nchains);
+  for (int c = 0, lo = 0; c < nchains; ++c) {
+    int hi = lo;
+    while (hi < n && chain_of[order[hi]] == c) ++hi;
+    auto& ch = g->chains[c];
+    std::vector<int> bg, ba, bs, bm, bf;
+    for (int i = lo; i < hi; ++i) {
+      const kkm::Dev& s = hr[i].s;
+      bg.push_back((s.b * 32 + 255) / 256);
+      ba.push_back((s.b + 31) / 32);
+      bs.push_back(1);
+      bm.push_back(std::max(1, (s.b + 7) / 8));
+      bf.push_back(s.k);
+      ch.sort_smem = std::max(ch.sort_smem, kkm::sort_plan_smem(s.k, s.b));
+    }
+    ch.gather.blocks = table(c, 0, lo, bg);
+    ch.argmin.blocks = table(c, 1, lo, ba);
+    ch.sort_plan.blocks = table(c, 2, lo, bs);
+    ch.move.blocks = table(c, 3, lo, bm);
+    ch.finalize.blocks = table(c, 4, lo, bf);
+    // the Gram passes balance their runs on the device (a weighted item
+    // space per class for the tensor-core passes, a flat one for the
+    // CUDA-core passes) over the chain's share of the SMs
+    const int share = std::max(1, (int)std::lround(sms * (total_load > 0 ? load[c] / total_load : 1.0)));
+    for (int i = lo; i < hi;) {
+      int j = i + 1;
+      while (j < hi && key(g->runs[order[j]]) == key(g->runs[order[i]])) ++j;
+      const kkm_ctx* c0 = g->runs[order[i]];
+      kkm_group::Pass p;
+      p.tc = c0->use_tc;
+      p.form = c0->s.form;
+      p.kind = c0->s.kind;
+      p.tn = c0->s.tn;
+      p.ph.blocks = p.tc ? share : 4 * share;
+      p.ph.g.nruns = j - i;
+      ch.dist.push_back(p);
+      dist_lo[c].push_back(i);
+      i = j;
+    }
+    for (int i = lo; i < hi;) {
+      int j = i + 1;
+      while (j < hi && wkey(g->runs[order[j]]) == wkey(g->runs[order[i]])) ++j;
+      const kkm_ctx* c0 = g->runs[order[i]];
+      kkm_group::Pass p;
+      p.tc = c0->use_tc;
+      p.form = c0->s.form;
+      p.kind = c0->s.kind;
+      p.tn = c0->s.tn;
+      p.ph.blocks = p.tc ? share : 4 * share;
+      p.ph.g.nruns = j - i;
+      ch.window.push_back(p);
+      win_lo[c].push_back(i);
+      i = j;
+    }
+    lo = hi;
+  }
+  e = cudaMalloc(&g->d_first, sizeof(int32_t) * first.size());
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(g->d_first, first.data(), sizeof(int32_t) * first.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  g->launches_per_step = 0;
+  for (const auto& q : pend) {
+    auto& ch = g->chains[q.chain];
+    kkm_group::Phase* ph[5] = {&ch.gather, &ch.argmin, &ch.sort_plan, &ch.move, &ch.finalize};
+    ph[q.which]->g = kkm::GroupPhase{g->d_runs + q.lo, g->d_first + q.off, q.cnt};
+  }
+  for (int c = 0; c < nchains; ++c) {
+    auto& ch = g->chains[c];
+    for (size_t i = 0; i < ch.dist.size(); ++i) {
+      ch.dist[i].ph.g.runs = g->d_runs + dist_lo[c][i];
+      ch.dist[i].ph.g.first = g->d_first;   // not read by the Gram passes
+    }
+    for (size_t i = 0; i < ch.window.size(); ++i) {
+      ch.window[i].ph.g.runs = g->d_runs + win_lo[c][i];
+      ch.window[i].ph.g.first = g->d_first;
+    }
+    g->launches_per_step += 5 + (int)ch.dist.size() + (int)ch.window.size();
+  }
+  g->batched = true;
+  return cudaSuccess;
+}
+
 }  // namespace
 
 KKM_API kkm_status kkm_group_create(kkm_group** out, kkm_ctx* const* runs, int32_t n, void* stream) {
   if (!out) return gfail(nullptr, KKM_EINVAL, "out is NULL");
   *out = nullptr;
   if (n < 1 || !runs) return gfail(nullptr, KKM_EINVAL, "a group needs n >= 1 runs");
+  if (n > 1024) return gfail(nullptr, KKM_EINVAL, "a group holds at most 1024 runs");
   for (int32_t i = 0; i < n; ++i) {
     if (!runs[i]) return gfail(nullptr, KKM_EINVAL, "null run");
     if (runs[i]->poisoned) return gfail(nullptr, KKM_ESTATE, "a run is poisoned");
@@ -1220,6 +1453,14 @@ KKM_API kkm_status kkm_group_create(kkm_group** out, kkm_ctx* const* runs, int32
     e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     if (e != cudaSuccess) return bail("event", e);
   }
+  bool all_windows = true;
+  for (kkm_ctx* c : g->runs) all_windows = all_windows && !c->tab;
+  if (all_windows) {
+    e = group_build_batched(g, n >= 16 ? 2 : 1);
+    if (e != cudaSuccess) return bail("group layout", e);
+  } else {
+    g->launches_per_step = 7 * n;   // seven kernels per run, on the run's branch
+  }
   *out = g;
   return KKM_OK;
 }
@@ -1258,11 +1499,38 @@ KKM_API kkm_status kkm_group_step(kkm_group* g) {
     const cudaError_t e = cudaGraphLaunch(g->gexec, g->stream);
     if (e != cudaSuccess) return gfail(g, KKM_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
   }
-  for (kkm_ctx* c : g->runs) {
-    c->launches += 7;
-    ++c->iteration;
-  }
+  for (kkm_ctx* c : g->runs) ++c->iteration;
+  g->launches += g->launches_per_step;
   ++g->steps;
+  return KKM_OK;
+}
+
+KKM_API kkm_status kkm_group_set_chains(kkm_group* g, int32_t chains) {
+  if (!g) return gfail(nullptr, KKM_EINVAL, "null group");
+  if (chains < 0 || chains > (int32_t)g->runs.size()) return gfail(g, KKM_EINVAL, "chains must be in [0, runs]");
+  if (g->steps > 0) return gfail(g, KKM_ESTATE, "chains are set before the first group step");
+  bool all_windows = true;
+  for (kkm_ctx* c : g->runs) all_windows = all_windows && !c->tab;
+  if (chains > 0 && !all_windows)
+    return gfail(g, KKM_ENOTSUP, "a group with table-form runs steps each run on its own branch");
+  if (cudaSetDevice(g->device) != cudaSuccess) return gfail(g, KKM_ECUDA, "cudaSetDevice failed");
+  g->chains_req = chains;
+  if (chains == 0) {             // one graph branch per run
+    g->batched = false;
+    g->chains.clear();
+    g->launches_per_step = 7 * (int)g->runs.size();
+    return KKM_OK;
+  }
+  const cudaError_t e = group_build_batched(g, chains);
+  if (e != cudaSuccess) return gfail(g, KKM_ECUDA, std::string("group layout: ") + cudaGetErrorString(e));
+  return KKM_OK;
+}
+
+KKM_API kkm_status kkm_group_launches(kkm_group* g, int64_t* launches, int32_t* per_step, int32_t reset) {
+  if (!g) return gfail(nullptr, KKM_EINVAL, "null group");
+  if (launches) *launches = g->launches;
+  if (per_step) *per_step = g->launches_per_step;
+  if (reset) g->launches = 0;
   return KKM_OK;
 }
 

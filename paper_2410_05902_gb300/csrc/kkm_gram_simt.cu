@@ -47,7 +47,8 @@ __device__ __forceinline__ float4 load4(const void* rowp, int k, int dp) {
 // acc[i][j] = sum_k A[ty*4+i][k] * B[tx*4+j][k] for a 64x64 tile. A and B point
 // at the tiles' first rows (element type by form); rows are `ld` elements apart
 // and the product runs over kend columns (zero padded, a multiple of BK).
-template <int F>
+// DIFF: acc[i][j] = sum_k (A[ty*4+i][k] - B[tx*4+j][k])^2 instead.
+template <int F, bool DIFF = false>
 __device__ __forceinline__ void gram_tile(const void* __restrict__ A, const void* __restrict__ B,
                                           int ld, int kend, int dp, float (&acc)[4][4],
                                           float (*As)[BM + 4], float (*Bs)[BN + 4]) {
@@ -76,7 +77,14 @@ __device__ __forceinline__ void gram_tile(const void* __restrict__ A, const void
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
+        for (int j = 0; j < 4; ++j) {
+          if constexpr (DIFF) {
+            const float t = ar[i] - br[j];
+            acc[i][j] = fmaf(t, t, acc[i][j]);
+          } else {
+            acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
+          }
+        }
     }
   }
 }
@@ -95,21 +103,25 @@ __device__ __forceinline__ float sum16(float v) {
   return v;
 }
 
+// Item w of a run's distance pass (row tile w % R of support tile w / R).
 template <int F>
-__global__ void __launch_bounds__(NT) k_dist_simt(Dev s, int rows) {
-  KKM_GRID_DEP_WAIT();
-  KKM_LAUNCH_DEPENDENTS();
-  __shared__ __align__(16) float As[BK][BM + 4];
-  __shared__ __align__(16) float Bs[BK][BN + 4];
+__device__ __forceinline__ void dist_simt_item(const Dev& s, int rows, int R, int w, float (*As)[BM + 4],
+                                               float (*Bs)[BN + 4]) {
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int R = (rows + BM - 1) / BM;
-  const int total = R * (*s.ntiles);
-  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+  const bool lap = s.kind == K_LAPLACE;
+  {
     const int t = w / R, rt = w % R;
     const Tile T = s.tiles[t];
     float acc[4][4];
-    gram_tile<F>(rows_ptr<F>(s, false, (int64_t)rt * BM), rows_ptr<F>(s, true, T.row0), s.ld,
-                 F == FORM_FP32 ? s.ld : s.dp, s.dp, acc, As, Bs);
+    // Laplacian kernel: ||x - y||^2 from the differences. Through ||x||^2 +
+    // ||y||^2 - 2 <x, y> a query row equal to a support row (no data index to
+    // recognise it by) keeps d2 ~ eps ||x||^2, which the square root magnifies.
+    if (lap)
+      gram_tile<F, true>(rows_ptr<F>(s, false, (int64_t)rt * BM), rows_ptr<F>(s, true, T.row0), s.ld,
+                         F == FORM_FP32 ? s.ld : s.dp, s.dp, acc, As, Bs);
+    else
+      gram_tile<F>(rows_ptr<F>(s, false, (int64_t)rt * BM), rows_ptr<F>(s, true, T.row0), s.ld,
+                   F == FORM_FP32 ? s.ld : s.dp, s.dp, acc, As, Bs);
     float yn[4], wy[4];
     int yi[4];
 #pragma unroll
@@ -130,8 +142,10 @@ __global__ void __launch_bounds__(NT) k_dist_simt(Dev s, int rows) {
       float sum = 0.0f;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const float kv = kernel_from_gram(s.kind, acc[i][j], xn, yn[j], xi >= 0 && xi == yi[j],
-                                          s.negc, (float)s.coef0, s.degree);
+        const bool same = xi >= 0 && xi == yi[j];
+        const float kv = lap ? exp2f(sqrtf(same ? 0.0f : acc[i][j]) * s.negc)
+                             : kernel_from_gram(s.kind, acc[i][j], xn, yn[j], same, s.negc, (float)s.coef0,
+                                                s.degree);
         sum += (tx * 4 + j < T.ncols) ? wy[j] * kv : 0.0f;
       }
       sum = sum16(sum);
@@ -141,15 +155,25 @@ __global__ void __launch_bounds__(NT) k_dist_simt(Dev s, int rows) {
 }
 
 template <int F>
-__global__ void __launch_bounds__(NT) k_wgram_simt(Dev s) {
+__device__ __forceinline__ void dist_simt_body(const Dev& s, int rows, int bid, int nblk) {
   KKM_GRID_DEP_WAIT();
   KKM_LAUNCH_DEPENDENTS();
   __shared__ __align__(16) float As[BK][BM + 4];
   __shared__ __align__(16) float Bs[BK][BN + 4];
-  __shared__ double red[4][NT / 32];
+  const int R = (rows + BM - 1) / BM;
+  const int total = R * (*s.ntiles);
+  for (int w = bid; w < total; w += nblk) dist_simt_item<F>(s, rows, R, w, As, Bs);
+}
+
+template <int F>
+__global__ void __launch_bounds__(NT) k_dist_simt(Dev s, int rows) { dist_simt_body<F>(s, rows, blockIdx.x, gridDim.x); }
+
+// Pair w of a run's window pass; its four sums go to wpart[w] (slot 0).
+template <int F>
+__device__ __forceinline__ void wgram_simt_item(const Dev& s, int w, float (*As)[BM + 4], float (*Bs)[BN + 4],
+                                                double (*red)[NT / 32]) {
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, lane = tid & 31, warp = tid >> 5;
-  const int total = *s.nwpairs;
-  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+  {
     const WPair pr = s.wpairs[w];
     const Plan P = s.plan[pr.j];
     const int64_t base = (int64_t)pr.j * s.cap;
@@ -211,6 +235,60 @@ __global__ void __launch_bounds__(NT) k_wgram_simt(Dev s) {
   }
 }
 
+template <int F>
+__device__ __forceinline__ void wgram_simt_body(const Dev& s, int bid, int nblk) {
+  KKM_GRID_DEP_WAIT();
+  KKM_LAUNCH_DEPENDENTS();
+  __shared__ __align__(16) float As[BK][BM + 4];
+  __shared__ __align__(16) float Bs[BK][BN + 4];
+  __shared__ double red[4][NT / 32];
+  const int total = *s.nwpairs;
+  for (int w = bid; w < total; w += nblk) wgram_simt_item<F>(s, w, As, Bs, red);
+}
+
+template <int F>
+__global__ void __launch_bounds__(NT) k_wgram_simt(Dev s) { wgram_simt_body<F>(s, blockIdx.x, gridDim.x); }
+
+// Run groups: the items of all the launch's runs laid end to end (distance
+// pass: row tiles x support tiles; window pass: pairs), block-strided, so the
+// blocks stay busy until the last item of any run. Item w of the flat space is
+// item w - off[r] of run r; every item writes only its own partials, so each
+// run computes what its own launch would.
+constexpr int GROUP_MAX_RUNS = 1024;
+
+template <int F, int MODE>
+__global__ void __launch_bounds__(NT) k_group_simt(GroupPhase g) {
+  KKM_GRID_DEP_WAIT();
+  KKM_LAUNCH_DEPENDENTS();
+  __shared__ __align__(16) float As[BK][BM + 4];
+  __shared__ __align__(16) float Bs[BK][BN + 4];
+  __shared__ double red[4][NT / 32];
+  __shared__ int off[GROUP_MAX_RUNS + 1];
+  const int nr = g.nruns < GROUP_MAX_RUNS ? g.nruns : GROUP_MAX_RUNS;
+  for (int r = threadIdx.x; r < nr; r += NT) {
+    const Dev& s = g.runs[r].s;
+    off[r + 1] = MODE == 0 ? ((s.b + BM - 1) / BM) * (*s.ntiles) : *s.nwpairs;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    off[0] = 0;
+    for (int r = 0; r < nr; ++r) off[r + 1] += off[r];
+  }
+  __syncthreads();
+  const int total = off[nr];
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    int lo = 0, hi = nr;                         // the run r with off[r] <= w < off[r + 1]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (off[mid] <= w) lo = mid;
+      else hi = mid;
+    }
+    const Dev& s = g.runs[lo].s;
+    if constexpr (MODE == 0) dist_simt_item<F>(s, s.b, (s.b + BM - 1) / BM, w - off[lo], As, Bs);
+    else wgram_simt_item<F>(s, w - off[lo], As, Bs, red);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_dist_simt(const Dev& s, int rows, cudaStream_t st) {
@@ -232,6 +310,22 @@ cudaError_t launch_wgram(const Dev& s, cudaStream_t st) {
     default: return launch_pdl(k_wgram_simt<FORM_BF16X3>, dim3(blocks), dim3(NT), 0, st, s);
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_group_simt(const GroupPhase& g, int mode, int form, int blocks, cudaStream_t st) {
+  const dim3 grid(blocks > 0 ? blocks : 1), block(NT);
+  if (mode == 0) {
+    switch (form) {
+      case FORM_FP32: return launch_pdl(k_group_simt<FORM_FP32, 0>, grid, block, 0, st, g);
+      case FORM_BF16: return launch_pdl(k_group_simt<FORM_BF16, 0>, grid, block, 0, st, g);
+      default: return launch_pdl(k_group_simt<FORM_BF16X3, 0>, grid, block, 0, st, g);
+    }
+  }
+  switch (form) {
+    case FORM_FP32: return launch_pdl(k_group_simt<FORM_FP32, 1>, grid, block, 0, st, g);
+    case FORM_BF16: return launch_pdl(k_group_simt<FORM_BF16, 1>, grid, block, 0, st, g);
+    default: return launch_pdl(k_group_simt<FORM_BF16X3, 1>, grid, block, 0, st, g);
+  }
 }
 
 }  // namespace kkm

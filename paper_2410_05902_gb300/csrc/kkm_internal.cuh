@@ -309,6 +309,35 @@ cudaError_t launch_tab_objective(const Dev& s, const TabBuf& q, const float* xn,
                                  cudaStream_t st);
 cudaError_t launch_mind_sum(const Dev& s, int rows, double scale, double* out, cudaStream_t st);  // scale * sum of mind
 
+// --------------------------------------------------------------- run groups
+// A run of a group as the group's launches see it: its four TMA descriptors
+// (tc_prepare's layout, used in place by the tcgen05 passes) and its Dev.
+struct alignas(64) GroupRun {
+  unsigned char maps[512];
+  Dev s;
+};
+static_assert(sizeof(GroupRun) % 64 == 0, "descriptors of consecutive runs stay 64-byte aligned");
+// One launch over several runs. The step phases: runs[r] owns blocks
+// [first[r], first[r + 1]) and each of them plays one block of that run's own
+// launch. The Gram passes read no `first`: they spread the runs' items over
+// the launch on the device (kkm_gram_tc.cuh, kkm_gram_simt.cu).
+struct GroupPhase {
+  const GroupRun* runs;   // device
+  const int32_t* first;   // device, nruns + 1 entries, non-decreasing, first[0] = 0
+  int32_t nruns;
+};
+cudaError_t launch_group_gather(const GroupPhase& g, int blocks, cudaStream_t st);
+cudaError_t launch_group_argmin(const GroupPhase& g, int blocks, cudaStream_t st);
+cudaError_t launch_group_sort_plan(const GroupPhase& g, int smem, cudaStream_t st);   // one block per run
+cudaError_t launch_group_move(const GroupPhase& g, int blocks, cudaStream_t st);
+cudaError_t launch_group_finalize(const GroupPhase& g, int blocks, cudaStream_t st);
+// distance pass (mode 0) or window pass (mode 1) of runs that share the form,
+// kernel kind and distance tile: tcgen05 (ctas persistent CTAs) ...
+cudaError_t launch_group_tc(const GroupPhase& g, int mode, int form, int kind, int tn, int ctas, cudaStream_t st);
+// ... or the FP32 CUDA-core passes
+cudaError_t launch_group_simt(const GroupPhase& g, int mode, int form, int blocks, cudaStream_t st);
+int sort_plan_smem(int k, int b);
+
 // ------------------------------------------------ full-batch kernel Lloyd
 // The Gram view's Dev (xb*: every row of X in the operand form, y*: the
 // support buffer of X sorted by center) plus these buffers (kkm_lloyd.cu).

@@ -233,18 +233,22 @@ __device__ __forceinline__ void gather_one(const Dev& s, const int32_t* __restri
 // staging reads nothing finalize writes (it loads the weights after its own
 // wait, which returns once this kernel, and so finalize, has completed).
 // Then the wait and the clear of fin_pending.
-__global__ void k_gather_batch(Dev s, const int32_t* __restrict__ idx, int rotated) {
+__device__ __forceinline__ void gather_body(const Dev& s, const int32_t* __restrict__ idx, int rotated, int bid) {
   if (!rotated) {
     KKM_GRID_DEP_WAIT();
     KKM_LAUNCH_DEPENDENTS();
   }
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int warp = (bid * blockDim.x + threadIdx.x) >> 5;
   if (warp < s.b) gather_one(s, idx, warp);
   if (rotated) {
     KKM_LAUNCH_DEPENDENTS();
     KKM_GRID_DEP_WAIT();
-    if (blockIdx.x == 0 && threadIdx.x == 0) *s.fin_pending = 0;
+    if (bid == 0 && threadIdx.x == 0) *s.fin_pending = 0;
   }
+}
+
+__global__ void k_gather_batch(Dev s, const int32_t* __restrict__ idx, int rotated) {
+  gather_body(s, idx, rotated, blockIdx.x);
 }
 
 __global__ void k_gather_query(Dev s, const float* __restrict__ Q, int64_t ldq, int rows) {
@@ -268,10 +272,9 @@ __global__ void k_gather_query(Dev s, const float* __restrict__ Q, int64_t ldq, 
 // before it adds anything, so a row costs a few memory latencies.
 constexpr int AM_WARPS = 16;
 
-__global__ void __launch_bounds__(32 * AM_WARPS) k_argmin(Dev s, int rows, const int32_t* __restrict__ forced,
-                                                          int32_t* __restrict__ assign_out,
-                                                          float* __restrict__ mind_out,
-                                                          float* __restrict__ dist_out, int update) {
+__device__ __forceinline__ void argmin_body(const Dev& s, int rows, const int32_t* __restrict__ forced,
+                                            int32_t* __restrict__ assign_out, float* __restrict__ mind_out,
+                                            float* __restrict__ dist_out, int update, int bid) {
   // Before the wait: the tile tables, the center norms, the batch rows' norms
   // and the forced assignments. They come from kernels that completed before
   // this one was launched (it is launched once the distance pass has passed
@@ -286,7 +289,7 @@ __global__ void __launch_bounds__(32 * AM_WARPS) k_argmin(Dev s, int rows, const
     c_norm[j] = s.cnorm32[j];
   }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int x = blockIdx.x * 32 + lane;
+  const int x = bid * 32 + lane;
   const bool live = x < rows;
   const int xr = live ? x : 0;
   const float kxx = (float)kernel_self(s.kind, (double)s.xbn[xr], s.coef0, s.degree);
@@ -358,6 +361,13 @@ __global__ void __launch_bounds__(32 * AM_WARPS) k_argmin(Dev s, int rows, const
   }
 }
 
+__global__ void __launch_bounds__(32 * AM_WARPS) k_argmin(Dev s, int rows, const int32_t* __restrict__ forced,
+                                                          int32_t* __restrict__ assign_out,
+                                                          float* __restrict__ mind_out,
+                                                          float* __restrict__ dist_out, int update) {
+  argmin_body(s, rows, forced, assign_out, mind_out, dist_out, update, blockIdx.x);
+}
+
 __device__ int tile_count(const Dev& s, int& head, int& size);
 __device__ void tiles_write(const Dev& s, int first, int nt, int head, int size, int total);
 
@@ -365,7 +375,7 @@ __device__ void tiles_write(const Dev& s, int first, int nt, int head, int size,
 // alpha_i^j, <C_j, cm(B_j)>, and the per-center window plan: compaction,
 // block push, the drops of Eq. (1), C_1 retirement, and the tile pairs of the
 // norm-recurrence Gram pass.
-__global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out, int set_pending) {
+__device__ __forceinline__ void sort_plan_body(const Dev& s, double* obj_out, int set_pending) {
   KKM_GRID_DEP_WAIT();
   KKM_LAUNCH_DEPENDENTS();   // the next kernel waits at its top (or only stages earlier steps' data)
   extern __shared__ __align__(16) unsigned char smem[];
@@ -614,19 +624,23 @@ __global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out, int 
   }
 }
 
+__global__ void __launch_bounds__(1024) k_sort_plan(Dev s, double* obj_out, int set_pending) {
+  sort_plan_body(s, obj_out, set_pending);
+}
+
 // The append of the new blocks and the compaction of the windows that need
 // it, one warp per row: work items 0..b-1 append batch row perm[w] at the end
 // of its center's window; items b.. copy the compacting windows' rows down to
 // row 0, all compactions laid end to end (comp_off). Sources and destinations
 // never overlap (see the capacity argument in kkm_internal.cuh).
-__global__ void k_move(Dev s) {
+__device__ __forceinline__ void move_body(const Dev& s, int bid, int nblk) {
   KKM_GRID_DEP_WAIT();
   KKM_LAUNCH_DEPENDENTS();   // the next kernel waits at its top (or only stages earlier steps' data)
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
-  const int nwarps = gridDim.x * wpb;
+  const int nwarps = nblk * wpb;
   const int items = s.b + *s.comp_total;
-  for (int w = blockIdx.x * wpb + (threadIdx.x >> 5); w < items; w += nwarps) {
+  for (int w = bid * wpb + (threadIdx.x >> 5); w < items; w += nwarps) {
     if (w < s.b) {
       const int x = s.perm[w];
       const int64_t dst = s.mvdst[w];              // the sort/plan's destination
@@ -657,6 +671,8 @@ __global__ void k_move(Dev s) {
     }
   }
 }
+
+__global__ void k_move(Dev s) { move_body(s, blockIdx.x, gridDim.x); }
 
 // Tile list of the distance pass (block of 1024, k <= 1024). Thread j < k
 // passes the window [head, head + size) of center j. Tiles start at head
@@ -737,7 +753,7 @@ __global__ void __launch_bounds__(1024) k_build_tiles(Dev s) {
 // The scalar chain has no FP64 division or square root: 1/b_j and the beta
 // rate sqrt(b_j / b) come from a table the host fills at kkm_init, and the
 // thread's operands are loaded before the window sums so their latency overlaps.
-__global__ void __launch_bounds__(256) k_finalize(Dev s, int if_pending) {
+__device__ __forceinline__ void finalize_body(const Dev& s, int if_pending, int bid) {
   // Before the wait: the pending flag, the plan, the running count, the old
   // norm, the rate table, the pair range and the sort/plan's partials of
   // <phi(x), C_j>. Their writers (the sort/plan, the gather, earlier weight
@@ -745,7 +761,7 @@ __global__ void __launch_bounds__(256) k_finalize(Dev s, int if_pending) {
   // the kernel ahead (the window pass, or a full dependency) has passed its
   // own wait. Only the window-pass sums need the wait, and no block returns
   // before it, so this kernel never completes ahead of the one it follows.
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, j = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, j = bid;
   const bool skip = if_pending && *s.fin_pending == 0;   // nothing to apply (the first step, or after a flush)
   const Plan P = s.plan[j];
   double ncum_j = 0.0, cn_old = 0.0, inv_n = 0.0, beta = 0.0;
@@ -839,6 +855,8 @@ __global__ void __launch_bounds__(256) k_finalize(Dev s, int if_pending) {
     s.w32[base + r] = wnew32;
   }
 }
+
+__global__ void __launch_bounds__(256) k_finalize(Dev s, int if_pending) { finalize_body(s, if_pending, blockIdx.x); }
 
 // Seeds every window with C_1^j = phi(x_{init_idx[j]}), weight 1, ||C||^2 = K(x,x).
 __global__ void k_init_centers(Dev s, const int32_t* __restrict__ init_idx) {
@@ -1187,6 +1205,50 @@ __global__ void __launch_bounds__(256) k_tab_objective(Dev s, TabBuf q, const fl
     for (int v = 0; v < 8; ++v) t += red[v];
     blk[blockIdx.x] = t;
   }
+}
+
+// ------------------------------------------------------------------------
+// Run groups: one launch per step phase for every run of a group. Block b of
+// such a launch belongs to the run r with first[r] <= b < first[r + 1] and
+// plays block b - first[r] of that run's own launch (the same block count as
+// a single-run launch, or any count for the grid-stride phases), so every run
+// computes exactly what its own launches would.
+__device__ __forceinline__ int group_run(const GroupPhase& g, int& local, int& nblk) {
+  const int r = last_le(g.first, g.nruns, (int)blockIdx.x);
+  local = (int)blockIdx.x - g.first[r];
+  nblk = g.first[r + 1] - g.first[r];
+  return r;
+}
+
+__global__ void k_group_gather(GroupPhase g) {
+  int local, nblk;
+  const int r = group_run(g, local, nblk);
+  gather_body(g.runs[r].s, nullptr, 0, local);
+}
+
+__global__ void __launch_bounds__(32 * AM_WARPS) k_group_argmin(GroupPhase g) {
+  int local, nblk;
+  const int r = group_run(g, local, nblk);
+  const Dev& s = g.runs[r].s;
+  argmin_body(s, s.b, nullptr, nullptr, nullptr, nullptr, 1, local);
+}
+
+__global__ void __launch_bounds__(1024) k_group_sort_plan(GroupPhase g) {
+  int local, nblk;
+  const int r = group_run(g, local, nblk);
+  sort_plan_body(g.runs[r].s, nullptr, 0);
+}
+
+__global__ void k_group_move(GroupPhase g) {
+  int local, nblk;
+  const int r = group_run(g, local, nblk);
+  move_body(g.runs[r].s, local, nblk);
+}
+
+__global__ void __launch_bounds__(256) k_group_finalize(GroupPhase g) {
+  int local, nblk;
+  const int r = group_run(g, local, nblk);
+  finalize_body(g.runs[r].s, 0, local);
 }
 
 // ------------------------------------------------------------------------
@@ -1565,6 +1627,30 @@ cudaError_t launch_lloyd_assign(const Dev& g, const LloydBuf& L, bool first, cud
 cudaError_t launch_lloyd_dist(const Dev& g, const LloydBuf& L, float* out, cudaStream_t st) {
   k_lloyd_dist<<<(unsigned)((g.n + 255) / 256), 256, 0, st>>>(g, L, out);
   return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- run groups
+cudaError_t launch_group_gather(const GroupPhase& g, int blocks, cudaStream_t st) {
+  return launch_pdl(k_group_gather, dim3(blocks), dim3(256), 0, st, g);
+}
+
+cudaError_t launch_group_argmin(const GroupPhase& g, int blocks, cudaStream_t st) {
+  return launch_pdl(k_group_argmin, dim3(blocks), dim3(32 * AM_WARPS), 0, st, g);
+}
+
+cudaError_t launch_group_sort_plan(const GroupPhase& g, int smem, cudaStream_t st) {
+  static std::atomic<uint64_t> attr{0};
+  cudaError_t e = smem_limit_once(k_group_sort_plan, 200 * 1024, attr);
+  if (e != cudaSuccess) return e;
+  return launch_pdl(k_group_sort_plan, dim3(g.nruns), dim3(1024), smem, st, g);
+}
+
+cudaError_t launch_group_move(const GroupPhase& g, int blocks, cudaStream_t st) {
+  return launch_pdl(k_group_move, dim3(blocks), dim3(256), 0, st, g);
+}
+
+cudaError_t launch_group_finalize(const GroupPhase& g, int blocks, cudaStream_t st) {
+  return launch_pdl(k_group_finalize, dim3(blocks), dim3(256), 0, st, g);
 }
 
 }  // namespace kkm

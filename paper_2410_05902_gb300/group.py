@@ -2,8 +2,9 @@
 with per-run kernel variants picked by measurement.
 
 ``Group(runs)`` wraps kkm_group_*: one ``step()`` advances every run by one
-iteration; from the second step on that is a single graph launch whose
-per-run branches run concurrently. ``autotune`` picks, for one run shape,
+iteration, as one launch per step phase over all runs (and one per Gram pass
+and class of runs that share a kernel template); from the second step on the
+step is replayed as one CUDA graph. ``autotune`` picks, for one run shape,
 the fastest of the candidate variants (precision form and distance-pass
 tile width) by timing graph-replayed steps with CUDA events; every
 candidate computes at FP32-level accuracy (FP32 or split-BF16 products).
@@ -45,6 +46,17 @@ class Group:
 
     def sync(self):
         self._check(load().kkm_group_sync(self._g))
+
+    def set_chains(self, chains: int):
+        """Before the first step: step the runs as `chains` concurrent chains of
+        per-phase launches, or (chains = 0) each run on a graph branch of its own."""
+        self._check(load().kkm_group_set_chains(self._g, int(chains)))
+
+    def launches(self, reset: bool = False) -> tuple[int, int]:
+        """(kernels the group's steps launched, kernels per group step)."""
+        la, per = ctypes.c_int64(), ctypes.c_int32()
+        self._check(load().kkm_group_launches(self._g, ctypes.byref(la), ctypes.byref(per), int(reset)))
+        return la.value, per.value
 
     def close(self):
         if getattr(self, "_g", None) is not None and self._g.value:

@@ -95,6 +95,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "kkm_set_cum_counts": ([_P, _P], c_int32),
         "kkm_group_create": ([POINTER(_P), _P, c_int32, _P], c_int32),
         "kkm_group_step": ([_P], c_int32),
+        "kkm_group_launches": ([_P, POINTER(c_int64), POINTER(c_int32), c_int32], c_int32),
+        "kkm_group_set_chains": ([_P, c_int32], c_int32),
         "kkm_group_sync": ([_P], c_int32),
         "kkm_group_last_error": ([_P], ctypes.c_char_p),
         "kkm_group_destroy": ([_P], c_int32),
