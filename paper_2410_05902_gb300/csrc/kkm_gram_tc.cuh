@@ -11,7 +11,7 @@
 // pairs (hi,hi), (hi,lo), (lo,hi) into the same accumulator.
 //
 // Distance pass (mode 0): an item is (128-row batch tile, TNV-row support tile
-// of one center; TNV = 128 by default, 64 or 256 on request), and it writes
+// of one center; TNV = 256 by default, 64 or 128 on request), and it writes
 // part[tile][x] = sum_y w_y K(x, y), one partial per row and tile.
 // Window pass (mode 1, the norm recurrence of Sec. 4 with the drops of
 // Eq. (1)): an item is (128 support rows, 128 support rows) of one center,
@@ -35,9 +35,10 @@
 // team and takes every fourth item whole; with two (256-column tiles) two
 // groups form a team, take every other item and split its columns, each
 // writing its own partial. Either way every waiter on a barrier sees each of
-// its phases in order. A CTA with fewer items than teams runs every item on
-// all four groups, each on a quarter of the columns, and the groups' sums
-// meet in shared memory.
+// its phases in order. A run with fewer than NTEAM items per SM runs every
+// item on all four groups, each on a quarter of the columns, and the groups'
+// sums meet in shared memory (chosen per run, so that a run's results do not
+// depend on how a launch splits its items).
 //
 // Gaussian kernel values without a per-element row term: with rc = -log2(e)
 // ||x||^2 / kappa and t = (2 log2(e) / kappa) g - log2(e) ||y||^2 / kappa,
