@@ -487,6 +487,17 @@ kkm_status kkm_distances_noalloc(const float* Q, int64_t m, int64_t ldq, int32_t
                                  float* dist_out, int32_t* assign_out, void* stream);
 const char* kkm_noalloc_last_error(void);
 
+/* kkm_probe_bounded_wait -- the failure-detection path of the tcgen05 passes
+ * on the current device. The paper has no counterpart. One thread waits on a
+ * shared-memory mbarrier (the kind every role of the passes waits on) with the
+ * passes' bounded wait, limited to limit_ns (1e3 .. 5e9). With arrive = 0
+ * nothing arrives, so the wait runs out and the call returns KKM_ETIMEOUT, as
+ * a step whose pass gave up reports through the context's status; with
+ * arrive = 1 the thread arrives first and the call returns KKM_OK. Allocates
+ * and frees one int of device memory and synchronises the stream. KKM_EINVAL
+ * for arguments out of range (checked before any CUDA call). */
+kkm_status kkm_probe_bounded_wait(int64_t limit_ns, int32_t arrive, void* stream);
+
 /* kkm_probe_unit_rate -- measured issue rate of one arithmetic unit on the
  * current device. The paper has no counterpart: it supplies the denominators
  * of the distance pass's roofline (the pass's epilogue spends one MUFU

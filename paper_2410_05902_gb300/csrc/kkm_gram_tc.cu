@@ -44,7 +44,25 @@ cudaError_t launch_mode(const Dev& s, const void* maps_in, int rows, cudaStream_
   }
 }
 
+// The passes' failure-detection path: thread 0 waits on an mbarrier of one
+// arrival with the passes' bounded wait. With arrive = 0 nothing arrives, so
+// the wait runs out after limit_ns; out[0] = 1 if it did.
+__global__ void k_wait_probe(uint64_t limit_ns, int arrive, int* out) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (arrive) mbar_arrive(&bar);
+  out[0] = mbar_wait(&bar, 0, limit_ns) ? 0 : 1;
+  mbar_inval(&bar);
+}
+
 }  // namespace
+
+cudaError_t launch_wait_probe(uint64_t limit_ns, int arrive, int* out, cudaStream_t st) {
+  k_wait_probe<<<1, 32, 0, st>>>(limit_ns, arrive, out);
+  return cudaGetLastError();
+}
 
 // Tensor maps of the batch rows and the support store: 2-D tensors of ld
 // columns (BF16, or FP32 for the TF32 form), boxes of one 128-byte row of

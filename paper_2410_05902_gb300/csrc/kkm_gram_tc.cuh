@@ -244,13 +244,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
 }
 
 // Waits for the phase of parity `parity` to complete; false after WAIT_LIMIT_NS.
-__device__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+__device__ bool mbar_wait(uint64_t* b, uint32_t parity, uint64_t limit_ns = WAIT_LIMIT_NS) {
   if (mbar_try_wait(b, parity)) return true;
   const uint64_t t0 = globaltimer();
   while (true) {
     for (int i = 0; i < 64; ++i)
       if (mbar_try_wait(b, parity)) return true;
-    if (globaltimer() - t0 > WAIT_LIMIT_NS) return false;
+    if (globaltimer() - t0 > limit_ns) return false;
   }
 }
 

@@ -374,6 +374,8 @@ cudaError_t launch_lloyd_dist(const Dev& g, const LloydBuf& L, float* out, cudaS
 // tensor-core passes (BF16, split-BF16 and TF32 forms)
 // maps: 512 bytes, 64-byte aligned, holding the four CUtensorMap of the passes
 cudaError_t tc_prepare(Dev& s, void* maps);
+// one bounded mbarrier wait (the passes' own), limited to limit_ns; out[0] = 1 when it ran out
+cudaError_t launch_wait_probe(uint64_t limit_ns, int arrive, int* out, cudaStream_t st);
 // partials the distance pass writes per tile of tn support rows (Dev::ppt)
 int tc_parts_per_tile(int tn);
 // stage_early: the kernel just ahead on `st` (the batch gather, or this pass

@@ -129,3 +129,19 @@ KKM_API kkm_status kkm_probe_unit_rate(int32_t op, int64_t iters, double* per_cl
   *per_second = ms > 0.0f ? per_block * sms / (ms * 1e-3) : 0.0;
   return KKM_OK;
 }
+
+// The failure-detection path of the tcgen05 passes: one bounded mbarrier wait
+// (the passes' own routine) that nothing satisfies when arrive == 0.
+KKM_API kkm_status kkm_probe_bounded_wait(int64_t limit_ns, int32_t arrive, void* stream) {
+  if (limit_ns < 1000 || limit_ns > 5000000000LL || (arrive != 0 && arrive != 1)) return KKM_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int* d_out = nullptr;
+  int h_out = -1;
+  cudaError_t e = cudaMalloc(&d_out, sizeof(int));
+  if (e == cudaSuccess) e = kkm::launch_wait_probe((uint64_t)limit_ns, arrive, d_out, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h_out, d_out, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (d_out) cudaFree(d_out);
+  if (e != cudaSuccess) return KKM_ECUDA;
+  return h_out == 1 ? KKM_ETIMEOUT : (h_out == 0 ? KKM_OK : KKM_ECUDA);
+}

@@ -87,6 +87,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "kkm_noalloc_last_error": ([], ctypes.c_char_p),
         "kkm_form_supported": ([c_int32, c_int32, c_int32], c_int32),
         "kkm_probe_unit_rate": ([c_int32, c_int64, POINTER(c_double), POINTER(c_double), _P], c_int32),
+        "kkm_probe_bounded_wait": ([c_int64, c_int32, _P], c_int32),
         "kkm_destroy": ([_P], c_int32),
         "kkm_step_eval": ([_P, _P, _P, _P], c_int32),
         "kkm_kmeanspp": ([_P, c_int64, c_int32, c_int64, c_int32, POINTER(kkm_kernel), c_uint64, _P, _P], c_int32),
@@ -302,6 +303,11 @@ def kkm_lloyd_info(run) -> tuple[int, int, int]:
 
 def kkm_lloyd_destroy(run) -> None:
     load().kkm_lloyd_destroy(run)
+
+
+def kkm_probe_bounded_wait(limit_ns: int, arrive: bool, stream: int | None = None) -> int:
+    """Status of one bounded mbarrier wait of the tcgen05 passes (KKM_ETIMEOUT when nothing arrives)."""
+    return load().kkm_probe_bounded_wait(int(limit_ns), 1 if arrive else 0, stream)
 
 
 def kkm_probe_unit_rate(op: int, iters: int, stream: int | None = None) -> tuple[float, float]:

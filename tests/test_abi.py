@@ -188,3 +188,8 @@ def test_lloyd_calls_reject_a_null_handle(lib):
     assert lib.kkm_lloyd_read(None, None, None, None) == kkm.KKM_EINVAL
     assert lib.kkm_lloyd_distances(None, None) == kkm.KKM_EINVAL
     assert lib.kkm_lloyd_destroy(None) == kkm.KKM_OK
+
+
+@pytest.mark.parametrize("limit,arrive", [(10, 0), (6_000_000_000, 0), (1_000_000, 2)])
+def test_bounded_wait_probe_rejects_bad_arguments(lib, limit, arrive):
+    assert lib.kkm_probe_bounded_wait(limit, arrive, None) == kkm.KKM_EINVAL
