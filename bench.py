@@ -708,33 +708,40 @@ def run_batching(args):
     for _ in range(args.warmup):
         g.step()
     g.sync()
-    stream = torch.cuda.current_stream(dev)
     clocks = Clocks(0).ready()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    # the group orders its work on a stream of its own: bracket it with syncs
-    torch.cuda.synchronize(dev)
+
+    # the group orders its work on a stream of its own: bracket each block of
+    # exactly K group steps with syncs; blocks for about args.min_time seconds
+    def block():
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            g.step()
+        g.sync()
+        return time.perf_counter() - t0
+
+    first = block()
+    nblk = max(3, int(args.min_time / max(first, 1e-6)))
     g.launches(reset=True)
     clocks.start()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        g.step()
-    g.sync()
-    wall = time.perf_counter() - t0
+    walls = [block() for _ in range(nblk)]
     clk = clocks.stop()
     launches, launches_per_step = g.launches(reset=True)
+    wall = statistics.median(walls)
     per_step = sum(sp.b * sp.k for sp in specs)
     value = per_step * args.steps / wall
     print(json.dumps({
         "metric": "batched sweep: sum over 64 runs of b*k batch-point x center distances/s per iteration on 1 GB300",
         "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "mixed (autotuned per class: f32 / bf16x3)", "data": "synthetic",
+        "vs_baseline": None, "dtype": "mixed (autotuned per class: f32 / bf16x3 / tf32)", "data": "synthetic",
         "config": {"workload": "batching: 64 runs, n ~ U[5000, 200000], d in {16, 64, 256}, k ~ U[5, 200], "
                                "b in {256, 512, 1024, 2048} (seed 777), isotropic mixtures with k_true = k, "
                                "Gaussian kernel kappa = 2 sigma_median^2 per run, tau = 200, beta rate",
-                   "timing": "host wall clock around the timed group steps with a device sync on both sides "
-                             "(every iteration of all runs is one CUDA graph launch on the group's stream: one "
-                             "kernel per step phase over all 64 runs, one per Gram pass and class of runs)",
+                   "timing": f"host wall clock around each of {nblk} blocks of exactly {args.steps} group steps "
+                             "with a device sync on both sides; ms_per_step from the median block (every "
+                             "iteration of all runs is one CUDA graph launch on the group's stream)",
+                   "block_ms": {"median": 1e3 * wall, "min": 1e3 * min(walls), "max": 1e3 * max(walls)},
                    "launches_per_group_step": launches_per_step, "chains": chains,
                    "chain_ms_per_step": chain_ms,
                    "distances_per_step": per_step, "state_prep_iters": PREP_ITERS,
