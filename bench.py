@@ -27,6 +27,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -662,6 +663,10 @@ def run_batching(args):
         sigma = inputs.median_sigma(X, seed=1)
         data.append((torch.from_numpy(X).to(dev), 2.0 * sigma * sigma, inputs.init_indices(sp.n, sp.k, seed=100 + i)))
         del X
+    def fill_iters(sp):   # iterations until a run's windows are full, with a margin for uneven centers
+        return int(1.25 * math.ceil(200 * sp.k / sp.b)) + 10
+
+    prep = max(PREP_ITERS, max(fill_iters(sp) for sp in specs))
     # autotune once per (d, b) class on its median-k run
     classes = {}
     for i, sp in enumerate(specs):
@@ -671,7 +676,10 @@ def run_batching(args):
         rep = sorted(idx, key=lambda i: specs[i].k)[len(idx) // 2]
         sp = specs[rep]
         Xd, kappa, init = data[rep]
-        best, times = autotune(Xd, sp.k, sp.b, "gaussian", kappa, 200, init, warm=args.warmup + 12, iters=8)
+        # past the point where the windows hold tau rows per center (tau k / b
+        # iterations on average), so that the variants are timed on full supports
+        best, times = autotune(Xd, sp.k, sp.b, "gaussian", kappa, 200, init,
+                               warm=max(args.warmup + 12, fill_iters(sp)), iters=8)
         choice[key] = best
         tune[f"d={key[0]},b={key[1]}"] = {"choice": f"{best[0]}/tile{best[1] or 'default'}",
                                           "ms_per_step": {f"{p}/tile{t or 'default'}": round(v, 4)
@@ -685,7 +693,7 @@ def run_batching(args):
     # fill the windows, then time a few group steps per chain count (the
     # group-level half of the autotuner) and keep the fastest
     g = Group(runs)
-    for _ in range(PREP_ITERS):
+    for _ in range(prep):
         g.step()
     g.sync()
     g.close()
@@ -744,7 +752,7 @@ def run_batching(args):
                    "block_ms": {"median": 1e3 * wall, "min": 1e3 * min(walls), "max": 1e3 * max(walls)},
                    "launches_per_group_step": launches_per_step, "chains": chains,
                    "chain_ms_per_step": chain_ms,
-                   "distances_per_step": per_step, "state_prep_iters": PREP_ITERS,
+                   "distances_per_step": per_step, "state_prep_iters": prep,
                    "l2": "inputs larger than L2 (the 64 datasets hold about "
                          f"{sum(int(d[0].numel()) for d in data) * 4 / 1e9:.1f} GB)"},
         "autotune": tune, "gpu_launches": launches, "clocks": clk,
