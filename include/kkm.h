@@ -261,6 +261,24 @@ kkm_status kkm_graph_enable(kkm_ctx* ctx, int32_t enable);
 kkm_status kkm_step_host(kkm_ctx* ctx, const int32_t* batch_idx, int32_t* assign_out,
                          double* batch_obj_out);
 
+/* kkm_steps_host -- n iterations of Algorithm 2 with host buffers, as n calls
+ * of kkm_step_host would run them, without a host round trip per step.
+ *   batch_idx     : host, n x b indices (step i's batch at i*b), or NULL for
+ *                   the built-in sampler.
+ *   assign_out    : host, n x b int32 (step i's assignments at i*b), or NULL.
+ *   batch_obj_out : host, n doubles f_{B_i}(C_i), or NULL.
+ * Steps go in chunks of 16 through two staging slots of the context in
+ * page-locked, device-mapped host memory: while the device runs one chunk
+ * (one CUDA graph replay when graphs are enabled), the call copies the next
+ * chunk's indices in and the previous chunk's results out. Every step's
+ * indices and results still cross the CPU-GPU link. A context's first step,
+ * and every step while timing is enabled, go through kkm_step_host. Returns
+ * once all n steps are done, after the device status check. n < 0 is
+ * KKM_EINVAL; an untruncated run (tau = 0) may not pass max_iters. On a
+ * failure the outputs are unspecified, and no staged work is left in flight. */
+kkm_status kkm_steps_host(kkm_ctx* ctx, int64_t n, const int32_t* batch_idx, int32_t* assign_out,
+                          double* batch_obj_out);
+
 /* kkm_assign -- nearest centers of arbitrary query points (the assignment
  * rule of Algorithms 1/2, applied to the current centers without updating
  * them).

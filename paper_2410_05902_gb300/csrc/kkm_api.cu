@@ -21,6 +21,9 @@
 
 using kkm::Dev;
 
+// Steps of one kkm_steps_host chunk (one graph replay per chunk).
+constexpr int HOST_CHUNK = 16;
+
 struct kkm_ctx {
   Dev s{};
   cudaStream_t stream = nullptr;
@@ -45,6 +48,16 @@ struct kkm_ctx {
   int32_t* d_hassign = nullptr;
   double* d_hobj = nullptr;
   bool host_pending = false;         // a kkm_step_host call queued work it has not yet waited for
+  // kkm_steps_host's staging: two slots of HOST_CHUNK steps each, page-locked
+  // and device-mapped like h_stage. A slot holds, for step i of its chunk, the
+  // indices at i * nb4 and the assignments at (HOST_CHUNK + i) * nb4, then the
+  // chunk's f_B values. One graph per slot and index source replays a chunk.
+  void* h_qstage = nullptr;
+  char* h_qslot[2] = {nullptr, nullptr};
+  char* d_qslot[2] = {nullptr, nullptr};
+  size_t q_nb4 = 0;
+  cudaEvent_t qdone[2] = {nullptr, nullptr};
+  cudaGraphExec_t gexec_q[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [slot][host indices]
   bool fin_pending = false;          // the last step's k_finalize is still to run (see flush)
   double* d_objpart = nullptr;
   double* d_obj2 = nullptr;   // kkm_fit: f_B before and after the update
@@ -104,6 +117,16 @@ cudaError_t dalloc(kkm_ctx* c, T** p, size_t count) {
 void free_all(kkm_ctx* c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   c->gexec = nullptr;
+  for (int q = 0; q < 2; ++q) {
+    for (int h = 0; h < 2; ++h) {
+      if (c->gexec_q[q][h]) cudaGraphExecDestroy(c->gexec_q[q][h]);
+      c->gexec_q[q][h] = nullptr;
+    }
+    if (c->qdone[q]) cudaEventDestroy(c->qdone[q]);
+    c->qdone[q] = nullptr;
+  }
+  if (c->h_qstage) cudaFreeHost(c->h_qstage);
+  c->h_qstage = nullptr;
   if (c->gexec_multi) cudaGraphExecDestroy(c->gexec_multi);
   c->gexec_multi = nullptr;
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -430,6 +453,22 @@ KKM_API kkm_status kkm_init(kkm_ctx** out, const float* X, int64_t n, int32_t d,
     c->d_hbatch = reinterpret_cast<int32_t*>(db);
     c->d_hassign = reinterpret_cast<int32_t*>(db + nb4);
     c->d_hobj = reinterpret_cast<double*>(db + 2 * nb4);
+    // kkm_steps_host's two chunk slots and their completion events
+    const size_t slot = (2 * HOST_CHUNK * nb4 + 8 * HOST_CHUNK + 127) & ~(size_t)127;
+    e = cudaHostAlloc(&c->h_qstage, 2 * slot, cudaHostAllocMapped);
+    dev = nullptr;
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&dev, c->h_qstage, 0);
+    for (int q = 0; q < 2 && e == cudaSuccess; ++q) e = cudaEventCreateWithFlags(&c->qdone[q], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      c->err = std::string("mapped host allocation (chunk staging): ") + cudaGetErrorString(e);
+      return bail(KKM_ENOMEM);
+    }
+    std::memset(c->h_qstage, 0, 2 * slot);
+    c->q_nb4 = nb4;
+    for (int q = 0; q < 2; ++q) {
+      c->h_qslot[q] = static_cast<char*>(c->h_qstage) + q * slot;
+      c->d_qslot[q] = static_cast<char*>(dev) + q * slot;
+    }
   }
   c->objpart_len = 1024;
   ALLOC(c->d_objpart, c->objpart_len);
@@ -680,6 +719,131 @@ KKM_API kkm_status kkm_step_host(kkm_ctx* c, const int32_t* batch_idx, int32_t* 
   if (assign_out) std::memcpy(assign_out, c->h_hassign, (size_t)b * sizeof(int32_t));
   if (batch_obj_out) *batch_obj_out = *c->h_hobj;
   return KKM_OK;
+}
+
+// kkm_steps_host: chunks of HOST_CHUNK steps alternate between the two
+// staging slots. While the device runs one chunk the host copies the next
+// chunk's indices in and the results of the chunk before out, so the steps
+// meet no host round trip. A slot is reused only after its event shows the
+// chunk that used it done.
+namespace {
+int32_t* q_idx(char* slot, size_t nb4, int i) { return reinterpret_cast<int32_t*>(slot + (size_t)i * nb4); }
+int32_t* q_asg(char* slot, size_t nb4, int i) {
+  return reinterpret_cast<int32_t*>(slot + (size_t)(HOST_CHUNK + i) * nb4);
+}
+double* q_obj(char* slot, size_t nb4, int i) {
+  return reinterpret_cast<double*>(slot + 2 * (size_t)HOST_CHUNK * nb4) + i;
+}
+
+// Queues m steps reading slot q (indices from it when host_idx, else the
+// built-in sampler) and writing their results there.
+kkm_status q_enqueue(kkm_ctx* c, int q, int m, bool host_idx) {
+  const size_t nb4 = c->q_nb4;
+  char* d = c->d_qslot[q];
+  if (c->graph_on && m == HOST_CHUNK) {
+    cudaGraphExec_t& ge = c->gexec_q[q][host_idx ? 1 : 0];
+    if (!ge) {
+      if (!c->cap_stream)
+        KKM_CU(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "capture stream");
+      KKM_CU(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+      kkm_status st = KKM_OK;
+      for (int i = 0; i < HOST_CHUNK && st == KKM_OK; ++i)
+        st = enqueue_step(c, c->cap_stream, host_idx ? q_idx(d, nb4, i) : nullptr, nullptr, q_asg(d, nb4, i),
+                          nullptr, q_obj(d, nb4, i), false, !c->tab);
+      cudaGraph_t g = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+      if (st != KKM_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+      }
+      if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+      const cudaError_t ei = cudaGraphInstantiate(&ge, g, 0);
+      cudaGraphDestroy(g);
+      if (ei != cudaSuccess) {
+        ge = nullptr;
+        return cuda_fail(c, ei, "graph instantiate");
+      }
+    }
+    KKM_CU(cudaGraphLaunch(ge, c->stream), "graph launch");
+  } else {
+    for (int i = 0; i < m; ++i) {
+      const kkm_status st = enqueue_step(c, c->stream, host_idx ? q_idx(d, nb4, i) : nullptr, nullptr,
+                                         q_asg(d, nb4, i), nullptr, q_obj(d, nb4, i), false, !c->tab);
+      if (st != KKM_OK) return st;
+      ++c->eager_steps;
+    }
+  }
+  c->launches += 7 * m;
+  c->iteration += m;
+  c->fin_pending = !c->tab;
+  return KKM_OK;
+}
+}  // namespace
+
+KKM_API kkm_status kkm_steps_host(kkm_ctx* c, int64_t n, const int32_t* batch_idx, int32_t* assign_out,
+                                  double* batch_obj_out) {
+  kkm_status st = check_usable(c);
+  if (st != KKM_OK) return st;
+  if (n < 0) return fail(c, KKM_EINVAL, "n must be >= 0");
+  if (c->s.tau == 0 && !c->tab && c->iteration - 1 + n > c->max_iters)
+    return fail(c, KKM_ESTATE, "untruncated run: n steps would pass max_iters");
+  const int b = c->s.b;
+  const size_t row = (size_t)b * sizeof(int32_t);
+  int64_t j = 0;
+  // a context's first step, and every step while timing is on, go one at a
+  // time through kkm_step_host (the first step runs eagerly, as kkm_step's does)
+  while (j < n && (c->eager_steps == 0 || c->timing)) {
+    st = kkm_step_host(c, batch_idx ? batch_idx + j * b : nullptr, assign_out ? assign_out + j * b : nullptr,
+                       batch_obj_out ? batch_obj_out + j : nullptr);
+    if (st != KKM_OK) return st;
+    ++j;
+  }
+  if (c->host_pending) {
+    st = sync_and_check(c);
+    if (st != KKM_OK) return st;
+    c->host_pending = false;
+  }
+  int64_t first[2] = {0, 0};
+  int cnt[2] = {0, 0};
+  // waits for the chunk in slot q and copies its results out
+  auto drain = [&](int q) -> kkm_status {
+    if (cnt[q] == 0) return KKM_OK;
+    const cudaError_t e = cudaEventSynchronize(c->qdone[q]);
+    if (e != cudaSuccess) return cuda_fail(c, e, "chunk wait");
+    for (int i = 0; i < cnt[q]; ++i) {
+      if (assign_out) std::memcpy(assign_out + (first[q] + i) * b, q_asg(c->h_qslot[q], c->q_nb4, i), row);
+      if (batch_obj_out) batch_obj_out[first[q] + i] = *q_obj(c->h_qslot[q], c->q_nb4, i);
+    }
+    cnt[q] = 0;
+    return KKM_OK;
+  };
+  // on a failure nothing may still read or write the slots once the call returns
+  auto abort_with = [&](kkm_status s) {
+    cudaStreamSynchronize(c->stream);
+    return s;
+  };
+  int q = 0;
+  while (j < n) {
+    const int m = (int)std::min<int64_t>(HOST_CHUNK, n - j);
+    st = drain(q);
+    if (st != KKM_OK) return abort_with(st);
+    if (batch_idx)
+      for (int i = 0; i < m; ++i) std::memcpy(q_idx(c->h_qslot[q], c->q_nb4, i), batch_idx + (j + i) * b, row);
+    st = q_enqueue(c, q, m, batch_idx != nullptr);
+    if (st != KKM_OK) return abort_with(st);
+    const cudaError_t e = cudaEventRecord(c->qdone[q], c->stream);
+    if (e != cudaSuccess) return abort_with(cuda_fail(c, e, "chunk event"));
+    first[q] = j;
+    cnt[q] = m;
+    j += m;
+    q ^= 1;
+  }
+  // the device status first: results of a context that went bad are not reported
+  st = sync_and_check(c);
+  if (st != KKM_OK) return st;
+  st = drain(q);   // the older of the two chunks in flight
+  if (st == KKM_OK) st = drain(q ^ 1);
+  return st;
 }
 
 // Runs the distance pass and argmin over query rows in chunks of b rows.

@@ -67,6 +67,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
                       c_int32, POINTER(kkm_config), POINTER(c_int64), _P], c_int32),
         "kkm_step": ([_P, _P, _P, _P, _P, _P], c_int32),
         "kkm_step_host": ([_P, _P, _P, _P], c_int32),
+        "kkm_steps_host": ([_P, c_int64, _P, _P, _P], c_int32),
         "kkm_assign": ([_P, _P, c_int64, c_int64, _P, _P, _P], c_int32),
         "kkm_objective": ([_P, _P, c_int64, c_int64, POINTER(c_double)], c_int32),
         "kkm_objective_fwd": ([_P, _P, c_int64, c_int64, _P, c_double, _P, _P], c_int32),
@@ -155,6 +156,12 @@ def kkm_step(ctx, batch_idx: int | None, forced_assign: int | None, assign_out: 
 def kkm_step_host(ctx, batch_idx: np.ndarray | None, assign_out: np.ndarray | None,
                   batch_obj_out: np.ndarray | None) -> None:
     _check(load().kkm_step_host(ctx, _np_ptr(batch_idx), _np_ptr(assign_out), _np_ptr(batch_obj_out)), ctx)
+
+
+def kkm_steps_host(ctx, n: int, batch_idx: np.ndarray | None, assign_out: np.ndarray | None,
+                   batch_obj_out: np.ndarray | None) -> None:
+    _check(load().kkm_steps_host(ctx, int(n), _np_ptr(batch_idx), _np_ptr(assign_out), _np_ptr(batch_obj_out)),
+           ctx)
 
 
 def kkm_assign(ctx, Q: int, m: int, ldq: int, assign_out: int | None, mind_out: int | None,
@@ -428,6 +435,21 @@ class KKM:
         o = np.zeros(1, np.float64)
         kkm_step_host(self.ctx, bi, a, o)
         return a, float(o[0])
+
+    def steps_host(self, batch_idx: np.ndarray | None = None, n: int | None = None):
+        """n iterations with host buffers (batch_idx: n x b indices, or None and n
+        for the built-in sampler); returns (assignments n x b, f_B per step)."""
+        if batch_idx is None:
+            if n is None:
+                raise ValueError("give batch_idx or n")
+            bi = None
+        else:
+            bi = np.ascontiguousarray(batch_idx, dtype=np.int32).reshape(-1, self.b)
+            n = bi.shape[0]
+        a = np.zeros((n, self.b), np.int32)
+        o = np.zeros(n, np.float64)
+        kkm_steps_host(self.ctx, n, bi, a, o)
+        return a, o
 
     def assign(self, Q, want_dist: bool = False):
         torch = self._torch

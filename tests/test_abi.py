@@ -94,6 +94,7 @@ def test_null_context_calls(lib):
     assert lib.kkm_sync(None) == kkm.KKM_EINVAL
     assert lib.kkm_flush(None) == kkm.KKM_EINVAL
     assert lib.kkm_steps(None, 5) == kkm.KKM_EINVAL
+    assert lib.kkm_steps_host(None, 5, None, None, None) == kkm.KKM_EINVAL
     out = ctypes.c_double()
     assert lib.kkm_objective(None, None, 0, 0, ctypes.byref(out)) == kkm.KKM_EINVAL
 

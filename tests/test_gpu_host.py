@@ -127,3 +127,32 @@ def test_steps_match_single_steps(precision, graph):
     _same_state(a, b_)
     a.close()
     b_.close()
+
+
+@pytest.mark.parametrize("precision,graph", [("bf16", True), ("bf16x3", True), ("fp32", False)])
+def test_steps_host_matches_single_host_steps(precision, graph):
+    """kkm_steps_host (chunks of 16 through two staging slots, one graph per
+    slot) gives, bit for bit, the assignments, f_B values and final state of
+    one kkm_step_host call per step: a context's first call (its first step
+    goes one at a time), two full chunks and a ragged tail, then a call with
+    the built-in sampler and a call of zero steps."""
+    torch, (m, s1), n, b = _twins(precision, graph)
+    batches = np.stack(inputs.batch_stream(n, b, 41, seed=35)).astype(np.int32)
+    a_m, f_m = m.steps_host(batches)
+    for i in range(41):
+        a_s, f_s = s1.step_host(batches[i])
+        assert np.array_equal(a_m[i], a_s), i
+        assert f_m[i] == f_s, i
+    _same_state(m, s1)
+    a_m, f_m = m.steps_host(None, n=19)
+    for i in range(19):
+        a_s, f_s = s1.step_host(None)
+        assert np.array_equal(a_m[i], a_s), i
+        assert f_m[i] == f_s, i
+    a_m, f_m = m.steps_host(None, n=0)
+    assert a_m.shape == (0, b) and f_m.shape == (0,)
+    _same_state(m, s1)
+    assert m.stats()[0] == s1.stats()[0] == 60
+    m.close()
+    s1.close()
+
